@@ -1,0 +1,657 @@
+/*
+ * elsr_oracle.c -- plain, slow, single-threaded CPU oracle for the variable
+ * neighbourhood search (VNS) of Antoniadis & Sifaleras (2017) on the
+ * uncapacitated multi-item economic lot-sizing problem with remanufacturing
+ * (ELSR).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may link, load or
+ * call this file: only the tests, the smoke check and the benchmark's CPU
+ * baseline leg use it.  It shares no code, header, table or helper with the
+ * CUDA library.
+ *
+ * It follows the paper step by step, in the paper's order and notation:
+ *   - Section 2 (problem statement): products k, periods t, setup costs
+ *     kM(k), kR(k), holding costs hM(k), hR(k), demand D(k,t), returns
+ *     R(k,t); decisions xM, xR (manufactured / remanufactured quantities) and
+ *     yM, yR (serviceable / recoverable stock); objective = setup + holding.
+ *   - Section 3: products are uncoupled, so the objective is a sum of
+ *     per-product row costs.
+ *   - Algorithm 1 (parallel VND): for each neighbourhood N_k, find each
+ *     product's best neighbour, sum the improvements (diff), repeat the whole
+ *     k = 1..kmax sweep until no improvement.
+ *   - Algorithm 2 (GVNS): shake, VND, keep the better solution.
+ *
+ * The paper defers the model's exact formulation, the initial solution, the
+ * neighbourhoods and the shaking operator to its reference [SK2016].  The
+ * readings adopted for them are stated at each function ("Reading:").
+ *
+ * Every decode is a full per-period pass over the row (O(T) per candidate);
+ * there are no prefix sums, no caching and no incremental evaluation here.
+ *
+ * Parity status: the decode, objective and neighbourhood search are pinned by
+ * hand-derived worked examples, closed forms, plan invariants, a
+ * Wagner-Whitin reduction and brute force.  The readings themselves (decode
+ * rule, neighbourhoods, shake, acceptance) cannot be pinned against the
+ * paper's unpublished [SK2016] rules: parity unpinned for those readings.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_INF INT64_MAX
+
+/* Problem data of Section 2.  D and R are row-major [K][T]; costs are [K]. */
+typedef struct {
+    int32_t K, T;
+    const int32_t *D, *R;
+    const int32_t *kM, *kR, *hM, *hR;
+} orc_instance;
+
+/* Per-run counters (Algorithm 1 / Algorithm 2 bookkeeping). */
+typedef struct {
+    int64_t moves_evaluated; /* sum over neighbourhood evaluations of |N_j| */
+    int64_t evals;           /* neighbourhood evaluations */
+    int64_t vnd_cycles;      /* full j = 1..3 sweeps of the VND repeat loop */
+    int64_t applied;         /* moves applied by VND */
+    int64_t iterations;      /* GVNS shaking iterations */
+    int64_t accepted;        /* iterations whose VND result was kept */
+} orc_counters;
+
+/* One trajectory entry per GVNS iteration: (it, k, f(x''), accepted). */
+typedef struct {
+    int32_t it;
+    int32_t k;
+    int64_t cost;
+    int32_t accepted;
+    int32_t pad;
+} orc_traj;
+
+static int64_t sat_add(int64_t a, int64_t b)
+{
+    if (a == ORC_INF || b == ORC_INF) return ORC_INF;
+    return a + b;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Decode and row cost (Section 2 objective; decode reading).                */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Decode one product row from its setup bits and return its cost.
+ *
+ * Section 2: the row cost is the manufacturing and remanufacturing setup
+ * costs plus the holding costs of serviceable stock yM and recoverable stock
+ * yR.  Reading (the formulation is in [SK2016], not in the paper):
+ *   yM(t) = yM(t-1) + xM(t) + xR(t) - D(t),  yR(t) = yR(t-1) + R(t) - xR(t),
+ *   yM(-1) = yR(-1) = 0, all quantities >= 0, holding charged on end-of-period
+ *   stock, setup cost charged on the setup bit, unit production costs 0.
+ * Decode reading: at each period with a setup, cover the demand up to the
+ * next setup; remanufacture first from the available recoverable stock when
+ * gR(t) = 1, manufacture the rest when gM(t) = 1; a shortfall is infeasible.
+ *
+ * gM, gR: the row's T setup bits (0/1).  plan (nullable): [4][T] receives
+ * xM, xR, yM, yR.  Returns ORC_INF for an infeasible row.
+ */
+int64_t orc_decode_row(const orc_instance *in, int32_t k,
+                       const uint8_t *gM, const uint8_t *gR, int64_t *plan)
+{
+    const int32_t T = in->T;
+    const int32_t *D = in->D + (int64_t)k * T;
+    const int32_t *R = in->R + (int64_t)k * T;
+    const int64_t kM = in->kM[k], kR = in->kR[k];
+    const int64_t hM = in->hM[k], hR = in->hR[k];
+    int64_t yM_prev = 0, yR_prev = 0, cost = 0;
+
+    for (int32_t t = 0; t < T; ++t) {
+        int64_t avail = yR_prev + R[t];
+        int64_t xm = 0, xr = 0;
+        if (gM[t] || gR[t]) {
+            int32_t n = t + 1;
+            while (n < T && !(gM[n] || gR[n])) ++n;
+            int64_t need = -yM_prev;
+            for (int32_t i = t; i < n; ++i) need += D[i];
+            if (gR[t]) xr = avail < need ? avail : need;
+            if (gM[t]) {
+                xm = need - xr;
+            } else if (xr < need) {
+                return ORC_INF; /* remanufacturing alone cannot cover demand */
+            }
+        }
+        int64_t yM = yM_prev + xm + xr - D[t];
+        if (yM < 0) return ORC_INF; /* demand not covered (e.g. before the first setup) */
+        int64_t yR = avail - xr;
+        cost += kM * gM[t] + kR * gR[t] + hM * yM + hR * yR;
+        if (plan) {
+            plan[t] = xm;
+            plan[T + t] = xr;
+            plan[2 * T + t] = yM;
+            plan[3 * T + t] = yR;
+        }
+        yM_prev = yM;
+        yR_prev = yR;
+    }
+    return cost;
+}
+
+/* Objective of Section 2: sum of the independent row costs (saturating). */
+int64_t orc_total_cost(const orc_instance *in, const uint8_t *gM,
+                       const uint8_t *gR, int64_t *rowcost)
+{
+    int64_t total = 0;
+    for (int32_t k = 0; k < in->K; ++k) {
+        int64_t c = orc_decode_row(in, k, gM + (int64_t)k * in->T,
+                                   gR + (int64_t)k * in->T, NULL);
+        if (rowcost) rowcost[k] = c;
+        total = sat_add(total, c);
+    }
+    return total;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Neighbourhoods (Section 3: "same as [SK2016]", omitted there; reading).   */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Reading of the neighbourhood structures N_1..N_3 (sizes 2*K*T + shift
+ * moves):
+ *   N_1: flip gM(k,t);                     global index k*T + t
+ *   N_2: flip gR(k,t);                     global index k*T + t
+ *   N_3: swap g_c(k,t) <-> g_c(k,t+1), c in {M=0, R=1}, t in [0, T-2];
+ *        local index c*(T-1) + t, global index k*2(T-1) + local.
+ */
+int64_t orc_nb_size(int32_t K, int32_t T, int32_t j)
+{
+    if (j == 1 || j == 2) return (int64_t)K * T;
+    if (j == 3) return (int64_t)K * 2 * (T - 1);
+    return 0;
+}
+
+int64_t orc_row_moves(int32_t T, int32_t j)
+{
+    if (j == 1 || j == 2) return T;
+    if (j == 3) return 2 * (int64_t)(T - 1);
+    return 0;
+}
+
+/* Apply move `local` of N_j to the bits of one row (in place). */
+void orc_apply_row_move(int32_t T, int32_t j, int64_t local, uint8_t *gM,
+                        uint8_t *gR)
+{
+    if (j == 1) {
+        gM[local] ^= 1;
+    } else if (j == 2) {
+        gR[local] ^= 1;
+    } else if (j == 3) {
+        int64_t c = local / (T - 1);
+        int64_t t = local % (T - 1);
+        uint8_t *g = c == 0 ? gM : gR;
+        uint8_t tmp = g[t];
+        g[t] = g[t + 1];
+        g[t + 1] = tmp;
+    }
+}
+
+/* Apply global move m of N_j to the full K x T solution (in place). */
+void orc_apply_move(int32_t K, int32_t T, int32_t j, int64_t m, uint8_t *gM,
+                    uint8_t *gR)
+{
+    int64_t per_row = orc_row_moves(T, j);
+    (void)K;
+    if (per_row <= 0) return;
+    int64_t k = m / per_row, local = m % per_row;
+    orc_apply_row_move(T, j, local, gM + k * T, gR + k * T);
+}
+
+/*
+ * New cost of the moved row for every move of N_j (global layout).  Each
+ * candidate is a copy of the row with the move applied, decoded in full.
+ */
+void orc_move_costs(const orc_instance *in, const uint8_t *gM,
+                    const uint8_t *gR, int32_t j, int64_t *out)
+{
+    const int32_t K = in->K, T = in->T;
+    int64_t per_row = orc_row_moves(T, j);
+    uint8_t *cm = malloc(T > 0 ? T : 1), *cr = malloc(T > 0 ? T : 1);
+    for (int32_t k = 0; k < K; ++k) {
+        for (int64_t l = 0; l < per_row; ++l) {
+            memcpy(cm, gM + (int64_t)k * T, T);
+            memcpy(cr, gR + (int64_t)k * T, T);
+            orc_apply_row_move(T, j, l, cm, cr);
+            out[k * per_row + l] = orc_decode_row(in, k, cm, cr, NULL);
+        }
+    }
+    free(cm);
+    free(cr);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Best neighbour (Algorithm 1, "find best neighbour" and diff).             */
+/* ------------------------------------------------------------------------ */
+
+/* Offsets of N_1, N_2, N_3 in the combined (all three neighbourhoods) move
+ * layout: per product [N_1 | N_2 | N_3], globally [N_1 | N_2 | N_3]. */
+static int64_t comb_local_off(int32_t T, int32_t j)
+{
+    return j == 1 ? 0 : (j == 2 ? T : 2 * (int64_t)T);
+}
+static int64_t comb_global_off(int32_t K, int32_t T, int32_t j)
+{
+    return j == 1 ? 0 : (j == 2 ? (int64_t)K * T : 2 * (int64_t)K * T);
+}
+
+/* Total after replacing row k's cost by c (mode G): the saturating sum of
+ * the other rows plus c. */
+static int64_t total_with_row(const int64_t *rowcost, int32_t K, int32_t k,
+                              int64_t c)
+{
+    int64_t s = c;
+    for (int32_t i = 0; i < K; ++i)
+        if (i != k) s = sat_add(s, rowcost[i]);
+    return s;
+}
+
+/*
+ * Evaluate the neighbourhoods in `mask` (bit j-1 selects N_j) at the current
+ * solution without applying anything.
+ *
+ * Mode P (mode = 0, Algorithm 1): for every product k, the best move of row
+ * k is the lexicographic minimum of (new row cost, combined local index);
+ * pp_cost[k], pp_move[k] receive it (cost ORC_INF, move -1 when the row has
+ * no moves).  *best_cost = s - diff, the objective after every product
+ * applies its best move when that move strictly improves its row;
+ * *best_move = the number of improving products.
+ *
+ * Mode G (mode = 1, single argmin): the best move over the whole
+ * neighbourhood is the lexicographic minimum of (new total, combined global
+ * index); *best_cost, *best_move receive it.  The per-product arrays are
+ * filled as in mode P.
+ *
+ * Output pointers may be NULL.  Returns the number of moves evaluated.
+ */
+int64_t orc_eval_neighbourhood(const orc_instance *in, const uint8_t *gM,
+                               const uint8_t *gR, uint32_t mask, int32_t mode,
+                               int64_t *best_cost, int64_t *best_move,
+                               int64_t *pp_cost, int64_t *pp_move)
+{
+    const int32_t K = in->K, T = in->T;
+    int64_t *rowcost = malloc(sizeof(int64_t) * (K > 0 ? K : 1));
+    int64_t total = orc_total_cost(in, gM, gR, rowcost);
+    int64_t g_cost = ORC_INF, g_move = -1, evaluated = 0;
+    int64_t s_after = 0, n_improving = 0;
+
+    for (int32_t k = 0; k < K; ++k) {
+        int64_t r_cost = ORC_INF, r_move = -1;
+        for (int32_t j = 1; j <= 3; ++j) {
+            if (!(mask & (1u << (j - 1)))) continue;
+            int64_t per_row = orc_row_moves(T, j);
+            if (per_row <= 0) continue;
+            int64_t *c = malloc(sizeof(int64_t) * per_row);
+            uint8_t *cm = malloc(T), *cr = malloc(T);
+            for (int64_t l = 0; l < per_row; ++l) {
+                memcpy(cm, gM + (int64_t)k * T, T);
+                memcpy(cr, gR + (int64_t)k * T, T);
+                orc_apply_row_move(T, j, l, cm, cr);
+                c[l] = orc_decode_row(in, k, cm, cr, NULL);
+            }
+            for (int64_t l = 0; l < per_row; ++l) {
+                int64_t li = comb_local_off(T, j) + l;
+                if (r_move < 0 || c[l] < r_cost || (c[l] == r_cost && li < r_move)) {
+                    r_cost = c[l];
+                    r_move = li;
+                }
+                int64_t nt = total_with_row(rowcost, K, k, c[l]);
+                int64_t gi = comb_global_off(K, T, j) + (int64_t)k * per_row + l;
+                if (g_move < 0 || nt < g_cost || (nt == g_cost && gi < g_move)) {
+                    g_cost = nt;
+                    g_move = gi;
+                }
+            }
+            evaluated += per_row;
+            free(c);
+            free(cm);
+            free(cr);
+        }
+        if (pp_cost) pp_cost[k] = r_cost;
+        if (pp_move) pp_move[k] = r_move;
+        if (r_move >= 0 && r_cost < rowcost[k]) {
+            s_after = sat_add(s_after, r_cost);
+            ++n_improving;
+        } else {
+            s_after = sat_add(s_after, rowcost[k]);
+        }
+    }
+    if (mode == 0) {
+        if (best_cost) *best_cost = s_after;
+        if (best_move) *best_move = n_improving;
+    } else {
+        if (best_cost) *best_cost = g_move < 0 ? total : g_cost;
+        if (best_move) *best_move = g_move;
+    }
+    free(rowcost);
+    return evaluated;
+}
+
+/* ------------------------------------------------------------------------ */
+/* VND (Algorithm 1, pipe form).                                             */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * One evaluation of N_j at the current solution followed by the update of
+ * Algorithm 1.  Mode P: every product whose best row move strictly improves
+ * its row takes it (all products see the same current solution; they are
+ * independent).  Mode G (reading): the single best move of the whole
+ * neighbourhood, by (new total, global index), is applied when its total is
+ * strictly below the current total.  Returns the number of applied moves.
+ */
+static int64_t vnd_step(const orc_instance *in, uint8_t *gM, uint8_t *gR,
+                        int32_t j, int32_t mode, orc_counters *cnt)
+{
+    const int32_t K = in->K, T = in->T;
+    int64_t per_row = orc_row_moves(T, j);
+    int64_t applied = 0;
+    cnt->evals += 1;
+    cnt->moves_evaluated += orc_nb_size(K, T, j);
+    if (per_row <= 0) return 0;
+
+    int64_t *rowcost = malloc(sizeof(int64_t) * K);
+    int64_t total = orc_total_cost(in, gM, gR, rowcost);
+    int64_t *c = malloc(sizeof(int64_t) * per_row * K);
+    orc_move_costs(in, gM, gR, j, c);
+
+    if (mode == 0) {
+        for (int32_t k = 0; k < K; ++k) {
+            int64_t bc = ORC_INF, bl = -1;
+            for (int64_t l = 0; l < per_row; ++l) {
+                int64_t v = c[k * per_row + l];
+                if (bl < 0 || v < bc) { /* strict: the lowest index wins ties */
+                    bc = v;
+                    bl = l;
+                }
+            }
+            if (bc < rowcost[k]) {
+                orc_apply_row_move(T, j, bl, gM + (int64_t)k * T, gR + (int64_t)k * T);
+                ++applied;
+            }
+        }
+    } else {
+        int64_t bt = ORC_INF, bm = -1;
+        for (int32_t k = 0; k < K; ++k) {
+            for (int64_t l = 0; l < per_row; ++l) {
+                int64_t nt = total_with_row(rowcost, K, k, c[k * per_row + l]);
+                if (bm < 0 || nt < bt) {
+                    bt = nt;
+                    bm = k * per_row + l;
+                }
+            }
+        }
+        if (bm >= 0 && bt < total) {
+            orc_apply_move(K, T, j, bm, gM, gR);
+            ++applied;
+        }
+    }
+    free(c);
+    free(rowcost);
+    cnt->applied += applied;
+    return applied;
+}
+
+/* VND of Algorithm 1: repeat the sweep j = 1..3 (no restart at j = 1 after
+ * an improvement) until a full sweep improves nothing.  A safety cap of
+ * 2^20 sweeps returns -1. */
+int32_t orc_vnd(const orc_instance *in, uint8_t *gM, uint8_t *gR, int32_t mode,
+                orc_counters *cnt)
+{
+    for (int64_t cycle = 0; cycle < (1 << 20); ++cycle) {
+        int improvement = 0;
+        cnt->vnd_cycles += 1;
+        for (int32_t j = 1; j <= 3; ++j)
+            if (vnd_step(in, gM, gR, j, mode, cnt) > 0) improvement = 1;
+        if (!improvement) return 0;
+    }
+    return -1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Shaking draws: splitmix64 (Steele, Lea & Flood 2014).                     */
+/* ------------------------------------------------------------------------ */
+
+/* One splitmix64 step from state z: advance by the golden-ratio increment,
+ * then the published output mix. */
+uint64_t orc_splitmix64(uint64_t z)
+{
+    z += 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+/* Draw for move j of a shake of strength k at iteration it (reading: keyed
+ * by seed, iteration and neighbourhood). */
+uint64_t orc_draw(uint64_t seed, uint64_t it, uint64_t k, uint64_t j)
+{
+    uint64_t a = orc_splitmix64(seed);
+    uint64_t b = orc_splitmix64(a ^ it);
+    return orc_splitmix64(b ^ ((k << 32) | j));
+}
+
+/* Shake(x, k) of Algorithm 2 (reading): apply k successive random moves of
+ * N_k, move j being draw(seed, it, k, j) mod |N_k| in N_k's global layout.
+ * Moves are applied even when they make a row infeasible. */
+void orc_shake(int32_t K, int32_t T, uint8_t *gM, uint8_t *gR, uint64_t seed,
+               int64_t it, int32_t k)
+{
+    int64_t size = orc_nb_size(K, T, k);
+    if (size <= 0) return;
+    for (int32_t j = 0; j < k; ++j) {
+        uint64_t m = orc_draw(seed, (uint64_t)it, (uint64_t)k, (uint64_t)j) % (uint64_t)size;
+        orc_apply_move(K, T, k, (int64_t)m, gM, gR);
+    }
+}
+
+/* Rolling trajectory hash: h <- mix(h ^ f), h <- mix(h ^ (it<<32 | k<<1 | acc)). */
+static uint64_t traj_hash_step(uint64_t h, int64_t it, int32_t k, int64_t f,
+                               int32_t acc)
+{
+    h = orc_splitmix64(h ^ (uint64_t)f);
+    h = orc_splitmix64(h ^ (((uint64_t)it << 32) | ((uint64_t)k << 1) | (uint64_t)acc));
+    return h;
+}
+
+/* ------------------------------------------------------------------------ */
+/* GVNS (Algorithm 2, reading).                                              */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Reading of Algorithm 2 (its k loop has no increment and its neighbourhood
+ * change is commented out; the time limit is replaced by an iteration
+ * budget):
+ *   x = VND(start); k = 1
+ *   for it = 0 .. iters-1:
+ *       x' = Shake(x, k, it); x'' = VND(x')
+ *       if f(x'') < f(x): x = x'', k = 1  else: k = k+1, back to 1 after kmax
+ * gM, gR: in = start solution, out = best solution x.  log (nullable):
+ * [iters] entries.  Returns 0, or -1 when a VND hit its cycle cap.
+ */
+int32_t orc_vns(const orc_instance *in, uint8_t *gM, uint8_t *gR, uint64_t seed,
+                int32_t iters, int32_t kmax, int32_t mode, orc_counters *cnt,
+                orc_traj *log, int64_t *best_cost, uint64_t *traj_hash)
+{
+    const int32_t K = in->K, T = in->T;
+    const size_t n = (size_t)K * T;
+    uint8_t *pM = malloc(n ? n : 1), *pR = malloc(n ? n : 1);
+    uint64_t h = 0;
+    int32_t rc = 0;
+
+    memset(cnt, 0, sizeof(*cnt));
+    if (orc_vnd(in, gM, gR, mode, cnt) != 0) rc = -1;
+    int64_t fx = orc_total_cost(in, gM, gR, NULL);
+    int32_t k = 1;
+    for (int32_t it = 0; it < iters && rc == 0; ++it) {
+        memcpy(pM, gM, n);
+        memcpy(pR, gR, n);
+        orc_shake(K, T, pM, pR, seed, it, k);
+        if (orc_vnd(in, pM, pR, mode, cnt) != 0) rc = -1;
+        int64_t f2 = orc_total_cost(in, pM, pR, NULL);
+        int32_t acc = f2 < fx;
+        if (log) {
+            log[it].it = it;
+            log[it].k = k;
+            log[it].cost = f2;
+            log[it].accepted = acc;
+            log[it].pad = 0;
+        }
+        h = traj_hash_step(h, it, k, f2, acc);
+        cnt->iterations += 1;
+        if (acc) {
+            memcpy(gM, pM, n);
+            memcpy(gR, pR, n);
+            fx = f2;
+            k = 1;
+            cnt->accepted += 1;
+        } else {
+            k = k + 1;
+            if (k > kmax) k = 1;
+        }
+    }
+    if (best_cost) *best_cost = fx;
+    if (traj_hash) *traj_hash = h;
+    free(pM);
+    free(pR);
+    return rc;
+}
+
+/* Initial solution (reading; the paper omits it): every setup open. */
+void orc_initial_solution(int32_t K, int32_t T, uint8_t *gM, uint8_t *gR)
+{
+    memset(gM, 1, (size_t)K * T);
+    memset(gR, 1, (size_t)K * T);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Measurement helper (not part of the method): decode window of a move.     */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Number of setup segments a delta evaluation of one move must visit: the
+ * setups of the moved row from s0 up to (not including) the merge setup,
+ * where
+ *   s0    = the last period <= t1 holding a setup both before and after the
+ *           move (t1 = first changed period), or the first setup of the moved
+ *           row when there is none;
+ *   merge = the first setup s after the last changed period t2 at which the
+ *           recoverable stock entering s, yR(s-1), is the same before and
+ *           after the move and the row before the move is feasible up to s.
+ * The walk also stops at the first infeasible segment, and it stops at once
+ * (0 segments) when the unchanged prefix before s0 is already infeasible or
+ * the move changes nothing.  This counts algorithmic work only; it is used to
+ * express throughput as integer operations per second.
+ */
+int64_t orc_move_window(const orc_instance *in, int32_t k, const uint8_t *gM,
+                        const uint8_t *gR, int32_t j, int64_t local)
+{
+    const int32_t T = in->T;
+    uint8_t *nm = malloc(T), *nr = malloc(T);
+    int64_t *po = malloc(sizeof(int64_t) * 4 * T), *pn = malloc(sizeof(int64_t) * 4 * T);
+    memcpy(nm, gM, T);
+    memcpy(nr, gR, T);
+    orc_apply_row_move(T, j, local, nm, nr);
+
+    int32_t t1 = -1, t2 = -1;
+    for (int32_t t = 0; t < T; ++t)
+        if (nm[t] != gM[t] || nr[t] != gR[t]) {
+            if (t1 < 0) t1 = t;
+            t2 = t;
+        }
+    int64_t count = 0;
+    if (t1 < 0) goto done; /* null move */
+
+    /* old row: per-period decode up to its first infeasible period */
+    int32_t bad = T; /* first setup whose segment fails, -1 before any setup */
+    {
+        int64_t yMp = 0, yRp = 0;
+        int32_t seg = -1;
+        for (int32_t t = 0; t < T; ++t) {
+            if (gM[t] || gR[t]) seg = t;
+            int64_t avail = yRp + in->R[(int64_t)k * T + t], xm = 0, xr = 0;
+            int fail = 0;
+            if (gM[t] || gR[t]) {
+                int32_t n = t + 1;
+                while (n < T && !(gM[n] || gR[n])) ++n;
+                int64_t need = -yMp;
+                for (int32_t i = t; i < n; ++i) need += in->D[(int64_t)k * T + i];
+                if (gR[t]) xr = avail < need ? avail : need;
+                if (gM[t]) xm = need - xr; else if (xr < need) fail = 1;
+            }
+            int64_t yM = yMp + xm + xr - in->D[(int64_t)k * T + t];
+            if (yM < 0) fail = 1;
+            if (fail) { bad = seg; break; }
+            po[2 * T + t] = yM;
+            po[3 * T + t] = avail - xr;
+            yMp = yM;
+            yRp = avail - xr;
+        }
+    }
+    int32_t s0 = -1;
+    for (int32_t t = t1; t >= 0; --t) {
+        int both = (gM[t] || gR[t]) && (nm[t] || nr[t]);
+        if (t < t1) both = gM[t] || gR[t]; /* unchanged below t1 */
+        if (both) { s0 = t; break; }
+    }
+    if (s0 >= 0 && s0 > bad) goto done; /* prefix already infeasible */
+    if (s0 < 0) {
+        int32_t f = 0;
+        while (f < T && !(nm[f] || nr[f])) ++f;
+        int64_t dsum = 0;
+        for (int32_t i = 0; i < f; ++i) dsum += in->D[(int64_t)k * T + i];
+        if (dsum > 0) goto done;
+        s0 = f;
+    }
+    /* new row decode, counting segments from s0 */
+    (void)orc_decode_row(in, k, nm, nr, pn);
+    {
+        int64_t yRp = 0, yMp = 0;
+        for (int32_t t = 0; t < s0; ++t) { /* stock entering s0 */
+            int64_t avail = yRp + in->R[(int64_t)k * T + t], xr = 0, xm = 0;
+            if (nm[t] || nr[t]) {
+                int32_t n = t + 1;
+                while (n < T && !(nm[n] || nr[n])) ++n;
+                int64_t need = -yMp;
+                for (int32_t i = t; i < n; ++i) need += in->D[(int64_t)k * T + i];
+                if (nr[t]) xr = avail < need ? avail : need;
+                if (nm[t]) xm = need - xr;
+            }
+            yMp = yMp + xm + xr - in->D[(int64_t)k * T + t];
+            yRp = avail - xr;
+        }
+        for (int32_t s = s0; s < T;) {
+            if (s > t2 && s <= bad) {
+                int64_t old_in = s > 0 ? po[3 * T + s - 1] : 0;
+                if (yRp == old_in) break; /* merged */
+            }
+            int32_t n = s + 1;
+            while (n < T && !(nm[n] || nr[n])) ++n;
+            ++count;
+            /* advance the new row's decode over [s, n) */
+            int fail = 0;
+            for (int32_t t = s; t < n; ++t) {
+                int64_t avail = yRp + in->R[(int64_t)k * T + t], xr = 0, xm = 0;
+                if (t == s) {
+                    int64_t need = -yMp;
+                    for (int32_t i = s; i < n; ++i) need += in->D[(int64_t)k * T + i];
+                    if (nr[t]) xr = avail < need ? avail : need;
+                    if (nm[t]) xm = need - xr; else if (xr < need) fail = 1;
+                }
+                yMp = yMp + xm + xr - in->D[(int64_t)k * T + t];
+                yRp = avail - xr;
+            }
+            if (fail) break;
+            s = n;
+        }
+    }
+done:
+    free(nm);
+    free(nr);
+    free(po);
+    free(pn);
+    return count;
+}

@@ -1,0 +1,335 @@
+"""Pins of the CPU oracle to things other than itself (no GPU needed).
+
+Each test names what fixes the expected value: hand-derived worked examples
+(tests/golden/worked_examples.txt), published splitmix64 outputs
+(tests/golden/splitmix64_vectors.txt), the closed form of the all-open
+initial solution, inventory invariants of Section 2's model, the
+Wagner-Whitin dynamic program (Wagner & Whitin 1958) at K=1, R=0, brute force
+over every setup pattern of tiny instances, and the product separability that
+Section 3 states ("no link exist between the products").
+"""
+import itertools
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1704_05132_gb300 import gen
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+INF = oracle.INF
+
+
+def _ints(s):
+    return [int(v) for v in s.split()]
+
+
+def _worked_examples():
+    rows = []
+    with open(os.path.join(GOLDEN, "worked_examples.txt")) as f:
+        for line in f:
+            if not line.strip() or line.startswith("#"):
+                continue
+            p = [c.strip() for c in line.split("|")]
+            rows.append(p)
+    return rows
+
+
+@pytest.mark.parametrize("row", _worked_examples(), ids=lambda r: r[0])
+def test_worked_examples(row):
+    name, D, R, costs, gM, gR, cost, xM, xR, yM, yR = row
+    kM, kR, hM, hR = _ints(costs)
+    inst = oracle.Instance(np.array([_ints(D)]), np.array([_ints(R)]),
+                           [kM], [kR], [hM], [hR])
+    c, plan = oracle.decode_row(inst, 0, np.array(_ints(gM)), np.array(_ints(gR)))
+    if cost == "INF":
+        assert c == INF
+        return
+    assert c == int(cost)
+    assert plan[0].tolist() == _ints(xM)
+    assert plan[1].tolist() == _ints(xR)
+    assert plan[2].tolist() == _ints(yM)
+    assert plan[3].tolist() == _ints(yR)
+
+
+def test_splitmix64_published_vector():
+    with open(os.path.join(GOLDEN, "splitmix64_vectors.txt")) as f:
+        expected = [int(l) for l in f if l.strip() and not l.startswith("#")]
+    x = 1234567
+    got = []
+    for _ in expected:
+        got.append(oracle.splitmix64(x))      # one step from state x
+        x = (x + gen.GOLDEN) & ((1 << 64) - 1)
+    assert got == expected
+    # the generator module's independent splitmix64 gives the same stream
+    assert [gen._mix_int((1234567 + i * gen.GOLDEN) & ((1 << 64) - 1))
+            for i in range(len(expected))] == expected
+
+
+def _check_plan(inst, k, gm, gr, cost, plan):
+    """Invariants of Section 2's model on one decoded feasible row."""
+    D, R = inst.D[k].astype(np.int64), inst.R[k].astype(np.int64)
+    xM, xR, yM, yR = plan
+    assert (plan >= 0).all()
+    ym_prev = np.concatenate([[0], yM[:-1]])
+    yr_prev = np.concatenate([[0], yR[:-1]])
+    assert (yM == ym_prev + xM + xR - D).all()          # serviceable balance
+    assert (yR == yr_prev + R - xR).all()               # recoverable balance
+    assert ((xM == 0) | (gm == 1)).all()                # production needs a setup
+    assert ((xR == 0) | (gr == 1)).all()
+    assert yM[-1] == 0                                  # no stock left over
+    assert xM.sum() + xR.sum() == D.sum()
+    assert xR.sum() <= R.sum()
+    setup = (gm | gr) == 1
+    assert (ym_prev[setup] == 0).all()                  # zero-inventory ordering
+    recomputed = (inst.kM[k] * gm.sum() + inst.kR[k] * gr.sum()
+                  + inst.hM[k] * yM.sum() + inst.hR[k] * yR.sum())
+    assert recomputed == cost
+
+
+def test_invariants_random_patterns():
+    rng = np.random.default_rng(7)
+    inst = oracle.Instance.from_arrays(gen.make_instance(11, 0, K=6, T=20))
+    n_feasible = 0
+    for i in range(600):
+        k = int(rng.integers(inst.K))
+        dens = rng.uniform(0.1, 0.9)
+        gm = (rng.random(inst.T) < dens).astype(np.uint8)
+        gr = (rng.random(inst.T) < dens).astype(np.uint8)
+        if i % 2:
+            gr &= gm   # no remanufacture-only setups: feasible when gm[0] = 1
+        gm[0] = 1 if rng.random() < 0.8 else gm[0]
+        c, plan = oracle.decode_row(inst, k, gm, gr)
+        if c == INF:
+            continue
+        n_feasible += 1
+        _check_plan(inst, k, gm, gr, c, plan)
+    assert n_feasible > 100
+
+
+def test_infeasible_patterns_really_short():
+    """A row reported infeasible has a period where the rule cannot cover
+    demand: either demand before the first setup, or a remanufacture-only
+    setup whose recoverable stock is below the demand it must cover."""
+    rng = np.random.default_rng(3)
+    inst = oracle.Instance.from_arrays(gen.make_instance(12, 0, K=1, T=10))
+    D, R = inst.D[0].astype(np.int64), inst.R[0].astype(np.int64)
+    for _ in range(300):
+        gm = (rng.random(inst.T) < 0.3).astype(np.uint8)
+        gr = (rng.random(inst.T) < 0.5).astype(np.uint8)
+        c, _ = oracle.decode_row(inst, 0, gm, gr)
+        setups = np.flatnonzero(gm | gr)
+        first = setups[0] if len(setups) else inst.T
+        pre_short = D[:first].sum() > 0
+        # walk the setups by hand with stock only (no cost)
+        short = pre_short
+        yr = R[:first].sum() if not pre_short else 0
+        if not pre_short:
+            for i, s in enumerate(setups):
+                n = setups[i + 1] if i + 1 < len(setups) else inst.T
+                need = D[s:n].sum()
+                avail = yr + R[s]
+                xr = min(avail, need) if gr[s] else 0
+                if not gm[s] and xr < need:
+                    short = True
+                    break
+                yr = avail - xr + R[s + 1:n].sum()
+        assert (c == INF) == short
+
+
+def test_closed_form_all_open():
+    """With R <= D and every setup open, no stock is ever held, so the cost of
+    the initial solution is sum_k T * (kM + kR)."""
+    for seed in range(5):
+        g = gen.make_instance(seed, 3, K=7, T=15)
+        assert (g.R <= g.D).all()
+        inst = oracle.Instance.from_arrays(g)
+        gm, gr = oracle.initial_solution(inst.K, inst.T)
+        total, _ = oracle.total_cost(inst, gm, gr)
+        assert total == int((inst.T * (inst.kM.astype(np.int64) + inst.kR)).sum())
+
+
+def _wagner_whitin(D, kM, hM):
+    """Textbook uncapacitated lot-sizing DP: F[t] = min cost of periods [0, t)."""
+    T = len(D)
+    F = [0] + [None] * T
+    for t in range(1, T + 1):
+        best = 0 if sum(D[:t]) == 0 else None
+        for s in range(t):
+            if F[s] is None:
+                continue
+            c = F[s] + kM + hM * sum(D[i] * (i - s) for i in range(s, t))
+            best = c if best is None else min(best, c)
+        F[t] = best
+    return F[T]
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_wagner_whitin_reduction(seed):
+    """K=1, R=0: the best decoded gM pattern (gR = 0) equals the Wagner-Whitin
+    optimum, and so does the best over all (gM, gR) pairs for T <= 8."""
+    rng = np.random.default_rng(100 + seed)
+    T = 12 if seed < 2 else 8
+    D = rng.integers(0, 40, T)
+    if seed == 1:
+        D[:3] = 0   # leading zero demand
+    kM, hM = int(rng.integers(20, 200)), int(rng.integers(1, 5))
+    inst = oracle.Instance(D[None, :], np.zeros((1, T), np.int64), [kM], [57], [hM], [1])
+    ww = _wagner_whitin(list(D), kM, hM)
+    zeros = np.zeros(T, np.uint8)
+    best = min(oracle.decode_row(inst, 0, np.array(p, np.uint8), zeros)[0]
+               for p in itertools.product((0, 1), repeat=T))
+    assert best == ww
+    if T <= 8:
+        best2 = min(oracle.decode_row(inst, 0, np.array(p[:T], np.uint8),
+                                      np.array(p[T:], np.uint8))[0]
+                    for p in itertools.product((0, 1), repeat=2 * T))
+        assert best2 == ww
+
+
+def _brute_force_row(inst, k):
+    T = inst.T
+    best = INF
+    for p in itertools.product((0, 1), repeat=2 * T):
+        c, _ = oracle.decode_row(inst, k, np.array(p[:T], np.uint8), np.array(p[T:], np.uint8))
+        best = min(best, c)
+    return best
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_vns_not_below_brute_force(seed):
+    g = gen.make_instance(20 + seed, 0, K=2, T=6)
+    inst = oracle.Instance.from_arrays(g)
+    opt = sum(_brute_force_row(inst, k) for k in range(inst.K))
+    for mode in (0, 1):
+        res = oracle.vns(inst, seed=seed, iters=30, kmax=3, mode=mode)
+        assert res.best_cost >= opt
+        # the reported cost is the cost of the returned solution
+        assert oracle.total_cost(inst, res.gM, res.gR)[0] == res.best_cost
+
+
+def _is_local_optimum(inst, gm, gr, mode):
+    total, rc = oracle.total_cost(inst, gm, gr)
+    for j in (1, 2, 3):
+        c = oracle.move_costs(inst, gm, gr, j)
+        per = oracle.row_moves(inst.T, j)
+        if per == 0:
+            continue
+        c = c.reshape(inst.K, per)
+        if mode == 0:
+            if (c < rc[:, None]).any():
+                return False
+        else:
+            others = total - rc[:, None]
+            if ((others + c)[c != INF] < total).any():
+                return False
+    return True
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_vnd_reaches_local_optimum(mode):
+    inst = oracle.Instance.from_arrays(gen.make_instance(4, 0, K=4, T=14))
+    gm, gr = oracle.initial_solution(inst.K, inst.T)
+    t0 = oracle.total_cost(inst, gm, gr)[0]
+    gm2, gr2, cnt = oracle.vnd(inst, gm, gr, mode)
+    t1 = oracle.total_cost(inst, gm2, gr2)[0]
+    assert t1 < t0
+    assert _is_local_optimum(inst, gm2, gr2, mode)
+    per_cycle = sum(oracle.nb_size(inst.K, inst.T, j) for j in (1, 2, 3))
+    assert cnt["moves_evaluated"] == cnt["vnd_cycles"] * per_cycle
+    assert cnt["evals"] == 3 * cnt["vnd_cycles"]
+
+
+def test_vnd_mode_p_separable():
+    """Products are uncoupled (Section 3), so the product-parallel VND of
+    Algorithm 1 gives, row by row, the VND of each product alone."""
+    g = gen.make_instance(8, 0, K=6, T=18)
+    inst = oracle.Instance.from_arrays(g)
+    gm, gr = oracle.initial_solution(inst.K, inst.T)
+    gm2, gr2, cnt = oracle.vnd(inst, gm, gr, 0)
+    cycles = []
+    for k in range(inst.K):
+        sub = inst.row(k)
+        a, b, c = oracle.vnd(sub, gm[k:k + 1], gr[k:k + 1], 0)
+        assert (a[0] == gm2[k]).all() and (b[0] == gr2[k]).all()
+        cycles.append(c["vnd_cycles"])
+    assert cnt["vnd_cycles"] == max(cycles)
+
+
+def test_move_layout_hand_cases():
+    """Neighbourhood index layout on a hand-made 2 x 4 solution."""
+    K, T = 2, 4
+    gm = np.array([[1, 0, 0, 1], [0, 1, 1, 0]], np.uint8)
+    gr = np.array([[0, 0, 1, 0], [1, 0, 0, 0]], np.uint8)
+    assert oracle.nb_size(K, T, 1) == 8 and oracle.nb_size(K, T, 3) == 12
+    a, b = gm.copy(), gr.copy()
+    oracle.apply_move(K, T, 1, 6, a, b)            # N1: flip gM(1, 2)
+    assert a[1].tolist() == [0, 1, 0, 0] and (b == gr).all()
+    a, b = gm.copy(), gr.copy()
+    oracle.apply_move(K, T, 2, 3, a, b)            # N2: flip gR(0, 3)
+    assert b[0].tolist() == [0, 0, 1, 1] and (a == gm).all()
+    a, b = gm.copy(), gr.copy()
+    oracle.apply_move(K, T, 3, 6 + 0, a, b)        # N3 row 1, c=M, t=0: swap
+    assert a[1].tolist() == [1, 0, 1, 0]
+    a, b = gm.copy(), gr.copy()
+    oracle.apply_move(K, T, 3, 0 * 6 + 3 + 1, a, b)  # N3 row 0, c=R, t=1
+    assert b[0].tolist() == [0, 1, 0, 0]
+
+
+def test_shake_follows_draws():
+    """Shake(x, k) applies k moves of N_k indexed by the splitmix64 draws;
+    the expected indices use the generator module's own splitmix64."""
+    K, T = 5, 9
+    mix = gen._mix_int
+    for seed, it, k in [(0, 0, 1), (3, 17, 2), (99, 5, 3)]:
+        gm = np.zeros((K, T), np.uint8)
+        gr = np.zeros((K, T), np.uint8)
+        gm[:, ::2] = 1
+        gr[:, 1::3] = 1
+        a, b = gm.copy(), gr.copy()
+        oracle.shake(K, T, a, b, seed, it, k)
+        size = oracle.nb_size(K, T, k)
+        for j in range(k):
+            d = mix(mix(mix(seed) ^ it) ^ ((k << 32) | j))
+            assert d == oracle.draw(seed, it, k, j)
+            oracle.apply_move(K, T, k, d % size, gm, gr)
+        assert (a == gm).all() and (b == gr).all()
+
+
+def test_gvns_trajectory_rules():
+    inst = oracle.Instance.from_arrays(gen.plain_small())
+    res = oracle.vns(inst, seed=0, iters=200, kmax=3, mode=0)
+    gm, gr = oracle.initial_solution(inst.K, inst.T)
+    gm, gr, _ = oracle.vnd(inst, gm, gr, 0)
+    fx = oracle.total_cost(inst, gm, gr)[0]
+    k = 1
+    for e in res.traj:
+        assert e["k"] == k
+        acc = e["cost"] < fx
+        assert bool(e["accepted"]) == acc
+        if acc:
+            fx, k = int(e["cost"]), 1
+        else:
+            k = k + 1 if k < 3 else 1
+    assert fx == res.best_cost
+    assert res.counters["iterations"] == 200
+    assert res.counters["accepted"] == int(res.traj["accepted"].sum())
+
+
+def test_eval_neighbourhood_matches_move_costs():
+    inst = oracle.Instance.from_arrays(gen.make_instance(9, 0, K=3, T=7))
+    rng = np.random.default_rng(1)
+    gm = (rng.random((3, 7)) < 0.5).astype(np.uint8)
+    gr = (rng.random((3, 7)) < 0.5).astype(np.uint8)
+    gm[:, 0] = 1
+    total, rc = oracle.total_cost(inst, gm, gr)
+    bc, bm, pc, pm, n = oracle.eval_neighbourhood(inst, gm, gr, 0b111, 1)
+    allc = []
+    for j in (1, 2, 3):
+        c = oracle.move_costs(inst, gm, gr, j).reshape(3, -1)
+        allc.append(c)
+    assert n == sum(c.size for c in allc)
+    for k in range(3):
+        row = np.concatenate([c[k] for c in allc])
+        assert pc[k] == row.min() and pm[k] == int(np.argmin(row))
