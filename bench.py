@@ -1,0 +1,301 @@
+"""Benchmark of the ELSR VNS hot path on GB300.
+
+Default workload: plain GVNS on one synthetic instance with K=50 products and
+T=52 periods (generator seed 1), 2000 shaking iterations, kmax=3, mode P
+(Algorithm 1's product-parallel VND).  One step = one whole GVNS run through
+the C ABI (stage the instance, VND, 2000 x (shake, VND, accept)), i.e. every
+step of the hot path.  Metric: candidate moves evaluated per second (the sum
+over neighbourhood evaluations of |N_j|, counted exactly as the oracle counts
+them); VNS instances/s is reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+``--impl reference`` times the CPU oracle (plain single-threaded C) on a
+bounded sample of the same workload.  Under torchrun (N > 1) every rank runs
+independent replicas (one instance, its own seed) and rank 0 prints one line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = {
+    "workload": "plain GVNS, one instance K=50 products x T=52 periods, seed 1, "
+                "2000 shaking iterations, kmax=3, mode P",
+    "K": 50, "T": 52, "gen_seed": 1, "vns_seed": 1, "iters": 2000, "kmax": 3, "mode": "P",
+}
+METRIC = "candidate moves evaluated/s"
+UNIT = "moves/s"
+INT_OPS_PER_SEGMENT = 16      # algorithmic integer operations per decode segment
+SMS, LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+            self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc or not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline(iters: int):
+    """The oracle as it stands, single-threaded, on the first `iters`
+    iterations of the workload (a bounded sample)."""
+    import oracle
+    from paper_1704_05132_gb300 import gen
+    inst = oracle.Instance.from_arrays(gen.plain_medium())
+    t0 = time.perf_counter()
+    r = oracle.vns(inst, WORKLOAD["vns_seed"], iters, WORKLOAD["kmax"], 0)
+    dt = time.perf_counter() - t0
+    return {"value": r.counters["moves_evaluated"] / dt, "unit": UNIT, "cores": 1,
+            "kind": "oracle",
+            "sample": f"first {iters} of {WORKLOAD['iters']} iterations of the workload "
+                      f"({r.counters['moves_evaluated']} moves, {dt:.2f} s)"}
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    from paper_1704_05132_gb300 import gen
+    oracle.build()
+    inst = oracle.Instance.from_arrays(gen.plain_medium())
+    iters = args.ref_iters
+    for _ in range(args.warmup):
+        oracle.vns(inst, WORKLOAD["vns_seed"], iters, WORKLOAD["kmax"], 0)
+    moves, t = 0, 0.0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = oracle.vns(inst, WORKLOAD["vns_seed"], iters, WORKLOAD["kmax"], 0)
+        t += time.perf_counter() - t0
+        moves += r.counters["moves_evaluated"]
+    v = moves / t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic", "config": dict(WORKLOAD, sample_iters=iters),
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"each step: the first {iters} of {WORKLOAD['iters']} "
+                                   "iterations of the workload"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    world, rank, local = _dist()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_1704_05132_gb300 import build, elsr, gen
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        dist.barrier()
+
+    g = gen.plain_medium()
+    K, T = g.K, g.T
+    seed = WORKLOAD["vns_seed"] + rank  # replicas: one seed per rank
+    stream = torch.cuda.current_stream(dev)
+    solver = elsr.Solver(g, stream=stream)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+
+    def step():
+        solver.vns_run(seed, WORKLOAD["iters"], WORKLOAD["kmax"], 0)
+
+    for _ in range(args.warmup):
+        step()
+    st = solver.result(solution=False, traj=False)
+    moves_per_step = st["moves_evaluated"]
+    segs_per_step = st["segments"]
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.add_(1)                       # L2 flush between steps (untimed)
+            starts[i].record(stream)
+            step()
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    st2 = solver.result(solution=False, traj=False)
+    assert st2["moves_evaluated"] == moves_per_step and st2["status"] == 0
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    t_local = sum(step_ms) / 1e3
+    t_max = t_local
+    moves_total = moves_per_step * args.steps
+    if world > 1:
+        tt = torch.tensor([t_local], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+        mv = torch.tensor([moves_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(mv, op=dist.ReduceOp.SUM)
+        moves_total = float(mv.item())
+    value = moves_total / t_max
+    kernel_s = t_local / args.steps
+
+    # ---- end to end through the public API, host buffers, copies inside ----
+    pinned = {f: torch.from_numpy(np.ascontiguousarray(getattr(g, f))).pin_memory()
+              for f in ("D", "R", "kM", "kR", "hM", "hR")}
+    host = gen.ElsrInstance(*(pinned[f].numpy() for f in ("D", "R", "kM", "kR", "hM", "hR")))
+    h2d = sum(int(a.numel()) * 4 for a in pinned.values())
+    d2h = 80 + K * 32 + 8  # run statistics, solution bits, best cost
+    e2e_moves, e2e_t = 0, 0.0
+    e2e_steps = max(1, min(args.steps, 5))
+    for i in range(e2e_steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s2 = elsr.Solver(host, stream=stream)
+        s2.vns_run(seed, WORKLOAD["iters"], WORKLOAD["kmax"], 0)
+        r2 = s2.result(solution=True, traj=False)
+        s2.close()
+        dt = time.perf_counter() - t0
+        if i > 0:  # first one is a warm-up
+            e2e_t += dt
+            e2e_moves += r2["moves_evaluated"]
+    e2e_value = e2e_moves / e2e_t * world
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    peaks = _peaks()
+    clocks = clk.summary()
+    peak_ops = SMS * LANES_PER_SM * SM_MAX_MHZ * 1e6
+    achieved_ops = INT_OPS_PER_SEGMENT * segs_per_step / kernel_s
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": dict(WORKLOAD, parallelism=f"replicas x{world}",
+                       l2="flushed between steps (256 MiB device write, untimed)",
+                       launch="1 persistent CTA per GVNS run"),
+        "instances_per_s": world * args.steps / t_max,
+        "moves_per_step": moves_per_step,
+        "clocks": clocks,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved_ops / 1e12, "peak": peak_ops / 1e12,
+                     "unit": "Tintop/s", "frac": achieved_ops / peak_ops, "traffic": None,
+                     "note": f"{INT_OPS_PER_SEGMENT} int ops per decode segment x "
+                             f"{segs_per_step} segments per launch; peak = {SMS} SMs x "
+                             f"{LANES_PER_SM} lanes x {SM_MAX_MHZ:.0f} MHz"},
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_iters)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-iters", type=int, default=1000)
+    ap.add_argument("--ref-iters", type=int, default=100)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,241 @@
+/*
+ * elsr.h -- C ABI of the GB300 engine for the variable neighbourhood search
+ * (VNS) of Antoniadis & Sifaleras (2017) on the uncapacitated multi-item
+ * economic lot-sizing problem with remanufacturing (ELSR).
+ *
+ * Model (Section 2): K products, T periods; per product k setup costs
+ * kM(k), kR(k), holding costs hM(k), hR(k); per (k,t) demand D(k,t) and
+ * returns R(k,t).  A solution is the pair of binary setup matrices
+ * gM(k,t), gR(k,t); decoding them gives manufactured / remanufactured
+ * quantities xM, xR and serviceable / recoverable stocks yM, yR, and the
+ * objective is setup plus holding cost.  Products are uncoupled (Section 3),
+ * so the objective is a sum of row costs.
+ *
+ * Conventions used by every call:
+ *   - integers only: quantities int32, costs int64; an infeasible row or
+ *     solution costs ELSR_INF (INT64_MAX);
+ *   - [K][T] arrays are row-major (product-major) and contiguous;
+ *   - setup matrices cross the ABI as uint8 0/1 arrays [K][T];
+ *   - every call returns ELSR_OK (0) or a negative ELSR_E_* code, and no
+ *     C++ exception crosses the ABI; elsr_last_error() gives a message;
+ *   - host pointers are read or written before the call returns, except
+ *     where a call is documented as asynchronous; the library copies its
+ *     inputs, so the caller keeps ownership of every buffer it passes;
+ *   - device work is issued on the handle's CUDA stream (elsr_set_stream;
+ *     default: the legacy default stream) on the device current at create.
+ *
+ * Decode rule (the paper defers the formulation to [SK2016]; this is the
+ * reading the library implements): at each period with a setup, cover the
+ * demand up to the next setup; remanufacture first from the recoverable
+ * stock when gR = 1, manufacture the rest when gM = 1; a shortfall, or
+ * demand before the first setup, is infeasible.  Initial stocks are zero,
+ * holding is charged on end-of-period stock and setup cost on the setup bit.
+ *
+ * Neighbourhoods (Section 3 omits them; reading): N1 flips gM(k,t), N2
+ * flips gR(k,t), N3 swaps g_c(k,t) with g_c(k,t+1) for c in {M, R}.
+ * Per-product (local) move index: N1 t, N2 t, N3 c*(T-1)+t.  Global index
+ * within N_j: k*|row moves of N_j| + local.  When several neighbourhoods are
+ * evaluated together the combined layouts are, per product,
+ * [N1 | N2 | N3] (offsets 0, T, 2T) and, globally, [N1 | N2 | N3]
+ * (offsets 0, K*T, 2*K*T).  Ties go to the lowest index.
+ */
+#ifndef ELSR_H
+#define ELSR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ELSR_OK 0
+#define ELSR_E_ARG (-1)   /* invalid argument (null pointer, size, value) */
+#define ELSR_E_RANGE (-2) /* instance exceeds the integer ranges below */
+#define ELSR_E_NOMEM (-3) /* device or host allocation failed */
+#define ELSR_E_CUDA (-4)  /* a CUDA runtime call or kernel failed */
+#define ELSR_E_CAP (-5)   /* a VND exceeded its sweep cap (2^20 sweeps) */
+#define ELSR_E_STATE (-6) /* call out of order (e.g. no result yet) */
+
+#define ELSR_T_MAX 128 /* periods per product */
+#define ELSR_MODE_P 0  /* Algorithm 1: each product takes its best move */
+#define ELSR_MODE_G 1  /* one best move over the whole neighbourhood */
+#define ELSR_INF INT64_MAX
+
+typedef struct elsr_ctx elsr_t;
+typedef struct elsr_batch elsr_batch_t;
+
+/* Per-run statistics (Algorithms 1 and 2 bookkeeping). */
+typedef struct {
+    int64_t best_cost;       /* f(x) of the returned solution x */
+    uint64_t traj_hash;      /* rolling hash of the trajectory (see below) */
+    int64_t moves_evaluated; /* sum over neighbourhood evaluations of |N_j| */
+    int64_t evals;           /* neighbourhood evaluations */
+    int64_t vnd_cycles;      /* full j = 1..3 sweeps of VND's repeat loop */
+    int64_t applied;         /* moves applied by VND (all products) */
+    int64_t iterations;      /* GVNS shaking iterations run */
+    int64_t accepted;        /* iterations whose VND result replaced x */
+    int64_t segments;        /* decode-window setup segments walked (work) */
+    int32_t status;          /* ELSR_OK or ELSR_E_CAP */
+    int32_t reserved;
+} elsr_stats_t;
+
+/* One trajectory entry per GVNS iteration: (it, k, f(x''), accepted).
+ * traj_hash folds the entries in order: h = mix(h ^ cost);
+ * h = mix(h ^ (it << 32 | k << 1 | accepted)), from h = 0, mix being one
+ * splitmix64 step. */
+typedef struct {
+    int32_t it;
+    int32_t k;
+    int64_t cost;
+    int32_t accepted;
+    int32_t reserved;
+} elsr_traj_t;
+
+/* Version of this ABI (major * 10000 + minor * 100 + patch). */
+int elsr_version(void);
+
+/* Static text for an ELSR_* code. */
+const char *elsr_strerror(int code);
+
+/* Message of the last failed call on h (h may be NULL for create errors;
+ * the text then describes the last failed create on this thread). */
+const char *elsr_last_error(const elsr_t *h);
+
+/*
+ * Create a handle for one instance (Section 2 parameters).  D, R: host
+ * [K][T]; kM, kR, hM, hR: host [K]; all int32, copied.  Requires 1 <= K,
+ * 1 <= T <= ELSR_T_MAX, every value >= 0, sum_t D(k,t) and sum_t R(k,t)
+ * below 2^31, and an objective bound
+ *   sum_k T*(kM+kR) + T*(hM*sum_t D + hR*sum_t R) + hM*sum_t D*(T-t)
+ *         + hR*sum_t R*(T-t)
+ * below 2^40 (ELSR_E_RANGE otherwise).  The current solution starts as the
+ * initial solution (every setup open).  Allocates device memory on the
+ * current device.  On failure *out is NULL.
+ */
+int elsr_create(elsr_t **out, int32_t K, int32_t T, const int32_t *D,
+                const int32_t *R, const int32_t *kM, const int32_t *kR,
+                const int32_t *hM, const int32_t *hR);
+
+/* Free the handle and its device memory (synchronises its stream). */
+void elsr_destroy(elsr_t *h);
+
+/* Issue the handle's device work on `stream` (a cudaStream_t; NULL = the
+ * legacy default stream). */
+int elsr_set_stream(elsr_t *h, void *stream);
+
+/* Kernel launch shape: sub-warp lanes per product row (4, 8, 16 or 32) and
+ * threads per block (multiple of 32, <= 1024); 0 keeps the default. */
+int elsr_set_launch(elsr_t *h, int32_t lanes_per_row, int32_t threads);
+
+/* Set the current solution from host 0/1 arrays gM, gR [K][T]; both NULL
+ * restores the initial solution (every setup open). */
+int elsr_set_state(elsr_t *h, const uint8_t *gM, const uint8_t *gR);
+
+/* Copy the current solution to host gM, gR [K][T] (0/1). */
+int elsr_get_state(elsr_t *h, uint8_t *gM, uint8_t *gR);
+
+/* Row costs of the current solution to host rowcost[K]; *total (nullable)
+ * receives their saturating sum (Section 2 objective). */
+int elsr_cost(elsr_t *h, int64_t *rowcost, int64_t *total);
+
+/*
+ * One best-improvement evaluation of the neighbourhoods in nb_mask (bit j-1
+ * selects N_j) at the current solution; nothing is applied.  This is
+ * Algorithm 1's "find best neighbour" over every product in one launch.
+ *   mode ELSR_MODE_P: pp_cost[k], pp_move[k] = lexicographic minimum of
+ *     (new row cost, combined local index) over product k's moves (cost
+ *     ELSR_INF / move -1 when the row has none); *best_cost = s - diff, the
+ *     objective after every product applies its best move when that move
+ *     strictly improves its row; *best_move = number of such products.
+ *   mode ELSR_MODE_G: *best_cost, *best_move = lexicographic minimum of
+ *     (new objective, combined global index); pp_* as in mode P.
+ * Outputs are host pointers and may be NULL.  Adds the moves to the
+ * handle's evaluation counter.  Synchronous.
+ */
+int elsr_eval_neighbourhood(elsr_t *h, uint32_t nb_mask, int32_t mode,
+                            int64_t *best_cost, int64_t *best_move,
+                            int64_t *pp_cost, int64_t *pp_move);
+
+/* New cost of the moved row for every move of N_nb (global layout, host
+ * costs[|N_nb|]); window (nullable, host int32[|N_nb|]) receives the setup
+ * segments each delta evaluation walked.  Synchronous. */
+int elsr_move_costs(elsr_t *h, int32_t nb, int64_t *costs, int32_t *window);
+
+/*
+ * GVNS of Algorithm 2 (reading: shake with k moves of N_k drawn by
+ * splitmix64 keyed by (seed, iteration, k, move), VND (Algorithm 1, pipe
+ * form), keep x'' iff f(x'') < f(x), k back to 1 on improvement, else k+1
+ * wrapping after kmax; an iteration budget replaces the time limit) from the
+ * current solution, entirely on the device.  iters >= 0, 1 <= kmax <= 3,
+ * mode ELSR_MODE_P or ELSR_MODE_G.  The current solution is not modified.
+ * Asynchronous: the work is queued on the handle's stream; elsr_result()
+ * waits for it.  iters = 0 runs VND alone.
+ */
+int elsr_vns_run(elsr_t *h, uint64_t seed, int32_t iters, int32_t kmax,
+                 int32_t mode);
+
+/*
+ * Results of the last elsr_vns_run (waits for it).  stats (nullable); gM,
+ * gR (nullable, host [K][T] 0/1) receive x; plan (nullable, host int32
+ * [4][K][T]) receives xM, xR, yM, yR of x; traj (nullable, host
+ * [traj_capacity]) receives the first min(iters, traj_capacity) entries.
+ * Returns the run's status (ELSR_OK or ELSR_E_CAP) or an error.
+ */
+int elsr_result(elsr_t *h, elsr_stats_t *stats, uint8_t *gM, uint8_t *gR,
+                int32_t *plan, elsr_traj_t *traj, int32_t traj_capacity);
+
+/*
+ * Multi-start GVNS on the handle's instance: nstarts independent runs from
+ * the current solution, start s using seed seed0 + s, run concurrently in one
+ * persistent launch; the best start is the lexicographic minimum of
+ * (cost, s), reduced on the device.  Synchronous.  best_cost, best_start
+ * (nullable) receive the winner; costs (nullable, host [nstarts]) every
+ * start's cost.  elsr_result() afterwards reports the winning start.
+ */
+int elsr_multistart_run(elsr_t *h, uint64_t seed0, int32_t nstarts,
+                        int32_t iters, int32_t kmax, int32_t mode,
+                        int64_t *best_cost, int32_t *best_start,
+                        int64_t *costs);
+
+/* Device moves evaluated since create (all calls on this handle). */
+int elsr_counters(elsr_t *h, int64_t *moves_evaluated);
+
+/*
+ * Batches: n independent instances of possibly different K and T, solved by
+ * one persistent launch (a CTA per run, runs taken from a device work
+ * queue in descending order of size).  Ks, Ts: host [n]; D, R: host arrays
+ * holding the instances' [K_i][T_i] blocks one after another; kM, kR, hM,
+ * hR: host arrays holding the [K_i] blocks one after another.  Each instance
+ * obeys the limits of elsr_create.  Copies everything.
+ */
+int elsr_batch_create(elsr_batch_t **out, int32_t n, const int32_t *Ks,
+                      const int32_t *Ts, const int32_t *D, const int32_t *R,
+                      const int32_t *kM, const int32_t *kR, const int32_t *hM,
+                      const int32_t *hR);
+void elsr_batch_destroy(elsr_batch_t *b);
+
+/* Message of the last failed call on batch b (b NULL: last failed create on
+ * this thread). */
+const char *elsr_batch_last_error(const elsr_batch_t *b);
+int elsr_batch_set_stream(elsr_batch_t *b, void *stream);
+int elsr_batch_set_launch(elsr_batch_t *b, int32_t lanes_per_row,
+                          int32_t threads);
+
+/* Queue GVNS runs of every instance i with seeds[i] (host [n]), from the
+ * initial solution.  Asynchronous, like elsr_vns_run. */
+int elsr_batch_run(elsr_batch_t *b, const uint64_t *seeds, int32_t iters,
+                   int32_t kmax, int32_t mode);
+
+/* Wait for the batch and copy per-instance results: stats (nullable, host
+ * [n]).  Returns ELSR_E_CAP when any run hit the cap. */
+int elsr_batch_results(elsr_batch_t *b, elsr_stats_t *stats);
+
+/* Solution of instance i of the last batch run: gM, gR host [K_i][T_i]. */
+int elsr_batch_solution(elsr_batch_t *b, int32_t i, uint8_t *gM, uint8_t *gR);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ELSR_H */

@@ -1,0 +1,874 @@
+// elsr_abi.cu -- C ABI of include/elsr.h: validation, device memory, launch
+// configuration and result marshalling around the kernels of
+// elsr_kernels.cu.  No arithmetic of the method runs here; every step of the
+// search runs in the kernels.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/elsr.h"
+#include "elsr_internal.h"
+
+using namespace elsr;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+const int kVndCap = 1 << 20;
+
+#define ELSR_TRY_CUDA(obj, call)                                          \
+  do {                                                                    \
+    cudaError_t e_ = (call);                                              \
+    if (e_ != cudaSuccess) {                                              \
+      (obj)->err = std::string(#call) + ": " + cudaGetErrorString(e_);    \
+      return ELSR_E_CUDA;                                                 \
+    }                                                                     \
+  } while (0)
+
+template <typename T>
+cudaError_t dev_alloc(T** p, size_t n) {
+  *p = nullptr;
+  if (n == 0) n = 1;
+  return cudaMalloc((void**)p, n * sizeof(T));
+}
+
+template <typename T>
+void dev_free(T*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+// Create-time checks of one instance (ranges documented in elsr.h).  Sets
+// *acc64 when a row's magnitude bound needs 64-bit accumulators.
+int check_instance(int32_t K, int32_t T, const int32_t* D, const int32_t* R,
+                   const int32_t* kM, const int32_t* kR, const int32_t* hM,
+                   const int32_t* hR, bool* acc64, unsigned __int128* total,
+                   std::string& err) {
+  if (K < 1 || T < 1 || T > ELSR_T_MAX) {
+    err = "K must be >= 1 and 1 <= T <= " + std::to_string(ELSR_T_MAX);
+    return ELSR_E_ARG;
+  }
+  if (!D || !R || !kM || !kR || !hM || !hR) {
+    err = "null instance array";
+    return ELSR_E_ARG;
+  }
+  if ((int64_t)K * (4 * (int64_t)T) >= (1 << 24)) {
+    err = "K*T too large for 24-bit move indices";
+    return ELSR_E_RANGE;
+  }
+  for (int32_t k = 0; k < K; ++k) {
+    if (kM[k] < 0 || kR[k] < 0 || hM[k] < 0 || hR[k] < 0) {
+      err = "negative cost in product " + std::to_string(k);
+      return ELSR_E_ARG;
+    }
+    int64_t sd = 0, sr = 0, wd = 0, wr = 0;
+    for (int32_t t = 0; t < T; ++t) {
+      const int32_t d = D[(int64_t)k * T + t], r = R[(int64_t)k * T + t];
+      if (d < 0 || r < 0) {
+        err = "negative demand or return at (" + std::to_string(k) + "," +
+              std::to_string(t) + ")";
+        return ELSR_E_ARG;
+      }
+      sd += d;
+      sr += r;
+      wd += (int64_t)d * (T - t);
+      wr += (int64_t)r * (T - t);
+    }
+    if (sd >= (1ll << 31) || sr >= (1ll << 31)) {
+      err = "sum of demand or returns of product " + std::to_string(k) +
+            " exceeds 2^31";
+      return ELSR_E_RANGE;
+    }
+    unsigned __int128 b = (unsigned __int128)T * ((uint64_t)kM[k] + (uint64_t)kR[k]);
+    b += (unsigned __int128)T * ((unsigned __int128)hM[k] * sd + (unsigned __int128)hR[k] * sr);
+    b += (unsigned __int128)hM[k] * wd + (unsigned __int128)hR[k] * wr;
+    if (b >= ((unsigned __int128)1 << 30)) *acc64 = true;
+    *total += b;
+  }
+  if (*total >= ((unsigned __int128)1 << 40) - 1) {
+    err = "objective bound exceeds 2^40";
+    return ELSR_E_RANGE;
+  }
+  return ELSR_OK;
+}
+
+int default_lanes(int T) { return T <= 8 ? 4 : (T <= 24 ? 8 : 16); }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Batch (a set of instances resident on the device)
+// ---------------------------------------------------------------------------
+struct elsr_batch {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  int32_t n = 0;
+  std::vector<InstDesc> insts;
+  int64_t cells = 0, rows = 0;
+  int maxK = 0, maxT = 0;
+  bool acc64 = false;
+  int lanes = 0, threads = 0;  // 0 = defaults
+  int sms = 0;
+
+  InstDesc* d_insts = nullptr;
+  int32_t *d_D = nullptr, *d_R = nullptr, *d_kM = nullptr, *d_kR = nullptr,
+          *d_hM = nullptr, *d_hR = nullptr;
+  int2* d_tab = nullptr;  // global prefix tables (staged on demand)
+  int64_t* d_C0 = nullptr;
+  bool tab_ready = false;
+
+  RunDesc* d_runs = nullptr;
+  size_t runs_cap = 0;
+  RunOut* d_out = nullptr;
+  size_t out_cap = 0;
+  RowBits* d_bits = nullptr;
+  size_t bits_cap = 0;
+  TrajEntry* d_traj = nullptr;
+  size_t traj_cap = 0;
+  int32_t* d_queue = nullptr;
+  uint64_t* d_bestkey = nullptr;
+
+  std::vector<RunDesc> h_runs;
+  std::vector<int32_t> out_of_inst;  // per instance: its output index
+  int32_t nruns = 0;
+  bool have_result = false;
+
+  InstPools pools() const {
+    InstPools p;
+    p.insts = d_insts;
+    p.D = d_D;
+    p.R = d_R;
+    p.kM = d_kM;
+    p.kR = d_kR;
+    p.hM = d_hM;
+    p.hR = d_hR;
+    p.gtab = d_tab;
+    p.gC0 = d_C0;
+    return p;
+  }
+
+  ~elsr_batch() {
+    if (d_insts) cudaStreamSynchronize(stream);
+    dev_free(d_insts);
+    dev_free(d_D);
+    dev_free(d_R);
+    dev_free(d_kM);
+    dev_free(d_kR);
+    dev_free(d_hM);
+    dev_free(d_hR);
+    dev_free(d_tab);
+    dev_free(d_C0);
+    dev_free(d_runs);
+    dev_free(d_out);
+    dev_free(d_bits);
+    dev_free(d_traj);
+    dev_free(d_queue);
+    dev_free(d_bestkey);
+  }
+};
+
+namespace {
+
+int batch_init(elsr_batch* b, int32_t n, const int32_t* Ks, const int32_t* Ts,
+               const int32_t* D, const int32_t* R, const int32_t* kM,
+               const int32_t* kR, const int32_t* hM, const int32_t* hR) {
+  if (n < 1 || !Ks || !Ts) {
+    b->err = "batch needs n >= 1 and K/T arrays";
+    return ELSR_E_ARG;
+  }
+  b->n = n;
+  b->insts.resize(n);
+  unsigned __int128 total_all = 0;
+  for (int32_t i = 0; i < n; ++i) {
+    InstDesc& d = b->insts[i];
+    d.K = Ks[i];
+    d.T = Ts[i];
+    if (d.K < 1 || d.T < 1 || d.T > ELSR_T_MAX) {
+      b->err = "instance " + std::to_string(i) + ": bad K or T";
+      return ELSR_E_ARG;
+    }
+    d.cell_off = b->cells;
+    d.row_off = b->rows;
+    d.tab_off = b->rows + b->cells;  // K*(T+1) = K*T + K entries
+    unsigned __int128 tot = 0;
+    bool a64 = false;
+    int rc = check_instance(d.K, d.T, D ? D + d.cell_off : nullptr,
+                            R ? R + d.cell_off : nullptr,
+                            kM ? kM + d.row_off : nullptr,
+                            kR ? kR + d.row_off : nullptr,
+                            hM ? hM + d.row_off : nullptr,
+                            hR ? hR + d.row_off : nullptr, &a64, &tot, b->err);
+    if (rc != ELSR_OK) {
+      b->err = "instance " + std::to_string(i) + ": " + b->err;
+      return rc;
+    }
+    b->acc64 = b->acc64 || a64;
+    total_all += tot;
+    b->cells += (int64_t)d.K * d.T;
+    b->rows += d.K;
+    b->maxK = std::max(b->maxK, d.K);
+    b->maxT = std::max(b->maxT, d.T);
+  }
+  (void)total_all;
+  ELSR_TRY_CUDA(b, cudaGetDevice(&b->device));
+  ELSR_TRY_CUDA(b, cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device));
+  ELSR_TRY_CUDA(b, dev_alloc(&b->d_insts, n));
+  ELSR_TRY_CUDA(b, dev_alloc(&b->d_D, b->cells));
+  ELSR_TRY_CUDA(b, dev_alloc(&b->d_R, b->cells));
+  ELSR_TRY_CUDA(b, dev_alloc(&b->d_kM, b->rows));
+  ELSR_TRY_CUDA(b, dev_alloc(&b->d_kR, b->rows));
+  ELSR_TRY_CUDA(b, dev_alloc(&b->d_hM, b->rows));
+  ELSR_TRY_CUDA(b, dev_alloc(&b->d_hR, b->rows));
+  ELSR_TRY_CUDA(b, dev_alloc(&b->d_queue, 1));
+  ELSR_TRY_CUDA(b, dev_alloc(&b->d_bestkey, 1));
+  ELSR_TRY_CUDA(b, cudaMemcpy(b->d_insts, b->insts.data(), n * sizeof(InstDesc), cudaMemcpyHostToDevice));
+  ELSR_TRY_CUDA(b, cudaMemcpy(b->d_D, D, b->cells * 4, cudaMemcpyHostToDevice));
+  ELSR_TRY_CUDA(b, cudaMemcpy(b->d_R, R, b->cells * 4, cudaMemcpyHostToDevice));
+  ELSR_TRY_CUDA(b, cudaMemcpy(b->d_kM, kM, b->rows * 4, cudaMemcpyHostToDevice));
+  ELSR_TRY_CUDA(b, cudaMemcpy(b->d_kR, kR, b->rows * 4, cudaMemcpyHostToDevice));
+  ELSR_TRY_CUDA(b, cudaMemcpy(b->d_hM, hM, b->rows * 4, cudaMemcpyHostToDevice));
+  ELSR_TRY_CUDA(b, cudaMemcpy(b->d_hR, hR, b->rows * 4, cudaMemcpyHostToDevice));
+  return ELSR_OK;
+}
+
+template <typename T>
+int ensure(elsr_batch* b, T** p, size_t* cap, size_t need) {
+  if (need <= *cap && *p) return ELSR_OK;
+  dev_free(*p);
+  *cap = 0;
+  ELSR_TRY_CUDA(b, dev_alloc(p, need));
+  *cap = need;
+  return ELSR_OK;
+}
+
+struct LaunchShape {
+  bool tab_smem;
+  size_t smem;
+  int threads, G, blocks;
+};
+
+// Launch shape of the persistent kernel for the runs in b->h_runs.
+int vns_shape(elsr_batch* b, LaunchShape* ls) {
+  const int acc = b->acc64 ? 8 : 4;
+  size_t need_s = 0, need_g = 0;
+  for (const RunDesc& r : b->h_runs) {
+    const InstDesc& d = b->insts[r.inst];
+    need_s = std::max<size_t>(need_s, vns_layout(d.K, d.T, acc, true).total);
+    need_g = std::max<size_t>(need_g, vns_layout(d.K, d.T, acc, false).total);
+  }
+  ls->tab_smem = need_s <= (size_t)kSmemLimit;
+  ls->smem = ls->tab_smem ? need_s : need_g;
+  if (ls->smem > (size_t)kSmemLimit) {
+    b->err = "instance too large for one CTA's shared memory (" +
+             std::to_string(ls->smem) + " bytes)";
+    return ELSR_E_RANGE;
+  }
+  ls->G = b->lanes ? b->lanes : default_lanes(b->maxT);
+  int thr = b->threads;
+  if (!thr) {
+    thr = ((b->maxK * ls->G + 31) / 32) * 32;
+    thr = std::min(1024, std::max(64, thr));
+  }
+  ls->threads = thr;
+  int bps = 0;
+  ELSR_TRY_CUDA(b, vns_prepare(b->acc64, ls->tab_smem, ls->smem, thr, &bps));
+  if (bps < 1) {
+    b->err = "persistent kernel does not fit on an SM with this shape";
+    return ELSR_E_RANGE;
+  }
+  ls->blocks = std::min<int64_t>((int64_t)bps * b->sms, (int64_t)b->h_runs.size());
+  return ELSR_OK;
+}
+
+// Queue the runs of b->h_runs (already ordered) on b->stream.
+int launch_runs(elsr_batch* b, const RowBits* start_bits, bool with_traj,
+                int64_t traj_entries) {
+  LaunchShape ls;
+  int rc = vns_shape(b, &ls);
+  if (rc != ELSR_OK) return rc;
+  const size_t nr = b->h_runs.size();
+  int64_t bits_total = 0;
+  for (const RunDesc& r : b->h_runs) bits_total = std::max<int64_t>(bits_total, r.bits_off + b->insts[r.inst].K);
+  if ((rc = ensure(b, &b->d_runs, &b->runs_cap, nr)) != ELSR_OK) return rc;
+  if ((rc = ensure(b, &b->d_out, &b->out_cap, nr)) != ELSR_OK) return rc;
+  if ((rc = ensure(b, &b->d_bits, &b->bits_cap, (size_t)bits_total)) != ELSR_OK) return rc;
+  if (with_traj && (rc = ensure(b, &b->d_traj, &b->traj_cap, (size_t)std::max<int64_t>(traj_entries, 1))) != ELSR_OK)
+    return rc;
+  if (!ls.tab_smem && !b->tab_ready) {
+    dev_free(b->d_tab);
+    dev_free(b->d_C0);
+    ELSR_TRY_CUDA(b, dev_alloc(&b->d_tab, (size_t)(b->cells + b->rows)));
+    ELSR_TRY_CUDA(b, dev_alloc(&b->d_C0, (size_t)b->rows));
+    StageParams sp;
+    sp.ip = b->pools();
+    sp.ninst = b->n;
+    sp.gtab = b->d_tab;
+    sp.gC0 = b->d_C0;
+    ELSR_TRY_CUDA(b, launch_stage(sp, (int)std::min<int64_t>(b->rows, 1 << 30), b->stream));
+    b->tab_ready = true;
+  }
+  ELSR_TRY_CUDA(b, cudaMemcpyAsync(b->d_runs, b->h_runs.data(), nr * sizeof(RunDesc),
+                                   cudaMemcpyHostToDevice, b->stream));
+  ELSR_TRY_CUDA(b, cudaMemsetAsync(b->d_queue, 0, sizeof(int32_t), b->stream));
+  VnsParams p;
+  p.ip = b->pools();
+  p.runs = b->d_runs;
+  p.nruns = (int32_t)nr;
+  p.G = ls.G;
+  p.vnd_cap = kVndCap;
+  p.pad = 0;
+  p.start_bits = start_bits;
+  p.out_bits = b->d_bits;
+  p.out = b->d_out;
+  p.traj = with_traj ? b->d_traj : nullptr;
+  p.queue = b->d_queue;
+  ELSR_TRY_CUDA(b, launch_vns(p, b->acc64, ls.tab_smem, ls.blocks, ls.threads, ls.smem, b->stream));
+  b->nruns = (int32_t)nr;
+  b->have_result = true;
+  return ELSR_OK;
+}
+
+void to_stats(const RunOut& o, elsr_stats_t* s) {
+  s->best_cost = o.best_cost;
+  s->traj_hash = o.traj_hash;
+  s->moves_evaluated = o.moves_evaluated;
+  s->evals = o.evals;
+  s->vnd_cycles = o.vnd_cycles;
+  s->applied = o.applied;
+  s->iterations = o.iterations;
+  s->accepted = o.accepted;
+  s->segments = o.segments;
+  s->status = o.status;
+  s->reserved = 0;
+}
+
+void unpack_bits(const std::vector<RowBits>& rb, int K, int T, uint8_t* gM, uint8_t* gR) {
+  for (int k = 0; k < K; ++k)
+    for (int t = 0; t < T; ++t) {
+      if (gM) gM[(int64_t)k * T + t] = (uint8_t)bit_of(rb[k].m0, rb[k].m1, t);
+      if (gR) gR[(int64_t)k * T + t] = (uint8_t)bit_of(rb[k].r0, rb[k].r1, t);
+    }
+}
+
+int pack_bits(const uint8_t* gM, const uint8_t* gR, int K, int T, std::vector<RowBits>& rb, std::string& err) {
+  rb.assign(K, RowBits{0, 0, 0, 0});
+  for (int k = 0; k < K; ++k)
+    for (int t = 0; t < T; ++t) {
+      const uint8_t m = gM[(int64_t)k * T + t], r = gR[(int64_t)k * T + t];
+      if (m > 1 || r > 1) {
+        err = "setup matrices must hold 0/1";
+        return ELSR_E_ARG;
+      }
+      if (m) flip(rb[k].m0, rb[k].m1, t);
+      if (r) flip(rb[k].r0, rb[k].r1, t);
+    }
+  return ELSR_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Single-instance handle
+// ---------------------------------------------------------------------------
+struct elsr_ctx {
+  elsr_batch b;
+  int32_t K = 0, T = 0;
+  RowBits* d_state = nullptr;
+  int64_t* d_rowcost = nullptr;
+  uint64_t* d_ppkey = nullptr;
+  uint64_t* d_scratch = nullptr;
+  int64_t* d_movecost = nullptr;
+  int32_t* d_movewin = nullptr;
+  int32_t* d_plan = nullptr;
+  int64_t moves_total = 0;
+  int last_kind = 0;  // 1: vns_run, 2: multistart
+  int32_t last_iters = 0;
+  int32_t best_out = 0;
+  bool counted = true;
+
+  ~elsr_ctx() {
+    if (b.d_insts) cudaStreamSynchronize(b.stream);
+    dev_free(d_state);
+    dev_free(d_rowcost);
+    dev_free(d_ppkey);
+    dev_free(d_scratch);
+    dev_free(d_movecost);
+    dev_free(d_movewin);
+    dev_free(d_plan);
+  }
+};
+
+namespace {
+
+int eval_launch(elsr_ctx* h, uint32_t mask, int32_t mode, int single_j,
+                bool write_rowcost) {
+  elsr_batch* b = &h->b;
+  const int G = b->lanes ? b->lanes : default_lanes(h->T);
+  const int threads = 256;
+  const int nsub = threads / G;
+  const size_t smem = eval_smem_bytes(nsub, h->T, b->acc64);
+  ELSR_TRY_CUDA(b, eval_prepare(b->acc64, smem));
+  EvalParams p;
+  p.ip = b->pools();
+  p.K = h->K;
+  p.T = h->T;
+  p.bits = h->d_state;
+  p.rowcost_in = h->d_rowcost;
+  p.mask = mask;
+  p.mode = mode;
+  p.G = G;
+  p.single_j = single_j;
+  p.rowcost_out = write_rowcost ? h->d_rowcost : nullptr;
+  p.pp_key = h->d_ppkey;
+  p.move_cost = single_j ? h->d_movecost : nullptr;
+  p.move_win = single_j ? h->d_movewin : nullptr;
+  p.scratch = h->d_scratch;
+  const uint64_t init[4] = {~0ull, 0ull, 0ull, 0ull};
+  ELSR_TRY_CUDA(b, cudaMemcpyAsync(h->d_scratch, init, sizeof(init), cudaMemcpyHostToDevice, b->stream));
+  const int blocks = (h->K + nsub - 1) / nsub;
+  ELSR_TRY_CUDA(b, launch_eval(p, b->acc64, blocks, threads, smem, b->stream));
+  return ELSR_OK;
+}
+
+int refresh_rowcost(elsr_ctx* h) { return eval_launch(h, 0u, 0, 0, true); }
+
+}  // namespace
+
+extern "C" {
+
+int elsr_version(void) { return 10000; }
+
+const char* elsr_strerror(int code) {
+  switch (code) {
+    case ELSR_OK: return "ok";
+    case ELSR_E_ARG: return "invalid argument";
+    case ELSR_E_RANGE: return "instance exceeds the supported integer ranges";
+    case ELSR_E_NOMEM: return "out of memory";
+    case ELSR_E_CUDA: return "CUDA error";
+    case ELSR_E_CAP: return "VND sweep cap reached";
+    case ELSR_E_STATE: return "call out of order";
+    default: return "unknown error";
+  }
+}
+
+const char* elsr_last_error(const elsr_t* h) {
+  return h ? h->b.err.c_str() : g_create_error.c_str();
+}
+
+int elsr_create(elsr_t** out, int32_t K, int32_t T, const int32_t* D,
+                const int32_t* R, const int32_t* kM, const int32_t* kR,
+                const int32_t* hM, const int32_t* hR) {
+  if (!out) {
+    g_create_error = "out is NULL";
+    return ELSR_E_ARG;
+  }
+  *out = nullptr;
+  elsr_ctx* h = new (std::nothrow) elsr_ctx();
+  if (!h) {
+    g_create_error = "host allocation failed";
+    return ELSR_E_NOMEM;
+  }
+  const int32_t Ks[1] = {K}, Ts[1] = {T};
+  int rc = batch_init(&h->b, 1, Ks, Ts, D, R, kM, kR, hM, hR);
+  if (rc == ELSR_OK) {
+    h->K = K;
+    h->T = T;
+    elsr_batch* b = &h->b;
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = dev_alloc(&h->d_state, K);
+    if (e == cudaSuccess) e = dev_alloc(&h->d_rowcost, K);
+    if (e == cudaSuccess) e = dev_alloc(&h->d_ppkey, K);
+    if (e == cudaSuccess) e = dev_alloc(&h->d_scratch, 4);
+    if (e == cudaSuccess) e = dev_alloc(&h->d_plan, (size_t)4 * K * T);
+    if (e != cudaSuccess) {
+      b->err = std::string("device allocation: ") + cudaGetErrorString(e);
+      rc = ELSR_E_NOMEM;
+    } else {
+      rc = elsr_set_state(h, nullptr, nullptr);
+    }
+  }
+  if (rc != ELSR_OK) {
+    g_create_error = h->b.err;
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return ELSR_OK;
+}
+
+void elsr_destroy(elsr_t* h) { delete h; }
+
+int elsr_set_stream(elsr_t* h, void* stream) {
+  if (!h) return ELSR_E_ARG;
+  h->b.stream = (cudaStream_t)stream;
+  return ELSR_OK;
+}
+
+int elsr_set_launch(elsr_t* h, int32_t lanes, int32_t threads) {
+  if (!h) return ELSR_E_ARG;
+  return elsr_batch_set_launch(&h->b, lanes, threads);
+}
+
+int elsr_set_state(elsr_t* h, const uint8_t* gM, const uint8_t* gR) {
+  if (!h) return ELSR_E_ARG;
+  if ((gM == nullptr) != (gR == nullptr)) {
+    h->b.err = "gM and gR must both be given or both be NULL";
+    return ELSR_E_ARG;
+  }
+  std::vector<uint8_t> ones;
+  if (!gM) {
+    ones.assign((size_t)h->K * h->T, 1);
+    gM = gR = ones.data();
+  }
+  std::vector<RowBits> rb;
+  int rc = pack_bits(gM, gR, h->K, h->T, rb, h->b.err);
+  if (rc != ELSR_OK) return rc;
+  ELSR_TRY_CUDA(&h->b, cudaMemcpyAsync(h->d_state, rb.data(), h->K * sizeof(RowBits),
+                                       cudaMemcpyHostToDevice, h->b.stream));
+  rc = refresh_rowcost(h);
+  if (rc != ELSR_OK) return rc;
+  ELSR_TRY_CUDA(&h->b, cudaStreamSynchronize(h->b.stream));
+  return ELSR_OK;
+}
+
+int elsr_get_state(elsr_t* h, uint8_t* gM, uint8_t* gR) {
+  if (!h || !gM || !gR) return ELSR_E_ARG;
+  std::vector<RowBits> rb(h->K);
+  ELSR_TRY_CUDA(&h->b, cudaMemcpyAsync(rb.data(), h->d_state, h->K * sizeof(RowBits),
+                                       cudaMemcpyDeviceToHost, h->b.stream));
+  ELSR_TRY_CUDA(&h->b, cudaStreamSynchronize(h->b.stream));
+  unpack_bits(rb, h->K, h->T, gM, gR);
+  return ELSR_OK;
+}
+
+int elsr_cost(elsr_t* h, int64_t* rowcost, int64_t* total) {
+  if (!h) return ELSR_E_ARG;
+  std::vector<int64_t> rc(h->K);
+  ELSR_TRY_CUDA(&h->b, cudaMemcpyAsync(rc.data(), h->d_rowcost, h->K * sizeof(int64_t),
+                                       cudaMemcpyDeviceToHost, h->b.stream));
+  ELSR_TRY_CUDA(&h->b, cudaStreamSynchronize(h->b.stream));
+  if (rowcost) memcpy(rowcost, rc.data(), h->K * sizeof(int64_t));
+  if (total) {
+    int64_t s = 0;
+    for (int64_t c : rc) s = (c == INT64_MAX || s == INT64_MAX) ? INT64_MAX : s + c;
+    *total = s;
+  }
+  return ELSR_OK;
+}
+
+int elsr_eval_neighbourhood(elsr_t* h, uint32_t nb_mask, int32_t mode,
+                            int64_t* best_cost, int64_t* best_move,
+                            int64_t* pp_cost, int64_t* pp_move) {
+  if (!h) return ELSR_E_ARG;
+  if ((nb_mask & ~7u) || (mode != ELSR_MODE_P && mode != ELSR_MODE_G)) {
+    h->b.err = "nb_mask must be within 0..7 and mode P or G";
+    return ELSR_E_ARG;
+  }
+  int rc = eval_launch(h, nb_mask, mode, 0, false);
+  if (rc != ELSR_OK) return rc;
+  std::vector<uint64_t> keys(h->K);
+  uint64_t sc[4];
+  ELSR_TRY_CUDA(&h->b, cudaMemcpyAsync(keys.data(), h->d_ppkey, h->K * sizeof(uint64_t),
+                                       cudaMemcpyDeviceToHost, h->b.stream));
+  ELSR_TRY_CUDA(&h->b, cudaMemcpyAsync(sc, h->d_scratch, sizeof(sc), cudaMemcpyDeviceToHost, h->b.stream));
+  ELSR_TRY_CUDA(&h->b, cudaStreamSynchronize(h->b.stream));
+  for (int k = 0; k < h->K; ++k) {
+    if (pp_cost) pp_cost[k] = keys[k] == ~0ull ? INT64_MAX : key_cost(keys[k]);
+    if (pp_move) pp_move[k] = keys[k] == ~0ull ? -1 : key_index(keys[k]);
+  }
+  int64_t moves = 0;
+  for (int j = 1; j <= 3; ++j)
+    if (nb_mask & (1u << (j - 1))) moves += (int64_t)h->K * row_moves(h->T, j);
+  h->moves_total += moves;
+  if (mode == ELSR_MODE_P) {
+    if (best_cost) *best_cost = sc[2] ? INT64_MAX : (int64_t)sc[1];
+    if (best_move) *best_move = (int64_t)sc[3];
+  } else {
+    if (sc[0] == ~0ull) {
+      int64_t tot = 0;
+      rc = elsr_cost(h, nullptr, &tot);
+      if (rc != ELSR_OK) return rc;
+      if (best_cost) *best_cost = tot;
+      if (best_move) *best_move = -1;
+    } else {
+      if (best_cost) *best_cost = key_cost(sc[0]);
+      if (best_move) *best_move = key_index(sc[0]);
+    }
+  }
+  return ELSR_OK;
+}
+
+int elsr_move_costs(elsr_t* h, int32_t nb, int64_t* costs, int32_t* window) {
+  if (!h || nb < 1 || nb > 3 || !costs) return ELSR_E_ARG;
+  const int64_t n = (int64_t)h->K * row_moves(h->T, nb);
+  if (n <= 0) return ELSR_OK;
+  elsr_batch* b = &h->b;
+  dev_free(h->d_movecost);
+  dev_free(h->d_movewin);
+  ELSR_TRY_CUDA(b, dev_alloc(&h->d_movecost, n));
+  ELSR_TRY_CUDA(b, dev_alloc(&h->d_movewin, n));
+  int rc = eval_launch(h, 1u << (nb - 1), ELSR_MODE_P, nb, false);
+  if (rc != ELSR_OK) return rc;
+  ELSR_TRY_CUDA(b, cudaMemcpyAsync(costs, h->d_movecost, n * sizeof(int64_t), cudaMemcpyDeviceToHost, b->stream));
+  if (window)
+    ELSR_TRY_CUDA(b, cudaMemcpyAsync(window, h->d_movewin, n * sizeof(int32_t), cudaMemcpyDeviceToHost, b->stream));
+  ELSR_TRY_CUDA(b, cudaStreamSynchronize(b->stream));
+  h->moves_total += n;
+  return ELSR_OK;
+}
+
+int elsr_vns_run(elsr_t* h, uint64_t seed, int32_t iters, int32_t kmax, int32_t mode) {
+  if (!h) return ELSR_E_ARG;
+  if (iters < 0 || kmax < 1 || kmax > 3 || (mode != ELSR_MODE_P && mode != ELSR_MODE_G)) {
+    h->b.err = "need iters >= 0, 1 <= kmax <= 3, mode P or G";
+    return ELSR_E_ARG;
+  }
+  elsr_batch* b = &h->b;
+  RunDesc r;
+  r.inst = 0;
+  r.iters = iters;
+  r.kmax = kmax;
+  r.mode = mode;
+  r.seed = seed;
+  r.out = 0;
+  r.pad = 0;
+  r.bits_off = 0;
+  r.start_off = 0;
+  r.traj_off = 0;
+  b->h_runs.assign(1, r);
+  int rc = launch_runs(b, h->d_state, true, iters);
+  if (rc != ELSR_OK) return rc;
+  h->last_kind = 1;
+  h->last_iters = iters;
+  h->best_out = 0;
+  h->counted = false;
+  return ELSR_OK;
+}
+
+int elsr_result(elsr_t* h, elsr_stats_t* stats, uint8_t* gM, uint8_t* gR,
+                int32_t* plan, elsr_traj_t* traj, int32_t traj_capacity) {
+  if (!h) return ELSR_E_ARG;
+  elsr_batch* b = &h->b;
+  if (!h->last_kind) {
+    b->err = "no run has been queued";
+    return ELSR_E_STATE;
+  }
+  ELSR_TRY_CUDA(b, cudaStreamSynchronize(b->stream));
+  ELSR_TRY_CUDA(b, cudaGetLastError());
+  RunOut o;
+  ELSR_TRY_CUDA(b, cudaMemcpy(&o, b->d_out + h->best_out, sizeof(RunOut), cudaMemcpyDeviceToHost));
+  if (!h->counted) {
+    h->moves_total += o.moves_evaluated;
+    h->counted = true;
+  }
+  if (stats) to_stats(o, stats);
+  const RowBits* sol = b->d_bits + (int64_t)h->best_out * h->K;
+  if (gM || gR) {
+    std::vector<RowBits> rb(h->K);
+    ELSR_TRY_CUDA(b, cudaMemcpy(rb.data(), sol, h->K * sizeof(RowBits), cudaMemcpyDeviceToHost));
+    unpack_bits(rb, h->K, h->T, gM, gR);
+  }
+  if (plan) {
+    PlanParams pp;
+    pp.ip = b->pools();
+    pp.inst = 0;
+    pp.bits = sol;
+    pp.plan = h->d_plan;
+    ELSR_TRY_CUDA(b, launch_plan(pp, h->K, b->stream));
+    ELSR_TRY_CUDA(b, cudaMemcpyAsync(plan, h->d_plan, (size_t)4 * h->K * h->T * sizeof(int32_t),
+                                     cudaMemcpyDeviceToHost, b->stream));
+    ELSR_TRY_CUDA(b, cudaStreamSynchronize(b->stream));
+  }
+  if (traj && traj_capacity > 0 && h->last_kind == 1) {
+    const int32_t n = std::min(traj_capacity, h->last_iters);
+    if (n > 0)
+      ELSR_TRY_CUDA(b, cudaMemcpy(traj, b->d_traj, n * sizeof(TrajEntry), cudaMemcpyDeviceToHost));
+  }
+  return o.status;
+}
+
+int elsr_multistart_run(elsr_t* h, uint64_t seed0, int32_t nstarts, int32_t iters,
+                        int32_t kmax, int32_t mode, int64_t* best_cost,
+                        int32_t* best_start, int64_t* costs) {
+  if (!h) return ELSR_E_ARG;
+  if (nstarts < 1 || nstarts >= (1 << 24) || iters < 0 || kmax < 1 || kmax > 3 ||
+      (mode != ELSR_MODE_P && mode != ELSR_MODE_G)) {
+    h->b.err = "need 1 <= nstarts < 2^24, iters >= 0, 1 <= kmax <= 3, mode P or G";
+    return ELSR_E_ARG;
+  }
+  elsr_batch* b = &h->b;
+  b->h_runs.resize(nstarts);
+  for (int32_t s = 0; s < nstarts; ++s) {
+    RunDesc& r = b->h_runs[s];
+    r.inst = 0;
+    r.iters = iters;
+    r.kmax = kmax;
+    r.mode = mode;
+    r.seed = seed0 + (uint64_t)s;
+    r.out = s;
+    r.pad = 0;
+    r.bits_off = (int64_t)s * h->K;
+    r.start_off = 0;
+    r.traj_off = -1;
+  }
+  int rc = launch_runs(b, h->d_state, false, 0);
+  if (rc != ELSR_OK) return rc;
+  BestofParams bp;
+  bp.out = b->d_out;
+  bp.n = nstarts;
+  bp.best_key = b->d_bestkey;
+  ELSR_TRY_CUDA(b, launch_bestof(bp, b->stream));
+  uint64_t key = 0;
+  ELSR_TRY_CUDA(b, cudaMemcpyAsync(&key, b->d_bestkey, sizeof(key), cudaMemcpyDeviceToHost, b->stream));
+  std::vector<RunOut> outs;
+  if (costs) {
+    outs.resize(nstarts);
+    ELSR_TRY_CUDA(b, cudaMemcpyAsync(outs.data(), b->d_out, nstarts * sizeof(RunOut),
+                                     cudaMemcpyDeviceToHost, b->stream));
+  }
+  ELSR_TRY_CUDA(b, cudaStreamSynchronize(b->stream));
+  if (costs)
+    for (int32_t s = 0; s < nstarts; ++s) costs[s] = outs[s].best_cost;
+  h->last_kind = 2;
+  h->last_iters = iters;
+  h->best_out = key_index(key);
+  if (best_cost) *best_cost = key_cost(key);
+  if (best_start) *best_start = h->best_out;
+  h->counted = true;
+  return ELSR_OK;
+}
+
+int elsr_counters(elsr_t* h, int64_t* moves) {
+  if (!h || !moves) return ELSR_E_ARG;
+  *moves = h->moves_total;
+  return ELSR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batch ABI
+// ---------------------------------------------------------------------------
+int elsr_batch_create(elsr_batch_t** out, int32_t n, const int32_t* Ks,
+                      const int32_t* Ts, const int32_t* D, const int32_t* R,
+                      const int32_t* kM, const int32_t* kR, const int32_t* hM,
+                      const int32_t* hR) {
+  if (!out) {
+    g_create_error = "out is NULL";
+    return ELSR_E_ARG;
+  }
+  *out = nullptr;
+  elsr_batch* b = new (std::nothrow) elsr_batch();
+  if (!b) {
+    g_create_error = "host allocation failed";
+    return ELSR_E_NOMEM;
+  }
+  int rc = batch_init(b, n, Ks, Ts, D, R, kM, kR, hM, hR);
+  if (rc != ELSR_OK) {
+    g_create_error = b->err;
+    delete b;
+    return rc;
+  }
+  *out = b;
+  return ELSR_OK;
+}
+
+void elsr_batch_destroy(elsr_batch_t* b) { delete b; }
+
+const char* elsr_batch_last_error(const elsr_batch_t* b) {
+  return b ? b->err.c_str() : g_create_error.c_str();
+}
+
+int elsr_batch_set_stream(elsr_batch_t* b, void* stream) {
+  if (!b) return ELSR_E_ARG;
+  b->stream = (cudaStream_t)stream;
+  return ELSR_OK;
+}
+
+int elsr_batch_set_launch(elsr_batch_t* b, int32_t lanes, int32_t threads) {
+  if (!b) return ELSR_E_ARG;
+  if (lanes && lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32) {
+    b->err = "lanes_per_row must be 4, 8, 16 or 32";
+    return ELSR_E_ARG;
+  }
+  if (threads && (threads % 32 || threads < 32 || threads > 1024)) {
+    b->err = "threads must be a multiple of 32 in [32, 1024]";
+    return ELSR_E_ARG;
+  }
+  b->lanes = lanes;
+  b->threads = threads;
+  return ELSR_OK;
+}
+
+int elsr_batch_run(elsr_batch_t* b, const uint64_t* seeds, int32_t iters, int32_t kmax,
+                   int32_t mode) {
+  if (!b || !seeds) return ELSR_E_ARG;
+  if (iters < 0 || kmax < 1 || kmax > 3 || (mode != ELSR_MODE_P && mode != ELSR_MODE_G)) {
+    b->err = "need iters >= 0, 1 <= kmax <= 3, mode P or G";
+    return ELSR_E_ARG;
+  }
+  // Longest-first order of the work queue (cost ~ K*T per sweep).
+  std::vector<int32_t> order(b->n);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t c) {
+    return (int64_t)b->insts[a].K * b->insts[a].T > (int64_t)b->insts[c].K * b->insts[c].T;
+  });
+  b->h_runs.resize(b->n);
+  b->out_of_inst.assign(b->n, 0);
+  for (int32_t q = 0; q < b->n; ++q) {
+    const int32_t i = order[q];
+    RunDesc& r = b->h_runs[q];
+    r.inst = i;
+    r.iters = iters;
+    r.kmax = kmax;
+    r.mode = mode;
+    r.seed = seeds[i];
+    r.out = i;
+    r.pad = 0;
+    r.bits_off = b->insts[i].row_off;
+    r.start_off = -1;
+    r.traj_off = -1;
+    b->out_of_inst[i] = i;
+  }
+  return launch_runs(b, nullptr, false, 0);
+}
+
+int elsr_batch_results(elsr_batch_t* b, elsr_stats_t* stats) {
+  if (!b) return ELSR_E_ARG;
+  if (!b->have_result) {
+    b->err = "no batch run has been queued";
+    return ELSR_E_STATE;
+  }
+  std::vector<RunOut> outs(b->n);
+  ELSR_TRY_CUDA(b, cudaMemcpyAsync(outs.data(), b->d_out, b->n * sizeof(RunOut),
+                                   cudaMemcpyDeviceToHost, b->stream));
+  ELSR_TRY_CUDA(b, cudaStreamSynchronize(b->stream));
+  int status = ELSR_OK;
+  for (int32_t i = 0; i < b->n; ++i) {
+    if (stats) to_stats(outs[i], &stats[i]);
+    if (outs[i].status != ELSR_OK) status = outs[i].status;
+  }
+  return status;
+}
+
+int elsr_batch_solution(elsr_batch_t* b, int32_t i, uint8_t* gM, uint8_t* gR) {
+  if (!b || i < 0 || i >= b->n || !gM || !gR) return ELSR_E_ARG;
+  if (!b->have_result) {
+    b->err = "no batch run has been queued";
+    return ELSR_E_STATE;
+  }
+  const InstDesc& d = b->insts[i];
+  std::vector<RowBits> rb(d.K);
+  ELSR_TRY_CUDA(b, cudaMemcpyAsync(rb.data(), b->d_bits + d.row_off, d.K * sizeof(RowBits),
+                                   cudaMemcpyDeviceToHost, b->stream));
+  ELSR_TRY_CUDA(b, cudaStreamSynchronize(b->stream));
+  unpack_bits(rb, d.K, d.T, gM, gR);
+  return ELSR_OK;
+}
+
+}  // extern "C"

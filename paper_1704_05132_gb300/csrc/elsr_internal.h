@@ -1,0 +1,169 @@
+// elsr_internal.h -- device data layout and kernel launchers shared by the
+// kernels (elsr_kernels.cu) and the C ABI (elsr_abi.cu).  Not installed.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "elsr_row.cuh"
+
+namespace elsr {
+
+constexpr int kTMax = 128;
+constexpr int kMaxShake = 3;        // kmax <= 3: at most 3 shaken rows
+constexpr int kSmemLimit = 227 * 1024;
+constexpr int kStatusCap = -5;      // ELSR_E_CAP
+
+// One instance of a batch: rows [row_off, row_off + K) of the per-row pools
+// and cells [cell_off, cell_off + K*T) of the D/R pools.
+struct InstDesc {
+  int32_t K, T;
+  int64_t cell_off;
+  int64_t row_off;
+  int64_t tab_off;  // into the global prefix-table pool (K*(T+1) entries)
+};
+
+// One GVNS run: instance, budget and where its outputs go.
+struct RunDesc {
+  int32_t inst;
+  int32_t iters;
+  int32_t kmax;
+  int32_t mode;
+  uint64_t seed;
+  int32_t out;        // index into the per-run outputs
+  int32_t pad;
+  int64_t bits_off;   // RowBits offset of this run's solution output
+  int64_t start_off;  // RowBits offset of its start solution (-1: all open)
+  int64_t traj_off;   // trajectory entry offset (-1: none)
+};
+
+struct RunOut {
+  int64_t best_cost;
+  uint64_t traj_hash;
+  int64_t moves_evaluated, evals, vnd_cycles, applied, iterations, accepted;
+  int64_t segments;
+  int32_t status;
+  int32_t reserved;
+};
+
+struct TrajEntry {
+  int32_t it;
+  int32_t k;
+  int64_t cost;
+  int32_t accepted;
+  int32_t reserved;
+};
+
+// Raw instance pools (device).
+struct InstPools {
+  const InstDesc* insts;
+  const int32_t* D;
+  const int32_t* R;
+  const int32_t* kM;
+  const int32_t* kR;
+  const int32_t* hM;
+  const int32_t* hR;
+  const int2* gtab;    // global prefix tables (when not staged in smem)
+  const int64_t* gC0;  // per-row constants matching gtab
+};
+
+struct VnsParams {
+  InstPools ip;
+  const RunDesc* runs;
+  int32_t nruns;
+  int32_t G;  // sub-warp lanes per row
+  int32_t vnd_cap;
+  int32_t pad;
+  const RowBits* start_bits;
+  RowBits* out_bits;
+  RunOut* out;
+  TrajEntry* traj;
+  int32_t* queue;  // work counter, zero at launch
+};
+
+struct StageParams {
+  InstPools ip;
+  int32_t ninst;
+  int2* gtab;
+  int64_t* gC0;
+};
+
+// Single-instance neighbourhood evaluation (instance 0 of the pools).
+struct EvalParams {
+  InstPools ip;
+  int32_t K, T;
+  const RowBits* bits;       // current solution [K]
+  const int64_t* rowcost_in; // [K] current row costs (mode G "others")
+  uint32_t mask;
+  int32_t mode;
+  int32_t G;
+  int32_t single_j;          // j of the per-move outputs (0: none)
+  int64_t* rowcost_out;      // [K] nullable
+  uint64_t* pp_key;          // [K] nullable: per-product best (cost, local)
+  int64_t* move_cost;        // [K*row_moves(single_j)] nullable
+  int32_t* move_win;         // same, nullable
+  uint64_t* scratch;         // [4]: gkey, sum_after, ninf_after, n_improving
+};
+
+struct BestofParams {
+  const RunOut* out;
+  int32_t n;
+  uint64_t* best_key;  // pack_key(cost, run)
+};
+
+struct PlanParams {
+  InstPools ip;
+  int32_t inst;
+  const RowBits* bits;  // [K]
+  int32_t* plan;        // [4][K][T]
+};
+
+// Shared-memory layout of one run in the persistent GVNS kernel.
+struct VnsLayout {
+  uint32_t tab, rc, C0, bits, S, bad, A, C, save, slot, total;
+};
+
+ELSR_HD uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
+
+ELSR_HD VnsLayout vns_layout(int K, int T, int acc_bytes, bool tab_smem) {
+  VnsLayout L;
+  uint32_t o = 0;
+  L.tab = o;
+  if (tab_smem) o = align16(o + (uint32_t)K * (T + 1) * 8u);
+  L.rc = o;
+  o = align16(o + (uint32_t)K * 16u);
+  L.C0 = o;
+  o = align16(o + (uint32_t)K * 8u);
+  L.bits = o;
+  o = align16(o + (uint32_t)K * 32u);
+  L.S = o;
+  o = align16(o + (uint32_t)K * acc_bytes);
+  L.bad = o;
+  o = align16(o + (uint32_t)K * 4u);
+  L.A = o;
+  o = align16(o + (uint32_t)K * T * 4u);
+  L.C = o;
+  o = align16(o + (uint32_t)K * T * acc_bytes);
+  // save slot: RowBits(32) S(8) bad(4) pad(4) | A[T] | C[T]
+  L.slot = align16(48u + (((uint32_t)T * 4u + 7u) & ~7u) + (uint32_t)T * acc_bytes);
+  L.save = o;
+  o += 2u * kMaxShake * L.slot;
+  L.total = o;
+  return L;
+}
+
+// Launchers (elsr_kernels.cu).  Each returns the launch error.
+cudaError_t launch_stage(const StageParams& p, int ninst_rows_max,
+                         cudaStream_t s);
+cudaError_t launch_eval(const EvalParams& p, bool acc64, int blocks,
+                        int threads, size_t smem, cudaStream_t s);
+cudaError_t launch_vns(const VnsParams& p, bool acc64, bool tab_smem,
+                       int blocks, int threads, size_t smem, cudaStream_t s);
+cudaError_t launch_bestof(const BestofParams& p, cudaStream_t s);
+cudaError_t launch_plan(const PlanParams& p, int K, cudaStream_t s);
+cudaError_t vns_prepare(bool acc64, bool tab_smem, size_t smem, int threads,
+                        int* blocks_per_sm);
+cudaError_t eval_prepare(bool acc64, size_t smem);
+size_t eval_smem_bytes(int rows, int T, bool acc64);
+
+}  // namespace elsr

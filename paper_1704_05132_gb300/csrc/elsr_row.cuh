@@ -1,0 +1,336 @@
+// elsr_row.cuh -- per-product-row arithmetic of the ELSR neighbourhood
+// evaluation: segment decode over prefix tables, delta re-decode of a moved
+// row, and the row cache that the delta re-decode starts and merges from.
+//
+// Model (Section 2 of Antoniadis & Sifaleras 2017): a row (product k) has T
+// periods, demand D(t), returns R(t), setup costs kM, kR, holding costs hM,
+// hR and setup bits gM(t), gR(t).  Decode rule (reading of the formulation
+// the paper defers to [SK2016]): a setup at s covers the demand of the
+// periods up to the next setup n, "need" = sum D[s..n); remanufacturing
+// takes xR = min(avail, need) when gR(s) = 1, where avail = recoverable
+// stock entering s plus R(s); manufacturing covers the rest when
+// gM(s) = 1, and a shortfall is infeasible.  Demand before the first setup
+// is infeasible.
+//
+// GB300 formulation (not the paper's, which re-ran a per-period loop):
+// with exclusive demand prefixes CD[j] = sum_{i<j} D(i) and inclusive return
+// prefixes CR1[j] = sum_{i<=j} R(i), one setup segment [s, n) costs O(1):
+//   need  = CD[n] - CD[s]
+//   xR    = gR(s) ? min(avail, need) : 0
+//   cost += kM*gM(s) + kR*gR(s) + (hM*need - hR*xR) * (T - s)
+//   avail = avail - xR + CR1[n] - CR1[s]          (stock entering n)
+// because the holding cost of a whole row telescopes: sum_t yM(t) =
+// sum_t (xM+xR-D)(t)*(T-t) and sum_t yR(t) = sum_t (R-xR)(t)*(T-t).  The row
+// cost is S + C0 with S the sum of segment terms and the per-row constant
+// C0 = hR * sum_t R(t)(T-t) - hM * sum_t D(t)(T-t).
+//
+// Row cache (per setup s of the current row): A[s] = avail at s and
+// C[s] = S accumulated before s.  A move changes periods t1..t2 (t2 <= t1+1);
+// its re-decode starts at s0, the last period <= t1 that is a setup both
+// before and after the move, and stops at the first setup s > t2 whose
+// entering stock equals the cached A[s]: from there the row is unchanged,
+// so new S = S_prefix + (S_old - C[s]).
+//
+// Functions are __host__ __device__ so that the same arithmetic can be
+// exercised by host-side unit tests of this header.
+#pragma once
+
+#include <stdint.h>
+
+#if defined(__CUDACC__)
+#define ELSR_HD __host__ __device__ __forceinline__
+#else
+// Host-only compilation (unit tests of this header): CUDA's int2.
+#define ELSR_HD static inline
+struct int2 {
+  int x, y;
+};
+#endif
+
+namespace elsr {
+
+// Sentinels for an infeasible row in the 32- and 64-bit accumulators.
+template <typename Acc> struct Inf;
+template <> struct Inf<int32_t> { static constexpr int32_t value = INT32_MAX; };
+template <> struct Inf<int64_t> { static constexpr int64_t value = INT64_MAX; };
+
+ELSR_HD int lowbit(uint64_t x) {
+#if defined(__CUDA_ARCH__)
+  return __ffsll((long long)x) - 1;
+#else
+  return __builtin_ctzll(x);
+#endif
+}
+
+ELSR_HD int highbit(uint64_t x) {
+#if defined(__CUDA_ARCH__)
+  return 63 - __clzll((long long)x);
+#else
+  return 63 - __builtin_clzll(x);
+#endif
+}
+
+// Setup bits of one row: T <= 128 periods in two 64-bit words per type.
+struct RowBits {
+  uint64_t m0, m1;  // gM(t): bit t of m0 for t < 64, bit t-64 of m1
+  uint64_t r0, r1;  // gR(t)
+};
+
+ELSR_HD int bit_of(uint64_t w0, uint64_t w1, int t) {
+  return (int)(((t < 64) ? (w0 >> t) : (w1 >> (t - 64))) & 1ull);
+}
+
+ELSR_HD void flip(uint64_t& w0, uint64_t& w1, int t) {
+  if (t < 64) w0 ^= (1ull << t); else w1 ^= (1ull << (t - 64));
+}
+
+// First set bit strictly after s (s >= -1), or T when none.  Bits at or
+// above T are always zero.
+ELSR_HD int next_set(uint64_t u0, uint64_t u1, int s, int T) {
+  int p = s + 1;
+  if (p < 64) {
+    uint64_t m = u0 & (~0ull << p);
+    if (m) return lowbit(m);
+    p = 64;
+  }
+  if (p < 128) {
+    uint64_t m = u1 & (~0ull << (p - 64));
+    if (m) return 64 + lowbit(m);
+  }
+  return T;
+}
+
+// Last set bit strictly before t (t >= 0), or -1 when none.
+ELSR_HD int prev_set(uint64_t u0, uint64_t u1, int t) {
+  if (t > 64) {
+    int q = t - 64;
+    uint64_t m = (q >= 64) ? u1 : (u1 & ((1ull << q) - 1ull));
+    if (m) return 64 + highbit(m);
+    t = 64;
+  }
+  uint64_t m = (t >= 64) ? u0 : (u0 & ((1ull << t) - 1ull));
+  return m ? highbit(m) : -1;
+}
+
+// Number of moves of N_j in one row (N1, N2: T; N3: 2(T-1)).
+ELSR_HD int row_moves(int T, int j) { return j == 3 ? 2 * (T - 1) : T; }
+
+// Apply move `local` of N_j to a row (N1 flip gM, N2 flip gR, N3 swap).
+ELSR_HD void apply_row_move(RowBits& b, int T, int j, int local) {
+  if (j == 1) {
+    flip(b.m0, b.m1, local);
+  } else if (j == 2) {
+    flip(b.r0, b.r1, local);
+  } else {
+    const int c = local >= (T - 1);
+    const int t = local - c * (T - 1);
+    uint64_t& w0 = c ? b.r0 : b.m0;
+    uint64_t& w1 = c ? b.r1 : b.m1;
+    if (bit_of(w0, w1, t) != bit_of(w0, w1, t + 1)) {
+      flip(w0, w1, t);
+      flip(w0, w1, t + 1);
+    }
+  }
+}
+
+// Per-row constants: costs and the row's prefix table tab[0..T] =
+// {CD[j], CR1[j]} (CR1[T] = total returns).
+struct RowCosts {
+  int32_t kM, kR, hM, hR;
+};
+
+// One segment [s, n) with setup flags gm, gr at s.  ts = tab[s], tn = tab[n].
+// Updates avail (stock entering n) and S; returns false on a shortfall.
+template <typename Acc>
+ELSR_HD bool seg_step(int s, int gm, int gr, int2 ts, int2 tn, int T,
+                      const RowCosts& rc, int32_t& avail, Acc& S) {
+  const int32_t need = tn.x - ts.x;
+  const int32_t xr = gr ? (avail < need ? avail : need) : 0;
+  if (!gm && xr < need) return false;
+  S += (Acc)(gm ? rc.kM : 0) + (Acc)(gr ? rc.kR : 0) +
+       ((Acc)rc.hM * (Acc)need - (Acc)rc.hR * (Acc)xr) * (Acc)(T - s);
+  avail = avail - xr + (tn.y - ts.y);
+  return true;
+}
+
+// Cache of the current row.  bad = T when the row is feasible; else the
+// first setup whose segment falls short (-1 when demand precedes the first
+// setup); A/C are valid at setups s <= bad.
+template <typename Acc>
+struct RowState {
+  RowBits b;
+  Acc S;    // segment sum of the current row (Inf when infeasible)
+  int bad;
+};
+
+// Decode a whole row from its bits, writing the cache A[s], C[s] at every
+// setup.  Returns S (Inf when infeasible) and sets bad.  segs counts the
+// segments walked.
+template <typename Acc>
+ELSR_HD Acc build_row(const int2* tab, int T, const RowCosts& rc,
+                      const RowBits& b, int32_t* A, Acc* C, int& bad,
+                      int& segs) {
+  const uint64_t u0 = b.m0 | b.r0, u1 = b.m1 | b.r1;
+  int s = next_set(u0, u1, -1, T);
+  int2 ts = tab[s];
+  if (ts.x != 0) {  // demand before the first setup
+    bad = -1;
+    return Inf<Acc>::value;
+  }
+  int32_t avail = ts.y;
+  Acc S = 0;
+  while (s < T) {
+    A[s] = avail;
+    C[s] = S;
+    const int n = next_set(u0, u1, s, T);
+    const int2 tn = tab[n];
+    ++segs;
+    if (!seg_step<Acc>(s, bit_of(b.m0, b.m1, s), bit_of(b.r0, b.r1, s), ts,
+                       tn, T, rc, avail, S)) {
+      bad = s;
+      return Inf<Acc>::value;
+    }
+    s = n;
+    ts = tn;
+  }
+  bad = T;
+  return S;
+}
+
+// Result of a delta re-decode.
+template <typename Acc>
+struct DeltaOut {
+  Acc S;      // new segment sum (Inf when the moved row is infeasible)
+  int merge;  // setup where the walk merged into the cached row (T if none)
+  Acc delta;  // new C[s] - old C[s] for setups s >= merge
+};
+
+// Delta re-decode of the row after move `local` of N_j (Section 3's "find
+// the best neighbour" for one candidate).  cur: current row cache; A, C: its
+// arrays.  With WRITE, the new row's cache entries in the walked window are
+// written to A, C (the caller then adds `delta` to C at setups >= merge);
+// WRITE is only used when the current row is feasible.
+template <typename Acc, bool WRITE>
+ELSR_HD DeltaOut<Acc> eval_move(const int2* tab, int T, const RowCosts& rc,
+                                const RowState<Acc>& cur, int32_t* A, Acc* C,
+                                int j, int local, int& segs) {
+  DeltaOut<Acc> out;
+  out.merge = T;
+  out.delta = 0;
+  RowBits nb = cur.b;
+  int t1, other;
+  if (j == 1) {
+    t1 = local;
+    flip(nb.m0, nb.m1, t1);
+    other = bit_of(nb.r0, nb.r1, t1);
+  } else if (j == 2) {
+    t1 = local;
+    flip(nb.r0, nb.r1, t1);
+    other = bit_of(nb.m0, nb.m1, t1);
+  } else {
+    const int c = local >= (T - 1);
+    t1 = local - c * (T - 1);
+    uint64_t& w0 = c ? nb.r0 : nb.m0;
+    uint64_t& w1 = c ? nb.r1 : nb.m1;
+    if (bit_of(w0, w1, t1) == bit_of(w0, w1, t1 + 1)) {  // null swap
+      out.S = cur.S;
+      return out;
+    }
+    flip(w0, w1, t1);
+    flip(w0, w1, t1 + 1);
+    other = c ? bit_of(nb.m0, nb.m1, t1) : bit_of(nb.r0, nb.r1, t1);
+  }
+  const int t2 = (j == 3) ? t1 + 1 : t1;
+  const uint64_t u0 = nb.m0 | nb.r0, u1 = nb.m1 | nb.r1;
+  // Below t1 the old and new rows agree; t1 keeps a setup iff the untouched
+  // type has one there.
+  const int s0 = other ? t1 : prev_set(u0, u1, t1);
+  int s;
+  int2 ts;
+  int32_t avail;
+  Acc S;
+  if (s0 >= 0) {
+    if (s0 > cur.bad) {  // the unchanged prefix already falls short
+      out.S = Inf<Acc>::value;
+      return out;
+    }
+    s = s0;
+    ts = tab[s];
+    avail = A[s];
+    S = C[s];
+  } else {
+    s = next_set(u0, u1, -1, T);
+    ts = tab[s];
+    if (ts.x != 0) {
+      out.S = Inf<Acc>::value;
+      return out;
+    }
+    avail = ts.y;
+    S = 0;
+  }
+  while (s < T) {
+    if (s > t2 && s <= cur.bad && avail == A[s]) {
+      if (cur.bad < T) {  // merged into a suffix that falls short
+        out.S = Inf<Acc>::value;
+        return out;
+      }
+      out.merge = s;
+      out.delta = S - C[s];
+      out.S = S + (cur.S - C[s]);
+      return out;
+    }
+    if (WRITE) {
+      A[s] = avail;
+      C[s] = S;
+    }
+    const int n = next_set(u0, u1, s, T);
+    const int2 tn = tab[n];
+    ++segs;
+    if (!seg_step<Acc>(s, bit_of(nb.m0, nb.m1, s), bit_of(nb.r0, nb.r1, s),
+                       ts, tn, T, rc, avail, S)) {
+      out.S = Inf<Acc>::value;
+      return out;
+    }
+    s = n;
+    ts = tn;
+  }
+  out.S = S;
+  return out;
+}
+
+// Row cost = S + C0 as int64 (ELSR_INF when infeasible).
+template <typename Acc>
+ELSR_HD int64_t row_cost(Acc S, int64_t C0) {
+  return S == Inf<Acc>::value ? INT64_MAX : (int64_t)S + C0;
+}
+
+// Packed argmin key: cost in the top 40 bits (all ones = infeasible), move
+// index in the low 24; a smaller key is a lexicographically smaller
+// (cost, index).  Costs are below 2^40 - 1 by the create-time bound.
+ELSR_HD uint64_t pack_key(int64_t cost, uint32_t idx) {
+  const uint64_t c = (cost == INT64_MAX) ? 0xFFFFFFFFFFull : (uint64_t)cost;
+  return (c << 24) | (uint64_t)(idx & 0xFFFFFFu);
+}
+ELSR_HD int64_t key_cost(uint64_t key) {
+  const uint64_t c = key >> 24;
+  return c == 0xFFFFFFFFFFull ? INT64_MAX : (int64_t)c;
+}
+ELSR_HD int key_index(uint64_t key) { return (int)(key & 0xFFFFFFu); }
+
+// One splitmix64 step (Steele, Lea & Flood 2014): advance the state by the
+// golden-ratio increment, then the published output mix.
+ELSR_HD uint64_t splitmix64(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Shake draw j of strength k at iteration it (keyed by seed, iteration,
+// neighbourhood and move).
+ELSR_HD uint64_t shake_draw(uint64_t seed, uint64_t it, uint64_t k,
+                            uint64_t j) {
+  return splitmix64(splitmix64(splitmix64(seed) ^ it) ^ ((k << 32) | j));
+}
+
+}  // namespace elsr

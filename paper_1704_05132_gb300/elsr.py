@@ -1,0 +1,239 @@
+"""Python API over the C ABI (argument marshalling only).
+
+``Solver`` wraps one instance handle (``elsr_t``), ``Batch`` a set of
+instances solved by one persistent launch (``elsr_batch_t``).  Inputs are
+numpy arrays; every step of the search runs in the CUDA kernels of
+``libelsr.so``.  Work is issued on a CUDA stream: by default PyTorch's current
+stream when PyTorch is importable, else the legacy default stream.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _native as nat
+from ._native import check, load
+
+P = ctypes.c_void_p
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(P)
+
+
+def _i32(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _u8(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.uint8)
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return int(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+class Solver:
+    """One ELSR instance resident on the device (``elsr_create``)."""
+
+    def __init__(self, inst, stream=None, lanes: int = 0, threads: int = 0):
+        lib = load()
+        self.K, self.T = int(inst.D.shape[0]), int(inst.D.shape[1])
+        arrs = [_i32(inst.D), _i32(inst.R), _i32(inst.kM), _i32(inst.kR),
+                _i32(inst.hM), _i32(inst.hR)]
+        h = P()
+        check(lib.elsr_create(ctypes.byref(h), self.K, self.T, *[_p(a) for a in arrs]), None)
+        self._h = h
+        self._lib = lib
+        self.set_stream(stream)
+        if lanes or threads:
+            self.set_launch(lanes, threads)
+        self._last_iters = 0
+
+    # -- plumbing --
+    def _chk(self, code):
+        return check(code, self._h)
+
+    def set_stream(self, stream=None):
+        s = _stream_handle(stream)
+        self._chk(self._lib.elsr_set_stream(self._h, P(s) if s else None))
+
+    def set_launch(self, lanes: int = 0, threads: int = 0):
+        self._chk(self._lib.elsr_set_launch(self._h, lanes, threads))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.elsr_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- state --
+    def set_state(self, gM=None, gR=None):
+        if gM is None and gR is None:
+            self._chk(self._lib.elsr_set_state(self._h, None, None))
+            return
+        gm, gr = _u8(gM).reshape(self.K, self.T), _u8(gR).reshape(self.K, self.T)
+        self._chk(self._lib.elsr_set_state(self._h, _p(gm), _p(gr)))
+
+    def get_state(self):
+        gm = np.zeros((self.K, self.T), np.uint8)
+        gr = np.zeros((self.K, self.T), np.uint8)
+        self._chk(self._lib.elsr_get_state(self._h, _p(gm), _p(gr)))
+        return gm, gr
+
+    def cost(self):
+        rc = np.zeros(self.K, np.int64)
+        tot = np.zeros(1, np.int64)
+        self._chk(self._lib.elsr_cost(self._h, _p(rc), _p(tot)))
+        return int(tot[0]), rc
+
+    # -- Algorithm 1: one neighbourhood evaluation --
+    def eval_neighbourhood(self, mask: int = 0b111, mode: int = nat.MODE_P):
+        bc = np.zeros(1, np.int64)
+        bm = np.zeros(1, np.int64)
+        pc = np.zeros(self.K, np.int64)
+        pm = np.zeros(self.K, np.int64)
+        self._chk(self._lib.elsr_eval_neighbourhood(self._h, mask, mode, _p(bc), _p(bm),
+                                                    _p(pc), _p(pm)))
+        return int(bc[0]), int(bm[0]), pc, pm
+
+    def move_costs(self, j: int):
+        n = self.K * (2 * (self.T - 1) if j == 3 else self.T)
+        c = np.zeros(max(n, 1), np.int64)
+        w = np.zeros(max(n, 1), np.int32)
+        self._chk(self._lib.elsr_move_costs(self._h, j, _p(c), _p(w)))
+        return c[:n], w[:n]
+
+    # -- Algorithm 2: GVNS --
+    def vns_run(self, seed: int, iters: int, kmax: int = 3, mode: int = nat.MODE_P):
+        """Queue a GVNS run on the stream (asynchronous)."""
+        self._chk(self._lib.elsr_vns_run(self._h, seed & ((1 << 64) - 1), iters, kmax, mode))
+        self._last_iters = iters
+
+    def result(self, solution: bool = True, plan: bool = False, traj: bool = True):
+        st = nat.Stats()
+        gm = np.zeros((self.K, self.T), np.uint8) if solution else None
+        gr = np.zeros((self.K, self.T), np.uint8) if solution else None
+        pl = np.zeros((4, self.K, self.T), np.int32) if plan else None
+        n = self._last_iters if traj else 0
+        tr = (nat.Traj * max(n, 1))()
+        code = self._lib.elsr_result(self._h, ctypes.byref(st),
+                                     _p(gm) if solution else None,
+                                     _p(gr) if solution else None,
+                                     _p(pl) if plan else None,
+                                     tr if n else None, n)
+        if code != nat.ELSR_E_CAP:
+            self._chk(code)
+        out = st.as_dict()
+        if solution:
+            out["gM"], out["gR"] = gm, gr
+        if plan:
+            out["plan"] = pl
+        if n:
+            out["traj"] = np.array([(e.it, e.k, e.cost, e.accepted) for e in tr[:n]],
+                                   dtype=[("it", np.int32), ("k", np.int32),
+                                          ("cost", np.int64), ("accepted", np.int32)])
+        return out
+
+    def vns(self, seed: int, iters: int, kmax: int = 3, mode: int = nat.MODE_P, **kw):
+        self.vns_run(seed, iters, kmax, mode)
+        return self.result(**kw)
+
+    def multistart(self, seed0: int, nstarts: int, iters: int, kmax: int = 3,
+                   mode: int = nat.MODE_P, costs: bool = False):
+        bc = np.zeros(1, np.int64)
+        bs = np.zeros(1, np.int32)
+        cs = np.zeros(nstarts, np.int64) if costs else None
+        self._chk(self._lib.elsr_multistart_run(self._h, seed0, nstarts, iters, kmax, mode,
+                                                _p(bc), _p(bs), _p(cs) if costs else None))
+        self._last_iters = 0
+        return int(bc[0]), int(bs[0]), cs
+
+    def moves_evaluated(self) -> int:
+        v = np.zeros(1, np.int64)
+        self._chk(self._lib.elsr_counters(self._h, _p(v)))
+        return int(v[0])
+
+
+class Batch:
+    """Many instances of uneven size solved by one persistent launch."""
+
+    def __init__(self, insts, stream=None, lanes: int = 0, threads: int = 0):
+        lib = load()
+        self._lib = lib
+        self.n = len(insts)
+        self.Ks = np.array([i.D.shape[0] for i in insts], np.int32)
+        self.Ts = np.array([i.D.shape[1] for i in insts], np.int32)
+        cat = lambda f: _i32(np.concatenate([np.ravel(getattr(i, f)) for i in insts]))
+        arrs = [cat("D"), cat("R"), cat("kM"), cat("kR"), cat("hM"), cat("hR")]
+        b = P()
+        code = lib.elsr_batch_create(ctypes.byref(b), self.n, _p(self.Ks), _p(self.Ts),
+                                     *[_p(a) for a in arrs])
+        check(code, None, batch=True)
+        self._b = b
+        self.set_stream(stream)
+        if lanes or threads:
+            self.set_launch(lanes, threads)
+
+    def _chk(self, code):
+        return check(code, self._b, batch=True)
+
+    def set_stream(self, stream=None):
+        s = _stream_handle(stream)
+        self._chk(self._lib.elsr_batch_set_stream(self._b, P(s) if s else None))
+
+    def set_launch(self, lanes: int = 0, threads: int = 0):
+        self._chk(self._lib.elsr_batch_set_launch(self._b, lanes, threads))
+
+    def run(self, seeds, iters: int, kmax: int = 3, mode: int = nat.MODE_P):
+        s = np.ascontiguousarray(seeds, dtype=np.uint64)
+        assert s.shape == (self.n,)
+        self._seeds = s
+        self._chk(self._lib.elsr_batch_run(self._b, _p(s), iters, kmax, mode))
+
+    def results(self):
+        st = (nat.Stats * self.n)()
+        code = self._lib.elsr_batch_results(self._b, st)
+        if code != nat.ELSR_E_CAP:
+            self._chk(code)
+        return [s.as_dict() for s in st]
+
+    def solution(self, i: int):
+        K, T = int(self.Ks[i]), int(self.Ts[i])
+        gm = np.zeros((K, T), np.uint8)
+        gr = np.zeros((K, T), np.uint8)
+        self._chk(self._lib.elsr_batch_solution(self._b, i, _p(gm), _p(gr)))
+        return gm, gr
+
+    def close(self):
+        if getattr(self, "_b", None):
+            self._lib.elsr_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

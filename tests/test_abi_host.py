@@ -1,0 +1,70 @@
+"""C ABI checks that need no GPU: the library builds, loads, exports every
+entry point declared in include/elsr.h, and rejects invalid instances in its
+host-side validation (before any device call)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1704_05132_gb300 import _native as nat
+from paper_1704_05132_gb300 import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return nat.load()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "elsr.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(elsr_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("elsr_create", "elsr_eval_neighbourhood", "elsr_vns_run", "elsr_result",
+              "elsr_destroy", "elsr_batch_run", "elsr_multistart_run"):
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for n in _declared():
+        assert hasattr(lib, n), n
+    assert set(_declared()) == set(nat.SIGNATURES)
+
+
+def test_version_and_strerror(lib):
+    assert lib.elsr_version() >= 10000
+    assert lib.elsr_strerror(nat.ELSR_E_RANGE)
+
+
+def _create(lib, K, T, D, R, c):
+    h = ctypes.c_void_p()
+    arrs = [np.ascontiguousarray(a, np.int32) for a in (D, R, c[0], c[1], c[2], c[3])]
+    code = lib.elsr_create(ctypes.byref(h), K, T, *[a.ctypes.data_as(ctypes.c_void_p) for a in arrs])
+    return code, h
+
+
+def test_validation_rejects_bad_instances(lib):
+    K, T = 2, 4
+    D = np.ones((K, T))
+    R = np.zeros((K, T))
+    c = [np.ones(K)] * 4
+    assert _create(lib, K, 0, D, R, c)[0] == nat.ELSR_E_ARG
+    assert _create(lib, K, 129, np.ones((K, 129)), np.zeros((K, 129)), c)[0] == nat.ELSR_E_ARG
+    assert _create(lib, 0, T, D, R, c)[0] == nat.ELSR_E_ARG
+    Dn = D.copy()
+    Dn[1, 2] = -1
+    code, h = _create(lib, K, T, Dn, R, c)
+    assert code == nat.ELSR_E_ARG and not h.value
+    assert b"negative" in lib.elsr_last_error(None)
+    big = np.full((K, T), 2**30)
+    assert _create(lib, K, T, big, R, c)[0] == nat.ELSR_E_RANGE
+    hm = [np.ones(K), np.ones(K), np.full(K, 2**30), np.ones(K)]
+    assert _create(lib, K, T, np.full((K, T), 1000), R, hm)[0] == nat.ELSR_E_RANGE

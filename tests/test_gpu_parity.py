@@ -1,0 +1,311 @@
+"""GPU vs oracle parity through the C ABI (needs a GB300).
+
+Integer work, so every comparison is bit-exact: per-move row costs and
+decode windows, per-product and global argmins, VND results, whole GVNS
+trajectories (entry by entry), final solutions, plans and counters.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1704_05132_gb300 import gen
+
+pytestmark = pytest.mark.gpu
+
+INF = oracle.INF
+
+
+@pytest.fixture(scope="module")
+def E():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1704_05132_gb300 import build, elsr
+    build.build()
+    oracle.build()
+    return elsr
+
+
+def _inst(g):
+    return oracle.Instance.from_arrays(g)
+
+
+def _states(rng, K, T, n):
+    """Setup matrices: all open, random (feasible and infeasible rows), sparse."""
+    yield np.ones((K, T), np.uint8), np.ones((K, T), np.uint8)
+    for i in range(n):
+        dm, dr = rng.uniform(0.05, 0.9), rng.uniform(0.05, 0.9)
+        gm = (rng.random((K, T)) < dm).astype(np.uint8)
+        gr = (rng.random((K, T)) < dr).astype(np.uint8)
+        if i % 3 == 0:
+            gm[:, 0] = 1
+        if i % 3 == 1:
+            gm[:, 0] = 1
+            gr &= gm
+        yield gm, gr
+
+
+def _big_costs(g):
+    """Same instance with holding costs large enough to need 64-bit rows."""
+    g2 = gen.ElsrInstance(g.D.copy(), g.R.copy(), g.kM.copy(), g.kR.copy(),
+                          (g.hM.astype(np.int64) * 20000).astype(np.int32),
+                          (g.hR.astype(np.int64) * 20000).astype(np.int32))
+    return g2
+
+
+CASES = [
+    ("plain_small", lambda: gen.plain_small()),
+    ("K3_T1", lambda: gen.make_instance(5, 1, K=3, T=1)),
+    ("K2_T2", lambda: gen.make_instance(5, 2, K=2, T=2)),
+    ("K7_T63", lambda: gen.make_instance(5, 3, K=7, T=63)),
+    ("K5_T64", lambda: gen.make_instance(5, 4, K=5, T=64)),
+    ("K6_T65", lambda: gen.make_instance(5, 5, K=6, T=65)),
+    ("K4_T128", lambda: gen.make_instance(5, 6, K=4, T=128)),
+    ("K37_T52", lambda: gen.make_instance(5, 7, K=37, T=52)),
+    ("wide_acc64", lambda: _big_costs(gen.make_instance(5, 8, K=9, T=40))),
+]
+
+
+@pytest.mark.parametrize("name,mk", CASES, ids=[c[0] for c in CASES])
+def test_move_costs_and_windows(E, name, mk):
+    g = mk()
+    inst = _inst(g)
+    rng = np.random.default_rng(len(name))
+    with E.Solver(g) as s:
+        for gm, gr in _states(rng, inst.K, inst.T, 4):
+            s.set_state(gm, gr)
+            tot, rc = s.cost()
+            otot, orc = oracle.total_cost(inst, gm, gr)
+            assert tot == otot
+            np.testing.assert_array_equal(rc, orc)
+            for j in (1, 2, 3):
+                if oracle.row_moves(inst.T, j) <= 0:
+                    continue
+                c, w = s.move_costs(j)
+                np.testing.assert_array_equal(c, oracle.move_costs(inst, gm, gr, j))
+                per = oracle.row_moves(inst.T, j)
+                # windows of a sample of moves, one by one through the oracle
+                for m in rng.choice(len(c), size=min(len(c), 40), replace=False):
+                    k, l = divmod(int(m), per)
+                    assert w[m] == oracle.move_window(inst, k, gm[k], gr[k], j, l)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("name,mk", CASES[:6] + CASES[8:], ids=[c[0] for c in CASES[:6] + CASES[8:]])
+def test_eval_neighbourhood(E, name, mk, mode):
+    g = mk()
+    inst = _inst(g)
+    rng = np.random.default_rng(99 + mode)
+    with E.Solver(g) as s:
+        for gm, gr in _states(rng, inst.K, inst.T, 3):
+            s.set_state(gm, gr)
+            for mask in (1, 2, 4, 3, 7):
+                got = s.eval_neighbourhood(mask, mode)
+                bc, bm, pc, pm, _ = oracle.eval_neighbourhood(inst, gm, gr, mask, mode)
+                assert got[0] == bc and got[1] == bm, (mask, got[:2], (bc, bm))
+                np.testing.assert_array_equal(got[2], pc)
+                np.testing.assert_array_equal(got[3], pm)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("name,mk", CASES, ids=[c[0] for c in CASES])
+def test_vnd_parity(E, name, mk, mode):
+    g = mk()
+    inst = _inst(g)
+    gm0, gr0 = oracle.initial_solution(inst.K, inst.T)
+    om, orr, cnt = oracle.vnd(inst, gm0, gr0, mode)
+    with E.Solver(g) as s:
+        r = s.vns(seed=0, iters=0, kmax=3, mode=mode)
+    np.testing.assert_array_equal(r["gM"], om)
+    np.testing.assert_array_equal(r["gR"], orr)
+    assert r["best_cost"] == oracle.total_cost(inst, om, orr)[0]
+    for key in ("moves_evaluated", "evals", "vnd_cycles", "applied"):
+        assert r[key] == cnt[key], key
+
+
+def _check_run(r, o):
+    assert r["best_cost"] == o.best_cost
+    np.testing.assert_array_equal(r["gM"], o.gM)
+    np.testing.assert_array_equal(r["gR"], o.gR)
+    for key in ("moves_evaluated", "evals", "vnd_cycles", "applied", "iterations", "accepted"):
+        assert r[key] == o.counters[key], key
+    assert r["traj_hash"] == o.traj_hash
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("kmax", [1, 3])
+def test_vns_small_trajectory(E, mode, kmax):
+    """Plain VNS, K=5 products, T=12 periods, seed 0, 200 iterations."""
+    g = gen.plain_small()
+    inst = _inst(g)
+    o = oracle.vns(inst, seed=0, iters=200, kmax=kmax, mode=mode)
+    with E.Solver(g) as s:
+        r = s.vns(seed=0, iters=200, kmax=kmax, mode=mode)
+    np.testing.assert_array_equal(r["traj"]["it"], o.traj["it"])
+    np.testing.assert_array_equal(r["traj"]["k"], o.traj["k"])
+    np.testing.assert_array_equal(r["traj"]["cost"], o.traj["cost"])
+    np.testing.assert_array_equal(r["traj"]["accepted"], o.traj["accepted"])
+    _check_run(r, o)
+
+
+@pytest.mark.parametrize("name,mk", [c for c in CASES if c[0] not in ("plain_small",)],
+                         ids=[c[0] for c in CASES if c[0] not in ("plain_small",)])
+def test_vns_edge_shapes(E, name, mk):
+    g = mk()
+    inst = _inst(g)
+    iters = 40 if inst.K * inst.T < 1000 else 10
+    o = oracle.vns(inst, seed=7, iters=iters, kmax=3, mode=0)
+    with E.Solver(g) as s:
+        r = s.vns(seed=7, iters=iters, kmax=3, mode=0)
+    np.testing.assert_array_equal(r["traj"]["cost"], o.traj["cost"])
+    _check_run(r, o)
+
+
+def test_vns_medium_full_trajectory(E):
+    """Plain VNS, K=50 products, T=52 periods, seed 1, 2000 iterations: the
+    benchmark's workload and launch shape, compared entry by entry."""
+    g = gen.plain_medium()
+    inst = _inst(g)
+    with E.Solver(g) as s:
+        r = s.vns(seed=1, iters=2000, kmax=3, mode=0, plan=True)
+    o = oracle.vns(inst, seed=1, iters=2000, kmax=3, mode=0)
+    np.testing.assert_array_equal(r["traj"]["cost"], o.traj["cost"])
+    np.testing.assert_array_equal(r["traj"]["accepted"], o.traj["accepted"])
+    _check_run(r, o)
+    for k in range(inst.K):
+        c, plan = oracle.decode_row(inst, k, o.gM[k], o.gR[k])
+        assert c != INF
+        np.testing.assert_array_equal(r["plan"][:, k, :], plan)
+    # windows walked: the sum of per-move decode windows of every evaluation
+    assert r["segments"] > 0
+
+
+def test_segments_equal_oracle_windows(E):
+    """The kernel's segment counter equals the sum of the oracle's per-move
+    decode windows over every neighbourhood evaluation of a VND."""
+    g = gen.make_instance(31, 0, K=6, T=20)
+    inst = _inst(g)
+    gm, gr = oracle.initial_solution(inst.K, inst.T)
+    total = 0
+    # replay the oracle's mode-P VND, summing windows at each evaluation
+    while True:
+        imp = False
+        for j in (1, 2, 3):
+            per = oracle.row_moves(inst.T, j)
+            for k in range(inst.K):
+                for l in range(per):
+                    total += oracle.move_window(inst, k, gm[k], gr[k], j, l)
+            c = oracle.move_costs(inst, gm, gr, j).reshape(inst.K, per)
+            _, rc = oracle.total_cost(inst, gm, gr)
+            for k in range(inst.K):
+                l = int(np.argmin(c[k]))
+                if c[k, l] < rc[k]:
+                    gm1, gr1 = gm[k:k + 1].copy(), gr[k:k + 1].copy()
+                    oracle.apply_move(1, inst.T, j, l, gm1, gr1)
+                    gm[k], gr[k] = gm1[0], gr1[0]
+                    imp = True
+        if not imp:
+            break
+    with E.Solver(g) as s:
+        r = s.vns(seed=0, iters=0, kmax=3, mode=0)
+    assert r["segments"] == total
+    np.testing.assert_array_equal(r["gM"], gm)
+
+
+def test_plan_matches_oracle_decode(E):
+    g = gen.make_instance(17, 0, K=8, T=30)
+    inst = _inst(g)
+    with E.Solver(g) as s:
+        r = s.vns(seed=3, iters=20, kmax=3, mode=0, plan=True)
+    for k in range(inst.K):
+        c, plan = oracle.decode_row(inst, k, r["gM"][k], r["gR"][k])
+        np.testing.assert_array_equal(r["plan"][:, k, :], plan)
+
+
+def test_multistart_best_of(E):
+    """Independent starts with seeds seed0 + s; device best-of = the
+    lexicographic (cost, start) minimum of the oracle's starts."""
+    g = gen.make_instance(0, 0, K=12, T=26)
+    inst = _inst(g)
+    seeds = list(range(40, 56))
+    best, outs = oracle.multistart(inst, seeds, iters=30, kmax=3, mode=0)
+    with E.Solver(g) as s:
+        bc, bs, costs = s.multistart(40, len(seeds), 30, 3, 0, costs=True)
+        r = s.result(traj=False)
+    np.testing.assert_array_equal(costs, [o.best_cost for o in outs])
+    assert (bc, bs) == (outs[best].best_cost, best)
+    np.testing.assert_array_equal(r["gM"], outs[best].gM)
+    assert r["traj_hash"] == outs[best].traj_hash
+
+
+def test_multistart_large_instance_sample(E):
+    """Multi-start case: K=100, T=104 (seed 0, id 0), the same launch shape as
+    the 4096-start workload; starts checked one by one against the oracle."""
+    g = gen.multistart_large()
+    inst = _inst(g)
+    with E.Solver(g) as s:
+        bc, bs, costs = s.multistart(0, 64, 3, 3, 0, costs=True)
+    for sidx in (0, 37):
+        o = oracle.vns(inst, seed=sidx, iters=3, kmax=3, mode=0)
+        assert costs[sidx] == o.best_cost
+    assert bc == costs.min() and bs == int(np.argmin(costs))
+
+
+def test_batch_uneven_sample(E):
+    """Batching: 1024 instances K ~ U{5..100}, T ~ U{12..52} in one persistent
+    launch; a sample of instances checked one by one against the oracle."""
+    insts = gen.batch_uneven(1024)
+    seeds = np.arange(1024, dtype=np.uint64)
+    b = E.Batch(insts)
+    b.run(seeds, iters=60, kmax=3, mode=0)
+    res = b.results()
+    sizes = np.array([i.K * i.T for i in insts])
+    sample = list(np.argsort(sizes)[:6]) + [int(np.argmax(sizes)), 500]
+    for i in sample:
+        inst = _inst(insts[i])
+        o = oracle.vns(inst, seed=int(seeds[i]), iters=60, kmax=3, mode=0)
+        assert res[i]["best_cost"] == o.best_cost, i
+        assert res[i]["traj_hash"] == o.traj_hash, i
+        gm, gr = b.solution(i)
+        np.testing.assert_array_equal(gm, o.gM)
+        np.testing.assert_array_equal(gr, o.gR)
+    for r in res:
+        assert r["status"] == 0 and r["iterations"] == 60
+    b.close()
+
+
+def test_batch_with_global_tables(E):
+    """Instances too large for shared-memory prefix tables (K=200, T=104) use
+    tables staged in global memory; parity with the oracle still holds."""
+    insts = [gen.make_instance(9, i, K=200, T=104) for i in range(2)] + \
+            [gen.make_instance(9, 5, K=7, T=13)]
+    b = E.Batch(insts)
+    b.run(np.array([3, 4, 5], np.uint64), iters=2, kmax=3, mode=0)
+    res = b.results()
+    for i, g in enumerate(insts):
+        o = oracle.vns(_inst(g), seed=3 + i, iters=2, kmax=3, mode=0)
+        assert res[i]["best_cost"] == o.best_cost
+        assert res[i]["traj_hash"] == o.traj_hash
+    b.close()
+
+
+def test_launch_shapes_give_identical_results(E):
+    g = gen.make_instance(2, 2, K=23, T=40)
+    ref = None
+    for lanes, threads in [(4, 64), (8, 256), (16, 512), (32, 1024), (16, 1024)]:
+        with E.Solver(g, lanes=lanes, threads=threads) as s:
+            r = s.vns(seed=11, iters=50, kmax=3, mode=0)
+        key = (r["best_cost"], r["traj_hash"], r["moves_evaluated"], r["segments"])
+        if ref is None:
+            ref = key
+        assert key == ref, (lanes, threads)
+
+
+def test_invalid_state_rejected(E):
+    g = gen.plain_small()
+    with E.Solver(g) as s:
+        bad = np.full((g.K, g.T), 2, np.uint8)
+        with pytest.raises(E.nat.ElsrError if hasattr(E, "nat") else Exception):
+            s.set_state(bad, bad)
+        with pytest.raises(Exception):
+            s.vns_run(0, 10, kmax=4)
