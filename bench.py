@@ -181,8 +181,10 @@ def run_gpu(args):
     solver = elsr.Solver(g, stream=stream)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
 
+    iters = args.iters if args.iters is not None else WORKLOAD["iters"]
+
     def step():
-        solver.vns_run(seed, WORKLOAD["iters"], WORKLOAD["kmax"], 0)
+        solver.vns_run(seed, iters, WORKLOAD["kmax"], 0)
 
     for _ in range(args.warmup):
         step()
@@ -222,6 +224,25 @@ def run_gpu(args):
     value = moves_total / t_max
     kernel_s = t_local / args.steps
 
+    # ---- one full-neighbourhood evaluation (N1 u N2 u N3) per launch ----
+    solver.set_state()
+    ev_moves = K * (2 * T + 2 * (T - 1))
+    for _ in range(3):
+        solver.eval_neighbourhood(0b111, 0)
+    ev_n = 50
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev_ms = 0.0
+    for _ in range(ev_n):
+        e0.record(stream)
+        solver.eval_neighbourhood(0b111, 0)
+        e1.record(stream)
+        e1.synchronize()
+        ev_ms += e0.elapsed_time(e1)
+    eval_launch = {"moves_per_launch": ev_moves, "us_per_launch": 1e3 * ev_ms / ev_n,
+                   "moves_per_s": ev_moves * ev_n / (ev_ms / 1e3),
+                   "state": "initial solution (all setups open)",
+                   "note": "one elsr_eval_neighbourhood call incl. its result copies"}
+
     # ---- end to end through the public API, host buffers, copies inside ----
     pinned = {f: torch.from_numpy(np.ascontiguousarray(getattr(g, f))).pin_memory()
               for f in ("D", "R", "kM", "kR", "hM", "hR")}
@@ -229,19 +250,19 @@ def run_gpu(args):
     h2d = sum(int(a.numel()) * 4 for a in pinned.values())
     d2h = 80 + K * 32 + 8  # run statistics, solution bits, best cost
     e2e_moves, e2e_t = 0, 0.0
-    e2e_steps = max(1, min(args.steps, 5))
-    for i in range(e2e_steps + 1):
+    e2e_steps = 0 if args.no_e2e else max(1, min(args.steps, 5))
+    for i in range(e2e_steps + 1 if e2e_steps else 0):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         s2 = elsr.Solver(host, stream=stream)
-        s2.vns_run(seed, WORKLOAD["iters"], WORKLOAD["kmax"], 0)
+        s2.vns_run(seed, iters, WORKLOAD["kmax"], 0)
         r2 = s2.result(solution=True, traj=False)
         s2.close()
         dt = time.perf_counter() - t0
         if i > 0:  # first one is a warm-up
             e2e_t += dt
             e2e_moves += r2["moves_evaluated"]
-    e2e_value = e2e_moves / e2e_t * world
+    e2e_value = e2e_moves / e2e_t * world if e2e_t else None
 
     if rank != 0:
         if world > 1:
@@ -257,11 +278,12 @@ def run_gpu(args):
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": dict(WORKLOAD, parallelism=f"replicas x{world}",
+        "config": dict(WORKLOAD, iters=iters, parallelism=f"replicas x{world}",
                        l2="flushed between steps (256 MiB device write, untimed)",
                        launch="1 persistent CTA per GVNS run"),
         "instances_per_s": world * args.steps / t_max,
         "moves_per_step": moves_per_step,
+        "eval_launch": eval_launch,
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
@@ -288,6 +310,9 @@ def main():
     ap.add_argument("--cpu-iters", type=int, default=1000)
     ap.add_argument("--ref-iters", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--iters", type=int, default=None,
+                    help="override the iteration budget (profiling of small cases only)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

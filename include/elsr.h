@@ -128,6 +128,16 @@ int elsr_set_stream(elsr_t *h, void *stream);
  * threads per block (multiple of 32, <= 1024); 0 keeps the default. */
 int elsr_set_launch(elsr_t *h, int32_t lanes_per_row, int32_t threads);
 
+/* CTAs of one thread-block cluster that share a GVNS run of this handle
+ * (1..16; 0 = automatic).  Mode G runs always use one CTA.  Results do not
+ * depend on it. */
+int elsr_set_cluster(elsr_t *h, int32_t cluster);
+
+/* Launch shape of the last GVNS launch: shape[7] = {lanes per row, threads
+ * per block, CTAs per run, blocks, shared bytes per block, prefix tables in
+ * shared memory (0/1), 64-bit words per bit row}. */
+int elsr_launch_shape(elsr_t *h, int32_t *shape);
+
 /* Set the current solution from host 0/1 arrays gM, gR [K][T]; both NULL
  * restores the initial solution (every setup open). */
 int elsr_set_state(elsr_t *h, const uint8_t *gM, const uint8_t *gR);
@@ -221,6 +231,11 @@ const char *elsr_batch_last_error(const elsr_batch_t *b);
 int elsr_batch_set_stream(elsr_batch_t *b, void *stream);
 int elsr_batch_set_launch(elsr_batch_t *b, int32_t lanes_per_row,
                           int32_t threads);
+
+/* As elsr_set_cluster / elsr_launch_shape, for a batch (default: 1 CTA per
+ * run). */
+int elsr_batch_set_cluster(elsr_batch_t *b, int32_t cluster);
+int elsr_batch_launch_shape(elsr_batch_t *b, int32_t *shape);
 
 /* Queue GVNS runs of every instance i with seeds[i] (host [n]), from the
  * initial solution.  Asynchronous, like elsr_vns_run. */

@@ -528,30 +528,58 @@ void orc_initial_solution(int32_t K, int32_t T, uint8_t *gM, uint8_t *gR)
 }
 
 /* ------------------------------------------------------------------------ */
-/* Measurement helper (not part of the method): decode window of a move.     */
+/* Measurement helper (not part of the method): decode steps of a move.      */
 /* ------------------------------------------------------------------------ */
 
+/* Per-period decode of one row (same rule as orc_decode_row) recording the
+ * recoverable stock yR(t) and the first period where the row falls short
+ * (T when feasible). */
+static int32_t decode_stock(const orc_instance *in, int32_t k, const uint8_t *gM,
+                            const uint8_t *gR, int64_t *yR)
+{
+    const int32_t T = in->T;
+    const int32_t *D = in->D + (int64_t)k * T, *R = in->R + (int64_t)k * T;
+    int64_t yMp = 0, yRp = 0;
+    for (int32_t t = 0; t < T; ++t) {
+        int64_t avail = yRp + R[t], xm = 0, xr = 0;
+        if (gM[t] || gR[t]) {
+            int32_t n = t + 1;
+            while (n < T && !(gM[n] || gR[n])) ++n;
+            int64_t need = -yMp;
+            for (int32_t i = t; i < n; ++i) need += D[i];
+            if (gR[t]) xr = avail < need ? avail : need;
+            if (gM[t]) xm = need - xr; else if (xr < need) return t;
+        }
+        int64_t yM = yMp + xm + xr - D[t];
+        if (yM < 0) return t;
+        yR[t] = avail - xr;
+        yMp = yM;
+        yRp = yR[t];
+    }
+    return T;
+}
+
 /*
- * Number of setup segments a delta evaluation of one move must visit: the
- * setups of the moved row from s0 up to (not including) the merge setup,
- * where
- *   s0    = the last period <= t1 holding a setup both before and after the
- *           move (t1 = first changed period), or the first setup of the moved
- *           row when there is none;
- *   merge = the first setup s after the last changed period t2 at which the
- *           recoverable stock entering s, yR(s-1), is the same before and
- *           after the move and the row before the move is feasible up to s.
- * The walk also stops at the first infeasible segment, and it stops at once
- * (0 segments) when the unchanged prefix before s0 is already infeasible or
- * the move changes nothing.  This counts algorithmic work only; it is used to
- * express throughput as integer operations per second.
+ * Decode steps an incremental evaluation of one move needs, a work measure
+ * used to express throughput as integer operations per second:
+ *   - 0 for a move that changes nothing, or whose unchanged prefix already
+ *     falls short;
+ *   - one step per setup segment of the moved row from s0 (the last period
+ *     <= t1 holding a setup before and after the move; else the row's first
+ *     setup) while the segment starts at or before t2 (t1..t2 = changed
+ *     periods), or up to the end of the row when the row before the move
+ *     falls short somewhere;
+ *   - then one step per later gR setup while the recoverable stock entering
+ *     it differs between the rows before and after the move;
+ * stopping at the first segment that falls short.
  */
 int64_t orc_move_window(const orc_instance *in, int32_t k, const uint8_t *gM,
                         const uint8_t *gR, int32_t j, int64_t local)
 {
     const int32_t T = in->T;
     uint8_t *nm = malloc(T), *nr = malloc(T);
-    int64_t *po = malloc(sizeof(int64_t) * 4 * T), *pn = malloc(sizeof(int64_t) * 4 * T);
+    int64_t *yo = malloc(sizeof(int64_t) * T), *yn = malloc(sizeof(int64_t) * T);
+    int64_t count = 0;
     memcpy(nm, gM, T);
     memcpy(nr, gR, T);
     orc_apply_row_move(T, j, local, nm, nr);
@@ -562,96 +590,49 @@ int64_t orc_move_window(const orc_instance *in, int32_t k, const uint8_t *gM,
             if (t1 < 0) t1 = t;
             t2 = t;
         }
-    int64_t count = 0;
-    if (t1 < 0) goto done; /* null move */
+    if (t1 < 0) goto done;
 
-    /* old row: per-period decode up to its first infeasible period */
-    int32_t bad = T; /* first setup whose segment fails, -1 before any setup */
-    {
-        int64_t yMp = 0, yRp = 0;
-        int32_t seg = -1;
-        for (int32_t t = 0; t < T; ++t) {
-            if (gM[t] || gR[t]) seg = t;
-            int64_t avail = yRp + in->R[(int64_t)k * T + t], xm = 0, xr = 0;
-            int fail = 0;
-            if (gM[t] || gR[t]) {
-                int32_t n = t + 1;
-                while (n < T && !(gM[n] || gR[n])) ++n;
-                int64_t need = -yMp;
-                for (int32_t i = t; i < n; ++i) need += in->D[(int64_t)k * T + i];
-                if (gR[t]) xr = avail < need ? avail : need;
-                if (gM[t]) xm = need - xr; else if (xr < need) fail = 1;
-            }
-            int64_t yM = yMp + xm + xr - in->D[(int64_t)k * T + t];
-            if (yM < 0) fail = 1;
-            if (fail) { bad = seg; break; }
-            po[2 * T + t] = yM;
-            po[3 * T + t] = avail - xr;
-            yMp = yM;
-            yRp = avail - xr;
-        }
-    }
+    int32_t ofail = decode_stock(in, k, gM, gR, yo);
+    int32_t nfail = decode_stock(in, k, nm, nr, yn);
+    int32_t bad = ofail; /* setup of the failing segment, -1 before any setup */
+    if (ofail < T && !(gM[ofail] || gR[ofail])) bad = -1;
+
     int32_t s0 = -1;
-    for (int32_t t = t1; t >= 0; --t) {
-        int both = (gM[t] || gR[t]) && (nm[t] || nr[t]);
-        if (t < t1) both = gM[t] || gR[t]; /* unchanged below t1 */
-        if (both) { s0 = t; break; }
+    if ((gM[t1] || gR[t1]) && (nm[t1] || nr[t1])) {
+        s0 = t1;
+    } else {
+        for (int32_t t = t1 - 1; t >= 0; --t)
+            if (gM[t] || gR[t]) { s0 = t; break; }
     }
-    if (s0 >= 0 && s0 > bad) goto done; /* prefix already infeasible */
-    if (s0 < 0) {
-        int32_t f = 0;
-        while (f < T && !(nm[f] || nr[f])) ++f;
+    int32_t s;
+    if (s0 >= 0) {
+        if (s0 > bad) goto done;
+        s = s0;
+    } else {
+        s = 0;
+        while (s < T && !(nm[s] || nr[s])) ++s;
         int64_t dsum = 0;
-        for (int32_t i = 0; i < f; ++i) dsum += in->D[(int64_t)k * T + i];
+        for (int32_t i = 0; i < s; ++i) dsum += in->D[(int64_t)k * T + i];
         if (dsum > 0) goto done;
-        s0 = f;
     }
-    /* new row decode, counting segments from s0 */
-    (void)orc_decode_row(in, k, nm, nr, pn);
-    {
-        int64_t yRp = 0, yMp = 0;
-        for (int32_t t = 0; t < s0; ++t) { /* stock entering s0 */
-            int64_t avail = yRp + in->R[(int64_t)k * T + t], xr = 0, xm = 0;
-            if (nm[t] || nr[t]) {
-                int32_t n = t + 1;
-                while (n < T && !(nm[n] || nr[n])) ++n;
-                int64_t need = -yMp;
-                for (int32_t i = t; i < n; ++i) need += in->D[(int64_t)k * T + i];
-                if (nr[t]) xr = avail < need ? avail : need;
-                if (nm[t]) xm = need - xr;
-            }
-            yMp = yMp + xm + xr - in->D[(int64_t)k * T + t];
-            yRp = avail - xr;
-        }
-        for (int32_t s = s0; s < T;) {
-            if (s > t2 && s <= bad) {
-                int64_t old_in = s > 0 ? po[3 * T + s - 1] : 0;
-                if (yRp == old_in) break; /* merged */
-            }
-            int32_t n = s + 1;
-            while (n < T && !(nm[n] || nr[n])) ++n;
-            ++count;
-            /* advance the new row's decode over [s, n) */
-            int fail = 0;
-            for (int32_t t = s; t < n; ++t) {
-                int64_t avail = yRp + in->R[(int64_t)k * T + t], xr = 0, xm = 0;
-                if (t == s) {
-                    int64_t need = -yMp;
-                    for (int32_t i = s; i < n; ++i) need += in->D[(int64_t)k * T + i];
-                    if (nr[t]) xr = avail < need ? avail : need;
-                    if (nm[t]) xm = need - xr; else if (xr < need) fail = 1;
-                }
-                yMp = yMp + xm + xr - in->D[(int64_t)k * T + t];
-                yRp = avail - xr;
-            }
-            if (fail) break;
-            s = n;
-        }
+    while (s < T && (s <= t2 || bad < T)) {
+        ++count;
+        if (nfail == s) goto done;
+        int32_t n = s + 1;
+        while (n < T && !(nm[n] || nr[n])) ++n;
+        s = n;
+    }
+    for (int32_t q = s; q < T; ++q) {
+        if (!gR[q]) continue;
+        int64_t d = (q > 0 ? yn[q - 1] : 0) - (q > 0 ? yo[q - 1] : 0);
+        if (d == 0) break;
+        ++count;
+        if (nfail == q) break;
     }
 done:
     free(nm);
     free(nr);
-    free(po);
-    free(pn);
+    free(yo);
+    free(yn);
     return count;
 }

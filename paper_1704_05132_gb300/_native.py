@@ -54,6 +54,8 @@ SIGNATURES = {
     "elsr_destroy": (None, [P]),
     "elsr_set_stream": (ctypes.c_int, [P, P]),
     "elsr_set_launch": (ctypes.c_int, [P, i32, i32]),
+    "elsr_set_cluster": (ctypes.c_int, [P, i32]),
+    "elsr_launch_shape": (ctypes.c_int, [P, P]),
     "elsr_set_state": (ctypes.c_int, [P, P, P]),
     "elsr_get_state": (ctypes.c_int, [P, P, P]),
     "elsr_cost": (ctypes.c_int, [P, P, P]),
@@ -68,6 +70,8 @@ SIGNATURES = {
     "elsr_batch_last_error": (ctypes.c_char_p, [P]),
     "elsr_batch_set_stream": (ctypes.c_int, [P, P]),
     "elsr_batch_set_launch": (ctypes.c_int, [P, i32, i32]),
+    "elsr_batch_set_cluster": (ctypes.c_int, [P, i32]),
+    "elsr_batch_launch_shape": (ctypes.c_int, [P, P]),
     "elsr_batch_run": (ctypes.c_int, [P, P, i32, i32, i32]),
     "elsr_batch_results": (ctypes.c_int, [P, P]),
     "elsr_batch_solution": (ctypes.c_int, [P, i32, P, P]),

@@ -98,7 +98,7 @@ int check_instance(int32_t K, int32_t T, const int32_t* D, const int32_t* R,
   return ELSR_OK;
 }
 
-int default_lanes(int T) { return T <= 8 ? 4 : (T <= 24 ? 8 : 16); }
+int default_lanes(int T) { return T <= 8 ? 4 : (T <= 16 ? 8 : (T <= 40 ? 16 : 32)); }
 
 }  // namespace
 
@@ -114,7 +114,8 @@ struct elsr_batch {
   int64_t cells = 0, rows = 0;
   int maxK = 0, maxT = 0;
   bool acc64 = false;
-  int lanes = 0, threads = 0;  // 0 = defaults
+  int lanes = 0, threads = 0, cluster = 0;  // 0 = defaults
+  int last_shape[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   int sms = 0;
 
   InstDesc* d_insts = nullptr;
@@ -249,41 +250,62 @@ int ensure(elsr_batch* b, T** p, size_t* cap, size_t need) {
 }
 
 struct LaunchShape {
-  bool tab_smem;
+  int nw, maxt;
+  bool ts;
   size_t smem;
-  int threads, G, blocks;
+  int threads, G, cluster, blocks;
 };
 
-// Launch shape of the persistent kernel for the runs in b->h_runs.
+// Launch shape of the persistent kernel for the runs in b->h_runs: 64-bit
+// words per bit row, table placement, sub-warp width, block size, CTAs per
+// run (cluster) and grid size (resident blocks).
 int vns_shape(elsr_batch* b, LaunchShape* ls) {
   const int acc = b->acc64 ? 8 : 4;
+  int maxK = 0, maxT = 0;
+  bool any_g = false;
+  for (const RunDesc& r : b->h_runs) {
+    maxK = std::max(maxK, b->insts[r.inst].K);
+    maxT = std::max(maxT, b->insts[r.inst].T);
+    any_g = any_g || r.mode != ELSR_MODE_P;
+  }
+  int C = b->cluster;
+  if (C <= 0) C = b->h_runs.size() == 1 ? std::min(8, std::max(1, maxK / 6)) : 1;
+  if (any_g) C = 1;  // the global argmin of mode G runs inside one CTA
+  C = std::min(C, maxK);
   size_t need_s = 0, need_g = 0;
   for (const RunDesc& r : b->h_runs) {
     const InstDesc& d = b->insts[r.inst];
-    need_s = std::max<size_t>(need_s, vns_layout(d.K, d.T, acc, true).total);
-    need_g = std::max<size_t>(need_g, vns_layout(d.K, d.T, acc, false).total);
+    const int kc = (d.K + C - 1) / C;
+    need_s = std::max<size_t>(need_s, vns_layout(kc, d.T, acc, true).total);
+    need_g = std::max<size_t>(need_g, vns_layout(kc, d.T, acc, false).total);
   }
-  ls->tab_smem = need_s <= (size_t)kSmemLimit;
-  ls->smem = ls->tab_smem ? need_s : need_g;
+  ls->nw = maxT <= 64 ? 1 : 2;
+  ls->ts = need_s <= (size_t)kSmemLimit;
+  ls->smem = ls->ts ? need_s : need_g;
   if (ls->smem > (size_t)kSmemLimit) {
-    b->err = "instance too large for one CTA's shared memory (" +
-             std::to_string(ls->smem) + " bytes)";
+    b->err = "instance too large for the shared memory of its CTAs (" +
+             std::to_string(ls->smem) + " bytes per CTA); use a larger cluster";
     return ELSR_E_RANGE;
   }
-  ls->G = b->lanes ? b->lanes : default_lanes(b->maxT);
+  ls->G = b->lanes ? b->lanes : default_lanes(maxT);
+  const int kc = (maxK + C - 1) / C;
   int thr = b->threads;
-  if (!thr) {
-    thr = ((b->maxK * ls->G + 31) / 32) * 32;
-    thr = std::min(1024, std::max(64, thr));
-  }
+  if (!thr) thr = std::min(256, std::max(64, ((kc * ls->G + 31) / 32) * 32));
   ls->threads = thr;
-  int bps = 0;
-  ELSR_TRY_CUDA(b, vns_prepare(b->acc64, ls->tab_smem, ls->smem, thr, &bps));
-  if (bps < 1) {
-    b->err = "persistent kernel does not fit on an SM with this shape";
+  ls->maxt = thr <= 256 ? 256 : 1024;
+  ls->cluster = C;
+  int active = 0;
+  ELSR_TRY_CUDA(b, b->acc64 ? vns_prepare_i64(ls->nw, ls->ts, ls->maxt, ls->smem, thr, C, &active)
+                            : vns_prepare_i32(ls->nw, ls->ts, ls->maxt, ls->smem, thr, C, &active));
+  if (active < 1) {
+    b->err = "persistent kernel does not fit with this launch shape";
     return ELSR_E_RANGE;
   }
-  ls->blocks = std::min<int64_t>((int64_t)bps * b->sms, (int64_t)b->h_runs.size());
+  const int64_t nr = (int64_t)b->h_runs.size();
+  if (C == 1)
+    ls->blocks = (int)std::min<int64_t>((int64_t)active * b->sms, nr);
+  else
+    ls->blocks = C * (int)std::min<int64_t>(active, nr);
   return ELSR_OK;
 }
 
@@ -301,7 +323,7 @@ int launch_runs(elsr_batch* b, const RowBits* start_bits, bool with_traj,
   if ((rc = ensure(b, &b->d_bits, &b->bits_cap, (size_t)bits_total)) != ELSR_OK) return rc;
   if (with_traj && (rc = ensure(b, &b->d_traj, &b->traj_cap, (size_t)std::max<int64_t>(traj_entries, 1))) != ELSR_OK)
     return rc;
-  if (!ls.tab_smem && !b->tab_ready) {
+  if (!ls.ts && !b->tab_ready) {
     dev_free(b->d_tab);
     dev_free(b->d_C0);
     ELSR_TRY_CUDA(b, dev_alloc(&b->d_tab, (size_t)(b->cells + b->rows)));
@@ -329,7 +351,15 @@ int launch_runs(elsr_batch* b, const RowBits* start_bits, bool with_traj,
   p.out = b->d_out;
   p.traj = with_traj ? b->d_traj : nullptr;
   p.queue = b->d_queue;
-  ELSR_TRY_CUDA(b, launch_vns(p, b->acc64, ls.tab_smem, ls.blocks, ls.threads, ls.smem, b->stream));
+  ELSR_TRY_CUDA(b, b->acc64 ? vns_launch_i64(ls.nw, ls.ts, ls.maxt, p, ls.blocks, ls.threads, ls.smem, ls.cluster, b->stream)
+                            : vns_launch_i32(ls.nw, ls.ts, ls.maxt, p, ls.blocks, ls.threads, ls.smem, ls.cluster, b->stream));
+  b->last_shape[0] = ls.G;
+  b->last_shape[1] = ls.threads;
+  b->last_shape[2] = ls.cluster;
+  b->last_shape[3] = ls.blocks;
+  b->last_shape[4] = (int)ls.smem;
+  b->last_shape[5] = ls.ts;
+  b->last_shape[6] = ls.nw;
   b->nruns = (int32_t)nr;
   b->have_result = true;
   return ELSR_OK;
@@ -411,10 +441,10 @@ int eval_launch(elsr_ctx* h, uint32_t mask, int32_t mode, int single_j,
                 bool write_rowcost) {
   elsr_batch* b = &h->b;
   const int G = b->lanes ? b->lanes : default_lanes(h->T);
-  const int threads = 256;
+  const int threads = 128;
   const int nsub = threads / G;
   const size_t smem = eval_smem_bytes(nsub, h->T, b->acc64);
-  ELSR_TRY_CUDA(b, eval_prepare(b->acc64, smem));
+  ELSR_TRY_CUDA(b, eval_prepare(b->acc64, h->T, smem));
   EvalParams p;
   p.ip = b->pools();
   p.K = h->K;
@@ -514,6 +544,16 @@ int elsr_set_stream(elsr_t* h, void* stream) {
 int elsr_set_launch(elsr_t* h, int32_t lanes, int32_t threads) {
   if (!h) return ELSR_E_ARG;
   return elsr_batch_set_launch(&h->b, lanes, threads);
+}
+
+int elsr_set_cluster(elsr_t* h, int32_t cluster) {
+  if (!h) return ELSR_E_ARG;
+  return elsr_batch_set_cluster(&h->b, cluster);
+}
+
+int elsr_launch_shape(elsr_t* h, int32_t* shape) {
+  if (!h || !shape) return ELSR_E_ARG;
+  return elsr_batch_launch_shape(&h->b, shape);
 }
 
 int elsr_set_state(elsr_t* h, const uint8_t* gM, const uint8_t* gR) {
@@ -802,6 +842,22 @@ int elsr_batch_set_launch(elsr_batch_t* b, int32_t lanes, int32_t threads) {
   }
   b->lanes = lanes;
   b->threads = threads;
+  return ELSR_OK;
+}
+
+int elsr_batch_set_cluster(elsr_batch_t* b, int32_t cluster) {
+  if (!b) return ELSR_E_ARG;
+  if (cluster < 0 || cluster > 16) {
+    b->err = "cluster must be 0 (automatic) or 1..16 CTAs";
+    return ELSR_E_ARG;
+  }
+  b->cluster = cluster;
+  return ELSR_OK;
+}
+
+int elsr_batch_launch_shape(elsr_batch_t* b, int32_t* shape) {
+  if (!b || !shape) return ELSR_E_ARG;
+  for (int i = 0; i < 7; ++i) shape[i] = b->last_shape[i];
   return ELSR_OK;
 }
 

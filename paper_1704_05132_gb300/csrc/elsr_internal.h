@@ -118,52 +118,67 @@ struct PlanParams {
   int32_t* plan;        // [4][K][T]
 };
 
-// Shared-memory layout of one run in the persistent GVNS kernel.
+// Shared-memory layout of the rows one CTA owns in the persistent GVNS
+// kernel (Kc rows of T periods).
 struct VnsLayout {
-  uint32_t tab, rc, C0, bits, S, bad, A, C, save, slot, total;
+  uint32_t tab, rc, C0, bits, S, bad, nR, A, C, L, save, slot, total;
 };
 
 ELSR_HD uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
 
-ELSR_HD VnsLayout vns_layout(int K, int T, int acc_bytes, bool tab_smem) {
+ELSR_HD VnsLayout vns_layout(int Kc, int T, int acc_bytes, bool tab_smem) {
   VnsLayout L;
   uint32_t o = 0;
+  const uint32_t K = (uint32_t)Kc, TT = (uint32_t)T, ab = (uint32_t)acc_bytes;
   L.tab = o;
-  if (tab_smem) o = align16(o + (uint32_t)K * (T + 1) * 8u);
+  if (tab_smem) o = align16(o + K * (TT + 1) * 8u);
   L.rc = o;
-  o = align16(o + (uint32_t)K * 16u);
+  o = align16(o + K * 16u);
   L.C0 = o;
-  o = align16(o + (uint32_t)K * 8u);
+  o = align16(o + K * 8u);
   L.bits = o;
-  o = align16(o + (uint32_t)K * 32u);
+  o = align16(o + K * 32u);
   L.S = o;
-  o = align16(o + (uint32_t)K * acc_bytes);
+  o = align16(o + K * ab);
   L.bad = o;
-  o = align16(o + (uint32_t)K * 4u);
+  o = align16(o + K * 4u);
+  L.nR = o;
+  o = align16(o + K * 4u);
   L.A = o;
-  o = align16(o + (uint32_t)K * T * 4u);
+  o = align16(o + K * TT * 4u);
   L.C = o;
-  o = align16(o + (uint32_t)K * T * acc_bytes);
-  // save slot: RowBits(32) S(8) bad(4) pad(4) | A[T] | C[T]
-  L.slot = align16(48u + (((uint32_t)T * 4u + 7u) & ~7u) + (uint32_t)T * acc_bytes);
+  o = align16(o + K * TT * ab);
+  L.L = o;
+  o = align16(o + K * TT * 8u);
+  // save slot: RowBits(32) S(8) bad(4) nR(4) | A[T] | C[T] | L[T]
+  L.slot = align16(48u + ((TT * 4u + 7u) & ~7u) + ((TT * ab + 7u) & ~7u) + TT * 8u);
   L.save = o;
   o += 2u * kMaxShake * L.slot;
   L.total = o;
   return L;
 }
 
-// Launchers (elsr_kernels.cu).  Each returns the launch error.
-cudaError_t launch_stage(const StageParams& p, int ninst_rows_max,
-                         cudaStream_t s);
+// Launchers.  Each returns the launch error.
+cudaError_t launch_stage(const StageParams& p, int total_rows, cudaStream_t s);
 cudaError_t launch_eval(const EvalParams& p, bool acc64, int blocks,
                         int threads, size_t smem, cudaStream_t s);
-cudaError_t launch_vns(const VnsParams& p, bool acc64, bool tab_smem,
-                       int blocks, int threads, size_t smem, cudaStream_t s);
+cudaError_t eval_prepare(bool acc64, int T, size_t smem);
+size_t eval_smem_bytes(int rows, int T, bool acc64);
 cudaError_t launch_bestof(const BestofParams& p, cudaStream_t s);
 cudaError_t launch_plan(const PlanParams& p, int K, cudaStream_t s);
-cudaError_t vns_prepare(bool acc64, bool tab_smem, size_t smem, int threads,
-                        int* blocks_per_sm);
-cudaError_t eval_prepare(bool acc64, size_t smem);
-size_t eval_smem_bytes(int rows, int T, bool acc64);
+
+// Persistent GVNS kernel variants: accumulator width, 64-bit words per bit
+// row (nw = 1 when T <= 64), prefix tables in shared memory (ts), block size
+// bound (maxt = 256 or 1024).  cluster = CTAs per run (1 = no cluster).
+// prepare sets the kernel attributes and returns the resident blocks per SM
+// (cluster == 1) or the resident clusters on the device (cluster > 1).
+cudaError_t vns_prepare_i32(int nw, bool ts, int maxt, size_t smem, int threads,
+                            int cluster, int* active);
+cudaError_t vns_prepare_i64(int nw, bool ts, int maxt, size_t smem, int threads,
+                            int cluster, int* active);
+cudaError_t vns_launch_i32(int nw, bool ts, int maxt, const VnsParams& p, int blocks,
+                           int threads, size_t smem, int cluster, cudaStream_t s);
+cudaError_t vns_launch_i64(int nw, bool ts, int maxt, const VnsParams& p, int blocks,
+                           int threads, size_t smem, int cluster, cudaStream_t s);
 
 }  // namespace elsr

@@ -25,11 +25,9 @@
 // C0 = hR * sum_t R(t)(T-t) - hM * sum_t D(t)(T-t).
 //
 // Row cache (per setup s of the current row): A[s] = avail at s and
-// C[s] = S accumulated before s.  A move changes periods t1..t2 (t2 <= t1+1);
-// its re-decode starts at s0, the last period <= t1 that is a setup both
-// before and after the move, and stops at the first setup s > t2 whose
-// entering stock equals the cached A[s]: from there the row is unchanged,
-// so new S = S_prefix + (S_old - C[s]).
+// C[s] = S accumulated before s, plus the list of gR setups.  A move changes
+// periods t1..t2 (t2 <= t1+1); its re-decode starts at s0, the last period
+// <= t1 that is a setup both before and after the move (see eval_move).
 //
 // Functions are __host__ __device__ so that the same arithmetic can be
 // exercised by host-side unit tests of this header.
@@ -153,25 +151,70 @@ ELSR_HD bool seg_step(int s, int gm, int gr, int2 ts, int2 tn, int T,
   return true;
 }
 
-// Cache of the current row.  bad = T when the row is feasible; else the
-// first setup whose segment falls short (-1 when demand precedes the first
-// setup); A/C are valid at setups s <= bad.
+// Cache of the current row (per product):
+//   A[s], C[s]  at every setup s: stock entering s and S accumulated before s
+//   L[0..nR)    the row's gR setups in period order: {need(s), s | gM(s)<<16}
+// bad = T when the row is feasible; else the first setup whose segment falls
+// short (-1 when demand precedes the first setup); A/C/L are valid before bad.
 template <typename Acc>
 struct RowState {
   RowBits b;
   Acc S;    // segment sum of the current row (Inf when infeasible)
   int bad;
+  int nR;   // entries of L
 };
 
-// Decode a whole row from its bits, writing the cache A[s], C[s] at every
-// setup.  Returns S (Inf when infeasible) and sets bad.  segs counts the
-// segments walked.
-template <typename Acc>
+// Bit helpers specialised on the number of 64-bit words per bit row (NW = 1
+// when T <= 64).
+template <int NW>
+ELSR_HD int nxt(uint64_t u0, uint64_t u1, int s, int T) {
+  if (NW == 1) {
+    const int p = s + 1;
+    const uint64_t m = p >= 64 ? 0ull : (u0 & (~0ull << p));
+    return m ? lowbit(m) : T;
+  }
+  return next_set(u0, u1, s, T);
+}
+
+template <int NW>
+ELSR_HD int prv(uint64_t u0, uint64_t u1, int t) {
+  if (NW == 1) {
+    const uint64_t m = t >= 64 ? u0 : (u0 & ((1ull << t) - 1ull));
+    return m ? highbit(m) : -1;
+  }
+  return prev_set(u0, u1, t);
+}
+
+template <int NW>
+ELSR_HD int bitat(uint64_t w0, uint64_t w1, int t) {
+  if (NW == 1) return (int)((w0 >> t) & 1ull);
+  return bit_of(w0, w1, t);
+}
+
+ELSR_HD int popc64(uint64_t x) {
+#if defined(__CUDA_ARCH__)
+  return __popcll((long long)x);
+#else
+  return __builtin_popcountll(x);
+#endif
+}
+
+// Number of set bits strictly below position s.
+template <int NW>
+ELSR_HD int rank_below(uint64_t w0, uint64_t w1, int s) {
+  if (NW == 1 || s <= 64) return popc64(s >= 64 ? w0 : (w0 & ((1ull << s) - 1ull)));
+  return popc64(w0) + popc64(s >= 128 ? w1 : (w1 & ((1ull << (s - 64)) - 1ull)));
+}
+
+// Decode a whole row from its bits, writing the cache.  Returns S (Inf when
+// infeasible) and sets bad and nR.  segs counts the segments walked.
+template <typename Acc, int NW>
 ELSR_HD Acc build_row(const int2* tab, int T, const RowCosts& rc,
-                      const RowBits& b, int32_t* A, Acc* C, int& bad,
-                      int& segs) {
+                      const RowBits& b, int32_t* A, Acc* C, int2* L, int& bad,
+                      int& nR, int& segs) {
   const uint64_t u0 = b.m0 | b.r0, u1 = b.m1 | b.r1;
-  int s = next_set(u0, u1, -1, T);
+  nR = 0;
+  int s = nxt<NW>(u0, u1, -1, T);
   int2 ts = tab[s];
   if (ts.x != 0) {  // demand before the first setup
     bad = -1;
@@ -182,11 +225,17 @@ ELSR_HD Acc build_row(const int2* tab, int T, const RowCosts& rc,
   while (s < T) {
     A[s] = avail;
     C[s] = S;
-    const int n = next_set(u0, u1, s, T);
+    const int n = nxt<NW>(u0, u1, s, T);
     const int2 tn = tab[n];
+    const int gm = bitat<NW>(b.m0, b.m1, s), gr = bitat<NW>(b.r0, b.r1, s);
     ++segs;
-    if (!seg_step<Acc>(s, bit_of(b.m0, b.m1, s), bit_of(b.r0, b.r1, s), ts,
-                       tn, T, rc, avail, S)) {
+    if (gr) {
+      int2 e;
+      e.x = tn.x - ts.x;
+      e.y = s | (gm << 16);
+      L[nR++] = e;
+    }
+    if (!seg_step<Acc>(s, gm, gr, ts, tn, T, rc, avail, S)) {
       bad = s;
       return Inf<Acc>::value;
     }
@@ -197,105 +246,94 @@ ELSR_HD Acc build_row(const int2* tab, int T, const RowCosts& rc,
   return S;
 }
 
-// Result of a delta re-decode.
-template <typename Acc>
-struct DeltaOut {
-  Acc S;      // new segment sum (Inf when the moved row is infeasible)
-  int merge;  // setup where the walk merged into the cached row (T if none)
-  Acc delta;  // new C[s] - old C[s] for setups s >= merge
-};
-
 // Delta re-decode of the row after move `local` of N_j (Section 3's "find
-// the best neighbour" for one candidate).  cur: current row cache; A, C: its
-// arrays.  With WRITE, the new row's cache entries in the walked window are
-// written to A, C (the caller then adds `delta` to C at setups >= merge);
-// WRITE is only used when the current row is feasible.
-template <typename Acc, bool WRITE>
-ELSR_HD DeltaOut<Acc> eval_move(const int2* tab, int T, const RowCosts& rc,
-                                const RowState<Acc>& cur, int32_t* A, Acc* C,
-                                int j, int local, int& segs) {
-  DeltaOut<Acc> out;
-  out.merge = T;
-  out.delta = 0;
+// the best neighbour" for one candidate).  Returns the new segment sum (Inf
+// when the moved row is infeasible).  steps counts the decode steps: the
+// segments of the changed region, then either the remaining segments (when
+// the current row is infeasible) or the gR setups visited by the stock
+// difference walk.
+//
+// Changed region: from s0 (the last period <= t1 that is a setup before and
+// after the move) segment by segment while the segment start is <= t2.  At
+// the first setup s1 > t2 both rows have the same setups from there on and
+// differ only in the recoverable stock, by delta = avail_new - A[s1].  With
+// the telescoped cost the suffix then costs its cached value plus, at every
+// later gR setup, -hR*(T-s)*dx where dx is the change of xR = min(avail,
+// need); delta shrinks by dx, and the walk stops when it reaches 0.
+template <typename Acc, int NW>
+ELSR_HD Acc eval_move(const int2* tab, int T, const RowCosts& rc,
+                      const RowState<Acc>& cur, const int32_t* A,
+                      const Acc* C, const int2* L, int j, int local,
+                      int& steps) {
   RowBits nb = cur.b;
   int t1, other;
   if (j == 1) {
     t1 = local;
     flip(nb.m0, nb.m1, t1);
-    other = bit_of(nb.r0, nb.r1, t1);
+    other = bitat<NW>(nb.r0, nb.r1, t1);
   } else if (j == 2) {
     t1 = local;
     flip(nb.r0, nb.r1, t1);
-    other = bit_of(nb.m0, nb.m1, t1);
+    other = bitat<NW>(nb.m0, nb.m1, t1);
   } else {
     const int c = local >= (T - 1);
     t1 = local - c * (T - 1);
     uint64_t& w0 = c ? nb.r0 : nb.m0;
     uint64_t& w1 = c ? nb.r1 : nb.m1;
-    if (bit_of(w0, w1, t1) == bit_of(w0, w1, t1 + 1)) {  // null swap
-      out.S = cur.S;
-      return out;
-    }
+    if (bitat<NW>(w0, w1, t1) == bitat<NW>(w0, w1, t1 + 1)) return cur.S;  // null swap
     flip(w0, w1, t1);
     flip(w0, w1, t1 + 1);
-    other = c ? bit_of(nb.m0, nb.m1, t1) : bit_of(nb.r0, nb.r1, t1);
+    other = c ? bitat<NW>(nb.m0, nb.m1, t1) : bitat<NW>(nb.r0, nb.r1, t1);
   }
   const int t2 = (j == 3) ? t1 + 1 : t1;
   const uint64_t u0 = nb.m0 | nb.r0, u1 = nb.m1 | nb.r1;
-  // Below t1 the old and new rows agree; t1 keeps a setup iff the untouched
-  // type has one there.
-  const int s0 = other ? t1 : prev_set(u0, u1, t1);
+  const int s0 = other ? t1 : prv<NW>(u0, u1, t1);
   int s;
   int2 ts;
   int32_t avail;
   Acc S;
   if (s0 >= 0) {
-    if (s0 > cur.bad) {  // the unchanged prefix already falls short
-      out.S = Inf<Acc>::value;
-      return out;
-    }
+    if (s0 > cur.bad) return Inf<Acc>::value;  // unchanged prefix falls short
     s = s0;
     ts = tab[s];
     avail = A[s];
     S = C[s];
   } else {
-    s = next_set(u0, u1, -1, T);
+    s = nxt<NW>(u0, u1, -1, T);
     ts = tab[s];
-    if (ts.x != 0) {
-      out.S = Inf<Acc>::value;
-      return out;
-    }
+    if (ts.x != 0) return Inf<Acc>::value;
     avail = ts.y;
     S = 0;
   }
-  while (s < T) {
-    if (s > t2 && s <= cur.bad && avail == A[s]) {
-      if (cur.bad < T) {  // merged into a suffix that falls short
-        out.S = Inf<Acc>::value;
-        return out;
-      }
-      out.merge = s;
-      out.delta = S - C[s];
-      out.S = S + (cur.S - C[s]);
-      return out;
-    }
-    if (WRITE) {
-      A[s] = avail;
-      C[s] = S;
-    }
-    const int n = next_set(u0, u1, s, T);
+  // changed region (and the whole rest when the current row falls short)
+  while (s < T && (s <= t2 || cur.bad < T)) {
+    const int n = nxt<NW>(u0, u1, s, T);
     const int2 tn = tab[n];
-    ++segs;
-    if (!seg_step<Acc>(s, bit_of(nb.m0, nb.m1, s), bit_of(nb.r0, nb.r1, s),
-                       ts, tn, T, rc, avail, S)) {
-      out.S = Inf<Acc>::value;
-      return out;
-    }
+    ++steps;
+    if (!seg_step<Acc>(s, bitat<NW>(nb.m0, nb.m1, s), bitat<NW>(nb.r0, nb.r1, s),
+                       ts, tn, T, rc, avail, S))
+      return Inf<Acc>::value;
     s = n;
     ts = tn;
   }
-  out.S = S;
-  return out;
+  if (s >= T) return S;
+  // suffix: cached cost plus the stock-difference walk over gR setups
+  int32_t delta = avail - A[s];
+  S += cur.S - C[s];
+  if (delta == 0) return S;
+  for (int r = rank_below<NW>(cur.b.r0, cur.b.r1, s); r < cur.nR; ++r) {
+    const int2 e = L[r];
+    const int sr = e.y & 0xFFFF;
+    const int32_t a = A[sr];
+    const int32_t an = a + delta;
+    ++steps;
+    if (!(e.y >> 16) && an < e.x) return Inf<Acc>::value;
+    const int32_t dx = (an < e.x ? an : e.x) - (a < e.x ? a : e.x);
+    S -= (Acc)rc.hR * (Acc)(T - sr) * (Acc)dx;
+    delta -= dx;
+    if (delta == 0) break;
+  }
+  return S;
 }
 
 // Row cost = S + C0 as int64 (ELSR_INF when infeasible).

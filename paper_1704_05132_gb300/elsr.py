@@ -47,7 +47,8 @@ def _stream_handle(stream) -> int | None:
 class Solver:
     """One ELSR instance resident on the device (``elsr_create``)."""
 
-    def __init__(self, inst, stream=None, lanes: int = 0, threads: int = 0):
+    def __init__(self, inst, stream=None, lanes: int = 0, threads: int = 0,
+                 cluster: int = 0):
         lib = load()
         self.K, self.T = int(inst.D.shape[0]), int(inst.D.shape[1])
         arrs = [_i32(inst.D), _i32(inst.R), _i32(inst.kM), _i32(inst.kR),
@@ -59,6 +60,8 @@ class Solver:
         self.set_stream(stream)
         if lanes or threads:
             self.set_launch(lanes, threads)
+        if cluster:
+            self.set_cluster(cluster)
         self._last_iters = 0
 
     # -- plumbing --
@@ -71,6 +74,15 @@ class Solver:
 
     def set_launch(self, lanes: int = 0, threads: int = 0):
         self._chk(self._lib.elsr_set_launch(self._h, lanes, threads))
+
+    def set_cluster(self, cluster: int = 0):
+        self._chk(self._lib.elsr_set_cluster(self._h, cluster))
+
+    def launch_shape(self) -> dict:
+        v = np.zeros(7, np.int32)
+        self._chk(self._lib.elsr_launch_shape(self._h, _p(v)))
+        return dict(zip(("lanes", "threads", "cluster", "blocks", "smem", "tables_in_smem",
+                         "words"), v.tolist()))
 
     def close(self):
         if getattr(self, "_h", None):
@@ -180,7 +192,8 @@ class Solver:
 class Batch:
     """Many instances of uneven size solved by one persistent launch."""
 
-    def __init__(self, insts, stream=None, lanes: int = 0, threads: int = 0):
+    def __init__(self, insts, stream=None, lanes: int = 0, threads: int = 0,
+                 cluster: int = 0):
         lib = load()
         self._lib = lib
         self.n = len(insts)
@@ -196,9 +209,17 @@ class Batch:
         self.set_stream(stream)
         if lanes or threads:
             self.set_launch(lanes, threads)
+        if cluster:
+            self._chk(self._lib.elsr_batch_set_cluster(self._b, cluster))
 
     def _chk(self, code):
         return check(code, self._b, batch=True)
+
+    def launch_shape(self) -> dict:
+        v = np.zeros(7, np.int32)
+        self._chk(self._lib.elsr_batch_launch_shape(self._b, _p(v)))
+        return dict(zip(("lanes", "threads", "cluster", "blocks", "smem", "tables_in_smem",
+                         "words"), v.tolist()))
 
     def set_stream(self, stream=None):
         s = _stream_handle(stream)

@@ -289,16 +289,38 @@ def test_batch_with_global_tables(E):
     b.close()
 
 
-def test_launch_shapes_give_identical_results(E):
-    g = gen.make_instance(2, 2, K=23, T=40)
+SHAPES = [(4, 64, 1), (8, 256, 1), (16, 512, 1), (32, 1024, 1), (16, 1024, 1),
+          (32, 64, 2), (16, 128, 3), (32, 224, 8), (8, 64, 16), (32, 32, 16)]
+
+
+@pytest.mark.parametrize("T", [40, 90])
+def test_launch_shapes_give_identical_results(E, T):
+    """Lanes per row, block size and CTAs per cluster change only speed."""
+    g = gen.make_instance(2, 2, K=23, T=T)
     ref = None
-    for lanes, threads in [(4, 64), (8, 256), (16, 512), (32, 1024), (16, 1024)]:
-        with E.Solver(g, lanes=lanes, threads=threads) as s:
+    for lanes, threads, cluster in SHAPES:
+        with E.Solver(g, lanes=lanes, threads=threads, cluster=cluster) as s:
             r = s.vns(seed=11, iters=50, kmax=3, mode=0)
-        key = (r["best_cost"], r["traj_hash"], r["moves_evaluated"], r["segments"])
+            shape = s.launch_shape()
+        assert shape["cluster"] == cluster and shape["threads"] == threads
+        key = (r["best_cost"], r["traj_hash"], r["moves_evaluated"], r["segments"],
+               r["applied"])
         if ref is None:
             ref = key
-        assert key == ref, (lanes, threads)
+        assert key == ref, (lanes, threads, cluster)
+        np.testing.assert_array_equal(r["traj"]["cost"][:5], r["traj"]["cost"][:5])
+
+
+def test_cluster_run_matches_oracle(E):
+    """The medium plain workload on an 8-CTA cluster, 300 iterations."""
+    g = gen.plain_medium()
+    inst = _inst(g)
+    o = oracle.vns(inst, seed=1, iters=300, kmax=3, mode=0)
+    with E.Solver(g, cluster=8) as s:
+        r = s.vns(seed=1, iters=300, kmax=3, mode=0)
+        assert s.launch_shape()["cluster"] == 8
+    np.testing.assert_array_equal(r["traj"]["cost"], o.traj["cost"])
+    _check_run(r, o)
 
 
 def test_invalid_state_rejected(E):

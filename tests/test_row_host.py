@@ -1,9 +1,9 @@
 """Host build of the CUDA path's row arithmetic vs the CPU oracle (no GPU).
 
 ``host_row_check.cpp`` compiles the kernels' ``elsr_row.cuh`` for the host.
-These tests compare its delta re-decode (prefix tables, cached setups,
-early merge) element by element with the oracle's full per-period decode,
-and its cache patching with a fresh decode.  The GPU tests then check the
+These tests compare its delta re-decode (prefix tables, cached setups, the
+recoverable-stock difference walk) element by element with the oracle's full
+per-period decode, and its decode-step counts with the oracle's definition.  The GPU tests then check the
 kernels that wrap the same header.
 """
 import ctypes
@@ -30,11 +30,8 @@ def hc(tmp_path_factory):
     lib = ctypes.CDLL(out)
     P = ctypes.c_void_p
     lib.hc_move_costs.restype = ctypes.c_int64
-    lib.hc_move_costs.argtypes = [ctypes.c_int32, ctypes.c_int32, P, P, P, P, P,
-                                  ctypes.c_int32, P, P]
-    lib.hc_apply_check.restype = ctypes.c_int32
-    lib.hc_apply_check.argtypes = [ctypes.c_int32, ctypes.c_int32, P, P, P, P, P,
-                                   ctypes.c_int32, ctypes.c_int32]
+    lib.hc_move_costs.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                  P, P, P, P, P, ctypes.c_int32, P, P]
     lib.hc_shake_draw.restype = ctypes.c_uint64
     lib.hc_shake_draw.argtypes = [ctypes.c_uint64] * 4
     return lib
@@ -64,8 +61,10 @@ def _random_states(rng, T, n):
 
 
 @pytest.mark.parametrize("T", [1, 2, 3, 12, 52, 63, 64, 65, 104, 128])
-@pytest.mark.parametrize("acc64", [0, 1])
-def test_delta_decode_matches_oracle(hc, T, acc64):
+@pytest.mark.parametrize("acc64,nw", [(0, 1), (1, 1), (0, 2), (1, 2)])
+def test_delta_decode_matches_oracle(hc, T, acc64, nw):
+    if nw == 1 and T > 64:
+        pytest.skip("one 64-bit word holds at most 64 periods")
     rng = np.random.default_rng(T * 7 + acc64)
     g = gen.make_instance(50 + T, 1, K=1, T=T)
     if T % 3 == 0:
@@ -80,30 +79,13 @@ def test_delta_decode_matches_oracle(hc, T, acc64):
                 continue
             out = np.zeros(M, np.int64)
             segs = np.zeros(M, np.int32)
-            cur = hc.hc_move_costs(acc64, T, _p(D), _p(R), _p(costs), _p(gm), _p(gr),
+            cur = hc.hc_move_costs(acc64, nw, T, _p(D), _p(R), _p(costs), _p(gm), _p(gr),
                                    j, _p(out), _p(segs))
             assert cur == oracle.decode_row(inst, 0, gm, gr)[0]
             ref = oracle.move_costs(inst, gm[None, :], gr[None, :], j)
             np.testing.assert_array_equal(out, ref)
             win = [oracle.move_window(inst, 0, gm, gr, j, m) for m in range(M)]
             np.testing.assert_array_equal(segs, win)
-
-
-@pytest.mark.parametrize("T", [5, 40, 64, 100])
-def test_cache_patch_equals_fresh_decode(hc, T):
-    rng = np.random.default_rng(T)
-    g = gen.make_instance(70 + T, 2, K=1, T=T)
-    inst = oracle.Instance.from_arrays(g)
-    costs = np.array([inst.kM[0], inst.kR[0], inst.hM[0], inst.hR[0]], np.int32)
-    D, R = inst.D[0].copy(), inst.R[0].copy()
-    checked = 0
-    for gm, gr in _random_states(rng, T, 30):
-        for j in (1, 2, 3):
-            for m in range(oracle.row_moves(T, j)):
-                r = hc.hc_apply_check(0, T, _p(D), _p(R), _p(costs), _p(gm), _p(gr), j, m)
-                assert r != 1, (j, m)
-                checked += r == 0
-    assert checked > 100
 
 
 def test_host_shake_draw_matches_oracle(hc):
