@@ -178,7 +178,8 @@ def run_gpu(args):
     K, T = g.K, g.T
     seed = WORKLOAD["vns_seed"] + rank  # replicas: one seed per rank
     stream = torch.cuda.current_stream(dev)
-    solver = elsr.Solver(g, stream=stream)
+    solver = elsr.Solver(g, stream=stream, lanes=args.lanes, threads=args.threads,
+                         cluster=args.cluster)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
 
     iters = args.iters if args.iters is not None else WORKLOAD["iters"]
@@ -280,7 +281,7 @@ def run_gpu(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": dict(WORKLOAD, iters=iters, parallelism=f"replicas x{world}",
                        l2="flushed between steps (256 MiB device write, untimed)",
-                       launch="1 persistent CTA per GVNS run"),
+                       launch="one persistent thread-block cluster per GVNS run"),
         "instances_per_s": world * args.steps / t_max,
         "moves_per_step": moves_per_step,
         "eval_launch": eval_launch,
@@ -288,6 +289,7 @@ def run_gpu(args):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": args.steps,
+        "launch_shape": solver.launch_shape(),
         "roofline": {"bound": "alu", "achieved": achieved_ops / 1e12, "peak": peak_ops / 1e12,
                      "unit": "Tintop/s", "frac": achieved_ops / peak_ops, "traffic": None,
                      "note": f"{INT_OPS_PER_SEGMENT} int ops per decode segment x "
@@ -311,6 +313,9 @@ def main():
     ap.add_argument("--ref-iters", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--lanes", type=int, default=0, help="lanes per row (0: automatic)")
+    ap.add_argument("--threads", type=int, default=0, help="threads per CTA (0: automatic)")
+    ap.add_argument("--cluster", type=int, default=0, help="CTAs per run (0: automatic)")
     ap.add_argument("--iters", type=int, default=None,
                     help="override the iteration budget (profiling of small cases only)")
     args = ap.parse_args()

@@ -273,18 +273,25 @@ int vns_shape(elsr_batch* b, LaunchShape* ls) {
   if (any_g) C = 1;  // the global argmin of mode G runs inside one CTA
   C = std::min(C, maxK);
   size_t need_s = 0, need_g = 0;
-  for (const RunDesc& r : b->h_runs) {
-    const InstDesc& d = b->insts[r.inst];
-    const int kc = (d.K + C - 1) / C;
-    need_s = std::max<size_t>(need_s, vns_layout(kc, d.T, acc, true).total);
-    need_g = std::max<size_t>(need_g, vns_layout(kc, d.T, acc, false).total);
+  // Grow the cluster until the largest run's rows fit the CTAs' shared
+  // memory (mode P only; mode G needs its rows in one CTA).
+  for (;;) {
+    need_s = need_g = 0;
+    for (const RunDesc& r : b->h_runs) {
+      const InstDesc& d = b->insts[r.inst];
+      const int kc = (d.K + C - 1) / C;
+      need_s = std::max<size_t>(need_s, vns_layout(kc, d.T, acc, true).total);
+      need_g = std::max<size_t>(need_g, vns_layout(kc, d.T, acc, false).total);
+    }
+    if (need_g <= (size_t)kSmemLimit || any_g || C >= 16 || C >= maxK) break;
+    ++C;
   }
   ls->nw = maxT <= 64 ? 1 : 2;
   ls->ts = need_s <= (size_t)kSmemLimit;
   ls->smem = ls->ts ? need_s : need_g;
   if (ls->smem > (size_t)kSmemLimit) {
     b->err = "instance too large for the shared memory of its CTAs (" +
-             std::to_string(ls->smem) + " bytes per CTA); use a larger cluster";
+             std::to_string(ls->smem) + " bytes per CTA)";
     return ELSR_E_RANGE;
   }
   ls->G = b->lanes ? b->lanes : default_lanes(maxT);
