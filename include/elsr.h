@@ -208,6 +208,43 @@ int elsr_multistart_run(elsr_t *h, uint64_t seed0, int32_t nstarts,
                         int64_t *best_cost, int32_t *best_start,
                         int64_t *costs);
 
+/*
+ * Allocation-free neighbourhood evaluation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory,
+ * such as a framework whose own pool owns all device memory, a serving loop
+ * that must never call cudaMalloc or cudaFree (both can synchronise the
+ * whole device), or code that records work while allocation is unavailable.
+ *
+ * It computes exactly what elsr_eval_neighbourhood computes (same modes,
+ * masks and outputs), but every pointer is a caller-owned DEVICE pointer:
+ * D, R int32 [K][T]; kM, kR, hM, hR int32 [K]; gM, gR uint8 0/1 [K][T];
+ * best int64 [2] receives (best_cost, best_move); pp_cost, pp_move int64
+ * [K] (nullable) receive the per-product results.  The instance must obey
+ * the value ranges of elsr_create; they are not checked here (values are on
+ * the device), and values outside them give unspecified results.
+ *
+ * Nothing is allocated: intermediate data lives in a fixed device array of
+ * ELSR_STATIC_BYTES, which every GPU that loads the library holds until the
+ * process exits.  Sizes beyond K <= ELSR_STATIC_K_MAX or T <= ELSR_T_MAX are
+ * rejected with ELSR_E_RANGE.  The work is queued on `stream` (a
+ * cudaStream_t, NULL = legacy default stream) and the call returns without
+ * waiting; outputs are valid once the stream reaches that point.  The first
+ * call on each device looks up the array's device address; make that first
+ * call before any stream capture.  All calls share the array and it keeps
+ * the last call's contents, so calls that may overlap on the device (other
+ * streams, other host threads) race on it and must be serialised.
+ */
+#define ELSR_STATIC_K_MAX 4096
+#define ELSR_STATIC_BYTES (512 + 48 * ELSR_STATIC_K_MAX)
+int elsr_eval_neighbourhood_static(int32_t K, int32_t T, const int32_t *D,
+                                   const int32_t *R, const int32_t *kM,
+                                   const int32_t *kR, const int32_t *hM,
+                                   const int32_t *hR, const uint8_t *gM,
+                                   const uint8_t *gR, uint32_t nb_mask,
+                                   int32_t mode, int64_t *best,
+                                   int64_t *pp_cost, int64_t *pp_move,
+                                   void *stream);
+
 /* Device moves evaluated since create (all calls on this handle). */
 int elsr_counters(elsr_t *h, int64_t *moves_evaluated);
 

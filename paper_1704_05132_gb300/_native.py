@@ -65,6 +65,8 @@ SIGNATURES = {
     "elsr_result": (ctypes.c_int, [P, P, P, P, P, P, i32]),
     "elsr_multistart_run": (ctypes.c_int, [P, u64, i32, i32, i32, i32, P, P, P]),
     "elsr_counters": (ctypes.c_int, [P, P]),
+    "elsr_eval_neighbourhood_static": (ctypes.c_int, [i32, i32, P, P, P, P, P, P, P, P,
+                                                      u32, i32, P, P, P, P]),
     "elsr_batch_create": (ctypes.c_int, [ctypes.POINTER(P), i32, P, P, P, P, P, P, P, P]),
     "elsr_batch_destroy": (None, [P]),
     "elsr_batch_last_error": (ctypes.c_char_p, [P]),

@@ -15,7 +15,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libelsr.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["elsr_vns_i32.cu", "elsr_vns_i64.cu", "elsr_kernels.cu", "elsr_abi.cu"]
+SOURCES = ["elsr_vns_i32.cu", "elsr_vns_i64.cu", "elsr_kernels.cu", "elsr_abi.cu",
+           "elsr_static.cu"]
 HEADERS = ["elsr_row.cuh", "elsr_internal.h", "elsr_vns.cuh"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
