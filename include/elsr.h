@@ -56,6 +56,7 @@ extern "C" {
 #define ELSR_E_CUDA (-4)  /* a CUDA runtime call or kernel failed */
 #define ELSR_E_CAP (-5)   /* a VND exceeded its sweep cap (2^20 sweeps) */
 #define ELSR_E_STATE (-6) /* call out of order (e.g. no result yet) */
+#define ELSR_E_TIMEOUT (-7) /* a device-side wait exceeded its limit */
 
 #define ELSR_T_MAX 128 /* periods per product */
 #define ELSR_MODE_P 0  /* Algorithm 1: each product takes its best move */
@@ -76,7 +77,7 @@ typedef struct {
     int64_t iterations;      /* GVNS shaking iterations run */
     int64_t accepted;        /* iterations whose VND result replaced x */
     int64_t segments;        /* decode-window setup segments walked (work) */
-    int32_t status;          /* ELSR_OK or ELSR_E_CAP */
+    int32_t status;          /* ELSR_OK, ELSR_E_CAP or ELSR_E_TIMEOUT */
     int32_t reserved;
 } elsr_stats_t;
 
@@ -125,7 +126,7 @@ void elsr_destroy(elsr_t *h);
 int elsr_set_stream(elsr_t *h, void *stream);
 
 /* Kernel launch shape: sub-warp lanes per product row (4, 8, 16 or 32) and
- * threads per block (multiple of 32, <= 1024); 0 keeps the default. */
+ * threads per block (multiple of 32, <= 512); 0 keeps the default. */
 int elsr_set_launch(elsr_t *h, int32_t lanes_per_row, int32_t threads);
 
 /* CTAs of one thread-block cluster that share a GVNS run of this handle
@@ -133,9 +134,15 @@ int elsr_set_launch(elsr_t *h, int32_t lanes_per_row, int32_t threads);
  * depend on it. */
 int elsr_set_cluster(elsr_t *h, int32_t cluster);
 
-/* Launch shape of the last GVNS launch: shape[7] = {lanes per row, threads
+/* Speculative execution of one mode-P GVNS run: up to `teams` clusters run
+ * consecutive iterations from the same incumbent and commit them in order up
+ * to the first acceptance, so trajectory, solution and counters equal the
+ * sequential run's.  0 = automatic (up to 16 teams), 1 = off. */
+int elsr_set_speculation(elsr_t *h, int32_t teams);
+
+/* Launch shape of the last GVNS launch: shape[8] = {lanes per row, threads
  * per block, CTAs per run, blocks, shared bytes per block, prefix tables in
- * shared memory (0/1), 64-bit words per bit row}. */
+ * shared memory (0/1), 64-bit words per bit row, speculative teams}. */
 int elsr_launch_shape(elsr_t *h, int32_t *shape);
 
 /* Set the current solution from host 0/1 arrays gM, gR [K][T]; both NULL
@@ -269,8 +276,8 @@ int elsr_batch_set_stream(elsr_batch_t *b, void *stream);
 int elsr_batch_set_launch(elsr_batch_t *b, int32_t lanes_per_row,
                           int32_t threads);
 
-/* As elsr_set_cluster / elsr_launch_shape, for a batch (default: 1 CTA per
- * run). */
+/* As elsr_set_cluster / elsr_launch_shape (shape[8]), for a batch (default:
+ * 1 CTA per run). */
 int elsr_batch_set_cluster(elsr_batch_t *b, int32_t cluster);
 int elsr_batch_launch_shape(elsr_batch_t *b, int32_t *shape);
 

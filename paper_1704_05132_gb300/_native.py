@@ -20,6 +20,7 @@ ELSR_E_NOMEM = -3
 ELSR_E_CUDA = -4
 ELSR_E_CAP = -5
 ELSR_E_STATE = -6
+ELSR_E_TIMEOUT = -7
 MODE_P = 0
 MODE_G = 1
 T_MAX = 128
@@ -55,6 +56,7 @@ SIGNATURES = {
     "elsr_set_stream": (ctypes.c_int, [P, P]),
     "elsr_set_launch": (ctypes.c_int, [P, i32, i32]),
     "elsr_set_cluster": (ctypes.c_int, [P, i32]),
+    "elsr_set_speculation": (ctypes.c_int, [P, i32]),
     "elsr_launch_shape": (ctypes.c_int, [P, P]),
     "elsr_set_state": (ctypes.c_int, [P, P, P]),
     "elsr_get_state": (ctypes.c_int, [P, P, P]),

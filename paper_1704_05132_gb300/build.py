@@ -15,8 +15,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libelsr.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["elsr_vns_i32.cu", "elsr_vns_i64.cu", "elsr_kernels.cu", "elsr_abi.cu",
-           "elsr_static.cu"]
+SOURCES = ["elsr_vns_i32_w1.cu", "elsr_vns_i32_w2.cu", "elsr_vns_i64_w1.cu",
+           "elsr_vns_i64_w2.cu", "elsr_kernels.cu", "elsr_abi.cu", "elsr_static.cu"]
 HEADERS = ["elsr_row.cuh", "elsr_internal.h", "elsr_vns.cuh"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -61,7 +61,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         return r.stdout + r.stderr
 
     logs = []
-    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+    workers = max(1, min(len(SOURCES), os.cpu_count() or 1))
+    with cf.ThreadPoolExecutor(max_workers=workers) as ex:
         logs = list(ex.map(run, jobs))
     if verbose or ptxas_info:
         for l in logs:

@@ -115,6 +115,7 @@ struct elsr_batch {
   int maxK = 0, maxT = 0;
   bool acc64 = false;
   int lanes = 0, threads = 0, cluster = 0;  // 0 = defaults
+  int spec = 0;                              // speculative teams (0 auto, 1 off)
   int last_shape[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   int sms = 0;
 
@@ -135,6 +136,10 @@ struct elsr_batch {
   size_t traj_cap = 0;
   int32_t* d_queue = nullptr;
   uint64_t* d_bestkey = nullptr;
+  SpecSlot* d_spec_slots = nullptr;
+  RowBits* d_spec_rows = nullptr;
+  int32_t* d_spec_bar = nullptr;
+  size_t spec_cap = 0;
 
   std::vector<RunDesc> h_runs;
   std::vector<int32_t> out_of_inst;  // per instance: its output index
@@ -172,6 +177,9 @@ struct elsr_batch {
     dev_free(d_traj);
     dev_free(d_queue);
     dev_free(d_bestkey);
+    dev_free(d_spec_slots);
+    dev_free(d_spec_rows);
+    dev_free(d_spec_bar);
   }
 };
 
@@ -254,6 +262,7 @@ struct LaunchShape {
   bool ts;
   size_t smem;
   int threads, G, cluster, blocks;
+  int active;  // resident blocks per SM (cluster 1) or clusters on the device
 };
 
 // Launch shape of the persistent kernel for the runs in b->h_runs: 64-bit
@@ -299,15 +308,15 @@ int vns_shape(elsr_batch* b, LaunchShape* ls) {
   int thr = b->threads;
   if (!thr) thr = std::min(256, std::max(64, ((kc * ls->G + 31) / 32) * 32));
   ls->threads = thr;
-  ls->maxt = thr <= 256 ? 256 : 1024;
+  ls->maxt = thr <= 256 ? 256 : 512;
   ls->cluster = C;
   int active = 0;
-  ELSR_TRY_CUDA(b, b->acc64 ? vns_prepare_i64(ls->nw, ls->ts, ls->maxt, ls->smem, thr, C, &active)
-                            : vns_prepare_i32(ls->nw, ls->ts, ls->maxt, ls->smem, thr, C, &active));
+  ELSR_TRY_CUDA(b, vns_prepare(b->acc64, ls->nw, ls->ts, ls->maxt, ls->smem, thr, C, &active));
   if (active < 1) {
     b->err = "persistent kernel does not fit with this launch shape";
     return ELSR_E_RANGE;
   }
+  ls->active = active;
   const int64_t nr = (int64_t)b->h_runs.size();
   if (C == 1)
     ls->blocks = (int)std::min<int64_t>((int64_t)active * b->sms, nr);
@@ -358,8 +367,53 @@ int launch_runs(elsr_batch* b, const RowBits* start_bits, bool with_traj,
   p.out = b->d_out;
   p.traj = with_traj ? b->d_traj : nullptr;
   p.queue = b->d_queue;
-  ELSR_TRY_CUDA(b, b->acc64 ? vns_launch_i64(ls.nw, ls.ts, ls.maxt, p, ls.blocks, ls.threads, ls.smem, ls.cluster, b->stream)
-                            : vns_launch_i32(ls.nw, ls.ts, ls.maxt, p, ls.blocks, ls.threads, ls.smem, ls.cluster, b->stream));
+  p.spec_teams = 0;
+  p.pad2 = 0;
+  p.spec_slots = nullptr;
+  p.spec_rows = nullptr;
+  p.spec_bar = nullptr;
+  // A single mode-P run may be spread over several teams that speculate on
+  // consecutive iterations (exact: the committed trajectory is the
+  // sequential one).
+  int teams = 1;
+  if (nr == 1 && b->h_runs[0].mode == ELSR_MODE_P && b->h_runs[0].iters > 1 && b->spec != 1) {
+    const int resident = ls.cluster == 1 ? ls.active * b->sms : ls.active;
+    const int want = b->spec > 1 ? b->spec : 16;
+    teams = std::max(1, std::min({want, resident, b->h_runs[0].iters}));
+  }
+  cudaError_t le = cudaErrorUnknown;
+  if (teams > 1) {
+    if (teams > (int)b->spec_cap) {
+      dev_free(b->d_spec_slots);
+      dev_free(b->d_spec_rows);
+      dev_free(b->d_spec_bar);
+      b->spec_cap = 0;
+      ELSR_TRY_CUDA(b, dev_alloc(&b->d_spec_slots, (size_t)2 * teams));
+      ELSR_TRY_CUDA(b, dev_alloc(&b->d_spec_rows, (size_t)2 * teams * kMaxShake));
+      ELSR_TRY_CUDA(b, dev_alloc(&b->d_spec_bar, 2));
+      b->spec_cap = teams;
+    }
+    ELSR_TRY_CUDA(b, cudaMemsetAsync(b->d_spec_bar, 0, 2 * sizeof(int32_t), b->stream));
+    p.spec_teams = teams;
+    p.spec_slots = b->d_spec_slots;
+    p.spec_rows = b->d_spec_rows;
+    p.spec_bar = b->d_spec_bar;
+    const int blocks = teams * ls.cluster;
+    le = vns_launch(b->acc64, ls.nw, ls.ts, ls.maxt, p, blocks, ls.threads, ls.smem, ls.cluster,
+                    b->stream);
+    if (le != cudaSuccess) {
+      cudaGetLastError();  // the cooperative launch was refused: run one team
+      teams = 1;
+    } else {
+      ls.blocks = blocks;
+    }
+  }
+  if (teams <= 1) {
+    p.spec_teams = 0;
+    ELSR_TRY_CUDA(b, vns_launch(b->acc64, ls.nw, ls.ts, ls.maxt, p, ls.blocks, ls.threads,
+                                ls.smem, ls.cluster, b->stream));
+  }
+  b->last_shape[7] = teams;
   b->last_shape[0] = ls.G;
   b->last_shape[1] = ls.threads;
   b->last_shape[2] = ls.cluster;
@@ -491,6 +545,7 @@ const char* elsr_strerror(int code) {
     case ELSR_E_CUDA: return "CUDA error";
     case ELSR_E_CAP: return "VND sweep cap reached";
     case ELSR_E_STATE: return "call out of order";
+    case ELSR_E_TIMEOUT: return "a device-side wait exceeded its limit";
     default: return "unknown error";
   }
 }
@@ -551,6 +606,16 @@ int elsr_set_stream(elsr_t* h, void* stream) {
 int elsr_set_launch(elsr_t* h, int32_t lanes, int32_t threads) {
   if (!h) return ELSR_E_ARG;
   return elsr_batch_set_launch(&h->b, lanes, threads);
+}
+
+int elsr_set_speculation(elsr_t* h, int32_t teams) {
+  if (!h) return ELSR_E_ARG;
+  if (teams < 0 || teams > 1024) {
+    h->b.err = "teams must be 0 (automatic), 1 (off) or 2..1024";
+    return ELSR_E_ARG;
+  }
+  h->b.spec = teams;
+  return ELSR_OK;
 }
 
 int elsr_set_cluster(elsr_t* h, int32_t cluster) {
@@ -843,8 +908,8 @@ int elsr_batch_set_launch(elsr_batch_t* b, int32_t lanes, int32_t threads) {
     b->err = "lanes_per_row must be 4, 8, 16 or 32";
     return ELSR_E_ARG;
   }
-  if (threads && (threads % 32 || threads < 32 || threads > 1024)) {
-    b->err = "threads must be a multiple of 32 in [32, 1024]";
+  if (threads && (threads % 32 || threads < 32 || threads > 512)) {
+    b->err = "threads must be a multiple of 32 in [32, 512]";
     return ELSR_E_ARG;
   }
   b->lanes = lanes;
@@ -864,7 +929,7 @@ int elsr_batch_set_cluster(elsr_batch_t* b, int32_t cluster) {
 
 int elsr_batch_launch_shape(elsr_batch_t* b, int32_t* shape) {
   if (!b || !shape) return ELSR_E_ARG;
-  for (int i = 0; i < 7; ++i) shape[i] = b->last_shape[i];
+  for (int i = 0; i < 8; ++i) shape[i] = b->last_shape[i];
   return ELSR_OK;
 }
 

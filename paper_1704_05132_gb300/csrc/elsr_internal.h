@@ -13,6 +13,7 @@ constexpr int kTMax = 128;
 constexpr int kMaxShake = 3;        // kmax <= 3: at most 3 shaken rows
 constexpr int kSmemLimit = 227 * 1024;
 constexpr int kStatusCap = -5;      // ELSR_E_CAP
+constexpr int kStatusTimeout = -7;  // ELSR_E_TIMEOUT
 
 // One instance of a batch: rows [row_off, row_off + K) of the per-row pools
 // and cells [cell_off, cell_off + K*T) of the D/R pools.
@@ -67,6 +68,15 @@ struct InstPools {
   const int64_t* gC0;  // per-row constants matching gtab
 };
 
+// One speculative team's result for one round (spec_kernel).
+struct SpecSlot {
+  long long f2;
+  int cycles;
+  int pad;
+  unsigned long long applied;
+  unsigned long long steps;
+};
+
 struct VnsParams {
   InstPools ip;
   const RunDesc* runs;
@@ -79,6 +89,12 @@ struct VnsParams {
   RunOut* out;
   TrajEntry* traj;
   int32_t* queue;  // work counter, zero at launch
+  // speculative single-run launches (spec_teams > 1)
+  int32_t spec_teams;
+  int32_t pad2;
+  SpecSlot* spec_slots;  // [2][spec_teams]
+  RowBits* spec_rows;    // [2][spec_teams][3]
+  int32_t* spec_bar;     // [2]: arrivals, generation; zero at launch
 };
 
 struct StageParams {
@@ -169,16 +185,38 @@ cudaError_t launch_plan(const PlanParams& p, int K, cudaStream_t s);
 
 // Persistent GVNS kernel variants: accumulator width, 64-bit words per bit
 // row (nw = 1 when T <= 64), prefix tables in shared memory (ts), block size
-// bound (maxt = 256 or 1024).  cluster = CTAs per run (1 = no cluster).
+// bound (maxt = 256 or 512).  cluster = CTAs per run (1 = no cluster).
 // prepare sets the kernel attributes and returns the resident blocks per SM
 // (cluster == 1) or the resident clusters on the device (cluster > 1).
-cudaError_t vns_prepare_i32(int nw, bool ts, int maxt, size_t smem, int threads,
-                            int cluster, int* active);
-cudaError_t vns_prepare_i64(int nw, bool ts, int maxt, size_t smem, int threads,
-                            int cluster, int* active);
-cudaError_t vns_launch_i32(int nw, bool ts, int maxt, const VnsParams& p, int blocks,
-                           int threads, size_t smem, int cluster, cudaStream_t s);
-cudaError_t vns_launch_i64(int nw, bool ts, int maxt, const VnsParams& p, int blocks,
-                           int threads, size_t smem, int cluster, cudaStream_t s);
+cudaError_t vns_prepare_i32_w1(bool ts, int maxt, size_t smem, int threads, int cluster, int* active);
+cudaError_t vns_prepare_i32_w2(bool ts, int maxt, size_t smem, int threads, int cluster, int* active);
+cudaError_t vns_prepare_i64_w1(bool ts, int maxt, size_t smem, int threads, int cluster, int* active);
+cudaError_t vns_prepare_i64_w2(bool ts, int maxt, size_t smem, int threads, int cluster, int* active);
+cudaError_t vns_launch_i32_w1(bool ts, int maxt, const VnsParams& p, int blocks, int threads,
+                              size_t smem, int cluster, cudaStream_t s);
+cudaError_t vns_launch_i32_w2(bool ts, int maxt, const VnsParams& p, int blocks, int threads,
+                              size_t smem, int cluster, cudaStream_t s);
+cudaError_t vns_launch_i64_w1(bool ts, int maxt, const VnsParams& p, int blocks, int threads,
+                              size_t smem, int cluster, cudaStream_t s);
+cudaError_t vns_launch_i64_w2(bool ts, int maxt, const VnsParams& p, int blocks, int threads,
+                              size_t smem, int cluster, cudaStream_t s);
+
+inline cudaError_t vns_prepare(bool acc64, int nw, bool ts, int maxt, size_t smem, int threads,
+                               int cluster, int* active) {
+  if (acc64)
+    return nw == 1 ? vns_prepare_i64_w1(ts, maxt, smem, threads, cluster, active)
+                   : vns_prepare_i64_w2(ts, maxt, smem, threads, cluster, active);
+  return nw == 1 ? vns_prepare_i32_w1(ts, maxt, smem, threads, cluster, active)
+                 : vns_prepare_i32_w2(ts, maxt, smem, threads, cluster, active);
+}
+
+inline cudaError_t vns_launch(bool acc64, int nw, bool ts, int maxt, const VnsParams& p,
+                              int blocks, int threads, size_t smem, int cluster, cudaStream_t s) {
+  if (acc64)
+    return nw == 1 ? vns_launch_i64_w1(ts, maxt, p, blocks, threads, smem, cluster, s)
+                   : vns_launch_i64_w2(ts, maxt, p, blocks, threads, smem, cluster, s);
+  return nw == 1 ? vns_launch_i32_w1(ts, maxt, p, blocks, threads, smem, cluster, s)
+                 : vns_launch_i32_w2(ts, maxt, p, blocks, threads, smem, cluster, s);
+}
 
 }  // namespace elsr

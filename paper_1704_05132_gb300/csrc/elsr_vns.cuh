@@ -133,17 +133,6 @@ __device__ __forceinline__ uint32_t slot_L_off(int T) {
   return slot_C_off<Acc>(T) + ((((uint32_t)T * (uint32_t)sizeof(Acc)) + 7u) & ~7u);
 }
 
-// Full rebuild of local row q's cache (one lane).
-template <typename Acc, int NW>
-__device__ __forceinline__ void rebuild(const Rows<Acc>& m, int q) {
-  const int T = m.T;
-  int b = T, nr = 0, dummy = 0;
-  m.S[q] = build_row<Acc, NW>(m.tab_row(q), T, m.rc[q], m.bits[q], m.A + q * T,
-                              m.C + q * T, m.L + q * T, b, nr, dummy);
-  m.bad[q] = b;
-  m.nR[q] = nr;
-}
-
 // Copy local row q to / from a save slot (sub-warp collective).
 template <typename Acc>
 __device__ __forceinline__ void save_row(const Rows<Acc>& m, int q, unsigned char* sl,
@@ -210,7 +199,150 @@ __device__ __forceinline__ uint64_t row_best(const Rows<Acc>& m, int q,
   return best;
 }
 
-// Team-wide barrier: the CTA, or the whole cluster.
+// ---------------------------------------------------------------------------
+// Lane-parallel rebuild of one row's cache (sub-warp collective).
+//
+// The recoverable stock follows y(t) = F_t(y(t-1)), y(-1) = 0, with
+//   F_t(y) = max(y + R(t) - need(t), 0)   at a gR setup (xR = min(avail, need))
+//   F_t(y) = y + R(t)                     elsewhere,
+// all of the form F(y) = max(y + p, q).  Such functions compose associatively,
+//   (F2 o F1)(y) = max(y + p1 + p2, max(q1 + p2, q2)),
+// so each lane composes its run of periods, a sub-warp scan hands every lane
+// the stock entering its periods, and each lane then fills A, the local part
+// of C and its gR-list entries; a second scan offsets C.
+// ---------------------------------------------------------------------------
+constexpr int64_t kNegInf = -(1ll << 62);
+
+template <typename Acc, int NW>
+__device__ __forceinline__ void rebuild_row(const Rows<Acc>& m, int q, int lane, int G,
+                                            unsigned smask) {
+  const int T = m.T;
+  const int2* tab = m.tab_row(q);
+  const RowBits b = m.bits[q];
+  const RowCosts rc = m.rc[q];
+  const uint64_t u0 = b.m0 | b.r0, u1 = b.m1 | b.r1;
+  int32_t* A = m.A + q * T;
+  Acc* C = m.C + q * T;
+  int2* L = m.L + q * T;
+  const int P = (T + G - 1) / G;
+  const int a = lane * P, e = a + P < T ? a + P : T;
+  // phase 1: composition of this lane's period functions
+  int64_t fp = 0, fq = kNegInf;
+  for (int t = a; t < e; ++t) {
+    const int2 tt = tab[t];
+    const int32_t Rt = tt.y - (t > 0 ? tab[t - 1].y : 0);
+    int64_t pt = Rt, qt = kNegInf;
+    if (bitat<NW>(b.r0, b.r1, t)) {
+      const int n = nxt<NW>(u0, u1, t, T);
+      pt = (int64_t)Rt - (int64_t)(tab[n].x - tt.x);
+      qt = 0;
+    }
+    fq = (fq + pt > qt) ? fq + pt : qt;
+    fp += pt;
+  }
+  // phase 2: exclusive scan of the compositions in lane order
+  for (int o = 1; o < G; o <<= 1) {
+    const int64_t pp = __shfl_up_sync(smask, fp, o, G);
+    const int64_t qq = __shfl_up_sync(smask, fq, o, G);
+    if (lane >= o) {
+      const int64_t nq = qq + fp;
+      fq = nq > fq ? nq : fq;
+      fp += pp;
+    }
+  }
+  int64_t ep = __shfl_up_sync(smask, fp, 1, G);
+  int64_t eq = __shfl_up_sync(smask, fq, 1, G);
+  if (lane == 0) {
+    ep = 0;
+    eq = kNegInf;
+  }
+  int64_t y = ep > eq ? ep : eq;  // stock entering period a
+  // phase 3: cache entries with local prefix sums
+  Acc lsum = 0;
+  int first_bad = T;
+  int r = rank_below<NW>(b.r0, b.r1, a);
+  for (int t = a; t < e; ++t) {
+    const int2 tt = tab[t];
+    const int32_t Rt = tt.y - (t > 0 ? tab[t - 1].y : 0);
+    const int32_t avail = (int32_t)(y + Rt);
+    if (bit_of(u0, u1, t)) {
+      const int n = nxt<NW>(u0, u1, t, T);
+      const int32_t need = tab[n].x - tt.x;
+      const int gm = bitat<NW>(b.m0, b.m1, t), gr = bitat<NW>(b.r0, b.r1, t);
+      const int32_t xr = gr ? (avail < need ? avail : need) : 0;
+      if (!gm && xr < need && first_bad == T) first_bad = t;
+      A[t] = avail;
+      C[t] = lsum;
+      lsum += (Acc)(gm ? rc.kM : 0) + (Acc)(gr ? rc.kR : 0) +
+              ((Acc)rc.hM * (Acc)need - (Acc)rc.hR * (Acc)xr) * (Acc)(T - t);
+      if (gr) {
+        int2 en;
+        en.x = need;
+        en.y = t | (gm << 16);
+        L[r++] = en;
+      }
+      y = avail - xr;
+    } else {
+      y = avail;
+    }
+  }
+  // phase 4: offsets of C, first shortfall, total
+  Acc off = lsum;
+  for (int o = 1; o < G; o <<= 1) {
+    const Acc v = __shfl_up_sync(smask, off, o, G);
+    if (lane >= o) off += v;
+  }
+  const Acc total = __shfl_sync(smask, off, G - 1, G);
+  off -= lsum;
+  for (int o = G >> 1; o > 0; o >>= 1) {
+    const int v = __shfl_xor_sync(smask, first_bad, o, G);
+    first_bad = v < first_bad ? v : first_bad;
+  }
+  if (off != 0)
+    for (int t = a; t < e; ++t)
+      if (bit_of(u0, u1, t)) C[t] += off;
+  if (lane == 0) {
+    const int f = nxt<NW>(u0, u1, -1, T);
+    int bad = first_bad;
+    if (tab[f].x != 0) bad = -1;  // demand before the first setup
+    m.bad[q] = bad;
+    m.S[q] = bad == T ? total : Inf<Acc>::value;
+    m.nR[q] = popc64(b.r0) + (NW == 1 ? 0 : popc64(b.r1));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Team context: the CTA's view of the run its cluster executes.
+// ---------------------------------------------------------------------------
+struct CtlShared {
+  int run;
+  int flag[2];
+  int ninf[2];
+  int Finf;
+  int abort;
+  int pad;
+  unsigned long long acc[2];
+  unsigned long long gkey[2];
+  long long F;
+  unsigned long long applied, steps;
+};
+
+template <typename Acc>
+struct Team {
+  Rows<Acc> m;
+  CtlShared* sh;
+  int K, T, Kc, Kcr, C, crank;
+  int G, lane, sub, nsub, tid, nthr, wlane, warp, nwarps;
+  unsigned smask;
+  int tp, fp;
+  uint32_t steps, applied;
+  int vnd_cap;
+
+  __device__ __forceinline__ bool owns(int k) const {
+    return k >= 0 && (k % C) == crank && ((k / C) % nsub) == sub;
+  }
+};
+
 __device__ __forceinline__ void team_sync(int C) {
   if (C == 1) {
     __syncthreads();
@@ -219,327 +351,409 @@ __device__ __forceinline__ void team_sync(int C) {
   }
 }
 
+// Set up the team for run rd: shared-memory layout, staging of the CTA's
+// rows (one warp per row: prefix tables, constants, start bits), control
+// words, and the cache of every owned row.
+template <typename Acc, int NW, bool TS>
+__device__ void team_begin(Team<Acc>& t, unsigned char* smem, CtlShared* sh,
+                           const VnsParams& p, const RunDesc& rd) {
+  const InstDesc id = p.ip.insts[rd.inst];
+  const int K = id.K, T = id.T, C = t.C, crank = t.crank;
+  t.sh = sh;
+  t.K = K;
+  t.T = T;
+  t.Kc = (K - crank + C - 1) / C;
+  t.Kcr = ((t.Kc + t.nsub - 1) / t.nsub) * t.nsub;
+  t.tp = t.fp = 0;
+  t.steps = t.applied = 0;
+  t.vnd_cap = p.vnd_cap;
+  const int Kmax = (K + C - 1) / C;
+  const VnsLayout Lay = vns_layout(Kmax, T, (int)sizeof(Acc), TS);
+  Rows<Acc>& m = t.m;
+  m.tab = TS ? (const int2*)(smem + Lay.tab) : (p.ip.gtab + id.tab_off);
+  m.rc = (RowCosts*)(smem + Lay.rc);
+  m.C0 = (int64_t*)(smem + Lay.C0);
+  m.bits = (RowBits*)(smem + Lay.bits);
+  m.S = (Acc*)(smem + Lay.S);
+  m.bad = (int32_t*)(smem + Lay.bad);
+  m.nR = (int32_t*)(smem + Lay.nR);
+  m.A = (int32_t*)(smem + Lay.A);
+  m.C = (Acc*)(smem + Lay.C);
+  m.L = (int2*)(smem + Lay.L);
+  m.save = smem + Lay.save;
+  m.slot = Lay.slot;
+  m.T = T;
+  m.C_ = C;
+  m.crank = crank;
+  m.ts = TS;
+  for (int q = t.warp; q < t.Kc; q += t.nwarps) {
+    const int k = q * C + crank;
+    const int64_t ro = id.row_off + k;
+    if (TS) {
+      stage_row_warp(p.ip.D + id.cell_off + (int64_t)k * T,
+                     p.ip.R + id.cell_off + (int64_t)k * T, T, t.wlane,
+                     (int2*)(smem + Lay.tab) + (int64_t)q * (T + 1), p.ip.hM[ro],
+                     p.ip.hR[ro], &m.C0[q]);
+    } else if (t.wlane == 0) {
+      m.C0[q] = p.ip.gC0[ro];
+    }
+    if (t.wlane == 0) {
+      m.rc[q] = RowCosts{p.ip.kM[ro], p.ip.kR[ro], p.ip.hM[ro], p.ip.hR[ro]};
+      m.bits[q] = rd.start_off >= 0 ? p.start_bits[rd.start_off + k] : all_open(T);
+    }
+  }
+  if (t.tid == 0) {
+    sh->acc[0] = sh->acc[1] = 0ull;
+    sh->ninf[0] = sh->ninf[1] = 0;
+    sh->flag[0] = sh->flag[1] = 0;
+    sh->gkey[0] = sh->gkey[1] = ~0ull;
+    sh->applied = 0ull;
+    sh->steps = 0ull;
+    sh->abort = 0;
+  }
+  __syncthreads();
+  for (int qq = t.sub; qq < t.Kcr; qq += t.nsub) {
+    if (qq < t.Kc) rebuild_row<Acc, NW>(m, qq, t.lane, t.G, t.smask);
+    __syncwarp();
+  }
+}
+
+// Saturating objective of the team (sum of row costs over the cluster).
+template <typename Acc>
+__device__ int64_t team_total(Team<Acc>& t) {
+  CtlShared* sh = t.sh;
+  const int tp = t.tp;
+  if (t.lane == 0) {
+    int64_t s = 0;
+    int ni = 0;
+    for (int q = t.sub; q < t.Kc; q += t.nsub) {
+      const int64_t c = t.m.cost(q);
+      if (c == INT64_MAX) ++ni; else s += c;
+    }
+    if (s) atomicAdd(&sh->acc[tp], (unsigned long long)s);
+    if (ni) atomicAdd(&sh->ninf[tp], ni);
+  }
+  __syncthreads();
+  int64_t tot;
+  if (t.C == 1) {
+    tot = sh->ninf[tp] ? INT64_MAX : (int64_t)sh->acc[tp];
+  } else {
+    cg::cluster_group cl = cg::this_cluster();
+    cl.sync();
+    unsigned long long a = 0;
+    int ni = 0;
+    if (t.wlane < t.C) {
+      a = *cl.map_shared_rank(&sh->acc[tp], t.wlane);
+      ni = *cl.map_shared_rank(&sh->ninf[tp], t.wlane);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(kFull, a, o);
+      ni += __shfl_xor_sync(kFull, ni, o);
+    }
+    tot = ni ? INT64_MAX : (int64_t)a;
+  }
+  if (t.tid == 0) {
+    sh->acc[tp ^ 1] = 0ull;
+    sh->ninf[tp ^ 1] = 0;
+  }
+  t.tp ^= 1;
+  return tot;
+}
+
+// VND of Algorithm 1 (pipe form), mode P: every product takes its best
+// strictly improving move of N_j; the j = 1..3 sweep repeats until no product
+// of the team improves.  Returns the sweeps run, or -1 at the cap.
+template <typename Acc, int NW>
+__device__ int vnd_p(Team<Acc>& t) {
+  const int T = t.T;
+  int cycles = 0;
+  for (;;) {
+    int improved = 0;
+    for (int j = 1; j <= 3; ++j) {
+      const int M = row_moves(T, j);
+      if (M <= 0) continue;
+      for (int qq = t.sub; qq < t.Kcr; qq += t.nsub) {
+        const bool valid = qq < t.Kc;
+        const int q = valid ? qq : 0;
+        uint64_t best = ~0ull;
+        if (valid) {
+          const RowState<Acc> cur = t.m.state(q);
+          best = row_best<Acc, NW>(t.m, q, cur, j, M, t.lane, t.G, t.steps);
+        }
+        best = subwarp_min(best, t.G);
+        const bool imp = valid && key_cost(best) < t.m.cost(q);
+        if (imp) {
+          if (t.lane == 0) {
+            RowBits nb = t.m.bits[q];
+            apply_row_move(nb, T, j, key_index(best));
+            t.m.bits[q] = nb;
+            ++t.applied;
+          }
+          __syncwarp(t.smask);
+          rebuild_row<Acc, NW>(t.m, q, t.lane, t.G, t.smask);
+          improved = 1;
+        }
+        __syncwarp();
+      }
+    }
+    ++cycles;
+    int any = __syncthreads_or(improved);
+    if (t.C > 1) {
+      cg::cluster_group cl = cg::this_cluster();
+      if (t.tid == 0) t.sh->flag[t.fp] = any;
+      cl.sync();
+      const int v = t.wlane < t.C ? *cl.map_shared_rank(&t.sh->flag[t.fp], t.wlane) : 0;
+      any = __any_sync(kFull, v);
+      t.fp ^= 1;
+    }
+    if (!any) break;
+    if (cycles >= t.vnd_cap) return -1;
+  }
+  return cycles;
+}
+
+// VND, mode G (single-CTA teams): one best move of the whole neighbourhood by
+// (new objective, global index), applied when it lowers the objective.
+template <typename Acc, int NW>
+__device__ int vnd_g(Team<Acc>& t) {
+  CtlShared* sh = t.sh;
+  const int T = t.T;
+  if (t.tid == 0) {
+    sh->F = 0;
+    sh->Finf = 0;
+    sh->gkey[0] = sh->gkey[1] = ~0ull;
+  }
+  __syncthreads();
+  if (t.lane == 0) {
+    long long s = 0;
+    int ni = 0;
+    for (int q = t.sub; q < t.Kc; q += t.nsub) {
+      const int64_t c = t.m.cost(q);
+      if (c == INT64_MAX) ++ni; else s += c;
+    }
+    if (s) atomicAdd((unsigned long long*)&sh->F, (unsigned long long)s);
+    if (ni) atomicAdd(&sh->Finf, ni);
+  }
+  __syncthreads();
+  int cycles = 0, e = 0;
+  for (;;) {
+    bool improved = false;
+    for (int j = 1; j <= 3; ++j) {
+      const int M = row_moves(T, j);
+      if (M <= 0) continue;
+      const int64_t F = sh->F;
+      const int Finf = sh->Finf;
+      const int64_t total = Finf ? INT64_MAX : F;
+      for (int qq = t.sub; qq < t.Kcr; qq += t.nsub) {
+        const bool valid = qq < t.Kc;
+        const int q = valid ? qq : 0;
+        uint64_t best = ~0ull;
+        if (valid) {
+          const RowState<Acc> cur = t.m.state(q);
+          const int64_t rck = t.m.cost(q);
+          const int infk = rck == INT64_MAX;
+          const int64_t others = (Finf - infk > 0) ? INT64_MAX : F - (infk ? 0 : rck);
+          const int2* tk = t.m.tab_row(q);
+          const RowCosts rc = t.m.rc[q];
+          const int64_t c0 = t.m.C0[q];
+          int st = 0;
+          for (int l = t.lane; l < M; l += t.G) {
+            const Acc S = eval_move<Acc, NW>(tk, T, rc, cur, t.m.A + q * T, t.m.C + q * T,
+                                             t.m.L + q * T, j, l, st);
+            const int64_t nc = row_cost<Acc>(S, c0);
+            const int64_t nt = (others == INT64_MAX || nc == INT64_MAX) ? INT64_MAX : others + nc;
+            best = umin64(best, pack_key(nt, (uint32_t)(q * M + l)));
+          }
+          t.steps += (uint32_t)st;
+        }
+        best = subwarp_min(best, t.G);
+        if (valid && t.lane == 0 && best != ~0ull) atomicMin(&sh->gkey[e], best);
+      }
+      __syncthreads();
+      const uint64_t gk = sh->gkey[e];
+      if (t.tid == 0) sh->gkey[e ^ 1] = ~0ull;
+      if (gk != ~0ull && key_cost(gk) < total) {
+        const int gi = key_index(gk);
+        const int qw = gi / M, lw = gi - qw * M;
+        if ((qw % t.nsub) == t.sub) {
+          int64_t old = 0;
+          if (t.lane == 0) {
+            old = t.m.cost(qw);
+            RowBits nb = t.m.bits[qw];
+            apply_row_move(nb, T, j, lw);
+            t.m.bits[qw] = nb;
+            ++t.applied;
+          }
+          __syncwarp(t.smask);
+          rebuild_row<Acc, NW>(t.m, qw, t.lane, t.G, t.smask);
+          __syncwarp(t.smask);
+          if (t.lane == 0) {
+            const int64_t nw = t.m.cost(qw);
+            if (old == INT64_MAX) {
+              sh->Finf = Finf - 1;
+              sh->F = F + nw;
+            } else {
+              sh->F = F - old + nw;
+            }
+          }
+        }
+        improved = true;
+      }
+      __syncthreads();
+      e ^= 1;
+    }
+    ++cycles;
+    if (!improved) break;
+    if (cycles >= t.vnd_cap) return -1;
+  }
+  return cycles;
+}
+
+template <typename Acc, int NW>
+__device__ __forceinline__ int vnd(Team<Acc>& t, int mode) {
+  return mode == 0 ? vnd_p<Acc, NW>(t) : vnd_g<Acc, NW>(t);
+}
+
+// Shake(x, k) of Algorithm 2: k moves of N_k from splitmix64 draws keyed by
+// (seed, iteration, k, move); `first` marks a row's first hit.
+struct ShakePlan {
+  int rows[kMaxShake], locs[kMaxShake];
+  bool first[kMaxShake];
+};
+
+__device__ __forceinline__ ShakePlan plan_shake(uint64_t seed, int it, int ks, int K, int T) {
+  ShakePlan pl;
+  const int per = row_moves(T, ks);
+  const int64_t size = per > 0 ? (int64_t)K * per : 0;
+#pragma unroll
+  for (int j = 0; j < kMaxShake; ++j) {
+    pl.rows[j] = -1;
+    pl.locs[j] = 0;
+    pl.first[j] = false;
+    if (j < ks && size > 0) {
+      const uint64_t d = shake_draw(seed, (uint64_t)it, (uint64_t)ks, (uint64_t)j);
+      const int64_t mv = (int64_t)(d % (uint64_t)size);
+      pl.rows[j] = (int)(mv / per);
+      pl.locs[j] = (int)(mv - (int64_t)pl.rows[j] * per);
+      pl.first[j] = true;
+      for (int q2 = 0; q2 < j; ++q2)
+        if (pl.rows[q2] == pl.rows[j]) pl.first[j] = false;
+    }
+  }
+  return pl;
+}
+
+// Apply a shake: the owner of each hit row saves it on first touch (for a
+// rejection), applies the moves in order, then rebuilds the row.
+template <typename Acc, int NW>
+__device__ void apply_shake(Team<Acc>& t, const ShakePlan& pl, int ks, int par) {
+#pragma unroll
+  for (int j = 0; j < kMaxShake; ++j) {
+    const int k = pl.rows[j];
+    const bool mine = t.owns(k);
+    if (mine && pl.first[j]) save_row<Acc>(t.m, k / t.C, t.m.slot_ptr(par, j), t.lane, t.G);
+    __syncwarp();
+    if (mine && t.lane == 0) {
+      RowBits b = t.m.bits[k / t.C];
+      apply_row_move(b, t.T, ks, pl.locs[j]);
+      t.m.bits[k / t.C] = b;
+    }
+    __syncwarp();
+  }
+#pragma unroll
+  for (int j = 0; j < kMaxShake; ++j) {
+    const int k = pl.rows[j];
+    if (t.owns(k) && pl.first[j]) rebuild_row<Acc, NW>(t.m, k / t.C, t.lane, t.G, t.smask);
+    __syncwarp();
+  }
+}
+
+// Undo a shake: the shaken rows go back to x (the other rows never moved:
+// they were locally optimal in x).
+template <typename Acc>
+__device__ void undo_shake(Team<Acc>& t, const ShakePlan& pl, int par) {
+#pragma unroll
+  for (int j = 0; j < kMaxShake; ++j) {
+    const int k = pl.rows[j];
+    if (t.owns(k) && pl.first[j]) restore_row<Acc>(t.m, k / t.C, t.m.slot_ptr(par, j), t.lane, t.G);
+    __syncwarp();
+  }
+}
+
+// Fold this CTA's per-thread counters into its control words.
+template <typename Acc>
+__device__ void flush_counters(Team<Acc>& t, unsigned long long* steps_dst,
+                               unsigned long long* applied_dst) {
+  unsigned long long v = t.steps, a = t.applied;
+  for (int o = 16; o > 0; o >>= 1) {
+    v += __shfl_xor_sync(kFull, v, o);
+    a += __shfl_xor_sync(kFull, a, o);
+  }
+  if (t.wlane == 0) {
+    if (v) atomicAdd(steps_dst, v);
+    if (a) atomicAdd(applied_dst, a);
+  }
+  t.steps = 0;
+  t.applied = 0;
+}
+
+template <typename Acc>
+__device__ __forceinline__ void team_init(Team<Acc>& t, int G) {
+  cg::cluster_group cl = cg::this_cluster();
+  t.C = (int)cl.num_blocks();
+  t.crank = (int)cl.block_rank();
+  t.tid = threadIdx.x;
+  t.nthr = blockDim.x;
+  t.G = G;
+  t.lane = t.tid & (G - 1);
+  t.sub = t.tid / G;
+  t.nsub = t.nthr / G;
+  t.wlane = t.tid & 31;
+  t.warp = t.tid >> 5;
+  t.nwarps = t.nthr >> 5;
+  t.smask = G == 32 ? kFull : (((1u << G) - 1u) << (t.wlane & ~(G - 1)));
+}
+
+// ---------------------------------------------------------------------------
+// vns_kernel: persistent batched GVNS, one team (cluster) per run, runs taken
+// from a device work queue.
+// ---------------------------------------------------------------------------
 template <typename Acc, int NW, bool TS, int MAXT>
 __global__ void __launch_bounds__(MAXT, 1) vns_kernel(const VnsParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int sh_run;
-  __shared__ unsigned long long sh_acc[2];
-  __shared__ int sh_ninf[2];
-  __shared__ int sh_flag[2];
-  __shared__ unsigned long long sh_gkey[2];
-  __shared__ long long sh_F;
-  __shared__ int sh_Finf;
-  __shared__ unsigned long long sh_applied, sh_steps;
-
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  const int G = p.G;
-  const int lane = tid & (G - 1), sub = tid / G, nsub = nthr / G;
-  const int wlane = tid & 31, warp = tid >> 5, nwarps = nthr >> 5;
+  __shared__ CtlShared sh;
+  Team<Acc> t;
+  team_init(t, p.G);
   cg::cluster_group cl = cg::this_cluster();
-  const int C = (int)cl.num_blocks();
-  const int crank = (int)cl.block_rank();
-
   for (;;) {
-    if (crank == 0 && tid == 0) sh_run = atomicAdd(p.queue, 1);
-    team_sync(C);
-    const int r = C == 1 ? sh_run : *cl.map_shared_rank(&sh_run, 0);
-    team_sync(C);
+    if (t.crank == 0 && t.tid == 0) sh.run = atomicAdd(p.queue, 1);
+    team_sync(t.C);
+    const int r = t.C == 1 ? sh.run : *cl.map_shared_rank(&sh.run, 0);
+    team_sync(t.C);
     if (r >= p.nruns) return;
     const RunDesc rd = p.runs[r];
-    const InstDesc id = p.ip.insts[rd.inst];
-    const int K = id.K, T = id.T;
-    const int Kc = (K - crank + C - 1) / C;  // rows owned by this CTA
-    const int Kmax = (K + C - 1) / C;
-    const VnsLayout Lay = vns_layout(Kmax, T, (int)sizeof(Acc), TS);
-    Rows<Acc> m;
-    m.tab = TS ? (const int2*)(smem + Lay.tab) : (p.ip.gtab + id.tab_off);
-    m.rc = (RowCosts*)(smem + Lay.rc);
-    m.C0 = (int64_t*)(smem + Lay.C0);
-    m.bits = (RowBits*)(smem + Lay.bits);
-    m.S = (Acc*)(smem + Lay.S);
-    m.bad = (int32_t*)(smem + Lay.bad);
-    m.nR = (int32_t*)(smem + Lay.nR);
-    m.A = (int32_t*)(smem + Lay.A);
-    m.C = (Acc*)(smem + Lay.C);
-    m.L = (int2*)(smem + Lay.L);
-    m.save = smem + Lay.save;
-    m.slot = Lay.slot;
-    m.T = T;
-    m.C_ = C;
-    m.crank = crank;
-    m.ts = TS;
-
-    // ---- stage this CTA's rows (one warp per row) ----
-    for (int q = warp; q < Kc; q += nwarps) {
-      const int k = q * C + crank;
-      const int64_t ro = id.row_off + k;
-      if (TS) {
-        stage_row_warp(p.ip.D + id.cell_off + (int64_t)k * T,
-                       p.ip.R + id.cell_off + (int64_t)k * T, T, wlane,
-                       (int2*)(smem + Lay.tab) + (int64_t)q * (T + 1), p.ip.hM[ro],
-                       p.ip.hR[ro], &m.C0[q]);
-      } else if (wlane == 0) {
-        m.C0[q] = p.ip.gC0[ro];
-      }
-      if (wlane == 0) {
-        m.rc[q] = RowCosts{p.ip.kM[ro], p.ip.kR[ro], p.ip.hM[ro], p.ip.hR[ro]};
-        m.bits[q] = rd.start_off >= 0 ? p.start_bits[rd.start_off + k] : all_open(T);
-      }
-    }
-    if (tid == 0) {
-      sh_acc[0] = sh_acc[1] = 0ull;
-      sh_ninf[0] = sh_ninf[1] = 0;
-      sh_flag[0] = sh_flag[1] = 0;
-      sh_gkey[0] = sh_gkey[1] = ~0ull;
-      sh_applied = 0ull;
-      sh_steps = 0ull;
-    }
-    __syncthreads();
-    if (lane == 0)
-      for (int q = sub; q < Kc; q += nsub) rebuild<Acc, NW>(m, q);
-    __syncwarp();
-
-    uint32_t my_steps = 0, my_applied = 0;
-    const int Kcr = ((Kc + nsub - 1) / nsub) * nsub;  // uniform row-loop bound
+    team_begin<Acc, NW, TS>(t, smem, &sh, p, rd);
+    const int K = t.K, T = t.T;
     const int64_t moves_per_cycle = (int64_t)K * (2 * T + (T > 1 ? 2 * (T - 1) : 0));
     int status = 0;
     int64_t cycles_total = 0;
-    int tp = 0, fp = 0;
-
-    // ---- saturating objective of the team (sum of row costs) ----
-    auto team_total = [&]() -> int64_t {
-      if (lane == 0) {
-        int64_t s = 0;
-        int ni = 0;
-        for (int q = sub; q < Kc; q += nsub) {
-          const int64_t c = m.cost(q);
-          if (c == INT64_MAX) ++ni; else s += c;
-        }
-        if (s) atomicAdd(&sh_acc[tp], (unsigned long long)s);
-        if (ni) atomicAdd(&sh_ninf[tp], ni);
-      }
-      __syncthreads();
-      int64_t tot;
-      if (C == 1) {
-        tot = sh_ninf[tp] ? INT64_MAX : (int64_t)sh_acc[tp];
-      } else {
-        cl.sync();
-        unsigned long long a = 0;
-        int ni = 0;
-        if (wlane < C) {
-          a = *cl.map_shared_rank(&sh_acc[tp], wlane);
-          ni = *cl.map_shared_rank(&sh_ninf[tp], wlane);
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-          a += __shfl_xor_sync(kFull, a, o);
-          ni += __shfl_xor_sync(kFull, ni, o);
-        }
-        tot = ni ? INT64_MAX : (int64_t)a;
-      }
-      if (tid == 0) {
-        sh_acc[tp ^ 1] = 0ull;
-        sh_ninf[tp ^ 1] = 0;
-      }
-      tp ^= 1;
-      return tot;
-    };
-
-    // ---- VND, mode P (Algorithm 1): every product takes its best strictly
-    // improving move of N_j; repeat the j = 1..3 sweep until no product of
-    // the team improves.  Returns the sweeps run, or -1 at the cap. ----
-    auto vnd_p = [&]() -> int {
-      int cycles = 0;
-      for (;;) {
-        int improved = 0;
-        for (int j = 1; j <= 3; ++j) {
-          const int M = row_moves(T, j);
-          if (M <= 0) continue;
-          for (int qq = sub; qq < Kcr; qq += nsub) {
-            const bool valid = qq < Kc;
-            const int q = valid ? qq : 0;
-            uint64_t best = ~0ull;
-            if (valid) {
-              const RowState<Acc> cur = m.state(q);
-              best = row_best<Acc, NW>(m, q, cur, j, M, lane, G, my_steps);
-            }
-            best = subwarp_min(best, G);
-            const bool imp = valid && key_cost(best) < m.cost(q);
-            if (imp && lane == 0) {
-              RowBits nb = m.bits[q];
-              apply_row_move(nb, T, j, key_index(best));
-              m.bits[q] = nb;
-              rebuild<Acc, NW>(m, q);
-              ++my_applied;
-            }
-            __syncwarp();
-            improved |= imp;
-          }
-        }
-        ++cycles;
-        int any = __syncthreads_or(improved);
-        if (C > 1) {
-          if (tid == 0) sh_flag[fp] = any;
-          cl.sync();
-          const int v = wlane < C ? *cl.map_shared_rank(&sh_flag[fp], wlane) : 0;
-          any = __any_sync(kFull, v);
-          fp ^= 1;
-        }
-        if (!any) break;
-        if (cycles >= p.vnd_cap) return -1;
-      }
-      return cycles;
-    };
-
-    // ---- VND, mode G (single CTA teams): one best move of the whole
-    // neighbourhood by (new objective, global index), applied when it
-    // lowers the objective. ----
-    auto vnd_g = [&]() -> int {
-      if (tid == 0) {
-        sh_F = 0;
-        sh_Finf = 0;
-        sh_gkey[0] = sh_gkey[1] = ~0ull;
-      }
-      __syncthreads();
-      if (lane == 0) {
-        long long s = 0;
-        int ni = 0;
-        for (int q = sub; q < Kc; q += nsub) {
-          const int64_t c = m.cost(q);
-          if (c == INT64_MAX) ++ni; else s += c;
-        }
-        if (s) atomicAdd((unsigned long long*)&sh_F, (unsigned long long)s);
-        if (ni) atomicAdd(&sh_Finf, ni);
-      }
-      __syncthreads();
-      int cycles = 0, e = 0;
-      for (;;) {
-        bool improved = false;
-        for (int j = 1; j <= 3; ++j) {
-          const int M = row_moves(T, j);
-          if (M <= 0) continue;
-          const int64_t F = sh_F;
-          const int Finf = sh_Finf;
-          const int64_t total = Finf ? INT64_MAX : F;
-          for (int qq = sub; qq < Kcr; qq += nsub) {
-            const bool valid = qq < Kc;
-            const int q = valid ? qq : 0;
-            uint64_t best = ~0ull;
-            if (valid) {
-              const RowState<Acc> cur = m.state(q);
-              const int64_t rck = m.cost(q);
-              const int infk = rck == INT64_MAX;
-              const int64_t others = (Finf - infk > 0) ? INT64_MAX : F - (infk ? 0 : rck);
-              const int2* tk = m.tab_row(q);
-              const RowCosts rc = m.rc[q];
-              const int64_t c0 = m.C0[q];
-              int st = 0;
-              for (int l = lane; l < M; l += G) {
-                const Acc S = eval_move<Acc, NW>(tk, T, rc, cur, m.A + q * T, m.C + q * T,
-                                                 m.L + q * T, j, l, st);
-                const int64_t nc = row_cost<Acc>(S, c0);
-                const int64_t nt =
-                    (others == INT64_MAX || nc == INT64_MAX) ? INT64_MAX : others + nc;
-                best = umin64(best, pack_key(nt, (uint32_t)(q * M + l)));
-              }
-              my_steps += (uint32_t)st;
-            }
-            best = subwarp_min(best, G);
-            if (valid && lane == 0 && best != ~0ull) atomicMin(&sh_gkey[e], best);
-          }
-          __syncthreads();
-          const uint64_t gk = sh_gkey[e];
-          if (tid == 0) sh_gkey[e ^ 1] = ~0ull;
-          if (gk != ~0ull && key_cost(gk) < total) {
-            const int gi = key_index(gk);
-            const int qw = gi / M, lw = gi - qw * M;
-            if ((qw % nsub) == sub && lane == 0) {
-              const int64_t old = m.cost(qw);
-              RowBits nb = m.bits[qw];
-              apply_row_move(nb, T, j, lw);
-              m.bits[qw] = nb;
-              rebuild<Acc, NW>(m, qw);
-              const int64_t nw = m.cost(qw);
-              if (old == INT64_MAX) {
-                sh_Finf = Finf - 1;
-                sh_F = F + nw;
-              } else {
-                sh_F = F - old + nw;
-              }
-              ++my_applied;
-            }
-            improved = true;
-          }
-          __syncthreads();
-          e ^= 1;
-        }
-        ++cycles;
-        if (!improved) break;
-        if (cycles >= p.vnd_cap) return -1;
-      }
-      return cycles;
-    };
-
-    // ---- initial VND and GVNS (Algorithm 2) ----
-    int cyc = rd.mode == 0 ? vnd_p() : vnd_g();
+    int cyc = vnd<Acc, NW>(t, rd.mode);
     if (cyc < 0) status = kStatusCap; else cycles_total += cyc;
-    int64_t fx = team_total();
+    int64_t fx = team_total(t);
     int kk = 1;  // neighbourhood index k of Algorithm 2
     uint64_t h = 0;
     int64_t iters_done = 0, accepted = 0;
-    const bool log = rd.traj_off >= 0 && crank == 0;
+    const bool log = rd.traj_off >= 0 && t.crank == 0 && t.tid == 0;
     for (int it = 0; it < rd.iters && status == 0; ++it) {
       const int par = it & 1;
       const int ks = kk;
-      // Shake(x, k): k moves of N_k from splitmix64 draws, applied by the
-      // owners of the hit rows; the first touch saves the row so that a
-      // rejected x'' can be undone.
-      const int per = row_moves(T, ks);
-      const int64_t size = per > 0 ? (int64_t)K * per : 0;
-      int rows[kMaxShake], locs[kMaxShake];
-      bool first[kMaxShake];
-#pragma unroll
-      for (int j = 0; j < kMaxShake; ++j) {
-        rows[j] = -1;
-        locs[j] = 0;
-        first[j] = false;
-        if (j < ks && size > 0) {
-          const uint64_t d = shake_draw(rd.seed, (uint64_t)it, (uint64_t)ks, (uint64_t)j);
-          const int64_t mv = (int64_t)(d % (uint64_t)size);
-          rows[j] = (int)(mv / per);
-          locs[j] = (int)(mv - (int64_t)rows[j] * per);
-          first[j] = true;
-          for (int q2 = 0; q2 < j; ++q2)
-            if (rows[q2] == rows[j]) first[j] = false;
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < kMaxShake; ++j) {
-        const int k = rows[j];
-        const bool mine = k >= 0 && (k % C) == crank && ((k / C) % nsub) == sub;
-        if (mine && first[j]) save_row<Acc>(m, k / C, m.slot_ptr(par, j), lane, G);
-        __syncwarp();
-        if (mine && lane == 0) {
-          RowBits b = m.bits[k / C];
-          apply_row_move(b, T, ks, locs[j]);
-          m.bits[k / C] = b;
-        }
-        __syncwarp();
-      }
-      if (lane == 0) {
-#pragma unroll
-        for (int j = 0; j < kMaxShake; ++j) {
-          const int k = rows[j];
-          if (k >= 0 && first[j] && (k % C) == crank && ((k / C) % nsub) == sub)
-            rebuild<Acc, NW>(m, k / C);
-        }
-      }
-      __syncwarp();
-      // VND(x')
-      cyc = rd.mode == 0 ? vnd_p() : vnd_g();
+      const ShakePlan pl = plan_shake(rd.seed, it, ks, K, T);
+      apply_shake<Acc, NW>(t, pl, ks, par);
+      cyc = vnd<Acc, NW>(t, rd.mode);
       if (cyc < 0) status = kStatusCap; else cycles_total += cyc;
-      const int64_t f2 = team_total();
+      const int64_t f2 = team_total(t);
       const int acc = f2 < fx;
-      if (tid == 0 && crank == 0) {
+      if (t.crank == 0 && t.tid == 0) {
         if (log) {
           TrajEntry te;
           te.it = it;
@@ -558,44 +772,20 @@ __global__ void __launch_bounds__(MAXT, 1) vns_kernel(const VnsParams p) {
         kk = 1;
         ++accepted;
       } else {
-        // x'' rejected: the shaken rows go back to x; the other rows never
-        // moved, being locally optimal in x.
-#pragma unroll
-        for (int j = 0; j < kMaxShake; ++j) {
-          const int k = rows[j];
-          const bool mine = k >= 0 && first[j] && (k % C) == crank && ((k / C) % nsub) == sub;
-          if (mine) restore_row<Acc>(m, k / C, m.slot_ptr(par, j), lane, G);
-          __syncwarp();
-        }
+        undo_shake<Acc>(t, pl, par);
         kk = kk % rd.kmax + 1;
       }
-      if ((it & 255) == 255) {  // keep the 32-bit per-thread counters small
-        unsigned long long v = my_steps;
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-        if (wlane == 0 && v) atomicAdd(&sh_steps, v);
-        my_steps = 0;
-      }
+      if ((it & 255) == 255) flush_counters(t, &sh.steps, &sh.applied);
     }
-
-    // ---- outputs ----
-    for (int q = tid; q < Kc; q += nthr) p.out_bits[rd.bits_off + q * C + crank] = m.bits[q];
-    {
-      unsigned long long v = my_steps, a = my_applied;
-      for (int o = 16; o > 0; o >>= 1) {
-        v += __shfl_xor_sync(kFull, v, o);
-        a += __shfl_xor_sync(kFull, a, o);
-      }
-      if (wlane == 0) {
-        if (v) atomicAdd(&sh_steps, v);
-        if (a) atomicAdd(&sh_applied, a);
-      }
-    }
-    team_sync(C);
-    if (tid == 0 && crank == 0) {
+    for (int q = t.tid; q < t.Kc; q += t.nthr)
+      p.out_bits[rd.bits_off + q * t.C + t.crank] = t.m.bits[q];
+    flush_counters(t, &sh.steps, &sh.applied);
+    team_sync(t.C);
+    if (t.tid == 0 && t.crank == 0) {
       unsigned long long steps = 0, applied = 0;
-      for (int c = 0; c < C; ++c) {
-        steps += C == 1 ? sh_steps : *cl.map_shared_rank(&sh_steps, c);
-        applied += C == 1 ? sh_applied : *cl.map_shared_rank(&sh_applied, c);
+      for (int c = 0; c < t.C; ++c) {
+        steps += t.C == 1 ? sh.steps : *cl.map_shared_rank(&sh.steps, c);
+        applied += t.C == 1 ? sh.applied : *cl.map_shared_rank(&sh.applied, c);
       }
       RunOut o;
       o.best_cost = fx;
@@ -611,8 +801,212 @@ __global__ void __launch_bounds__(MAXT, 1) vns_kernel(const VnsParams p) {
       o.reserved = 0;
       p.out[rd.out] = o;
     }
-    team_sync(C);
+    team_sync(t.C);
   }
+}
+
+// ---------------------------------------------------------------------------
+// spec_kernel: one GVNS run (mode P) executed by W teams that speculate on
+// consecutive iterations.  In a round every team starts from the same
+// incumbent x; team i runs iteration it0 + i (its k assumes iterations it0 ..
+// it0 + i - 1 were rejected), publishes f(x'') and its changed rows, and
+// waits at a grid barrier.  The round then commits iterations in order up to
+// the first acceptance a, exactly as the sequential loop would: every team
+// undoes its own shake, adopts the changed rows of team a, and the next round
+// starts at it0 + a + 1 (or it0 + W when nothing was accepted).  Trajectory,
+// solution and counters are those of the sequential run; work of discarded
+// speculative iterations is not counted.
+// ---------------------------------------------------------------------------
+constexpr long kSpinLimit = 1l << 24;  // grid-barrier polls (x ~200 ns) before giving up
+
+// Grid barrier over the W teams.  Returns false (and the team must stop)
+// when the wait exceeded its limit.
+template <typename Acc>
+__device__ bool grid_barrier(Team<Acc>& t, int* bar, int W) {
+  __threadfence();
+  team_sync(t.C);
+  if (t.crank == 0 && t.tid == 0) {
+    volatile int* vgen = bar + 1;
+    const int gen = *vgen;
+    __threadfence();
+    if (atomicAdd(bar, 1) == W - 1) {
+      atomicExch(bar, 0);
+      __threadfence();
+      atomicAdd(bar + 1, 1);
+    } else {
+      long n = 0;
+      while (*vgen == gen) {
+        if (++n > kSpinLimit) {
+          t.sh->abort = 1;
+          break;
+        }
+        __nanosleep(200);
+      }
+    }
+    __threadfence();
+  }
+  team_sync(t.C);
+  cg::cluster_group cl = cg::this_cluster();
+  const int ab = t.C == 1 ? t.sh->abort : *cl.map_shared_rank(&t.sh->abort, 0);
+  return ab == 0;
+}
+
+__device__ __forceinline__ RowBits ldcg_bits(const RowBits* p) {
+  RowBits b;
+  b.m0 = __ldcg(&p->m0);
+  b.m1 = __ldcg(&p->m1);
+  b.r0 = __ldcg(&p->r0);
+  b.r1 = __ldcg(&p->r1);
+  return b;
+}
+
+template <typename Acc, int NW, bool TS, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) spec_kernel(const VnsParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ CtlShared sh;
+  Team<Acc> t;
+  team_init(t, p.G);
+  cg::cluster_group cl = cg::this_cluster();
+  const int W = p.spec_teams;
+  const int team = blockIdx.x / t.C;
+  const RunDesc rd = p.runs[0];
+  team_begin<Acc, NW, TS>(t, smem, &sh, p, rd);
+  const int K = t.K, T = t.T;
+  const int64_t moves_per_cycle = (int64_t)K * (2 * T + (T > 1 ? 2 * (T - 1) : 0));
+  int status = 0;
+  int64_t cycles_total = 0;
+  int cyc = vnd_p<Acc, NW>(t);
+  if (cyc < 0) status = kStatusCap; else cycles_total += cyc;
+  int64_t fx = team_total(t);
+  flush_counters(t, &sh.steps, &sh.applied);  // the initial VND counts once (team 0)
+  unsigned long long c_steps = 0, c_applied = 0;  // committed speculative work
+  uint64_t h = 0;
+  int64_t accepted = 0;
+  int it0 = 0, k0 = 1, round = 0;
+  const bool leader = team == 0 && t.crank == 0 && t.tid == 0;
+  while (it0 < rd.iters && status == 0) {
+    const int par = round & 1;
+    const int nact = (rd.iters - it0) < W ? (rd.iters - it0) : W;
+    const bool active = team < nact;
+    const int ks = (k0 - 1 + team) % rd.kmax + 1;
+    SpecSlot* slot = p.spec_slots + par * W + team;
+    ShakePlan pl;
+    if (active) {
+      if (t.crank == 0 && t.tid == 0) {
+        slot->applied = 0ull;
+        slot->steps = 0ull;
+      }
+      pl = plan_shake(rd.seed, it0 + team, ks, K, T);
+      apply_shake<Acc, NW>(t, pl, ks, par);
+      cyc = vnd_p<Acc, NW>(t);
+      const int64_t f2 = team_total(t);
+      flush_counters(t, &slot->steps, &slot->applied);
+#pragma unroll
+      for (int j = 0; j < kMaxShake; ++j)
+        if (t.owns(pl.rows[j]) && pl.first[j] && t.lane == 0)
+          p.spec_rows[(par * W + team) * kMaxShake + j] = t.m.bits[pl.rows[j] / t.C];
+      if (t.crank == 0 && t.tid == 0) {
+        slot->f2 = f2;
+        slot->cycles = cyc;
+      }
+    }
+    if (!grid_barrier(t, p.spec_bar, W)) {
+      status = kStatusTimeout;
+      break;
+    }
+    // commit in iteration order up to the first acceptance
+    const SpecSlot* slots = p.spec_slots + par * W;
+    int a = -1, capped = 0;
+    for (int i = 0; i < nact; ++i) {
+      if (__ldcg(&slots[i].cycles) < 0) capped = 1;
+      if (__ldcg(&slots[i].f2) < fx) {
+        a = i;
+        break;
+      }
+    }
+    const int ncommit = a >= 0 ? a + 1 : nact;
+    for (int i = 0; i < ncommit; ++i) {
+      const int c = __ldcg(&slots[i].cycles);
+      cycles_total += c > 0 ? c : 0;
+    }
+    if (leader) {
+      for (int i = 0; i < ncommit; ++i) {
+        const int64_t f2 = __ldcg(&slots[i].f2);
+        const int ki = (k0 - 1 + i) % rd.kmax + 1;
+        const int acc = i == a;
+        if (rd.traj_off >= 0) {
+          TrajEntry te;
+          te.it = it0 + i;
+          te.k = ki;
+          te.cost = f2;
+          te.accepted = acc;
+          te.reserved = 0;
+          p.traj[rd.traj_off + it0 + i] = te;
+        }
+        h = splitmix64(h ^ (uint64_t)f2);
+        h = splitmix64(h ^ (((uint64_t)(it0 + i) << 32) | ((uint64_t)ki << 1) | (uint64_t)acc));
+        c_steps += __ldcg(&slots[i].steps);
+        c_applied += __ldcg(&slots[i].applied);
+      }
+    }
+    if (capped) {
+      status = kStatusCap;
+      break;
+    }
+    // every team moves to the committed solution
+    if (active && team != a) undo_shake<Acc>(t, pl, par);
+    if (a >= 0 && team != a) {
+      const int ka = (k0 - 1 + a) % rd.kmax + 1;
+      const ShakePlan pw = plan_shake(rd.seed, it0 + a, ka, K, T);
+#pragma unroll
+      for (int j = 0; j < kMaxShake; ++j) {
+        const int k = pw.rows[j];
+        if (t.owns(k) && pw.first[j]) {
+          if (t.lane == 0)
+            t.m.bits[k / t.C] = ldcg_bits(p.spec_rows + (par * W + a) * kMaxShake + j);
+          __syncwarp(t.smask);
+          rebuild_row<Acc, NW>(t.m, k / t.C, t.lane, t.G, t.smask);
+        }
+        __syncwarp();
+      }
+    }
+    if (a >= 0) {
+      fx = __ldcg(&slots[a].f2);
+      k0 = 1;
+      ++accepted;
+    } else {
+      k0 = (k0 - 1 + nact) % rd.kmax + 1;
+    }
+    it0 += ncommit;
+    ++round;
+  }
+  // outputs (team 0)
+  if (team == 0) {
+    for (int q = t.tid; q < t.Kc; q += t.nthr)
+      p.out_bits[rd.bits_off + q * t.C + t.crank] = t.m.bits[q];
+  }
+  team_sync(t.C);
+  if (leader) {
+    unsigned long long steps = c_steps, applied = c_applied;
+    for (int c = 0; c < t.C; ++c) {
+      steps += t.C == 1 ? sh.steps : *cl.map_shared_rank(&sh.steps, c);
+      applied += t.C == 1 ? sh.applied : *cl.map_shared_rank(&sh.applied, c);
+    }
+    RunOut o;
+    o.best_cost = fx;
+    o.traj_hash = h;
+    o.moves_evaluated = cycles_total * moves_per_cycle;
+    o.evals = cycles_total * 3;
+    o.vnd_cycles = cycles_total;
+    o.applied = (int64_t)applied;
+    o.iterations = it0;
+    o.accepted = accepted;
+    o.segments = (int64_t)steps;
+    o.status = status;
+    o.reserved = 0;
+    p.out[rd.out] = o;
+  }
+  team_sync(t.C);
 }
 
 }  // namespace vns
@@ -620,10 +1014,14 @@ __global__ void __launch_bounds__(MAXT, 1) vns_kernel(const VnsParams p) {
 template <typename Acc, int NW, bool TS, int MAXT>
 cudaError_t vns_prepare_t(size_t smem, int threads, int cluster, int* active) {
   auto kern = vns::vns_kernel<Acc, NW, TS, MAXT>;
+  auto spec = vns::spec_kernel<Acc, NW, TS, MAXT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(spec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (cluster > 8) {
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(spec, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
   }
   if (cluster <= 1)
@@ -642,23 +1040,35 @@ cudaError_t vns_prepare_t(size_t smem, int threads, int cluster, int* active) {
   return cudaOccupancyMaxActiveClusters(active, kern, &cfg);
 }
 
+// Launch the batched kernel, or the speculative one when p.spec_teams > 1
+// (then blocks = teams x cluster, launched cooperatively so that every team
+// is resident for the grid barrier).
 template <typename Acc, int NW, bool TS, int MAXT>
 cudaError_t vns_launch_t(const VnsParams& p, int blocks, int threads, size_t smem,
                          int cluster, cudaStream_t s) {
-  auto kern = vns::vns_kernel<Acc, NW, TS, MAXT>;
   cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = cluster < 1 ? 1 : cluster;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
+  cudaLaunchAttribute attr[2];
+  int na = 0;
+  if (cluster > 1) {
+    attr[na].id = cudaLaunchAttributeClusterDimension;
+    attr[na].val.clusterDim.x = cluster;
+    attr[na].val.clusterDim.y = 1;
+    attr[na].val.clusterDim.z = 1;
+    ++na;
+  }
   cfg.gridDim = dim3(blocks, 1, 1);
   cfg.blockDim = dim3(threads, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cfg.attrs = attr;
-  cfg.numAttrs = cluster > 1 ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, kern, p);
+  if (p.spec_teams <= 1) {
+    cfg.numAttrs = na;
+    return cudaLaunchKernelEx(&cfg, vns::vns_kernel<Acc, NW, TS, MAXT>, p);
+  }
+  attr[na].id = cudaLaunchAttributeCooperative;
+  attr[na].val.cooperative = 1;
+  cfg.numAttrs = na + 1;
+  return cudaLaunchKernelEx(&cfg, vns::spec_kernel<Acc, NW, TS, MAXT>, p);
 }
 
 }  // namespace elsr

@@ -1,0 +1,33 @@
+// elsr_vns_i32_w2.cu -- instantiations of the GVNS kernels with int32_t row
+// accumulators and 2 64-bit word(s) per setup-bit row (one translation unit
+// per combination, built in parallel).
+#include "elsr_vns.cuh"
+
+namespace elsr {
+
+template <bool TS>
+static cudaError_t prep2(int maxt, size_t smem, int threads, int cluster, int* active) {
+  return maxt == 256 ? vns_prepare_t<int32_t, 2, TS, 256>(smem, threads, cluster, active)
+                     : vns_prepare_t<int32_t, 2, TS, 512>(smem, threads, cluster, active);
+}
+
+template <bool TS>
+static cudaError_t launch2(int maxt, const VnsParams& p, int blocks, int threads, size_t smem,
+                           int cluster, cudaStream_t s) {
+  return maxt == 256 ? vns_launch_t<int32_t, 2, TS, 256>(p, blocks, threads, smem, cluster, s)
+                     : vns_launch_t<int32_t, 2, TS, 512>(p, blocks, threads, smem, cluster, s);
+}
+
+cudaError_t vns_prepare_i32_w2(bool ts, int maxt, size_t smem, int threads, int cluster,
+                                  int* active) {
+  return ts ? prep2<true>(maxt, smem, threads, cluster, active)
+            : prep2<false>(maxt, smem, threads, cluster, active);
+}
+
+cudaError_t vns_launch_i32_w2(bool ts, int maxt, const VnsParams& p, int blocks,
+                                 int threads, size_t smem, int cluster, cudaStream_t s) {
+  return ts ? launch2<true>(maxt, p, blocks, threads, smem, cluster, s)
+            : launch2<false>(maxt, p, blocks, threads, smem, cluster, s);
+}
+
+}  // namespace elsr

@@ -16,6 +16,8 @@ from . import _native as nat
 from ._native import check, load
 
 P = ctypes.c_void_p
+SHAPE_KEYS = ("lanes", "threads", "cluster", "blocks", "smem", "tables_in_smem", "words",
+              "teams")
 
 
 def _p(a: np.ndarray):
@@ -48,7 +50,7 @@ class Solver:
     """One ELSR instance resident on the device (``elsr_create``)."""
 
     def __init__(self, inst, stream=None, lanes: int = 0, threads: int = 0,
-                 cluster: int = 0):
+                 cluster: int = 0, speculation: int = 0):
         lib = load()
         self.K, self.T = int(inst.D.shape[0]), int(inst.D.shape[1])
         arrs = [_i32(inst.D), _i32(inst.R), _i32(inst.kM), _i32(inst.kR),
@@ -62,6 +64,8 @@ class Solver:
             self.set_launch(lanes, threads)
         if cluster:
             self.set_cluster(cluster)
+        if speculation:
+            self.set_speculation(speculation)
         self._last_iters = 0
 
     # -- plumbing --
@@ -78,11 +82,13 @@ class Solver:
     def set_cluster(self, cluster: int = 0):
         self._chk(self._lib.elsr_set_cluster(self._h, cluster))
 
+    def set_speculation(self, teams: int = 0):
+        self._chk(self._lib.elsr_set_speculation(self._h, teams))
+
     def launch_shape(self) -> dict:
-        v = np.zeros(7, np.int32)
+        v = np.zeros(8, np.int32)
         self._chk(self._lib.elsr_launch_shape(self._h, _p(v)))
-        return dict(zip(("lanes", "threads", "cluster", "blocks", "smem", "tables_in_smem",
-                         "words"), v.tolist()))
+        return dict(zip(SHAPE_KEYS, v.tolist()))
 
     def close(self):
         if getattr(self, "_h", None):
@@ -156,7 +162,7 @@ class Solver:
                                      _p(gr) if solution else None,
                                      _p(pl) if plan else None,
                                      tr if n else None, n)
-        if code != nat.ELSR_E_CAP:
+        if code not in (nat.ELSR_E_CAP, nat.ELSR_E_TIMEOUT):
             self._chk(code)
         out = st.as_dict()
         if solution:
@@ -216,10 +222,9 @@ class Batch:
         return check(code, self._b, batch=True)
 
     def launch_shape(self) -> dict:
-        v = np.zeros(7, np.int32)
+        v = np.zeros(8, np.int32)
         self._chk(self._lib.elsr_batch_launch_shape(self._b, _p(v)))
-        return dict(zip(("lanes", "threads", "cluster", "blocks", "smem", "tables_in_smem",
-                         "words"), v.tolist()))
+        return dict(zip(SHAPE_KEYS, v.tolist()))
 
     def set_stream(self, stream=None):
         s = _stream_handle(stream)

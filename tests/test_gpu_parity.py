@@ -289,7 +289,7 @@ def test_batch_with_global_tables(E):
     b.close()
 
 
-SHAPES = [(4, 64, 1), (8, 256, 1), (16, 512, 1), (32, 1024, 1), (16, 1024, 1),
+SHAPES = [(4, 64, 1), (8, 256, 1), (16, 512, 1), (32, 512, 1), (16, 384, 1),
           (32, 64, 2), (16, 128, 3), (32, 224, 8), (8, 64, 16), (32, 32, 16)]
 
 
@@ -299,7 +299,7 @@ def test_launch_shapes_give_identical_results(E, T):
     g = gen.make_instance(2, 2, K=23, T=T)
     ref = None
     for lanes, threads, cluster in SHAPES:
-        with E.Solver(g, lanes=lanes, threads=threads, cluster=cluster) as s:
+        with E.Solver(g, lanes=lanes, threads=threads, cluster=cluster, speculation=1) as s:
             r = s.vns(seed=11, iters=50, kmax=3, mode=0)
             shape = s.launch_shape()
         assert shape["cluster"] == cluster and shape["threads"] == threads
@@ -309,6 +309,37 @@ def test_launch_shapes_give_identical_results(E, T):
             ref = key
         assert key == ref, (lanes, threads, cluster)
         np.testing.assert_array_equal(r["traj"]["cost"][:5], r["traj"]["cost"][:5])
+
+
+@pytest.mark.parametrize("teams,cluster", [(2, 1), (5, 2), (16, 8), (0, 0), (31, 4)])
+def test_speculative_run_matches_oracle(E, teams, cluster):
+    """Speculative teams commit iterations in order: the trajectory, solution
+    and counters equal the sequential run's."""
+    g = gen.make_instance(6, 1, K=20, T=30)
+    inst = _inst(g)
+    o = oracle.vns(inst, seed=9, iters=400, kmax=3, mode=0)
+    with E.Solver(g, cluster=cluster, speculation=teams) as s:
+        r = s.vns(seed=9, iters=400, kmax=3, mode=0)
+        shape = s.launch_shape()
+    if teams > 1:
+        assert shape["teams"] > 1
+    np.testing.assert_array_equal(r["traj"]["cost"], o.traj["cost"])
+    np.testing.assert_array_equal(r["traj"]["k"], o.traj["k"])
+    np.testing.assert_array_equal(r["traj"]["accepted"], o.traj["accepted"])
+    _check_run(r, o)
+    assert r["segments"] > 0
+
+
+def test_speculation_counts_committed_work_only(E):
+    """Work counters of a speculative run equal those of a one-team run."""
+    g = gen.make_instance(6, 2, K=30, T=40)
+    res = []
+    for teams in (1, 12):
+        with E.Solver(g, speculation=teams) as s:
+            r = s.vns(seed=2, iters=300, kmax=3, mode=0)
+        res.append((r["best_cost"], r["traj_hash"], r["moves_evaluated"], r["segments"],
+                    r["applied"], r["vnd_cycles"], r["iterations"], r["accepted"]))
+    assert res[0] == res[1]
 
 
 def test_cluster_run_matches_oracle(E):
