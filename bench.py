@@ -179,7 +179,7 @@ def run_gpu(args):
     seed = WORKLOAD["vns_seed"] + rank  # replicas: one seed per rank
     stream = torch.cuda.current_stream(dev)
     solver = elsr.Solver(g, stream=stream, lanes=args.lanes, threads=args.threads,
-                         cluster=args.cluster)
+                         cluster=args.cluster, speculation=args.speculation)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
 
     iters = args.iters if args.iters is not None else WORKLOAD["iters"]
@@ -255,7 +255,8 @@ def run_gpu(args):
     for i in range(e2e_steps + 1 if e2e_steps else 0):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        s2 = elsr.Solver(host, stream=stream)
+        s2 = elsr.Solver(host, stream=stream, lanes=args.lanes, threads=args.threads,
+                         cluster=args.cluster, speculation=args.speculation)
         s2.vns_run(seed, iters, WORKLOAD["kmax"], 0)
         r2 = s2.result(solution=True, traj=False)
         s2.close()
@@ -303,6 +304,109 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def run_batched(args):
+    """Batched workloads (secondary measurements): 'batch' = independent
+    instances K ~ U{5..100}, T ~ U{12..52} (seed 0, ids 0..n-1), one GVNS run
+    each in one persistent launch; 'multistart' = one instance K=100, T=104
+    (seed 0, id 0) with independent starts seeded 0..n-1 and a device best-of.
+    One step = one launch over the whole batch."""
+    import torch
+    from paper_1704_05132_gb300 import build, elsr, gen
+    build.build()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    if args.workload == "batch":
+        n = args.n or 1024
+        iters = args.iters if args.iters is not None else 500
+        insts = gen.batch_uneven(n)
+        b = elsr.Batch(insts, stream=stream, lanes=args.lanes, threads=args.threads,
+                       cluster=args.cluster)
+        seeds = np.arange(n, dtype=np.uint64)
+
+        def step():
+            b.run(seeds, iters, 3, 0)
+
+        def stats():
+            return b.results()
+        cfg = {"workload": f"batch of {n} instances, K ~ U{{5..100}}, T ~ U{{12..52}}, "
+                           f"{iters} iterations each, kmax=3, mode P", "instances": n,
+               "iters": iters}
+    else:
+        n = args.n or 4096
+        iters = args.iters if args.iters is not None else 1000
+        g = gen.multistart_large()
+        sv = elsr.Solver(g, stream=stream, lanes=args.lanes, threads=args.threads,
+                         cluster=args.cluster)
+        box = {}
+
+        def step():
+            box["best"] = sv.multistart(0, n, iters, 3, 0)
+
+        def stats():
+            return sv.multistart_stats(n)
+        cfg = {"workload": f"multi-start, one instance K=100 x T=104, {n} starts "
+                           f"(seeds 0..{n - 1}), {iters} iterations each, device best-of",
+               "starts": n, "iters": iters}
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ms = []
+    moves = 0
+    for _ in range(args.steps):
+        flush.add_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    st = stats()
+    moves_step = sum(r["moves_evaluated"] for r in st)
+    segs_step = sum(r["segments"] for r in st)
+    shape = b.launch_shape() if args.workload == "batch" else sv.launch_shape()
+    t = sum(ms) / 1e3
+    line = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "dtype": "int32", "data": "synthetic", "config": cfg,
+            "instances_per_s": n * args.steps / t, "launch_shape": shape}
+    line["value"] = moves_step * args.steps / t
+    line["segments_per_step"] = segs_step
+    if args.workload == "multistart":
+        line["best_of"] = box["best"][:2]
+    print(json.dumps(line), flush=True)
+
+
+def run_serve(args):
+    """Serving workload (secondary measurement): Poisson arrivals (mean
+    `--rate` requests/s) of instances K ~ U{5..200}, T ~ U{12..104} (seed 5,
+    id = request id), 300 iterations each, continuous batching over CUDA
+    streams; p50/p99 latency and instances/s."""
+    import torch
+    from paper_1704_05132_gb300 import build, serve
+    build.build()
+    torch.cuda.set_device(0)
+    n = args.n or 2000
+    iters = args.iters if args.iters is not None else 300
+    warm = serve.poisson_requests(64, args.rate, iters, seed=5, id0=10 ** 6)
+    serve.Server(slots=args.slots).run(warm, realtime=False)
+    reqs = serve.poisson_requests(n, args.rate, iters, seed=5)
+    srv = serve.Server(slots=args.slots)
+    with ClockSampler(0) as clk:
+        stats = srv.run(reqs)
+    s = stats.summary()
+    line = {"metric": METRIC, "value": s["moves_per_s"], "unit": UNIT, "n_gpus": 1,
+            "higher_is_better": True, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": f"serving, Poisson arrivals mean {args.rate:g} req/s, "
+                                   f"{n} requests K ~ U{{5..200}}, T ~ U{{12..104}}, "
+                                   f"{iters} iterations each, {args.slots} stream slots",
+                       "requests": n, "iters": iters},
+            "instances_per_s": s["instances_per_s"], "p50_ms": s["p50_ms"],
+            "p99_ms": s["p99_ms"], "mean_ms": s["mean_ms"], "batches": s["batches"],
+            "span_s": s["span_s"], "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -316,6 +420,13 @@ def main():
     ap.add_argument("--lanes", type=int, default=0, help="lanes per row (0: automatic)")
     ap.add_argument("--threads", type=int, default=0, help="threads per CTA (0: automatic)")
     ap.add_argument("--cluster", type=int, default=0, help="CTAs per run (0: automatic)")
+    ap.add_argument("--speculation", type=int, default=0,
+                    help="speculative teams for the single run (0: automatic, 1: off)")
+    ap.add_argument("--workload", default="plain",
+                    choices=["plain", "batch", "multistart", "serve"])
+    ap.add_argument("--rate", type=float, default=2000.0, help="serving arrivals per second")
+    ap.add_argument("--slots", type=int, default=4, help="serving stream slots")
+    ap.add_argument("--n", type=int, default=0, help="instances / starts of a batched workload")
     ap.add_argument("--iters", type=int, default=None,
                     help="override the iteration budget (profiling of small cases only)")
     args = ap.parse_args()
@@ -323,6 +434,10 @@ def main():
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload in ("batch", "multistart"):
+        run_batched(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_gpu(args)
 

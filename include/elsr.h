@@ -96,6 +96,13 @@ typedef struct {
 /* Version of this ABI (major * 10000 + minor * 100 + patch). */
 int elsr_version(void);
 
+/* Resources one GVNS run of a K x T instance needs: shared memory per CTA
+ * when the run uses one CTA (int32, nullable) and device memory held while
+ * it is resident in a batch (int64 bytes, nullable).  For admission control
+ * by callers that pack runs into batches. */
+int elsr_run_footprint(int32_t K, int32_t T, int32_t *smem_one_cta,
+                       int64_t *device_bytes);
+
 /* Static text for an ELSR_* code. */
 const char *elsr_strerror(int code);
 
@@ -252,6 +259,10 @@ int elsr_eval_neighbourhood_static(int32_t K, int32_t T, const int32_t *D,
                                    int64_t *pp_cost, int64_t *pp_move,
                                    void *stream);
 
+/* Statistics of the first n starts of the last elsr_multistart_run (host
+ * stats[n], start order). */
+int elsr_multistart_stats(elsr_t *h, elsr_stats_t *stats, int32_t n);
+
 /* Device moves evaluated since create (all calls on this handle). */
 int elsr_counters(elsr_t *h, int64_t *moves_evaluated);
 
@@ -267,6 +278,14 @@ int elsr_batch_create(elsr_batch_t **out, int32_t n, const int32_t *Ks,
                       const int32_t *Ts, const int32_t *D, const int32_t *R,
                       const int32_t *kM, const int32_t *kR, const int32_t *hM,
                       const int32_t *hR);
+/* As elsr_batch_create, with the batch's device memory allocated (stream
+ * ordered) and its work issued on `stream` (a cudaStream_t) from the start;
+ * elsr_batch_destroy then frees stream-ordered too, so creating and
+ * destroying batches does not synchronise the device. */
+int elsr_batch_create_on(elsr_batch_t **out, int32_t n, const int32_t *Ks,
+                         const int32_t *Ts, const int32_t *D, const int32_t *R,
+                         const int32_t *kM, const int32_t *kR,
+                         const int32_t *hM, const int32_t *hR, void *stream);
 void elsr_batch_destroy(elsr_batch_t *b);
 
 /* Message of the last failed call on batch b (b NULL: last failed create on

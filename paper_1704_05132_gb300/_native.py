@@ -49,6 +49,7 @@ P = ctypes.c_void_p
 i32, i64, u32, u64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64
 SIGNATURES = {
     "elsr_version": (ctypes.c_int, []),
+    "elsr_run_footprint": (ctypes.c_int, [i32, i32, P, P]),
     "elsr_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "elsr_last_error": (ctypes.c_char_p, [P]),
     "elsr_create": (ctypes.c_int, [ctypes.POINTER(P), i32, i32, P, P, P, P, P, P]),
@@ -67,9 +68,11 @@ SIGNATURES = {
     "elsr_result": (ctypes.c_int, [P, P, P, P, P, P, i32]),
     "elsr_multistart_run": (ctypes.c_int, [P, u64, i32, i32, i32, i32, P, P, P]),
     "elsr_counters": (ctypes.c_int, [P, P]),
+    "elsr_multistart_stats": (ctypes.c_int, [P, P, i32]),
     "elsr_eval_neighbourhood_static": (ctypes.c_int, [i32, i32, P, P, P, P, P, P, P, P,
                                                       u32, i32, P, P, P, P]),
     "elsr_batch_create": (ctypes.c_int, [ctypes.POINTER(P), i32, P, P, P, P, P, P, P, P]),
+    "elsr_batch_create_on": (ctypes.c_int, [ctypes.POINTER(P), i32, P, P, P, P, P, P, P, P, P]),
     "elsr_batch_destroy": (None, [P]),
     "elsr_batch_last_error": (ctypes.c_char_p, [P]),
     "elsr_batch_set_stream": (ctypes.c_int, [P, P]),

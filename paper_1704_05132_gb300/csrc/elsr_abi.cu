@@ -31,16 +31,19 @@ const int kVndCap = 1 << 20;
     }                                                                     \
   } while (0)
 
+// Device memory is stream-ordered (cudaMallocAsync / cudaFreeAsync on the
+// owner's stream), so allocating or freeing a batch never synchronises the
+// device while other batches run.
 template <typename T>
-cudaError_t dev_alloc(T** p, size_t n) {
+cudaError_t dev_alloc(T** p, size_t n, cudaStream_t s) {
   *p = nullptr;
   if (n == 0) n = 1;
-  return cudaMalloc((void**)p, n * sizeof(T));
+  return cudaMallocAsync((void**)p, n * sizeof(T), s);
 }
 
 template <typename T>
-void dev_free(T*& p) {
-  if (p) cudaFree((void*)p);
+void dev_free(T*& p, cudaStream_t s) {
+  if (p) cudaFreeAsync((void*)p, s);
   p = nullptr;
 }
 
@@ -98,7 +101,12 @@ int check_instance(int32_t K, int32_t T, const int32_t* D, const int32_t* R,
   return ELSR_OK;
 }
 
-int default_lanes(int T) { return T <= 8 ? 4 : (T <= 16 ? 8 : (T <= 40 ? 16 : 32)); }
+// Default lanes per row: single runs are latency-bound and spread each row
+// over more lanes; batches are throughput-bound and keep more rows in flight.
+int default_lanes(int T, bool single) {
+  if (single) return T <= 8 ? 4 : (T <= 16 ? 8 : (T <= 40 ? 16 : 32));
+  return T <= 8 ? 4 : (T <= 24 ? 8 : (T <= 64 ? 16 : 32));
+}
 
 }  // namespace
 
@@ -162,24 +170,24 @@ struct elsr_batch {
 
   ~elsr_batch() {
     if (d_insts) cudaStreamSynchronize(stream);
-    dev_free(d_insts);
-    dev_free(d_D);
-    dev_free(d_R);
-    dev_free(d_kM);
-    dev_free(d_kR);
-    dev_free(d_hM);
-    dev_free(d_hR);
-    dev_free(d_tab);
-    dev_free(d_C0);
-    dev_free(d_runs);
-    dev_free(d_out);
-    dev_free(d_bits);
-    dev_free(d_traj);
-    dev_free(d_queue);
-    dev_free(d_bestkey);
-    dev_free(d_spec_slots);
-    dev_free(d_spec_rows);
-    dev_free(d_spec_bar);
+    dev_free(d_insts, stream);
+    dev_free(d_D, stream);
+    dev_free(d_R, stream);
+    dev_free(d_kM, stream);
+    dev_free(d_kR, stream);
+    dev_free(d_hM, stream);
+    dev_free(d_hR, stream);
+    dev_free(d_tab, stream);
+    dev_free(d_C0, stream);
+    dev_free(d_runs, stream);
+    dev_free(d_out, stream);
+    dev_free(d_bits, stream);
+    dev_free(d_traj, stream);
+    dev_free(d_queue, stream);
+    dev_free(d_bestkey, stream);
+    dev_free(d_spec_slots, stream);
+    dev_free(d_spec_rows, stream);
+    dev_free(d_spec_bar, stream);
   }
 };
 
@@ -228,31 +236,32 @@ int batch_init(elsr_batch* b, int32_t n, const int32_t* Ks, const int32_t* Ts,
   (void)total_all;
   ELSR_TRY_CUDA(b, cudaGetDevice(&b->device));
   ELSR_TRY_CUDA(b, cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device));
-  ELSR_TRY_CUDA(b, dev_alloc(&b->d_insts, n));
-  ELSR_TRY_CUDA(b, dev_alloc(&b->d_D, b->cells));
-  ELSR_TRY_CUDA(b, dev_alloc(&b->d_R, b->cells));
-  ELSR_TRY_CUDA(b, dev_alloc(&b->d_kM, b->rows));
-  ELSR_TRY_CUDA(b, dev_alloc(&b->d_kR, b->rows));
-  ELSR_TRY_CUDA(b, dev_alloc(&b->d_hM, b->rows));
-  ELSR_TRY_CUDA(b, dev_alloc(&b->d_hR, b->rows));
-  ELSR_TRY_CUDA(b, dev_alloc(&b->d_queue, 1));
-  ELSR_TRY_CUDA(b, dev_alloc(&b->d_bestkey, 1));
-  ELSR_TRY_CUDA(b, cudaMemcpy(b->d_insts, b->insts.data(), n * sizeof(InstDesc), cudaMemcpyHostToDevice));
-  ELSR_TRY_CUDA(b, cudaMemcpy(b->d_D, D, b->cells * 4, cudaMemcpyHostToDevice));
-  ELSR_TRY_CUDA(b, cudaMemcpy(b->d_R, R, b->cells * 4, cudaMemcpyHostToDevice));
-  ELSR_TRY_CUDA(b, cudaMemcpy(b->d_kM, kM, b->rows * 4, cudaMemcpyHostToDevice));
-  ELSR_TRY_CUDA(b, cudaMemcpy(b->d_kR, kR, b->rows * 4, cudaMemcpyHostToDevice));
-  ELSR_TRY_CUDA(b, cudaMemcpy(b->d_hM, hM, b->rows * 4, cudaMemcpyHostToDevice));
-  ELSR_TRY_CUDA(b, cudaMemcpy(b->d_hR, hR, b->rows * 4, cudaMemcpyHostToDevice));
+  ELSR_TRY_CUDA(b, dev_alloc(&b->d_insts, n, b->stream));
+  ELSR_TRY_CUDA(b, dev_alloc(&b->d_D, b->cells, b->stream));
+  ELSR_TRY_CUDA(b, dev_alloc(&b->d_R, b->cells, b->stream));
+  ELSR_TRY_CUDA(b, dev_alloc(&b->d_kM, b->rows, b->stream));
+  ELSR_TRY_CUDA(b, dev_alloc(&b->d_kR, b->rows, b->stream));
+  ELSR_TRY_CUDA(b, dev_alloc(&b->d_hM, b->rows, b->stream));
+  ELSR_TRY_CUDA(b, dev_alloc(&b->d_hR, b->rows, b->stream));
+  ELSR_TRY_CUDA(b, dev_alloc(&b->d_queue, 1, b->stream));
+  ELSR_TRY_CUDA(b, dev_alloc(&b->d_bestkey, 1, b->stream));
+  ELSR_TRY_CUDA(b, cudaMemcpyAsync(b->d_insts, b->insts.data(), n * sizeof(InstDesc), cudaMemcpyHostToDevice, b->stream));
+  ELSR_TRY_CUDA(b, cudaMemcpyAsync(b->d_D, D, b->cells * 4, cudaMemcpyHostToDevice, b->stream));
+  ELSR_TRY_CUDA(b, cudaMemcpyAsync(b->d_R, R, b->cells * 4, cudaMemcpyHostToDevice, b->stream));
+  ELSR_TRY_CUDA(b, cudaMemcpyAsync(b->d_kM, kM, b->rows * 4, cudaMemcpyHostToDevice, b->stream));
+  ELSR_TRY_CUDA(b, cudaMemcpyAsync(b->d_kR, kR, b->rows * 4, cudaMemcpyHostToDevice, b->stream));
+  ELSR_TRY_CUDA(b, cudaMemcpyAsync(b->d_hM, hM, b->rows * 4, cudaMemcpyHostToDevice, b->stream));
+  ELSR_TRY_CUDA(b, cudaMemcpyAsync(b->d_hR, hR, b->rows * 4, cudaMemcpyHostToDevice, b->stream));
+  ELSR_TRY_CUDA(b, cudaStreamSynchronize(b->stream));  // host arrays may be freed on return
   return ELSR_OK;
 }
 
 template <typename T>
 int ensure(elsr_batch* b, T** p, size_t* cap, size_t need) {
   if (need <= *cap && *p) return ELSR_OK;
-  dev_free(*p);
+  dev_free(*p, b->stream);
   *cap = 0;
-  ELSR_TRY_CUDA(b, dev_alloc(p, need));
+  ELSR_TRY_CUDA(b, dev_alloc(p, need, b->stream));
   *cap = need;
   return ELSR_OK;
 }
@@ -303,18 +312,30 @@ int vns_shape(elsr_batch* b, LaunchShape* ls) {
              std::to_string(ls->smem) + " bytes per CTA)";
     return ELSR_E_RANGE;
   }
-  ls->G = b->lanes ? b->lanes : default_lanes(maxT);
+  const bool single = b->h_runs.size() == 1;
+  ls->G = b->lanes ? b->lanes : default_lanes(maxT, single);
   const int kc = (maxK + C - 1) / C;
   int thr = b->threads;
-  if (!thr) thr = std::min(256, std::max(64, ((kc * ls->G + 31) / 32) * 32));
+  if (!thr) thr = std::min(single ? 256 : 512, std::max(64, ((kc * ls->G + 31) / 32) * 32));
   ls->threads = thr;
   ls->maxt = thr <= 256 ? 256 : 512;
   ls->cluster = C;
   int active = 0;
-  ELSR_TRY_CUDA(b, vns_prepare(b->acc64, ls->nw, ls->ts, ls->maxt, ls->smem, thr, C, &active));
-  if (active < 1) {
-    b->err = "persistent kernel does not fit with this launch shape";
-    return ELSR_E_RANGE;
+  cudaError_t pe = vns_prepare(b->acc64, ls->nw, ls->ts, ls->maxt, ls->smem, thr, C, &active);
+  if ((pe != cudaSuccess || active < 1) && !b->threads && thr > 256) {
+    cudaGetLastError();  // retry with the smaller block bound
+    thr = 256;
+    ls->threads = thr;
+    ls->maxt = 256;
+    pe = vns_prepare(b->acc64, ls->nw, ls->ts, ls->maxt, ls->smem, thr, C, &active);
+  }
+  if (pe != cudaSuccess || active < 1) {
+    b->err = std::string("launch shape rejected (") + cudaGetErrorString(pe) +
+             "): threads " + std::to_string(thr) + ", cluster " + std::to_string(C) +
+             ", shared bytes " + std::to_string(ls->smem) + ", tables in shared " +
+             std::to_string((int)ls->ts) + ", words " + std::to_string(ls->nw);
+    cudaGetLastError();
+    return pe != cudaSuccess ? ELSR_E_CUDA : ELSR_E_RANGE;
   }
   ls->active = active;
   const int64_t nr = (int64_t)b->h_runs.size();
@@ -327,7 +348,7 @@ int vns_shape(elsr_batch* b, LaunchShape* ls) {
 
 // Queue the runs of b->h_runs (already ordered) on b->stream.
 int launch_runs(elsr_batch* b, const RowBits* start_bits, bool with_traj,
-                int64_t traj_entries) {
+                int64_t traj_entries, bool allow_spec = false) {
   LaunchShape ls;
   int rc = vns_shape(b, &ls);
   if (rc != ELSR_OK) return rc;
@@ -340,10 +361,10 @@ int launch_runs(elsr_batch* b, const RowBits* start_bits, bool with_traj,
   if (with_traj && (rc = ensure(b, &b->d_traj, &b->traj_cap, (size_t)std::max<int64_t>(traj_entries, 1))) != ELSR_OK)
     return rc;
   if (!ls.ts && !b->tab_ready) {
-    dev_free(b->d_tab);
-    dev_free(b->d_C0);
-    ELSR_TRY_CUDA(b, dev_alloc(&b->d_tab, (size_t)(b->cells + b->rows)));
-    ELSR_TRY_CUDA(b, dev_alloc(&b->d_C0, (size_t)b->rows));
+    dev_free(b->d_tab, b->stream);
+    dev_free(b->d_C0, b->stream);
+    ELSR_TRY_CUDA(b, dev_alloc(&b->d_tab, (size_t)(b->cells + b->rows), b->stream));
+    ELSR_TRY_CUDA(b, dev_alloc(&b->d_C0, (size_t)b->rows, b->stream));
     StageParams sp;
     sp.ip = b->pools();
     sp.ninst = b->n;
@@ -368,7 +389,7 @@ int launch_runs(elsr_batch* b, const RowBits* start_bits, bool with_traj,
   p.traj = with_traj ? b->d_traj : nullptr;
   p.queue = b->d_queue;
   p.spec_teams = 0;
-  p.pad2 = 0;
+  p.cluster = ls.cluster;
   p.spec_slots = nullptr;
   p.spec_rows = nullptr;
   p.spec_bar = nullptr;
@@ -376,7 +397,8 @@ int launch_runs(elsr_batch* b, const RowBits* start_bits, bool with_traj,
   // consecutive iterations (exact: the committed trajectory is the
   // sequential one).
   int teams = 1;
-  if (nr == 1 && b->h_runs[0].mode == ELSR_MODE_P && b->h_runs[0].iters > 1 && b->spec != 1) {
+  if (allow_spec && nr == 1 && b->h_runs[0].mode == ELSR_MODE_P && b->h_runs[0].iters > 1 &&
+      b->spec != 1) {
     const int resident = ls.cluster == 1 ? ls.active * b->sms : ls.active;
     const int want = b->spec > 1 ? b->spec : 16;
     teams = std::max(1, std::min({want, resident, b->h_runs[0].iters}));
@@ -384,13 +406,13 @@ int launch_runs(elsr_batch* b, const RowBits* start_bits, bool with_traj,
   cudaError_t le = cudaErrorUnknown;
   if (teams > 1) {
     if (teams > (int)b->spec_cap) {
-      dev_free(b->d_spec_slots);
-      dev_free(b->d_spec_rows);
-      dev_free(b->d_spec_bar);
+      dev_free(b->d_spec_slots, b->stream);
+      dev_free(b->d_spec_rows, b->stream);
+      dev_free(b->d_spec_bar, b->stream);
       b->spec_cap = 0;
-      ELSR_TRY_CUDA(b, dev_alloc(&b->d_spec_slots, (size_t)2 * teams));
-      ELSR_TRY_CUDA(b, dev_alloc(&b->d_spec_rows, (size_t)2 * teams * kMaxShake));
-      ELSR_TRY_CUDA(b, dev_alloc(&b->d_spec_bar, 2));
+      ELSR_TRY_CUDA(b, dev_alloc(&b->d_spec_slots, (size_t)2 * teams, b->stream));
+      ELSR_TRY_CUDA(b, dev_alloc(&b->d_spec_rows, (size_t)2 * teams * kMaxShake, b->stream));
+      ELSR_TRY_CUDA(b, dev_alloc(&b->d_spec_bar, 2, b->stream));
       b->spec_cap = teams;
     }
     ELSR_TRY_CUDA(b, cudaMemsetAsync(b->d_spec_bar, 0, 2 * sizeof(int32_t), b->stream));
@@ -402,7 +424,7 @@ int launch_runs(elsr_batch* b, const RowBits* start_bits, bool with_traj,
     le = vns_launch(b->acc64, ls.nw, ls.ts, ls.maxt, p, blocks, ls.threads, ls.smem, ls.cluster,
                     b->stream);
     if (le != cudaSuccess) {
-      cudaGetLastError();  // the cooperative launch was refused: run one team
+      cudaGetLastError();  // the speculative launch was refused: run one team
       teams = 1;
     } else {
       ls.blocks = blocks;
@@ -486,13 +508,14 @@ struct elsr_ctx {
 
   ~elsr_ctx() {
     if (b.d_insts) cudaStreamSynchronize(b.stream);
-    dev_free(d_state);
-    dev_free(d_rowcost);
-    dev_free(d_ppkey);
-    dev_free(d_scratch);
-    dev_free(d_movecost);
-    dev_free(d_movewin);
-    dev_free(d_plan);
+    const cudaStream_t stream = b.stream;
+    dev_free(d_state, stream);
+    dev_free(d_rowcost, stream);
+    dev_free(d_ppkey, stream);
+    dev_free(d_scratch, stream);
+    dev_free(d_movecost, stream);
+    dev_free(d_movewin, stream);
+    dev_free(d_plan, stream);
   }
 };
 
@@ -501,7 +524,7 @@ namespace {
 int eval_launch(elsr_ctx* h, uint32_t mask, int32_t mode, int single_j,
                 bool write_rowcost) {
   elsr_batch* b = &h->b;
-  const int G = b->lanes ? b->lanes : default_lanes(h->T);
+  const int G = b->lanes ? b->lanes : default_lanes(h->T, true);
   const int threads = 128;
   const int nsub = threads / G;
   const size_t smem = eval_smem_bytes(nsub, h->T, b->acc64);
@@ -535,6 +558,21 @@ int refresh_rowcost(elsr_ctx* h) { return eval_launch(h, 0u, 0, 0, true); }
 extern "C" {
 
 int elsr_version(void) { return 10000; }
+
+int elsr_run_footprint(int32_t K, int32_t T, int32_t* smem_one_cta, int64_t* device_bytes) {
+  if (K < 1 || T < 1 || T > ELSR_T_MAX) return ELSR_E_ARG;
+  if (smem_one_cta) {
+    const uint32_t with_tab = vns_layout(K, T, 4, true).total;
+    const uint32_t without = vns_layout(K, T, 4, false).total;
+    *smem_one_cta = (int32_t)(with_tab <= (uint32_t)kSmemLimit ? with_tab : without);
+  }
+  if (device_bytes) {
+    // instance pools, prefix tables, descriptors, solution and statistics
+    *device_bytes = (int64_t)K * T * 8 + (int64_t)K * (T + 1) * 8 + (int64_t)K * (16 + 8 + 32) +
+                    (int64_t)(sizeof(InstDesc) + sizeof(RunDesc) + sizeof(RunOut));
+  }
+  return ELSR_OK;
+}
 
 const char* elsr_strerror(int code) {
   switch (code) {
@@ -574,11 +612,11 @@ int elsr_create(elsr_t** out, int32_t K, int32_t T, const int32_t* D,
     h->T = T;
     elsr_batch* b = &h->b;
     cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = dev_alloc(&h->d_state, K);
-    if (e == cudaSuccess) e = dev_alloc(&h->d_rowcost, K);
-    if (e == cudaSuccess) e = dev_alloc(&h->d_ppkey, K);
-    if (e == cudaSuccess) e = dev_alloc(&h->d_scratch, 4);
-    if (e == cudaSuccess) e = dev_alloc(&h->d_plan, (size_t)4 * K * T);
+    if (e == cudaSuccess) e = dev_alloc(&h->d_state, K, b->stream);
+    if (e == cudaSuccess) e = dev_alloc(&h->d_rowcost, K, b->stream);
+    if (e == cudaSuccess) e = dev_alloc(&h->d_ppkey, K, b->stream);
+    if (e == cudaSuccess) e = dev_alloc(&h->d_scratch, 4, b->stream);
+    if (e == cudaSuccess) e = dev_alloc(&h->d_plan, (size_t)4 * K * T, b->stream);
     if (e != cudaSuccess) {
       b->err = std::string("device allocation: ") + cudaGetErrorString(e);
       rc = ELSR_E_NOMEM;
@@ -722,10 +760,10 @@ int elsr_move_costs(elsr_t* h, int32_t nb, int64_t* costs, int32_t* window) {
   const int64_t n = (int64_t)h->K * row_moves(h->T, nb);
   if (n <= 0) return ELSR_OK;
   elsr_batch* b = &h->b;
-  dev_free(h->d_movecost);
-  dev_free(h->d_movewin);
-  ELSR_TRY_CUDA(b, dev_alloc(&h->d_movecost, n));
-  ELSR_TRY_CUDA(b, dev_alloc(&h->d_movewin, n));
+  dev_free(h->d_movecost, b->stream);
+  dev_free(h->d_movewin, b->stream);
+  ELSR_TRY_CUDA(b, dev_alloc(&h->d_movecost, n, b->stream));
+  ELSR_TRY_CUDA(b, dev_alloc(&h->d_movewin, n, b->stream));
   int rc = eval_launch(h, 1u << (nb - 1), ELSR_MODE_P, nb, false);
   if (rc != ELSR_OK) return rc;
   ELSR_TRY_CUDA(b, cudaMemcpyAsync(costs, h->d_movecost, n * sizeof(int64_t), cudaMemcpyDeviceToHost, b->stream));
@@ -755,7 +793,7 @@ int elsr_vns_run(elsr_t* h, uint64_t seed, int32_t iters, int32_t kmax, int32_t 
   r.start_off = 0;
   r.traj_off = 0;
   b->h_runs.assign(1, r);
-  int rc = launch_runs(b, h->d_state, true, iters);
+  int rc = launch_runs(b, h->d_state, true, iters, true);
   if (rc != ELSR_OK) return rc;
   h->last_kind = 1;
   h->last_iters = iters;
@@ -775,7 +813,9 @@ int elsr_result(elsr_t* h, elsr_stats_t* stats, uint8_t* gM, uint8_t* gR,
   ELSR_TRY_CUDA(b, cudaStreamSynchronize(b->stream));
   ELSR_TRY_CUDA(b, cudaGetLastError());
   RunOut o;
-  ELSR_TRY_CUDA(b, cudaMemcpy(&o, b->d_out + h->best_out, sizeof(RunOut), cudaMemcpyDeviceToHost));
+  ELSR_TRY_CUDA(b, cudaMemcpyAsync(&o, b->d_out + h->best_out, sizeof(RunOut), cudaMemcpyDeviceToHost,
+                                   b->stream));
+  ELSR_TRY_CUDA(b, cudaStreamSynchronize(b->stream));
   if (!h->counted) {
     h->moves_total += o.moves_evaluated;
     h->counted = true;
@@ -784,7 +824,9 @@ int elsr_result(elsr_t* h, elsr_stats_t* stats, uint8_t* gM, uint8_t* gR,
   const RowBits* sol = b->d_bits + (int64_t)h->best_out * h->K;
   if (gM || gR) {
     std::vector<RowBits> rb(h->K);
-    ELSR_TRY_CUDA(b, cudaMemcpy(rb.data(), sol, h->K * sizeof(RowBits), cudaMemcpyDeviceToHost));
+    ELSR_TRY_CUDA(b, cudaMemcpyAsync(rb.data(), sol, h->K * sizeof(RowBits), cudaMemcpyDeviceToHost,
+                                     b->stream));
+    ELSR_TRY_CUDA(b, cudaStreamSynchronize(b->stream));
     unpack_bits(rb, h->K, h->T, gM, gR);
   }
   if (plan) {
@@ -801,7 +843,9 @@ int elsr_result(elsr_t* h, elsr_stats_t* stats, uint8_t* gM, uint8_t* gR,
   if (traj && traj_capacity > 0 && h->last_kind == 1) {
     const int32_t n = std::min(traj_capacity, h->last_iters);
     if (n > 0)
-      ELSR_TRY_CUDA(b, cudaMemcpy(traj, b->d_traj, n * sizeof(TrajEntry), cudaMemcpyDeviceToHost));
+      ELSR_TRY_CUDA(b, cudaMemcpyAsync(traj, b->d_traj, n * sizeof(TrajEntry), cudaMemcpyDeviceToHost,
+                                       b->stream));
+    ELSR_TRY_CUDA(b, cudaStreamSynchronize(b->stream));
   }
   return o.status;
 }
@@ -857,6 +901,24 @@ int elsr_multistart_run(elsr_t* h, uint64_t seed0, int32_t nstarts, int32_t iter
   return ELSR_OK;
 }
 
+int elsr_multistart_stats(elsr_t* h, elsr_stats_t* stats, int32_t n) {
+  if (!h || !stats || n < 0) return ELSR_E_ARG;
+  elsr_batch* b = &h->b;
+  if (h->last_kind != 2) {
+    b->err = "no multi-start run has been queued";
+    return ELSR_E_STATE;
+  }
+  const int32_t m = std::min(n, b->nruns);
+  std::vector<RunOut> outs(m > 0 ? m : 1);
+  if (m > 0) {
+    ELSR_TRY_CUDA(b, cudaMemcpyAsync(outs.data(), b->d_out, m * sizeof(RunOut),
+                                     cudaMemcpyDeviceToHost, b->stream));
+    ELSR_TRY_CUDA(b, cudaStreamSynchronize(b->stream));
+  }
+  for (int32_t i = 0; i < m; ++i) to_stats(outs[i], &stats[i]);
+  return ELSR_OK;
+}
+
 int elsr_counters(elsr_t* h, int64_t* moves) {
   if (!h || !moves) return ELSR_E_ARG;
   *moves = h->moves_total;
@@ -870,6 +932,13 @@ int elsr_batch_create(elsr_batch_t** out, int32_t n, const int32_t* Ks,
                       const int32_t* Ts, const int32_t* D, const int32_t* R,
                       const int32_t* kM, const int32_t* kR, const int32_t* hM,
                       const int32_t* hR) {
+  return elsr_batch_create_on(out, n, Ks, Ts, D, R, kM, kR, hM, hR, nullptr);
+}
+
+int elsr_batch_create_on(elsr_batch_t** out, int32_t n, const int32_t* Ks,
+                         const int32_t* Ts, const int32_t* D, const int32_t* R,
+                         const int32_t* kM, const int32_t* kR, const int32_t* hM,
+                         const int32_t* hR, void* stream) {
   if (!out) {
     g_create_error = "out is NULL";
     return ELSR_E_ARG;
@@ -880,6 +949,7 @@ int elsr_batch_create(elsr_batch_t** out, int32_t n, const int32_t* Ks,
     g_create_error = "host allocation failed";
     return ELSR_E_NOMEM;
   }
+  b->stream = (cudaStream_t)stream;
   int rc = batch_init(b, n, Ks, Ts, D, R, kM, kR, hM, hR);
   if (rc != ELSR_OK) {
     g_create_error = b->err;

@@ -11,9 +11,10 @@ namespace elsr {
 
 constexpr int kTMax = 128;
 constexpr int kMaxShake = 3;        // kmax <= 3: at most 3 shaken rows
-constexpr int kSmemLimit = 227 * 1024;
+constexpr int kSmemLimit = 227 * 1024 - 256;  // dynamic bytes; static control words take the rest
 constexpr int kStatusCap = -5;      // ELSR_E_CAP
 constexpr int kStatusTimeout = -7;  // ELSR_E_TIMEOUT
+constexpr int kStatusLaunch = -4;   // ELSR_E_CUDA: launch geometry mismatch
 
 // One instance of a batch: rows [row_off, row_off + K) of the per-row pools
 // and cells [cell_off, cell_off + K*T) of the D/R pools.
@@ -91,7 +92,7 @@ struct VnsParams {
   int32_t* queue;  // work counter, zero at launch
   // speculative single-run launches (spec_teams > 1)
   int32_t spec_teams;
-  int32_t pad2;
+  int32_t cluster;       // CTAs per team the launch was configured with
   SpecSlot* spec_slots;  // [2][spec_teams]
   RowBits* spec_rows;    // [2][spec_teams][3]
   int32_t* spec_bar;     // [2]: arrivals, generation; zero at launch

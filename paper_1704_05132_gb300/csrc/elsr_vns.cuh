@@ -354,8 +354,17 @@ __device__ __forceinline__ void team_sync(int C) {
 // Set up the team for run rd: shared-memory layout, staging of the CTA's
 // rows (one warp per row: prefix tables, constants, start bits), control
 // words, and the cache of every owned row.
+__device__ __forceinline__ uint32_t dynamic_smem_bytes() {
+  uint32_t v;
+  asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(v));
+  return v;
+}
+
+// Returns false (uniformly over the team) when the launch does not match
+// what the run needs: another cluster size than configured, or less dynamic
+// shared memory than the run's layout; nothing is touched then.
 template <typename Acc, int NW, bool TS>
-__device__ void team_begin(Team<Acc>& t, unsigned char* smem, CtlShared* sh,
+__device__ bool team_begin(Team<Acc>& t, unsigned char* smem, CtlShared* sh,
                            const VnsParams& p, const RunDesc& rd) {
   const InstDesc id = p.ip.insts[rd.inst];
   const int K = id.K, T = id.T, C = t.C, crank = t.crank;
@@ -369,6 +378,7 @@ __device__ void team_begin(Team<Acc>& t, unsigned char* smem, CtlShared* sh,
   t.vnd_cap = p.vnd_cap;
   const int Kmax = (K + C - 1) / C;
   const VnsLayout Lay = vns_layout(Kmax, T, (int)sizeof(Acc), TS);
+  if (C != p.cluster || Lay.total > dynamic_smem_bytes()) return false;
   Rows<Acc>& m = t.m;
   m.tab = TS ? (const int2*)(smem + Lay.tab) : (p.ip.gtab + id.tab_off);
   m.rc = (RowCosts*)(smem + Lay.rc);
@@ -416,6 +426,15 @@ __device__ void team_begin(Team<Acc>& t, unsigned char* smem, CtlShared* sh,
     if (qq < t.Kc) rebuild_row<Acc, NW>(m, qq, t.lane, t.G, t.smask);
     __syncwarp();
   }
+  return true;
+}
+
+__device__ __forceinline__ void write_failed_run(const VnsParams& p, const RunDesc& rd,
+                                                 int status) {
+  RunOut o = {};
+  o.best_cost = INT64_MAX;
+  o.status = status;
+  p.out[rd.out] = o;
 }
 
 // Saturating objective of the team (sum of row costs over the cluster).
@@ -732,7 +751,11 @@ __global__ void __launch_bounds__(MAXT, 1) vns_kernel(const VnsParams p) {
     team_sync(t.C);
     if (r >= p.nruns) return;
     const RunDesc rd = p.runs[r];
-    team_begin<Acc, NW, TS>(t, smem, &sh, p, rd);
+    if (!team_begin<Acc, NW, TS>(t, smem, &sh, p, rd)) {
+      if (t.crank == 0 && t.tid == 0) write_failed_run(p, rd, kStatusLaunch);
+      team_sync(t.C);
+      continue;
+    }
     const int K = t.K, T = t.T;
     const int64_t moves_per_cycle = (int64_t)K * (2 * T + (T > 1 ? 2 * (T - 1) : 0));
     int status = 0;
@@ -777,6 +800,7 @@ __global__ void __launch_bounds__(MAXT, 1) vns_kernel(const VnsParams p) {
       }
       if ((it & 255) == 255) flush_counters(t, &sh.steps, &sh.applied);
     }
+    __syncthreads();  // restores of the last iteration are complete
     for (int q = t.tid; q < t.Kc; q += t.nthr)
       p.out_bits[rd.bits_off + q * t.C + t.crank] = t.m.bits[q];
     flush_counters(t, &sh.steps, &sh.applied);
@@ -870,7 +894,10 @@ __global__ void __launch_bounds__(MAXT, 1) spec_kernel(const VnsParams p) {
   const int W = p.spec_teams;
   const int team = blockIdx.x / t.C;
   const RunDesc rd = p.runs[0];
-  team_begin<Acc, NW, TS>(t, smem, &sh, p, rd);
+  if (W < 2 || (int)gridDim.x != W * t.C || !team_begin<Acc, NW, TS>(t, smem, &sh, p, rd)) {
+    if (blockIdx.x == 0 && t.tid == 0) write_failed_run(p, rd, kStatusLaunch);
+    return;
+  }
   const int K = t.K, T = t.T;
   const int64_t moves_per_cycle = (int64_t)K * (2 * T + (T > 1 ? 2 * (T - 1) : 0));
   int status = 0;
@@ -981,6 +1008,7 @@ __global__ void __launch_bounds__(MAXT, 1) spec_kernel(const VnsParams p) {
     ++round;
   }
   // outputs (team 0)
+  __syncthreads();  // undo / adoption of the last round are complete
   if (team == 0) {
     for (int q = t.tid; q < t.Kc; q += t.nthr)
       p.out_bits[rd.bits_off + q * t.C + t.crank] = t.m.bits[q];
@@ -1041,8 +1069,10 @@ cudaError_t vns_prepare_t(size_t smem, int threads, int cluster, int* active) {
 }
 
 // Launch the batched kernel, or the speculative one when p.spec_teams > 1
-// (then blocks = teams x cluster, launched cooperatively so that every team
-// is resident for the grid barrier).
+// (then blocks = teams x cluster; the host sizes the teams to what the
+// occupancy query reports resident, and the grid barrier's waits are
+// bounded, so teams that could not all be resident end with a timeout
+// status instead of waiting forever).
 template <typename Acc, int NW, bool TS, int MAXT>
 cudaError_t vns_launch_t(const VnsParams& p, int blocks, int threads, size_t smem,
                          int cluster, cudaStream_t s) {
@@ -1065,9 +1095,7 @@ cudaError_t vns_launch_t(const VnsParams& p, int blocks, int threads, size_t sme
     cfg.numAttrs = na;
     return cudaLaunchKernelEx(&cfg, vns::vns_kernel<Acc, NW, TS, MAXT>, p);
   }
-  attr[na].id = cudaLaunchAttributeCooperative;
-  attr[na].val.cooperative = 1;
-  cfg.numAttrs = na + 1;
+  cfg.numAttrs = na;
   return cudaLaunchKernelEx(&cfg, vns::spec_kernel<Acc, NW, TS, MAXT>, p);
 }
 

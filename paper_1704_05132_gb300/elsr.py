@@ -189,6 +189,11 @@ class Solver:
         self._last_iters = 0
         return int(bc[0]), int(bs[0]), cs
 
+    def multistart_stats(self, n: int):
+        st = (nat.Stats * max(n, 1))()
+        self._chk(self._lib.elsr_multistart_stats(self._h, st, n))
+        return [s.as_dict() for s in st[:n]]
+
     def moves_evaluated(self) -> int:
         v = np.zeros(1, np.int64)
         self._chk(self._lib.elsr_counters(self._h, _p(v)))
@@ -208,11 +213,11 @@ class Batch:
         cat = lambda f: _i32(np.concatenate([np.ravel(getattr(i, f)) for i in insts]))
         arrs = [cat("D"), cat("R"), cat("kM"), cat("kR"), cat("hM"), cat("hR")]
         b = P()
-        code = lib.elsr_batch_create(ctypes.byref(b), self.n, _p(self.Ks), _p(self.Ts),
-                                     *[_p(a) for a in arrs])
+        sh = _stream_handle(stream)
+        code = lib.elsr_batch_create_on(ctypes.byref(b), self.n, _p(self.Ks), _p(self.Ts),
+                                        *[_p(a) for a in arrs], P(sh) if sh else None)
         check(code, None, batch=True)
         self._b = b
-        self.set_stream(stream)
         if lanes or threads:
             self.set_launch(lanes, threads)
         if cluster:
