@@ -1,0 +1,124 @@
+"""Autotuner for the persistent GVNS launch shape.
+
+Knobs (none changes a result; only speed):
+  lanes    -- lanes of a sub-warp that share one product row (4..32): each
+              lane evaluates ceil(|row moves| / lanes) candidates per sweep,
+              a warp holds 32 / lanes rows;
+  threads  -- threads per CTA (rows in flight per CTA = threads / lanes);
+  cluster  -- CTAs that share one run (1 for batches of small instances;
+              larger clusters split a big instance's rows over several SMs);
+  teams    -- speculative teams for a single run.
+A probe runs each candidate for a few iterations of the real workload and
+times it with CUDA events; the best moves/s wins.  Choices are cached per
+workload signature (bucketed K, T and batch size) in memory and, optionally,
+in a JSON file.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+import numpy as np
+
+from .elsr import Batch, Solver
+
+_cache: dict = {}
+
+
+def _bucket(x: int) -> int:
+    return 1 << max(0, int(x - 1).bit_length())
+
+
+def signature(insts, kind: str) -> str:
+    K = max(int(i.D.shape[0]) for i in insts)
+    T = max(int(i.D.shape[1]) for i in insts)
+    return f"{kind}:K{_bucket(K)}:T{_bucket(T)}:n{_bucket(len(insts))}"
+
+
+def _timed(fn):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    e0.record(stream)
+    out = fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1), out
+
+
+BATCH_CANDIDATES = [dict(lanes=l, threads=t, cluster=1) for l in (8, 16, 32)
+                    for t in (256, 512)]
+SINGLE_CANDIDATES = [dict(lanes=32, cluster=c, teams=s) for c in (4, 8, 16) for s in (1, 16)]
+
+
+def tune_batch(insts, probe_iters: int = 10, candidates=None, cache_file: str | None = None):
+    """Best launch shape for a batch of instances (dict lanes/threads/cluster)."""
+    key = signature(insts, "batch")
+    hit = _lookup(key, cache_file)
+    if hit:
+        return hit
+    seeds = np.arange(len(insts), dtype=np.uint64)
+    best, best_rate = None, -1.0
+    for cand in candidates or BATCH_CANDIDATES:
+        b = Batch(insts, lanes=cand["lanes"], threads=cand["threads"], cluster=cand["cluster"])
+        try:
+            b.run(seeds, 1, 3, 0)  # warm-up (kernel attributes, first touch)
+            b.results()
+            ms, _ = _timed(lambda: b.run(seeds, probe_iters, 3, 0))
+            rate = sum(r["moves_evaluated"] for r in b.results()) / ms
+        except Exception:
+            rate = -1.0
+        finally:
+            b.close()
+        if rate > best_rate:
+            best, best_rate = dict(cand), rate
+    _store(key, best, cache_file)
+    return best
+
+
+def tune_single(inst, probe_iters: int = 100, candidates=None, cache_file: str | None = None):
+    """Best launch shape for one GVNS run (dict lanes/cluster/teams)."""
+    key = signature([inst], "single")
+    hit = _lookup(key, cache_file)
+    if hit:
+        return hit
+    best, best_rate = None, -1.0
+    for cand in candidates or SINGLE_CANDIDATES:
+        with Solver(inst, lanes=cand["lanes"], cluster=cand["cluster"],
+                    speculation=cand["teams"]) as s:
+            try:
+                s.vns(0, 2, 3, 0, traj=False, solution=False)
+                ms, _ = _timed(lambda: s.vns_run(0, probe_iters, 3, 0))
+                rate = s.result(traj=False, solution=False)["moves_evaluated"] / ms
+            except Exception:
+                rate = -1.0
+        if rate > best_rate:
+            best, best_rate = dict(cand), rate
+    _store(key, best, cache_file)
+    return best
+
+
+def _lookup(key, cache_file):
+    if key in _cache:
+        return _cache[key]
+    if cache_file and os.path.exists(cache_file):
+        with open(cache_file) as f:
+            disk = json.load(f)
+        if key in disk:
+            _cache[key] = disk[key]
+            return disk[key]
+    return None
+
+
+def _store(key, value, cache_file):
+    _cache[key] = value
+    if cache_file:
+        disk = {}
+        if os.path.exists(cache_file):
+            with open(cache_file) as f:
+                disk = json.load(f)
+        disk[key] = value
+        tmp = cache_file + ".tmp"
+        with open(tmp, "w") as f:
+            json.dump(disk, f, indent=1, sort_keys=True)
+        os.replace(tmp, cache_file)

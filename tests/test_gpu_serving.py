@@ -69,3 +69,26 @@ def test_batched_beats_plain_at_equal_budget(E):
     for i in range(16):
         assert plain[i]["best_cost"] == res[i]["best_cost"]
     assert tb < tp
+
+
+def test_autotuner_picks_a_valid_shape_with_identical_results(E, tmp_path):
+    elsr, serve = E
+    from paper_1704_05132_gb300 import autotune, gen
+    insts = gen.batch_uneven(64, seed=7)
+    cache = str(tmp_path / "tune.json")
+    shape = autotune.tune_batch(insts, probe_iters=3, cache_file=cache)
+    assert shape in autotune.BATCH_CANDIDATES
+    assert autotune.tune_batch(insts, cache_file=cache) == shape   # cached
+    seeds = np.arange(64, dtype=np.uint64)
+    ref = elsr.Batch(insts)
+    ref.run(seeds, 15, 3, 0)
+    tuned = elsr.Batch(insts, lanes=shape["lanes"], threads=shape["threads"],
+                       cluster=shape["cluster"])
+    tuned.run(seeds, 15, 3, 0)
+    a, b = ref.results(), tuned.results()
+    assert [(r["best_cost"], r["traj_hash"]) for r in a] == \
+        [(r["best_cost"], r["traj_hash"]) for r in b]
+    single = autotune.tune_single(gen.plain_small(), probe_iters=20,
+                                  candidates=[dict(lanes=8, cluster=1, teams=1),
+                                              dict(lanes=8, cluster=1, teams=4)])
+    assert single["lanes"] == 8
