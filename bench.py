@@ -391,7 +391,7 @@ def run_serve(args):
     warm = serve.poisson_requests(64, args.rate, iters, seed=5, id0=10 ** 6)
     serve.Server(slots=args.slots).run(warm, realtime=False)
     reqs = serve.poisson_requests(n, args.rate, iters, seed=5)
-    srv = serve.Server(slots=args.slots)
+    srv = serve.Server(slots=args.slots, max_batch=args.max_batch)
     with ClockSampler(0) as clk:
         stats = srv.run(reqs)
     s = stats.summary()
@@ -399,7 +399,8 @@ def run_serve(args):
             "higher_is_better": True, "dtype": "int32", "data": "synthetic",
             "config": {"workload": f"serving, Poisson arrivals mean {args.rate:g} req/s, "
                                    f"{n} requests K ~ U{{5..200}}, T ~ U{{12..104}}, "
-                                   f"{iters} iterations each, {args.slots} stream slots",
+                                   f"{iters} iterations each, {args.slots} stream slots, "
+                                   f"at most {args.max_batch} requests per batch",
                        "requests": n, "iters": iters},
             "instances_per_s": s["instances_per_s"], "p50_ms": s["p50_ms"],
             "p99_ms": s["p99_ms"], "mean_ms": s["mean_ms"], "batches": s["batches"],
@@ -426,6 +427,7 @@ def main():
                     choices=["plain", "batch", "multistart", "serve"])
     ap.add_argument("--rate", type=float, default=2000.0, help="serving arrivals per second")
     ap.add_argument("--slots", type=int, default=4, help="serving stream slots")
+    ap.add_argument("--max-batch", type=int, default=304, help="serving requests per batch")
     ap.add_argument("--n", type=int, default=0, help="instances / starts of a batched workload")
     ap.add_argument("--iters", type=int, default=None,
                     help="override the iteration budget (profiling of small cases only)")
