@@ -138,7 +138,7 @@ struct PlanParams {
 // Shared-memory layout of the rows one CTA owns in the persistent GVNS
 // kernel (Kc rows of T periods).
 struct VnsLayout {
-  uint32_t tab, rc, C0, bits, S, bad, nR, A, C, L, save, slot, total;
+  uint32_t tab, rc, C0, bits, S, bad, nR, A, C, L, P, Q, save, slot, total;
 };
 
 ELSR_HD uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
@@ -167,8 +167,13 @@ ELSR_HD VnsLayout vns_layout(int Kc, int T, int acc_bytes, bool tab_smem) {
   o = align16(o + K * TT * ab);
   L.L = o;
   o = align16(o + K * TT * 8u);
-  // save slot: RowBits(32) S(8) bad(4) nR(4) | A[T] | C[T] | L[T]
-  L.slot = align16(48u + ((TT * 4u + 7u) & ~7u) + ((TT * ab + 7u) & ~7u) + TT * 8u);
+  L.P = o;
+  o = align16(o + K * (TT + 1) * 4u);
+  L.Q = o;
+  o = align16(o + K * (TT + 1) * ab);
+  // save slot: RowBits(32) S(8) bad(4) nR(4) | A[T] | C[T] | L[T] | P[T+1] | Q[T+1]
+  L.slot = align16(48u + ((TT * 4u + 7u) & ~7u) + ((TT * ab + 7u) & ~7u) + TT * 8u +
+                   (((TT + 1) * 4u + 7u) & ~7u) + (TT + 1) * ab);
   L.save = o;
   o += 2u * kMaxShake * L.slot;
   L.total = o;

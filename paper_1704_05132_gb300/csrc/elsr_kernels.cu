@@ -61,7 +61,7 @@ __global__ void stage_kernel(const StageParams p) {
 // ---------------------------------------------------------------------------
 template <typename Acc>
 struct EvalLayout {
-  uint32_t C0, A, C, L, total;
+  uint32_t C0, A, C, L, P, Q, total;
   __host__ __device__ EvalLayout(int rows, int T) {
     uint32_t o = align16((uint32_t)rows * (T + 1) * 8u);
     C0 = o;
@@ -71,7 +71,11 @@ struct EvalLayout {
     C = o;
     o = align16(o + (uint32_t)rows * T * (uint32_t)sizeof(Acc));
     L = o;
-    o += (uint32_t)rows * T * 8u;
+    o = align16(o + (uint32_t)rows * T * 8u);
+    P = o;
+    o = align16(o + (uint32_t)rows * (T + 1) * 4u);
+    Q = o;
+    o += (uint32_t)rows * (T + 1) * (uint32_t)sizeof(Acc);
     total = o;
   }
 };
@@ -93,6 +97,8 @@ __global__ void __launch_bounds__(1024) eval_kernel(const EvalParams p) {
   int32_t* A = (int32_t*)(smem + lay.A);
   Acc* C = (Acc*)(smem + lay.C);
   int2* Lst = (int2*)(smem + lay.L);
+  int32_t* Pst = (int32_t*)(smem + lay.P);
+  Acc* Qst = (Acc*)(smem + lay.Q);
 
   for (int i = warp; i < nsub; i += nwarps) {
     const int k = row0 + i;
@@ -131,6 +137,8 @@ __global__ void __launch_bounds__(1024) eval_kernel(const EvalParams p) {
   int32_t* Ak = A + sub * T;
   Acc* Ck = C + sub * T;
   int2* Lk = Lst + sub * T;
+  int32_t* Pk = Pst + sub * (T + 1);
+  Acc* Qk = Qst + sub * (T + 1);
   cur.S = 0;
   cur.bad = T;
   cur.nR = 0;
@@ -141,7 +149,7 @@ __global__ void __launch_bounds__(1024) eval_kernel(const EvalParams p) {
     cur.b = p.bits[k];
     if (lane == 0) {
       int dummy = 0;
-      cur.S = build_row<Acc, NW>(tk, T, rc, cur.b, Ak, Ck, Lk, cur.bad, cur.nR, dummy);
+      cur.S = build_row<Acc, NW>(tk, T, rc, cur.b, Ak, Ck, Lk, Pk, Qk, cur.bad, cur.nR, dummy);
     }
   }
   __syncwarp();
@@ -165,7 +173,7 @@ __global__ void __launch_bounds__(1024) eval_kernel(const EvalParams p) {
     const uint32_t goff = j == 1 ? 0u : (j == 2 ? (uint32_t)(K * T) : 2u * K * T);
     for (int l = lane; l < M; l += G) {
       int st = 0;
-      const Acc S = eval_move<Acc, NW>(tk, T, rc, cur, Ak, Ck, Lk, j, l, st);
+      const Acc S = eval_move<Acc, NW>(tk, T, rc, cur, Ak, Ck, Lk, Pk, Qk, j, l, st);
       const int64_t nc = row_cost<Acc>(S, c0);
       bestP = umin64(bestP, pack_key(nc, loff + (uint32_t)l));
       if (p.mode == 1) {

@@ -154,6 +154,8 @@ ELSR_HD bool seg_step(int s, int gm, int gr, int2 ts, int2 tn, int T,
 // Cache of the current row (per product):
 //   A[s], C[s]  at every setup s: stock entering s and S accumulated before s
 //   L[0..nR)    the row's gR setups in period order: {need(s), s | gM(s)<<16}
+//   P, Q[0..nR] exclusive prefix sums over L of room = max(0, need - A) and
+//               hR*(T-s)*room
 // bad = T when the row is feasible; else the first setup whose segment falls
 // short (-1 when demand precedes the first setup); A/C/L are valid before bad.
 template <typename Acc>
@@ -207,13 +209,17 @@ ELSR_HD int rank_below(uint64_t w0, uint64_t w1, int s) {
 }
 
 // Decode a whole row from its bits, writing the cache.  Returns S (Inf when
-// infeasible) and sets bad and nR.  segs counts the segments walked.
+// infeasible) and sets bad and nR.  P, Q ([nR+1]) receive exclusive prefix
+// sums over the gR list of room(r) = max(0, need - avail) and
+// hR*(T-s)*room(r).  segs counts the segments walked.
 template <typename Acc, int NW>
 ELSR_HD Acc build_row(const int2* tab, int T, const RowCosts& rc,
-                      const RowBits& b, int32_t* A, Acc* C, int2* L, int& bad,
-                      int& nR, int& segs) {
+                      const RowBits& b, int32_t* A, Acc* C, int2* L,
+                      int32_t* P, Acc* Q, int& bad, int& nR, int& segs) {
   const uint64_t u0 = b.m0 | b.r0, u1 = b.m1 | b.r1;
   nR = 0;
+  P[0] = 0;
+  Q[0] = 0;
   int s = nxt<NW>(u0, u1, -1, T);
   int2 ts = tab[s];
   if (ts.x != 0) {  // demand before the first setup
@@ -233,7 +239,11 @@ ELSR_HD Acc build_row(const int2* tab, int T, const RowCosts& rc,
       int2 e;
       e.x = tn.x - ts.x;
       e.y = s | (gm << 16);
-      L[nR++] = e;
+      L[nR] = e;
+      const int32_t room = e.x > avail ? e.x - avail : 0;
+      P[nR + 1] = P[nR] + room;
+      Q[nR + 1] = Q[nR] + (Acc)rc.hR * (Acc)(T - s) * (Acc)room;
+      ++nR;
     }
     if (!seg_step<Acc>(s, gm, gr, ts, tn, T, rc, avail, S)) {
       bad = s;
@@ -263,8 +273,8 @@ ELSR_HD Acc build_row(const int2* tab, int T, const RowCosts& rc,
 template <typename Acc, int NW>
 ELSR_HD Acc eval_move(const int2* tab, int T, const RowCosts& rc,
                       const RowState<Acc>& cur, const int32_t* A,
-                      const Acc* C, const int2* L, int j, int local,
-                      int& steps) {
+                      const Acc* C, const int2* L, const int32_t* P,
+                      const Acc* Q, int j, int local, int& steps) {
   RowBits nb = cur.b;
   int t1, other;
   if (j == 1) {
@@ -317,11 +327,36 @@ ELSR_HD Acc eval_move(const int2* tab, int T, const RowCosts& rc,
     ts = tn;
   }
   if (s >= T) return S;
-  // suffix: cached cost plus the stock-difference walk over gR setups
+  // suffix: cached cost plus the effect of the stock difference delta
   int32_t delta = avail - A[s];
   S += cur.S - C[s];
   if (delta == 0) return S;
-  for (int r = rank_below<NW>(cur.b.r0, cur.b.r1, s); r < cur.nR; ++r) {
+  const int r0 = rank_below<NW>(cur.b.r0, cur.b.r1, s);
+  if (delta > 0) {
+    // More stock: each later gR setup absorbs up to its room (need minus the
+    // stock it had), lowering xM by as much, until delta is used up.  With
+    // the prefix sums P (room) and Q (hR*(T-s)*room) the setup z where the
+    // rest of delta is absorbed is a binary search, and the cost is closed
+    // form.  The step count is that of the walk: z - r0 + 1 setups (or all
+    // remaining ones when delta is never used up).
+    const int32_t target = P[r0] + delta;
+    if (P[cur.nR] < target) {
+      steps += cur.nR - r0;
+      return S - (Q[cur.nR] - Q[r0]);
+    }
+    int lo = r0, hi = cur.nR - 1;  // smallest z with P[z+1] >= target
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (P[mid + 1] >= target) hi = mid; else lo = mid + 1;
+    }
+    steps += lo - r0 + 1;
+    const int sz = L[lo].y & 0xFFFF;
+    return S - (Q[lo] - Q[r0]) -
+           (Acc)rc.hR * (Acc)(T - sz) * (Acc)(target - P[lo]);
+  }
+  // Less stock: walk the gR setups while delta < 0 (a shortfall at a
+  // remanufacture-only setup is infeasible).
+  for (int r = r0; r < cur.nR; ++r) {
     const int2 e = L[r];
     const int sr = e.y & 0xFFFF;
     const int32_t a = A[sr];

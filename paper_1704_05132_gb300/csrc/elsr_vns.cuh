@@ -101,6 +101,8 @@ struct Rows {
   int32_t* A;  // [Kc][T]
   Acc* C;      // [Kc][T]
   int2* L;     // [Kc][T]
+  int32_t* P;  // [Kc][T+1]
+  Acc* Q;      // [Kc][T+1]
   unsigned char* save;
   uint32_t slot;
   int T, C_, crank;
@@ -132,6 +134,14 @@ template <typename Acc>
 __device__ __forceinline__ uint32_t slot_L_off(int T) {
   return slot_C_off<Acc>(T) + ((((uint32_t)T * (uint32_t)sizeof(Acc)) + 7u) & ~7u);
 }
+template <typename Acc>
+__device__ __forceinline__ uint32_t slot_P_off(int T) {
+  return slot_L_off<Acc>(T) + (uint32_t)T * 8u;
+}
+template <typename Acc>
+__device__ __forceinline__ uint32_t slot_Q_off(int T) {
+  return slot_P_off<Acc>(T) + ((((uint32_t)T + 1u) * 4u + 7u) & ~7u);
+}
 
 // Copy local row q to / from a save slot (sub-warp collective).
 template <typename Acc>
@@ -141,11 +151,17 @@ __device__ __forceinline__ void save_row(const Rows<Acc>& m, int q, unsigned cha
   int32_t* sA = (int32_t*)(sl + 48);
   Acc* sC = (Acc*)(sl + slot_C_off<Acc>(T));
   int2* sL = (int2*)(sl + slot_L_off<Acc>(T));
+  int32_t* sP = (int32_t*)(sl + slot_P_off<Acc>(T));
+  Acc* sQ = (Acc*)(sl + slot_Q_off<Acc>(T));
   const int nr = m.nR[q];
   for (int s = lane; s < T; s += G) {
     sA[s] = m.A[q * T + s];
     sC[s] = m.C[q * T + s];
     if (s < nr) sL[s] = m.L[q * T + s];
+  }
+  for (int s = lane; s <= nr; s += G) {
+    sP[s] = m.P[q * (T + 1) + s];
+    sQ[s] = m.Q[q * (T + 1) + s];
   }
   if (lane == 0) {
     *(RowBits*)sl = m.bits[q];
@@ -162,11 +178,17 @@ __device__ __forceinline__ void restore_row(const Rows<Acc>& m, int q,
   const int32_t* sA = (const int32_t*)(sl + 48);
   const Acc* sC = (const Acc*)(sl + slot_C_off<Acc>(T));
   const int2* sL = (const int2*)(sl + slot_L_off<Acc>(T));
+  const int32_t* sP = (const int32_t*)(sl + slot_P_off<Acc>(T));
+  const Acc* sQ = (const Acc*)(sl + slot_Q_off<Acc>(T));
   const int nr = *(const int32_t*)(sl + 44);
   for (int s = lane; s < T; s += G) {
     m.A[q * T + s] = sA[s];
     m.C[q * T + s] = sC[s];
     if (s < nr) m.L[q * T + s] = sL[s];
+  }
+  for (int s = lane; s <= nr; s += G) {
+    m.P[q * (T + 1) + s] = sP[s];
+    m.Q[q * (T + 1) + s] = sQ[s];
   }
   if (lane == 0) {
     m.bits[q] = *(const RowBits*)sl;
@@ -187,12 +209,14 @@ __device__ __forceinline__ uint64_t row_best(const Rows<Acc>& m, int q,
   const int32_t* Aq = m.A + q * T;
   const Acc* Cq = m.C + q * T;
   const int2* Lq = m.L + q * T;
+  const int32_t* Pq = m.P + q * (T + 1);
+  const Acc* Qq = m.Q + q * (T + 1);
   const RowCosts rc = m.rc[q];
   const int64_t c0 = m.C0[q];
   uint64_t best = ~0ull;
   int st = 0;
   for (int l = lane; l < M; l += G) {
-    const Acc S = eval_move<Acc, NW>(tk, T, rc, cur, Aq, Cq, Lq, j, l, st);
+    const Acc S = eval_move<Acc, NW>(tk, T, rc, cur, Aq, Cq, Lq, Pq, Qq, j, l, st);
     best = umin64(best, pack_key(row_cost<Acc>(S, c0), (uint32_t)l));
   }
   steps += (uint32_t)st;
@@ -224,6 +248,8 @@ __device__ __forceinline__ void rebuild_row(const Rows<Acc>& m, int q, int lane,
   int32_t* A = m.A + q * T;
   Acc* C = m.C + q * T;
   int2* L = m.L + q * T;
+  int32_t* Pr = m.P + q * (T + 1);
+  Acc* Qr = m.Q + q * (T + 1);
   const int P = (T + G - 1) / G;
   const int a = lane * P, e = a + P < T ? a + P : T;
   // phase 1: composition of this lane's period functions
@@ -258,9 +284,11 @@ __device__ __forceinline__ void rebuild_row(const Rows<Acc>& m, int q, int lane,
   }
   int64_t y = ep > eq ? ep : eq;  // stock entering period a
   // phase 3: cache entries with local prefix sums
-  Acc lsum = 0;
+  Acc lsum = 0, lwroom = 0;
+  int32_t lroom = 0;
   int first_bad = T;
-  int r = rank_below<NW>(b.r0, b.r1, a);
+  const int r_begin = rank_below<NW>(b.r0, b.r1, a);
+  int r = r_begin;
   for (int t = a; t < e; ++t) {
     const int2 tt = tab[t];
     const int32_t Rt = tt.y - (t > 0 ? tab[t - 1].y : 0);
@@ -279,21 +307,42 @@ __device__ __forceinline__ void rebuild_row(const Rows<Acc>& m, int q, int lane,
         int2 en;
         en.x = need;
         en.y = t | (gm << 16);
-        L[r++] = en;
+        L[r] = en;
+        Pr[r] = lroom;
+        Qr[r] = lwroom;
+        const int32_t room = need > avail ? need - avail : 0;
+        lroom += room;
+        lwroom += (Acc)rc.hR * (Acc)(T - t) * (Acc)room;
+        ++r;
       }
       y = avail - xr;
     } else {
       y = avail;
     }
   }
-  // phase 4: offsets of C, first shortfall, total
-  Acc off = lsum;
+  // phase 4: offsets of C, P, Q; first shortfall; totals
+  Acc off = lsum, offQ = lwroom;
+  int32_t offP = lroom;
   for (int o = 1; o < G; o <<= 1) {
     const Acc v = __shfl_up_sync(smask, off, o, G);
-    if (lane >= o) off += v;
+    const Acc vq = __shfl_up_sync(smask, offQ, o, G);
+    const int32_t vp = __shfl_up_sync(smask, offP, o, G);
+    if (lane >= o) {
+      off += v;
+      offQ += vq;
+      offP += vp;
+    }
   }
   const Acc total = __shfl_sync(smask, off, G - 1, G);
+  const Acc totQ = __shfl_sync(smask, offQ, G - 1, G);
+  const int32_t totP = __shfl_sync(smask, offP, G - 1, G);
   off -= lsum;
+  offQ -= lwroom;
+  offP -= lroom;
+  for (int i = r_begin; i < r; ++i) {
+    Pr[i] += offP;
+    Qr[i] += offQ;
+  }
   for (int o = G >> 1; o > 0; o >>= 1) {
     const int v = __shfl_xor_sync(smask, first_bad, o, G);
     first_bad = v < first_bad ? v : first_bad;
@@ -307,7 +356,10 @@ __device__ __forceinline__ void rebuild_row(const Rows<Acc>& m, int q, int lane,
     if (tab[f].x != 0) bad = -1;  // demand before the first setup
     m.bad[q] = bad;
     m.S[q] = bad == T ? total : Inf<Acc>::value;
-    m.nR[q] = popc64(b.r0) + (NW == 1 ? 0 : popc64(b.r1));
+    const int nr = popc64(b.r0) + (NW == 1 ? 0 : popc64(b.r1));
+    m.nR[q] = nr;
+    Pr[nr] = totP;
+    Qr[nr] = totQ;
   }
 }
 
@@ -390,6 +442,8 @@ __device__ bool team_begin(Team<Acc>& t, unsigned char* smem, CtlShared* sh,
   m.A = (int32_t*)(smem + Lay.A);
   m.C = (Acc*)(smem + Lay.C);
   m.L = (int2*)(smem + Lay.L);
+  m.P = (int32_t*)(smem + Lay.P);
+  m.Q = (Acc*)(smem + Lay.Q);
   m.save = smem + Lay.save;
   m.slot = Lay.slot;
   m.T = T;
@@ -578,7 +632,8 @@ __device__ int vnd_g(Team<Acc>& t) {
           int st = 0;
           for (int l = t.lane; l < M; l += t.G) {
             const Acc S = eval_move<Acc, NW>(tk, T, rc, cur, t.m.A + q * T, t.m.C + q * T,
-                                             t.m.L + q * T, j, l, st);
+                                             t.m.L + q * T, t.m.P + q * (T + 1),
+                                             t.m.Q + q * (T + 1), j, l, st);
             const int64_t nc = row_cost<Acc>(S, c0);
             const int64_t nt = (others == INT64_MAX || nc == INT64_MAX) ? INT64_MAX : others + nc;
             best = umin64(best, pack_key(nt, (uint32_t)(q * M + l)));

@@ -39,14 +39,16 @@ int64_t move_costs(int T, const int32_t* D, const int32_t* R,
   std::vector<int32_t> A(T, 0);
   std::vector<Acc> C(T, 0);
   std::vector<int2> L(T, int2{0, 0});
+  std::vector<int32_t> Pv(T + 1, 0);
+  std::vector<Acc> Qv(T + 1, 0);
   int segs = 0;
   st.S = build_row<Acc, NW>(tab.data(), T, rc, st.b, A.data(), C.data(), L.data(),
-                            st.bad, st.nR, segs);
+                            Pv.data(), Qv.data(), st.bad, st.nR, segs);
   const int M = row_moves(T, j);
   for (int m = 0; m < M; ++m) {
     int steps = 0;
     const Acc S = eval_move<Acc, NW>(tab.data(), T, rc, st, A.data(), C.data(),
-                                     L.data(), j, m, steps);
+                                     L.data(), Pv.data(), Qv.data(), j, m, steps);
     out[m] = row_cost<Acc>(S, C0);
     steps_out[m] = steps;
   }
