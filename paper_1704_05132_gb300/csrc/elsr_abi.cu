@@ -104,7 +104,7 @@ int check_instance(int32_t K, int32_t T, const int32_t* D, const int32_t* R,
 // Default lanes per row: single runs are latency-bound and spread each row
 // over more lanes; batches are throughput-bound and keep more rows in flight.
 int default_lanes(int T, bool single) {
-  if (single) return T <= 8 ? 4 : (T <= 16 ? 8 : (T <= 40 ? 16 : 32));
+  if (single) return T <= 8 ? 4 : (T <= 16 ? 8 : (T <= 24 ? 16 : (T <= 40 ? 32 : 64)));
   return T <= 8 ? 4 : (T <= 24 ? 8 : (T <= 64 ? 16 : 32));
 }
 
@@ -314,9 +314,15 @@ int vns_shape(elsr_batch* b, LaunchShape* ls) {
   }
   const bool single = b->h_runs.size() == 1;
   ls->G = b->lanes ? b->lanes : default_lanes(maxT, single);
+  if (ls->G > 32 && any_g) ls->G = 32;  // rows wider than a warp: mode P only
   const int kc = (maxK + C - 1) / C;
   int thr = b->threads;
-  if (!thr) thr = std::min(single ? 256 : 512, std::max(64, ((kc * ls->G + 31) / 32) * 32));
+  if (!thr) thr = std::min(single && ls->G <= 32 ? 256 : 512, std::max(64, ((kc * ls->G + 31) / 32) * 32));
+  if (ls->G > 32) {
+    thr = std::max(thr, ls->G);
+    thr -= thr % ls->G;
+    thr = std::min(thr, 15 * ls->G);  // named barriers 1..15, one per row group
+  }
   ls->threads = thr;
   ls->maxt = thr <= 256 ? 256 : 512;
   ls->cluster = C;
@@ -524,7 +530,8 @@ namespace {
 int eval_launch(elsr_ctx* h, uint32_t mask, int32_t mode, int single_j,
                 bool write_rowcost) {
   elsr_batch* b = &h->b;
-  const int G = b->lanes ? b->lanes : default_lanes(h->T, true);
+  // the evaluation kernel reduces within a warp: at most 32 lanes per row
+  const int G = std::min(32, b->lanes ? b->lanes : default_lanes(h->T, true));
   const int threads = 128;
   const int nsub = threads / G;
   const size_t smem = eval_smem_bytes(nsub, h->T, b->acc64);
@@ -974,8 +981,9 @@ int elsr_batch_set_stream(elsr_batch_t* b, void* stream) {
 
 int elsr_batch_set_launch(elsr_batch_t* b, int32_t lanes, int32_t threads) {
   if (!b) return ELSR_E_ARG;
-  if (lanes && lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32) {
-    b->err = "lanes_per_row must be 4, 8, 16 or 32";
+  if (lanes && lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32 && lanes != 64 &&
+      lanes != 128) {
+    b->err = "lanes_per_row must be 4, 8, 16, 32, 64 or 128";
     return ELSR_E_ARG;
   }
   if (threads && (threads % 32 || threads < 32 || threads > 512)) {

@@ -11,7 +11,7 @@ namespace elsr {
 
 constexpr int kTMax = 128;
 constexpr int kMaxShake = 3;        // kmax <= 3: at most 3 shaken rows
-constexpr int kSmemLimit = 227 * 1024 - 256;  // dynamic bytes; static control words take the rest
+constexpr int kSmemLimit = 227 * 1024 - 1024;  // dynamic bytes; static control words (< 1 KB) take the rest
 constexpr int kStatusCap = -5;      // ELSR_E_CAP
 constexpr int kStatusTimeout = -7;  // ELSR_E_TIMEOUT
 constexpr int kStatusLaunch = -4;   // ELSR_E_CUDA: launch geometry mismatch

@@ -377,7 +377,10 @@ struct CtlShared {
   unsigned long long gkey[2];
   long long F;
   unsigned long long applied, steps;
+  unsigned long long gmin[64];  // per row group and warp: partial minima (groups > 32 lanes)
 };
+// kSmemLimit leaves 1 KB of the CTA's shared memory to static words.
+static_assert(sizeof(CtlShared) <= 768, "static control words outgrow their reserve");
 
 template <typename Acc>
 struct Team {
@@ -394,6 +397,42 @@ struct Team {
     return k >= 0 && (k % C) == crank && ((k / C) % nsub) == sub;
   }
 };
+
+// Row groups wider than a warp (G = 64 or 128 lanes, mode P): the group's
+// warps meet at named barrier 1 + group index.
+template <typename Acc>
+__device__ __forceinline__ void group_sync(const Team<Acc>& t) {
+  if (t.G <= 32) {
+    __syncwarp(t.smask);
+  } else {
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + t.sub), "r"(t.G) : "memory");
+  }
+}
+
+// Minimum of a key over the row group.
+template <typename Acc>
+__device__ __forceinline__ uint64_t group_min(const Team<Acc>& t, uint64_t v) {
+  if (t.G <= 32) return subwarp_min(v, t.G);
+  v = subwarp_min(v, 32);
+  if (t.wlane == 0) t.sh->gmin[t.sub * 4 + (t.lane >> 5)] = v;
+  group_sync(t);
+  uint64_t m = ~0ull;
+  for (int w = 0; w < (t.G >> 5); ++w) m = umin64(m, t.sh->gmin[t.sub * 4 + w]);
+  group_sync(t);
+  return m;
+}
+
+// Rebuild of local row q by the row group (its first warp when the group is
+// wider than a warp), then a group barrier.
+template <typename Acc, int NW>
+__device__ __forceinline__ void group_rebuild(const Team<Acc>& t, int q) {
+  if (t.G <= 32) {
+    rebuild_row<Acc, NW>(t.m, q, t.lane, t.G, t.smask);
+  } else if (t.lane < 32) {
+    rebuild_row<Acc, NW>(t.m, q, t.lane, 32, kFull);
+  }
+  group_sync(t);
+}
 
 __device__ __forceinline__ void team_sync(int C) {
   if (C == 1) {
@@ -477,8 +516,8 @@ __device__ bool team_begin(Team<Acc>& t, unsigned char* smem, CtlShared* sh,
   }
   __syncthreads();
   for (int qq = t.sub; qq < t.Kcr; qq += t.nsub) {
-    if (qq < t.Kc) rebuild_row<Acc, NW>(m, qq, t.lane, t.G, t.smask);
-    __syncwarp();
+    if (qq < t.Kc) group_rebuild<Acc, NW>(t, qq);
+    if (t.G <= 32) __syncwarp();
   }
   return true;
 }
@@ -553,7 +592,7 @@ __device__ int vnd_p(Team<Acc>& t) {
           const RowState<Acc> cur = t.m.state(q);
           best = row_best<Acc, NW>(t.m, q, cur, j, M, t.lane, t.G, t.steps);
         }
-        best = subwarp_min(best, t.G);
+        best = group_min(t, best);
         const bool imp = valid && key_cost(best) < t.m.cost(q);
         if (imp) {
           if (t.lane == 0) {
@@ -562,11 +601,11 @@ __device__ int vnd_p(Team<Acc>& t) {
             t.m.bits[q] = nb;
             ++t.applied;
           }
-          __syncwarp(t.smask);
-          rebuild_row<Acc, NW>(t.m, q, t.lane, t.G, t.smask);
+          group_sync(t);
+          group_rebuild<Acc, NW>(t, q);
           improved = 1;
         }
-        __syncwarp();
+        if (t.G <= 32) __syncwarp();
       }
     }
     ++cycles;
@@ -724,22 +763,23 @@ __device__ void apply_shake(Team<Acc>& t, const ShakePlan& pl, int ks, int par) 
 #pragma unroll
   for (int j = 0; j < kMaxShake; ++j) {
     const int k = pl.rows[j];
-    const bool mine = t.owns(k);
-    if (mine && pl.first[j]) save_row<Acc>(t.m, k / t.C, t.m.slot_ptr(par, j), t.lane, t.G);
-    __syncwarp();
-    if (mine && t.lane == 0) {
-      RowBits b = t.m.bits[k / t.C];
-      apply_row_move(b, t.T, ks, pl.locs[j]);
-      t.m.bits[k / t.C] = b;
+    if (t.owns(k)) {  // uniform over the row group
+      if (pl.first[j]) save_row<Acc>(t.m, k / t.C, t.m.slot_ptr(par, j), t.lane, t.G);
+      group_sync(t);
+      if (t.lane == 0) {
+        RowBits b = t.m.bits[k / t.C];
+        apply_row_move(b, t.T, ks, pl.locs[j]);
+        t.m.bits[k / t.C] = b;
+      }
+      group_sync(t);
     }
-    __syncwarp();
   }
 #pragma unroll
   for (int j = 0; j < kMaxShake; ++j) {
     const int k = pl.rows[j];
-    if (t.owns(k) && pl.first[j]) rebuild_row<Acc, NW>(t.m, k / t.C, t.lane, t.G, t.smask);
-    __syncwarp();
+    if (t.owns(k) && pl.first[j]) group_rebuild<Acc, NW>(t, k / t.C);
   }
+  if (t.G <= 32) __syncwarp();
 }
 
 // Undo a shake: the shaken rows go back to x (the other rows never moved:
@@ -749,9 +789,12 @@ __device__ void undo_shake(Team<Acc>& t, const ShakePlan& pl, int par) {
 #pragma unroll
   for (int j = 0; j < kMaxShake; ++j) {
     const int k = pl.rows[j];
-    if (t.owns(k) && pl.first[j]) restore_row<Acc>(t.m, k / t.C, t.m.slot_ptr(par, j), t.lane, t.G);
-    __syncwarp();
+    if (t.owns(k) && pl.first[j]) {
+      restore_row<Acc>(t.m, k / t.C, t.m.slot_ptr(par, j), t.lane, t.G);
+      group_sync(t);
+    }
   }
+  if (t.G <= 32) __syncwarp();
 }
 
 // Fold this CTA's per-thread counters into its control words.
@@ -785,7 +828,7 @@ __device__ __forceinline__ void team_init(Team<Acc>& t, int G) {
   t.wlane = t.tid & 31;
   t.warp = t.tid >> 5;
   t.nwarps = t.nthr >> 5;
-  t.smask = G == 32 ? kFull : (((1u << G) - 1u) << (t.wlane & ~(G - 1)));
+  t.smask = G >= 32 ? kFull : (((1u << G) - 1u) << (t.wlane & ~(G - 1)));
 }
 
 // ---------------------------------------------------------------------------
@@ -1046,10 +1089,10 @@ __global__ void __launch_bounds__(MAXT, 1) spec_kernel(const VnsParams p) {
         if (t.owns(k) && pw.first[j]) {
           if (t.lane == 0)
             t.m.bits[k / t.C] = ldcg_bits(p.spec_rows + (par * W + a) * kMaxShake + j);
-          __syncwarp(t.smask);
-          rebuild_row<Acc, NW>(t.m, k / t.C, t.lane, t.G, t.smask);
+          group_sync(t);
+          group_rebuild<Acc, NW>(t, k / t.C);
         }
-        __syncwarp();
+        if (t.G <= 32) __syncwarp();
       }
     }
     if (a >= 0) {

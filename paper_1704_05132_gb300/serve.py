@@ -28,7 +28,7 @@ import numpy as np
 from . import _native as nat
 from .elsr import Batch
 
-SMEM_ONE_CTA = 227 * 1024 - 256  # dynamic shared bytes per CTA (static control words take the rest)
+SMEM_ONE_CTA = 227 * 1024 - 1024  # dynamic shared bytes per CTA (static control words < 1 KB)
 
 
 @dataclass
