@@ -134,7 +134,7 @@ int elsr_set_stream(elsr_t *h, void *stream);
 
 /* Kernel launch shape: lanes per product row (4, 8, 16 or 32 lanes of one
  * warp; 64 or 128 = a row spread over 2 or 4 warps, mode P only) and threads
- * per block (multiple of 32 and of the lanes, <= 512); 0 keeps the default. */
+ * per block (multiple of 32 and of the lanes, <= 1024); 0 keeps the default. */
 int elsr_set_launch(elsr_t *h, int32_t lanes_per_row, int32_t threads);
 
 /* CTAs of one thread-block cluster that share a GVNS run of this handle

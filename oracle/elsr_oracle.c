@@ -534,8 +534,15 @@ void orc_initial_solution(int32_t K, int32_t T, uint8_t *gM, uint8_t *gR)
 /* Per-period decode of one row (same rule as orc_decode_row) recording the
  * recoverable stock yR(t) and the first period where the row falls short
  * (T when feasible). */
-static int32_t decode_stock(const orc_instance *in, int32_t k, const uint8_t *gM,
-                            const uint8_t *gR, int64_t *yR)
+/*
+ * Recoverable stock after every period under the decode rule; returns the
+ * first period that falls short (T when none).  With `relaxed` set, a
+ * remanufacture-only setup that falls short takes all the stock it has and
+ * its deficit counts as manufactured, and the decode goes on (demand before
+ * the first setup still ends it).
+ */
+static int32_t decode_stock_mode(const orc_instance *in, int32_t k, const uint8_t *gM,
+                                 const uint8_t *gR, int64_t *yR, int relaxed)
 {
     const int32_t T = in->T;
     const int32_t *D = in->D + (int64_t)k * T, *R = in->R + (int64_t)k * T;
@@ -548,7 +555,11 @@ static int32_t decode_stock(const orc_instance *in, int32_t k, const uint8_t *gM
             int64_t need = -yMp;
             for (int32_t i = t; i < n; ++i) need += D[i];
             if (gR[t]) xr = avail < need ? avail : need;
-            if (gM[t]) xm = need - xr; else if (xr < need) return t;
+            if (gM[t]) xm = need - xr;
+            else if (xr < need) {
+                if (!relaxed) return t;
+                xm = need - xr;
+            }
         }
         int64_t yM = yMp + xm + xr - D[t];
         if (yM < 0) return t;
@@ -559,6 +570,12 @@ static int32_t decode_stock(const orc_instance *in, int32_t k, const uint8_t *gM
     return T;
 }
 
+static int32_t decode_stock(const orc_instance *in, int32_t k, const uint8_t *gM,
+                            const uint8_t *gR, int64_t *yR)
+{
+    return decode_stock_mode(in, k, gM, gR, yR, 0);
+}
+
 /*
  * Decode steps an incremental evaluation of one move needs, a work measure
  * used to express throughput as integer operations per second:
@@ -567,10 +584,12 @@ static int32_t decode_stock(const orc_instance *in, int32_t k, const uint8_t *gM
  *   - one step per setup segment of the moved row from s0 (the last period
  *     <= t1 holding a setup before and after the move; else the row's first
  *     setup) while the segment starts at or before t2 (t1..t2 = changed
- *     periods), or up to the end of the row when the row before the move
- *     falls short somewhere;
+ *     periods), or up to the end of the row when the row before the move has
+ *     demand before its first setup;
  *   - then one step per later gR setup while the recoverable stock entering
- *     it differs between the rows before and after the move;
+ *     it differs between the moved row and the row before the move, the
+ *     latter in its relaxed decode (a remanufacture-only setup that falls
+ *     short counts its deficit as manufactured and the decode goes on);
  * stopping at the first segment that falls short.
  */
 int64_t orc_move_window(const orc_instance *in, int32_t k, const uint8_t *gM,
@@ -592,7 +611,8 @@ int64_t orc_move_window(const orc_instance *in, int32_t k, const uint8_t *gM,
         }
     if (t1 < 0) goto done;
 
-    int32_t ofail = decode_stock(in, k, gM, gR, yo);
+    int32_t ofail = decode_stock(in, k, gM, gR, yn);
+    decode_stock_mode(in, k, gM, gR, yo, 1);
     int32_t nfail = decode_stock(in, k, nm, nr, yn);
     int32_t bad = ofail; /* setup of the failing segment, -1 before any setup */
     if (ofail < T && !(gM[ofail] || gR[ofail])) bad = -1;
@@ -615,7 +635,7 @@ int64_t orc_move_window(const orc_instance *in, int32_t k, const uint8_t *gM,
         for (int32_t i = 0; i < s; ++i) dsum += in->D[(int64_t)k * T + i];
         if (dsum > 0) goto done;
     }
-    while (s < T && (s <= t2 || bad < T)) {
+    while (s < T && (s <= t2 || bad < 0)) {
         ++count;
         if (nfail == s) goto done;
         int32_t n = s + 1;

@@ -147,6 +147,7 @@ struct elsr_batch {
   SpecSlot* d_spec_slots = nullptr;
   RowBits* d_spec_rows = nullptr;
   int32_t* d_spec_bar = nullptr;
+  int32_t* d_spec_dec = nullptr;
   size_t spec_cap = 0;
 
   std::vector<RunDesc> h_runs;
@@ -188,6 +189,7 @@ struct elsr_batch {
     dev_free(d_spec_slots, stream);
     dev_free(d_spec_rows, stream);
     dev_free(d_spec_bar, stream);
+    dev_free(d_spec_dec, stream);
   }
 };
 
@@ -324,7 +326,7 @@ int vns_shape(elsr_batch* b, LaunchShape* ls) {
     thr = std::min(thr, 15 * ls->G);  // named barriers 1..15, one per row group
   }
   ls->threads = thr;
-  ls->maxt = thr <= 256 ? 256 : 512;
+  ls->maxt = thr <= 256 ? 256 : (thr <= 512 ? 512 : 1024);
   ls->cluster = C;
   int active = 0;
   cudaError_t pe = vns_prepare(b->acc64, ls->nw, ls->ts, ls->maxt, ls->smem, thr, C, &active);
@@ -399,6 +401,7 @@ int launch_runs(elsr_batch* b, const RowBits* start_bits, bool with_traj,
   p.spec_slots = nullptr;
   p.spec_rows = nullptr;
   p.spec_bar = nullptr;
+  p.spec_dec = nullptr;
   // A single mode-P run may be spread over several teams that speculate on
   // consecutive iterations (exact: the committed trajectory is the
   // sequential one).
@@ -415,17 +418,23 @@ int launch_runs(elsr_batch* b, const RowBits* start_bits, bool with_traj,
       dev_free(b->d_spec_slots, b->stream);
       dev_free(b->d_spec_rows, b->stream);
       dev_free(b->d_spec_bar, b->stream);
+      dev_free(b->d_spec_dec, b->stream);
       b->spec_cap = 0;
       ELSR_TRY_CUDA(b, dev_alloc(&b->d_spec_slots, (size_t)2 * teams, b->stream));
       ELSR_TRY_CUDA(b, dev_alloc(&b->d_spec_rows, (size_t)2 * teams * kMaxShake, b->stream));
       ELSR_TRY_CUDA(b, dev_alloc(&b->d_spec_bar, 2, b->stream));
+      ELSR_TRY_CUDA(b, dev_alloc(&b->d_spec_dec, 2, b->stream));
       b->spec_cap = teams;
     }
     ELSR_TRY_CUDA(b, cudaMemsetAsync(b->d_spec_bar, 0, 2 * sizeof(int32_t), b->stream));
+    // decision words start undecided; slot round tags start at -1
+    ELSR_TRY_CUDA(b, cudaMemsetAsync(b->d_spec_dec, 0x7f, 2 * sizeof(int32_t), b->stream));
+    ELSR_TRY_CUDA(b, cudaMemsetAsync(b->d_spec_slots, 0xff, 2 * teams * sizeof(SpecSlot), b->stream));
     p.spec_teams = teams;
     p.spec_slots = b->d_spec_slots;
     p.spec_rows = b->d_spec_rows;
     p.spec_bar = b->d_spec_bar;
+    p.spec_dec = b->d_spec_dec;
     const int blocks = teams * ls.cluster;
     le = vns_launch(b->acc64, ls.nw, ls.ts, ls.maxt, p, blocks, ls.threads, ls.smem, ls.cluster,
                     b->stream);
@@ -986,8 +995,8 @@ int elsr_batch_set_launch(elsr_batch_t* b, int32_t lanes, int32_t threads) {
     b->err = "lanes_per_row must be 4, 8, 16, 32, 64 or 128";
     return ELSR_E_ARG;
   }
-  if (threads && (threads % 32 || threads < 32 || threads > 512)) {
-    b->err = "threads must be a multiple of 32 in [32, 512]";
+  if (threads && (threads % 32 || threads < 32 || threads > 1024)) {
+    b->err = "threads must be a multiple of 32 in [32, 1024]";
     return ELSR_E_ARG;
   }
   b->lanes = lanes;

@@ -73,7 +73,7 @@ struct InstPools {
 struct SpecSlot {
   long long f2;
   int cycles;
-  int pad;
+  int done;  // round number whose result this slot holds
   unsigned long long applied;
   unsigned long long steps;
 };
@@ -96,6 +96,7 @@ struct VnsParams {
   SpecSlot* spec_slots;  // [2][spec_teams]
   RowBits* spec_rows;    // [2][spec_teams][3]
   int32_t* spec_bar;     // [2]: arrivals, generation; zero at launch
+  int32_t* spec_dec;     // [2]: per round parity, first accepting team once known
 };
 
 struct StageParams {
@@ -138,7 +139,7 @@ struct PlanParams {
 // Shared-memory layout of the rows one CTA owns in the persistent GVNS
 // kernel (Kc rows of T periods).
 struct VnsLayout {
-  uint32_t tab, rc, C0, bits, S, bad, nR, A, C, L, P, Q, save, slot, total;
+  uint32_t tab, rc, C0, bits, S, mark, nR, A, C, L, P, Q, save, slot, total;
 };
 
 ELSR_HD uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
@@ -157,7 +158,7 @@ ELSR_HD VnsLayout vns_layout(int Kc, int T, int acc_bytes, bool tab_smem) {
   o = align16(o + K * 32u);
   L.S = o;
   o = align16(o + K * ab);
-  L.bad = o;
+  L.mark = o;
   o = align16(o + K * 4u);
   L.nR = o;
   o = align16(o + K * 4u);
@@ -171,7 +172,7 @@ ELSR_HD VnsLayout vns_layout(int Kc, int T, int acc_bytes, bool tab_smem) {
   o = align16(o + K * (TT + 1) * 4u);
   L.Q = o;
   o = align16(o + K * (TT + 1) * ab);
-  // save slot: RowBits(32) S(8) bad(4) nR(4) | A[T] | C[T] | L[T] | P[T+1] | Q[T+1]
+  // save slot: RowBits(32) S(8) mark(4) nR(4) | A[T] | C[T] | L[T] | P[T+1] | Q[T+1]
   L.slot = align16(48u + ((TT * 4u + 7u) & ~7u) + ((TT * ab + 7u) & ~7u) + TT * 8u +
                    (((TT + 1) * 4u + 7u) & ~7u) + (TT + 1) * ab);
   L.save = o;
@@ -191,7 +192,7 @@ cudaError_t launch_plan(const PlanParams& p, int K, cudaStream_t s);
 
 // Persistent GVNS kernel variants: accumulator width, 64-bit words per bit
 // row (nw = 1 when T <= 64), prefix tables in shared memory (ts), block size
-// bound (maxt = 256 or 512).  cluster = CTAs per run (1 = no cluster).
+// bound (maxt = 256, 512 or 1024).  cluster = CTAs per run (1 = no cluster).
 // prepare sets the kernel attributes and returns the resident blocks per SM
 // (cluster == 1) or the resident clusters on the device (cluster > 1).
 cudaError_t vns_prepare_i32_w1(bool ts, int maxt, size_t smem, int threads, int cluster, int* active);

@@ -142,6 +142,7 @@ __global__ void __launch_bounds__(1024) eval_kernel(const EvalParams p) {
   cur.S = 0;
   cur.bad = T;
   cur.nR = 0;
+  cur.ld = -1;
   if (valid) {
     const int64_t ro = id.row_off + k;
     rc = RowCosts{p.ip.kM[ro], p.ip.kR[ro], p.ip.hM[ro], p.ip.hR[ro]};
@@ -149,7 +150,8 @@ __global__ void __launch_bounds__(1024) eval_kernel(const EvalParams p) {
     cur.b = p.bits[k];
     if (lane == 0) {
       int dummy = 0;
-      cur.S = build_row<Acc, NW>(tk, T, rc, cur.b, Ak, Ck, Lk, Pk, Qk, cur.bad, cur.nR, dummy);
+      cur.S = build_row<Acc, NW>(tk, T, rc, cur.b, Ak, Ck, Lk, Pk, Qk, cur.bad, cur.nR, cur.ld,
+                                 dummy);
     }
   }
   __syncwarp();
@@ -158,8 +160,9 @@ __global__ void __launch_bounds__(1024) eval_kernel(const EvalParams p) {
     cur.S = __shfl_sync(kFull, cur.S, leader);
     cur.bad = __shfl_sync(kFull, cur.bad, leader);
     cur.nR = __shfl_sync(kFull, cur.nR, leader);
+    cur.ld = __shfl_sync(kFull, cur.ld, leader);
   }
-  const int64_t rck = valid ? row_cost<Acc>(cur.S, c0) : 0;
+  const int64_t rck = valid ? state_cost<Acc>(cur.S, cur.bad, T, c0) : 0;
   if (valid && lane == 0 && p.rowcost_out) p.rowcost_out[k] = rck;
 
   const int infk = rck == INT64_MAX;

@@ -24,8 +24,9 @@
 // cost is S + C0 with S the sum of segment terms and the per-row constant
 // C0 = hR * sum_t R(t)(T-t) - hM * sum_t D(t)(T-t).
 //
-// Row cache (per setup s of the current row): A[s] = avail at s and
-// C[s] = S accumulated before s, plus the list of gR setups.  A move changes
+// Row cache (per setup s of the current row, from its relaxed decode):
+// A[s] = avail at s and C[s] = S accumulated before s, plus the list of gR
+// setups with prefix sums of their room.  A move changes
 // periods t1..t2 (t2 <= t1+1); its re-decode starts at s0, the last period
 // <= t1 that is a setup both before and after the move (see eval_move).
 //
@@ -151,20 +152,36 @@ ELSR_HD bool seg_step(int s, int gm, int gr, int2 ts, int2 tn, int T,
   return true;
 }
 
-// Cache of the current row (per product):
+// Cache of the current row (per product), from its relaxed decode: the
+// decode rule applied to every setup, where a remanufacture-only setup whose
+// stock falls short still takes xR = avail and its deficit is treated as
+// manufactured.  For a feasible row this is the decode itself.
 //   A[s], C[s]  at every setup s: stock entering s and S accumulated before s
 //   L[0..nR)    the row's gR setups in period order: {need(s), s | gM(s)<<16}
 //   P, Q[0..nR] exclusive prefix sums over L of room = max(0, need - A) and
 //               hR*(T-s)*room
-// bad = T when the row is feasible; else the first setup whose segment falls
-// short (-1 when demand precedes the first setup); A/C/L are valid before bad.
+// bad = T when the row is feasible; else its first setup that falls short
+// (-1 when demand precedes the first setup: then nothing is cached); ld = the
+// L index of its last setup that falls short (-1 when none).
 template <typename Acc>
 struct RowState {
   RowBits b;
-  Acc S;    // segment sum of the current row (Inf when infeasible)
+  Acc S;    // segment sum of the relaxed decode
   int bad;
   int nR;   // entries of L
+  int ld;
 };
+
+// Per-row marks as stored with the row cache.
+struct RowMark {
+  int16_t bad, ld;
+};
+
+// Objective of a row from its state: Inf when it falls short anywhere.
+template <typename Acc>
+ELSR_HD int64_t state_cost(Acc S, int bad, int T, int64_t C0) {
+  return bad < T ? INT64_MAX : (int64_t)S + C0;
+}
 
 // Bit helpers specialised on the number of 64-bit words per bit row (NW = 1
 // when T <= 64).
@@ -208,24 +225,26 @@ ELSR_HD int rank_below(uint64_t w0, uint64_t w1, int s) {
   return popc64(w0) + popc64(s >= 128 ? w1 : (w1 & ((1ull << (s - 64)) - 1ull)));
 }
 
-// Decode a whole row from its bits, writing the cache.  Returns S (Inf when
-// infeasible) and sets bad and nR.  P, Q ([nR+1]) receive exclusive prefix
-// sums over the gR list of room(r) = max(0, need - avail) and
+// Relaxed decode of a whole row from its bits, writing the cache.  Returns
+// the relaxed S and sets bad, nR and ld.  P, Q ([nR+1]) receive exclusive
+// prefix sums over the gR list of room(r) = max(0, need - avail) and
 // hR*(T-s)*room(r).  segs counts the segments walked.
 template <typename Acc, int NW>
 ELSR_HD Acc build_row(const int2* tab, int T, const RowCosts& rc,
                       const RowBits& b, int32_t* A, Acc* C, int2* L,
-                      int32_t* P, Acc* Q, int& bad, int& nR, int& segs) {
+                      int32_t* P, Acc* Q, int& bad, int& nR, int& ld, int& segs) {
   const uint64_t u0 = b.m0 | b.r0, u1 = b.m1 | b.r1;
   nR = 0;
+  ld = -1;
   P[0] = 0;
   Q[0] = 0;
   int s = nxt<NW>(u0, u1, -1, T);
   int2 ts = tab[s];
   if (ts.x != 0) {  // demand before the first setup
     bad = -1;
-    return Inf<Acc>::value;
+    return 0;
   }
+  bad = T;
   int32_t avail = ts.y;
   Acc S = 0;
   while (s < T) {
@@ -234,42 +253,50 @@ ELSR_HD Acc build_row(const int2* tab, int T, const RowCosts& rc,
     const int n = nxt<NW>(u0, u1, s, T);
     const int2 tn = tab[n];
     const int gm = bitat<NW>(b.m0, b.m1, s), gr = bitat<NW>(b.r0, b.r1, s);
+    const int32_t need = tn.x - ts.x;
+    const int32_t xr = gr ? (avail < need ? avail : need) : 0;
     ++segs;
     if (gr) {
       int2 e;
-      e.x = tn.x - ts.x;
+      e.x = need;
       e.y = s | (gm << 16);
       L[nR] = e;
-      const int32_t room = e.x > avail ? e.x - avail : 0;
+      const int32_t room = need > avail ? need - avail : 0;
       P[nR + 1] = P[nR] + room;
       Q[nR + 1] = Q[nR] + (Acc)rc.hR * (Acc)(T - s) * (Acc)room;
+      if (!gm && xr < need) {  // deficit, taken as manufactured
+        if (bad == T) bad = s;
+        ld = nR;
+      }
       ++nR;
     }
-    if (!seg_step<Acc>(s, gm, gr, ts, tn, T, rc, avail, S)) {
-      bad = s;
-      return Inf<Acc>::value;
-    }
+    S += (Acc)(gm ? rc.kM : 0) + (Acc)(gr ? rc.kR : 0) +
+         ((Acc)rc.hM * (Acc)need - (Acc)rc.hR * (Acc)xr) * (Acc)(T - s);
+    avail = avail - xr + (tn.y - ts.y);
     s = n;
     ts = tn;
   }
-  bad = T;
   return S;
 }
 
 // Delta re-decode of the row after move `local` of N_j (Section 3's "find
 // the best neighbour" for one candidate).  Returns the new segment sum (Inf
 // when the moved row is infeasible).  steps counts the decode steps: the
-// segments of the changed region, then either the remaining segments (when
-// the current row is infeasible) or the gR setups visited by the stock
-// difference walk.
+// segments of the changed region, then the gR setups that the stock
+// difference reaches (walked, or located by the binary search).
 //
 // Changed region: from s0 (the last period <= t1 that is a setup before and
-// after the move) segment by segment while the segment start is <= t2.  At
-// the first setup s1 > t2 both rows have the same setups from there on and
-// differ only in the recoverable stock, by delta = avail_new - A[s1].  With
-// the telescoped cost the suffix then costs its cached value plus, at every
-// later gR setup, -hR*(T-s)*dx where dx is the change of xR = min(avail,
-// need); delta shrinks by dx, and the walk stops when it reaches 0.
+// after the move) segment by segment while the segment start is <= t2 (to
+// the end of the row when the current row has demand before its first
+// setup, where nothing is cached).  At the first setup s1 > t2 both rows
+// have the same setups from there on and differ only in the recoverable
+// stock, by delta = avail_new - A[s1].  With the telescoped cost the suffix
+// then costs its cached (relaxed) value plus, at every later gR setup,
+// -hR*(T-s)*dx where dx is the change of xR = min(avail, need); delta
+// shrinks by dx, and the walk stops when it reaches 0.  A setup of the
+// current row that falls short (a deficit in the relaxed decode) is fixed
+// only when delta still covers its room there, so the moved row is feasible
+// only when delta covers the rooms of all such setups from s1 on.
 template <typename Acc, int NW>
 ELSR_HD Acc eval_move(const int2* tab, int T, const RowCosts& rc,
                       const RowState<Acc>& cur, const int32_t* A,
@@ -290,7 +317,8 @@ ELSR_HD Acc eval_move(const int2* tab, int T, const RowCosts& rc,
     t1 = local - c * (T - 1);
     uint64_t& w0 = c ? nb.r0 : nb.m0;
     uint64_t& w1 = c ? nb.r1 : nb.m1;
-    if (bitat<NW>(w0, w1, t1) == bitat<NW>(w0, w1, t1 + 1)) return cur.S;  // null swap
+    if (bitat<NW>(w0, w1, t1) == bitat<NW>(w0, w1, t1 + 1))  // null swap
+      return cur.bad < T ? Inf<Acc>::value : cur.S;
     flip(w0, w1, t1);
     flip(w0, w1, t1 + 1);
     other = c ? bitat<NW>(nb.m0, nb.m1, t1) : bitat<NW>(nb.r0, nb.r1, t1);
@@ -315,8 +343,8 @@ ELSR_HD Acc eval_move(const int2* tab, int T, const RowCosts& rc,
     avail = ts.y;
     S = 0;
   }
-  // changed region (and the whole rest when the current row falls short)
-  while (s < T && (s <= t2 || cur.bad < T)) {
+  // changed region (and the whole rest when nothing is cached)
+  while (s < T && (s <= t2 || cur.bad < 0)) {
     const int n = nxt<NW>(u0, u1, s, T);
     const int2 tn = tab[n];
     ++steps;
@@ -330,15 +358,16 @@ ELSR_HD Acc eval_move(const int2* tab, int T, const RowCosts& rc,
   // suffix: cached cost plus the effect of the stock difference delta
   int32_t delta = avail - A[s];
   S += cur.S - C[s];
-  if (delta == 0) return S;
   const int r0 = rank_below<NW>(cur.b.r0, cur.b.r1, s);
+  if (delta == 0) return cur.ld >= r0 ? Inf<Acc>::value : S;
   if (delta > 0) {
     // More stock: each later gR setup absorbs up to its room (need minus the
     // stock it had), lowering xM by as much, until delta is used up.  With
     // the prefix sums P (room) and Q (hR*(T-s)*room) the setup z where the
     // rest of delta is absorbed is a binary search, and the cost is closed
     // form.  The step count is that of the walk: z - r0 + 1 setups (or all
-    // remaining ones when delta is never used up).
+    // remaining ones when delta is never used up).  A deficit setup after z,
+    // or at z with room left over, still falls short.
     const int32_t target = P[r0] + delta;
     if (P[cur.nR] < target) {
       steps += cur.nR - r0;
@@ -350,12 +379,13 @@ ELSR_HD Acc eval_move(const int2* tab, int T, const RowCosts& rc,
       if (P[mid + 1] >= target) hi = mid; else lo = mid + 1;
     }
     steps += lo - r0 + 1;
+    if (cur.ld > lo || (cur.ld == lo && P[lo + 1] != target)) return Inf<Acc>::value;
     const int sz = L[lo].y & 0xFFFF;
     return S - (Q[lo] - Q[r0]) -
            (Acc)rc.hR * (Acc)(T - sz) * (Acc)(target - P[lo]);
   }
   // Less stock: walk the gR setups while delta < 0 (a shortfall at a
-  // remanufacture-only setup is infeasible).
+  // remanufacture-only setup is infeasible, and so is any deficit left).
   for (int r = r0; r < cur.nR; ++r) {
     const int2 e = L[r];
     const int sr = e.y & 0xFFFF;
@@ -368,7 +398,7 @@ ELSR_HD Acc eval_move(const int2* tab, int T, const RowCosts& rc,
     delta -= dx;
     if (delta == 0) break;
   }
-  return S;
+  return cur.ld >= r0 ? Inf<Acc>::value : S;
 }
 
 // Row cost = S + C0 as int64 (ELSR_INF when infeasible).

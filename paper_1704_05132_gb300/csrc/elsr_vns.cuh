@@ -95,8 +95,8 @@ struct Rows {
   RowCosts* rc;
   int64_t* C0;
   RowBits* bits;
-  Acc* S;
-  int32_t* bad;
+  Acc* S;          // relaxed segment sums
+  RowMark* mark;   // first shortfall setup, L index of the last one
   int32_t* nR;
   int32_t* A;  // [Kc][T]
   Acc* C;      // [Kc][T]
@@ -116,11 +116,15 @@ struct Rows {
     RowState<Acc> st;
     st.b = bits[q];
     st.S = S[q];
-    st.bad = bad[q];
+    const RowMark mk = mark[q];
+    st.bad = mk.bad;
+    st.ld = mk.ld;
     st.nR = nR[q];
     return st;
   }
-  __device__ __forceinline__ int64_t cost(int q) const { return row_cost<Acc>(S[q], C0[q]); }
+  __device__ __forceinline__ int64_t cost(int q) const {
+    return state_cost<Acc>(S[q], mark[q].bad, T, C0[q]);
+  }
   __device__ __forceinline__ unsigned char* slot_ptr(int par, int j) const {
     return save + (uint32_t)(par * kMaxShake + j) * slot;
   }
@@ -166,7 +170,7 @@ __device__ __forceinline__ void save_row(const Rows<Acc>& m, int q, unsigned cha
   if (lane == 0) {
     *(RowBits*)sl = m.bits[q];
     *(int64_t*)(sl + 32) = (int64_t)m.S[q];
-    *(int32_t*)(sl + 40) = m.bad[q];
+    *(RowMark*)(sl + 40) = m.mark[q];
     *(int32_t*)(sl + 44) = nr;
   }
 }
@@ -193,7 +197,7 @@ __device__ __forceinline__ void restore_row(const Rows<Acc>& m, int q,
   if (lane == 0) {
     m.bits[q] = *(const RowBits*)sl;
     m.S[q] = (Acc)(*(const int64_t*)(sl + 32));
-    m.bad[q] = *(const int32_t*)(sl + 40);
+    m.mark[q] = *(const RowMark*)(sl + 40);
     m.nR[q] = nr;
   }
 }
@@ -286,7 +290,7 @@ __device__ __forceinline__ void rebuild_row(const Rows<Acc>& m, int q, int lane,
   // phase 3: cache entries with local prefix sums
   Acc lsum = 0, lwroom = 0;
   int32_t lroom = 0;
-  int first_bad = T;
+  int first_bad = T, last_def = -1;
   const int r_begin = rank_below<NW>(b.r0, b.r1, a);
   int r = r_begin;
   for (int t = a; t < e; ++t) {
@@ -298,7 +302,10 @@ __device__ __forceinline__ void rebuild_row(const Rows<Acc>& m, int q, int lane,
       const int32_t need = tab[n].x - tt.x;
       const int gm = bitat<NW>(b.m0, b.m1, t), gr = bitat<NW>(b.r0, b.r1, t);
       const int32_t xr = gr ? (avail < need ? avail : need) : 0;
-      if (!gm && xr < need && first_bad == T) first_bad = t;
+      if (!gm && xr < need) {  // deficit, taken as manufactured (relaxed decode)
+        if (first_bad == T) first_bad = t;
+        last_def = r;
+      }
       A[t] = avail;
       C[t] = lsum;
       lsum += (Acc)(gm ? rc.kM : 0) + (Acc)(gr ? rc.kR : 0) +
@@ -345,7 +352,9 @@ __device__ __forceinline__ void rebuild_row(const Rows<Acc>& m, int q, int lane,
   }
   for (int o = G >> 1; o > 0; o >>= 1) {
     const int v = __shfl_xor_sync(smask, first_bad, o, G);
+    const int w = __shfl_xor_sync(smask, last_def, o, G);
     first_bad = v < first_bad ? v : first_bad;
+    last_def = w > last_def ? w : last_def;
   }
   if (off != 0)
     for (int t = a; t < e; ++t)
@@ -354,8 +363,11 @@ __device__ __forceinline__ void rebuild_row(const Rows<Acc>& m, int q, int lane,
     const int f = nxt<NW>(u0, u1, -1, T);
     int bad = first_bad;
     if (tab[f].x != 0) bad = -1;  // demand before the first setup
-    m.bad[q] = bad;
-    m.S[q] = bad == T ? total : Inf<Acc>::value;
+    RowMark mk;
+    mk.bad = (int16_t)bad;
+    mk.ld = (int16_t)last_def;
+    m.mark[q] = mk;
+    m.S[q] = total;
     const int nr = popc64(b.r0) + (NW == 1 ? 0 : popc64(b.r1));
     m.nR[q] = nr;
     Pr[nr] = totP;
@@ -476,7 +488,7 @@ __device__ bool team_begin(Team<Acc>& t, unsigned char* smem, CtlShared* sh,
   m.C0 = (int64_t*)(smem + Lay.C0);
   m.bits = (RowBits*)(smem + Lay.bits);
   m.S = (Acc*)(smem + Lay.S);
-  m.bad = (int32_t*)(smem + Lay.bad);
+  m.mark = (RowMark*)(smem + Lay.mark);
   m.nR = (int32_t*)(smem + Lay.nR);
   m.A = (int32_t*)(smem + Lay.A);
   m.C = (Acc*)(smem + Lay.C);
@@ -575,8 +587,11 @@ __device__ int64_t team_total(Team<Acc>& t) {
 // VND of Algorithm 1 (pipe form), mode P: every product takes its best
 // strictly improving move of N_j; the j = 1..3 sweep repeats until no product
 // of the team improves.  Returns the sweeps run, or -1 at the cap.
+// `stop` (speculative teams): a decision word in global memory and this
+// team's index; the VND gives up (returns -2) at a sweep boundary once the
+// word names an earlier team, whose iteration makes this one moot.
 template <typename Acc, int NW>
-__device__ int vnd_p(Team<Acc>& t) {
+__device__ int vnd_p(Team<Acc>& t, const int* stop = nullptr, int my_index = 0) {
   const int T = t.T;
   int cycles = 0;
   for (;;) {
@@ -609,15 +624,26 @@ __device__ int vnd_p(Team<Acc>& t) {
       }
     }
     ++cycles;
+    if (stop && t.C == 1 && t.tid == 0) t.sh->flag[t.fp] = *(volatile const int*)stop < my_index;
     int any = __syncthreads_or(improved);
+    int quit = 0;
     if (t.C > 1) {
       cg::cluster_group cl = cg::this_cluster();
-      if (t.tid == 0) t.sh->flag[t.fp] = any;
+      if (t.tid == 0) {
+        int f = any;
+        if (stop && t.crank == 0 && *(volatile const int*)stop < my_index) f |= 2;
+        t.sh->flag[t.fp] = f;
+      }
       cl.sync();
       const int v = t.wlane < t.C ? *cl.map_shared_rank(&t.sh->flag[t.fp], t.wlane) : 0;
-      any = __any_sync(kFull, v);
+      any = __any_sync(kFull, v & 1);
+      quit = __any_sync(kFull, v & 2);
+      t.fp ^= 1;
+    } else if (stop) {
+      quit = t.sh->flag[t.fp];
       t.fp ^= 1;
     }
+    if (quit) return -2;
     if (!any) break;
     if (cycles >= t.vnd_cap) return -1;
   }
@@ -1015,6 +1041,11 @@ __global__ void __launch_bounds__(MAXT, 1) spec_kernel(const VnsParams p) {
     const bool active = team < nact;
     const int ks = (k0 - 1 + team) % rd.kmax + 1;
     SpecSlot* slot = p.spec_slots + par * W + team;
+    SpecSlot* slots_w = p.spec_slots + par * W;
+    int* dec = p.spec_dec + par;
+    // the other parity's decision word is next written after this round's
+    // barrier; reset it now
+    if (leader) p.spec_dec[par ^ 1] = 0x7fffffff;
     ShakePlan pl;
     if (active) {
       if (t.crank == 0 && t.tid == 0) {
@@ -1023,55 +1054,112 @@ __global__ void __launch_bounds__(MAXT, 1) spec_kernel(const VnsParams p) {
       }
       pl = plan_shake(rd.seed, it0 + team, ks, K, T);
       apply_shake<Acc, NW>(t, pl, ks, par);
-      cyc = vnd_p<Acc, NW>(t);
-      const int64_t f2 = team_total(t);
-      flush_counters(t, &slot->steps, &slot->applied);
+      cyc = vnd_p<Acc, NW>(t, dec, team);
+      if (cyc != -2) {  // -2: an earlier team's iteration was accepted
+        const int64_t f2 = team_total(t);
+        flush_counters(t, &slot->steps, &slot->applied);
 #pragma unroll
-      for (int j = 0; j < kMaxShake; ++j)
-        if (t.owns(pl.rows[j]) && pl.first[j] && t.lane == 0)
-          p.spec_rows[(par * W + team) * kMaxShake + j] = t.m.bits[pl.rows[j] / t.C];
-      if (t.crank == 0 && t.tid == 0) {
-        slot->f2 = f2;
-        slot->cycles = cyc;
+        for (int j = 0; j < kMaxShake; ++j)
+          if (t.owns(pl.rows[j]) && pl.first[j] && t.lane == 0)
+            p.spec_rows[(par * W + team) * kMaxShake + j] = t.m.bits[pl.rows[j] / t.C];
+        __threadfence();
+        team_sync(t.C);
+        if (t.crank == 0 && t.warp == 0) {
+          if (t.wlane == 0) {
+            slot->f2 = f2;
+            slot->cycles = cyc;
+            __threadfence();
+            atomicExch(&slot->done, 2 * round + (f2 < fx ? 1 : 0));
+          }
+          __syncwarp();
+          // The round is decided once a finished prefix of the teams holds
+          // the first acceptance (or every team finished without one).
+          int d = -1;
+          for (int base = 0; base < nact && d < 0; base += 32) {
+            const int i = base + t.wlane;
+            const int v = i < nact ? *(volatile const int*)&slots_w[i].done : -1;
+            const unsigned fin = __ballot_sync(kFull, i < nact && (v >> 1) == round);
+            const unsigned acc = __ballot_sync(kFull, i < nact && (v >> 1) == round && (v & 1));
+            const int nfin = __ffs(~fin) - 1;  // finished prefix of this chunk (-1: all 32)
+            const unsigned pre = nfin < 0 ? kFull : ((1u << nfin) - 1u);
+            if (acc & pre) {
+              d = base + __ffs(acc & pre) - 1;
+            } else if (nfin >= 0 && base + nfin < nact) {
+              break;  // an unfinished team precedes any acceptance
+            } else if (base + 32 >= nact) {
+              d = nact;  // every team finished, none accepted
+            }
+          }
+          if (t.wlane == 0 && d >= 0) atomicMin(dec, d);
+        }
+      } else {
+        t.steps = 0;
+        t.applied = 0;
       }
     }
     if (!grid_barrier(t, p.spec_bar, W)) {
       status = kStatusTimeout;
       break;
     }
-    // commit in iteration order up to the first acceptance
+    // commit in iteration order up to the first acceptance: a finished team's
+    // done word is 2 * round + accepted; teams that gave up hold an older
+    // round and all sit after the first acceptance
     const SpecSlot* slots = p.spec_slots + par * W;
-    int a = -1, capped = 0;
-    for (int i = 0; i < nact; ++i) {
-      if (__ldcg(&slots[i].cycles) < 0) capped = 1;
-      if (__ldcg(&slots[i].f2) < fx) {
-        a = i;
+    int a = -1;
+    for (int base = 0; base < nact; base += 32) {
+      const int i = base + t.wlane;
+      const int v = i < nact ? __ldcg(&slots[i].done) : -1;
+      const unsigned accb = __ballot_sync(kFull, v == 2 * round + 1);
+      if (accb) {
+        a = base + __ffs(accb) - 1;
         break;
       }
     }
     const int ncommit = a >= 0 ? a + 1 : nact;
-    for (int i = 0; i < ncommit; ++i) {
-      const int c = __ldcg(&slots[i].cycles);
-      cycles_total += c > 0 ? c : 0;
+    int capped = 0;
+    for (int base = 0; base < ncommit; base += 32) {
+      const int i = base + t.wlane;
+      const int c = i < ncommit ? __ldcg(&slots[i].cycles) : 0;
+      capped |= __any_sync(kFull, c < 0);
+      int cs = c > 0 ? c : 0;
+      for (int o = 16; o > 0; o >>= 1) cs += __shfl_xor_sync(kFull, cs, o);
+      cycles_total += cs;
     }
-    if (leader) {
-      for (int i = 0; i < ncommit; ++i) {
-        const int64_t f2 = __ldcg(&slots[i].f2);
-        const int ki = (k0 - 1 + i) % rd.kmax + 1;
-        const int acc = i == a;
-        if (rd.traj_off >= 0) {
-          TrajEntry te;
-          te.it = it0 + i;
-          te.k = ki;
-          te.cost = f2;
-          te.accepted = acc;
-          te.reserved = 0;
-          p.traj[rd.traj_off + it0 + i] = te;
+    if (team == 0 && t.crank == 0 && t.warp == 0) {
+      for (int base = 0; base < ncommit; base += 32) {
+        const int i = base + t.wlane;
+        const bool in = i < ncommit;
+        const int64_t f2i = in ? __ldcg(&slots[i].f2) : 0;
+        unsigned long long st = in ? __ldcg(&slots[i].steps) : 0ull;
+        unsigned long long ap = in ? __ldcg(&slots[i].applied) : 0ull;
+        for (int o = 16; o > 0; o >>= 1) {
+          st += __shfl_xor_sync(kFull, st, o);
+          ap += __shfl_xor_sync(kFull, ap, o);
         }
-        h = splitmix64(h ^ (uint64_t)f2);
-        h = splitmix64(h ^ (((uint64_t)(it0 + i) << 32) | ((uint64_t)ki << 1) | (uint64_t)acc));
-        c_steps += __ldcg(&slots[i].steps);
-        c_applied += __ldcg(&slots[i].applied);
+        const int n = ncommit - base < 32 ? ncommit - base : 32;
+        for (int jj = 0; jj < n; ++jj) {
+          const int64_t f2 = __shfl_sync(kFull, f2i, jj);
+          if (t.wlane == 0) {
+            const int ii = base + jj;
+            const int ki = (k0 - 1 + ii) % rd.kmax + 1;
+            const int acc = ii == a;
+            if (rd.traj_off >= 0) {
+              TrajEntry te;
+              te.it = it0 + ii;
+              te.k = ki;
+              te.cost = f2;
+              te.accepted = acc;
+              te.reserved = 0;
+              p.traj[rd.traj_off + it0 + ii] = te;
+            }
+            h = splitmix64(h ^ (uint64_t)f2);
+            h = splitmix64(h ^ (((uint64_t)(it0 + ii) << 32) | ((uint64_t)ki << 1) | (uint64_t)acc));
+          }
+        }
+        if (t.wlane == 0) {
+          c_steps += st;
+          c_applied += ap;
+        }
       }
     }
     if (capped) {

@@ -7,15 +7,17 @@ namespace elsr {
 
 template <bool TS>
 static cudaError_t prep2(int maxt, size_t smem, int threads, int cluster, int* active) {
-  return maxt == 256 ? vns_prepare_t<int64_t, 1, TS, 256>(smem, threads, cluster, active)
-                     : vns_prepare_t<int64_t, 1, TS, 512>(smem, threads, cluster, active);
+  if (maxt == 256) return vns_prepare_t<int64_t, 1, TS, 256>(smem, threads, cluster, active);
+  if (maxt == 512) return vns_prepare_t<int64_t, 1, TS, 512>(smem, threads, cluster, active);
+  return vns_prepare_t<int64_t, 1, TS, 1024>(smem, threads, cluster, active);
 }
 
 template <bool TS>
 static cudaError_t launch2(int maxt, const VnsParams& p, int blocks, int threads, size_t smem,
                            int cluster, cudaStream_t s) {
-  return maxt == 256 ? vns_launch_t<int64_t, 1, TS, 256>(p, blocks, threads, smem, cluster, s)
-                     : vns_launch_t<int64_t, 1, TS, 512>(p, blocks, threads, smem, cluster, s);
+  if (maxt == 256) return vns_launch_t<int64_t, 1, TS, 256>(p, blocks, threads, smem, cluster, s);
+  if (maxt == 512) return vns_launch_t<int64_t, 1, TS, 512>(p, blocks, threads, smem, cluster, s);
+  return vns_launch_t<int64_t, 1, TS, 1024>(p, blocks, threads, smem, cluster, s);
 }
 
 cudaError_t vns_prepare_i64_w1(bool ts, int maxt, size_t smem, int threads, int cluster,

@@ -43,7 +43,7 @@ int64_t move_costs(int T, const int32_t* D, const int32_t* R,
   std::vector<Acc> Qv(T + 1, 0);
   int segs = 0;
   st.S = build_row<Acc, NW>(tab.data(), T, rc, st.b, A.data(), C.data(), L.data(),
-                            Pv.data(), Qv.data(), st.bad, st.nR, segs);
+                            Pv.data(), Qv.data(), st.bad, st.nR, st.ld, segs);
   const int M = row_moves(T, j);
   for (int m = 0; m < M; ++m) {
     int steps = 0;
@@ -52,7 +52,7 @@ int64_t move_costs(int T, const int32_t* D, const int32_t* R,
     out[m] = row_cost<Acc>(S, C0);
     steps_out[m] = steps;
   }
-  return row_cost<Acc>(st.S, C0);
+  return state_cost<Acc>(st.S, st.bad, T, C0);
 }
 
 }  // namespace
