@@ -225,6 +225,78 @@ ELSR_HD int rank_below(uint64_t w0, uint64_t w1, int s) {
   return popc64(w0) + popc64(s >= 128 ? w1 : (w1 & ((1ull << (s - 64)) - 1ull)));
 }
 
+// Position of the set bit of rank i (0-based) in a 32-bit word holding more
+// than i set bits, by halving with population counts.
+ELSR_HD int select32(uint32_t w, int i) {
+  int base = 0;
+#if defined(__CUDA_ARCH__)
+#define ELSR_POPC32(x) __popc(x)
+#else
+#define ELSR_POPC32(x) __builtin_popcount(x)
+#endif
+  int c = ELSR_POPC32(w & 0xFFFFu);
+  if (i >= c) { i -= c; w >>= 16; base += 16; }
+  c = ELSR_POPC32(w & 0xFFu);
+  if (i >= c) { i -= c; w >>= 8; base += 8; }
+  c = ELSR_POPC32(w & 0xFu);
+  if (i >= c) { i -= c; w >>= 4; base += 4; }
+  c = ELSR_POPC32(w & 0x3u);
+  if (i >= c) { i -= c; w >>= 2; base += 2; }
+  if (i >= (int)(w & 1u)) base += 1;
+#undef ELSR_POPC32
+  return base;
+}
+
+// Position of the set bit of rank i in a bit row (w0: bits 0..63, w1: bits
+// 64..127); the row holds more than i set bits.
+template <int NW>
+ELSR_HD int select_bit(uint64_t w0, uint64_t w1, int i) {
+  if (NW == 2) {
+    const int c0 = popc64(w0);
+    if (i >= c0) return 64 + select_bit<1>(w1, 0, i - c0);
+  }
+  const int c = popc64(w0 & 0xFFFFFFFFull);
+  if (i < c) return select32((uint32_t)w0, i);
+  return 32 + select32((uint32_t)(w0 >> 32), i - c);
+}
+
+// The swaps of N3 that change the row: positions t <= T-2 whose bit differs
+// from bit t+1, for the gM row (x0, x1) and the gR row (y0, y1).  A null swap
+// leaves the row as it is, so it can never be a strictly improving move.
+struct SwapMasks {
+  uint64_t x0, x1, y0, y1;
+  int nm, n;  // non-null swaps of gM, of both rows
+};
+
+template <int NW>
+ELSR_HD SwapMasks swap_masks(const RowBits& b, int T) {
+  SwapMasks s;
+  const int P = T - 1;  // swap positions 0..T-2
+  const uint64_t k0 = P >= 64 ? ~0ull : (P <= 0 ? 0ull : ((1ull << P) - 1ull));
+  const uint64_t k1 = P > 64 ? ((P >= 128) ? ~0ull : ((1ull << (P - 64)) - 1ull)) : 0ull;
+  if (NW == 1) {
+    s.x0 = (b.m0 ^ (b.m0 >> 1)) & k0;
+    s.y0 = (b.r0 ^ (b.r0 >> 1)) & k0;
+    s.x1 = s.y1 = 0ull;
+  } else {
+    s.x0 = (b.m0 ^ ((b.m0 >> 1) | (b.m1 << 63))) & k0;
+    s.x1 = (b.m1 ^ (b.m1 >> 1)) & k1;
+    s.y0 = (b.r0 ^ ((b.r0 >> 1) | (b.r1 << 63))) & k0;
+    s.y1 = (b.r1 ^ (b.r1 >> 1)) & k1;
+  }
+  s.nm = popc64(s.x0) + popc64(s.x1);
+  s.n = s.nm + popc64(s.y0) + popc64(s.y1);
+  return s;
+}
+
+// Local N3 index of the non-null swap of rank i (i < s.n): gM swaps first,
+// then gR swaps, each in period order (so ranks keep the index order).
+template <int NW>
+ELSR_HD int swap_of_rank(const SwapMasks& s, int T, int i) {
+  return i < s.nm ? select_bit<NW>(s.x0, s.x1, i)
+                  : (T - 1) + select_bit<NW>(s.y0, s.y1, i - s.nm);
+}
+
 // Relaxed decode of a whole row from its bits, writing the cache.  Returns
 // the relaxed S and sets bad, nR and ld.  P, Q ([nR+1]) receive exclusive
 // prefix sums over the gR list of room(r) = max(0, need - avail) and

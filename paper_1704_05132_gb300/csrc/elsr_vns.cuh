@@ -219,9 +219,20 @@ __device__ __forceinline__ uint64_t row_best(const Rows<Acc>& m, int q,
   const int64_t c0 = m.C0[q];
   uint64_t best = ~0ull;
   int st = 0;
-  for (int l = lane; l < M; l += G) {
-    const Acc S = eval_move<Acc, NW>(tk, T, rc, cur, Aq, Cq, Lq, Pq, Qq, j, l, st);
-    best = umin64(best, pack_key(row_cost<Acc>(S, c0), (uint32_t)l));
+  if (j == 3) {
+    // only the swaps that change the row can improve it; lanes take them
+    // by rank (null swaps keep the row's cost and never win)
+    const SwapMasks sw = swap_masks<NW>(cur.b, T);
+    for (int i = lane; i < sw.n; i += G) {
+      const int l = swap_of_rank<NW>(sw, T, i);
+      const Acc S = eval_move<Acc, NW>(tk, T, rc, cur, Aq, Cq, Lq, Pq, Qq, 3, l, st);
+      best = umin64(best, pack_key(row_cost<Acc>(S, c0), (uint32_t)l));
+    }
+  } else {
+    for (int l = lane; l < M; l += G) {
+      const Acc S = eval_move<Acc, NW>(tk, T, rc, cur, Aq, Cq, Lq, Pq, Qq, j, l, st);
+      best = umin64(best, pack_key(row_cost<Acc>(S, c0), (uint32_t)l));
+    }
   }
   steps += (uint32_t)st;
   return best;
@@ -695,7 +706,10 @@ __device__ int vnd_g(Team<Acc>& t) {
           const RowCosts rc = t.m.rc[q];
           const int64_t c0 = t.m.C0[q];
           int st = 0;
-          for (int l = t.lane; l < M; l += t.G) {
+          const SwapMasks sw = swap_masks<NW>(cur.b, T);
+          const int Mj = j == 3 ? sw.n : M;  // N3: non-null swaps only
+          for (int i = t.lane; i < Mj; i += t.G) {
+            const int l = j == 3 ? swap_of_rank<NW>(sw, T, i) : i;
             const Acc S = eval_move<Acc, NW>(tk, T, rc, cur, t.m.A + q * T, t.m.C + q * T,
                                              t.m.L + q * T, t.m.P + q * (T + 1),
                                              t.m.Q + q * (T + 1), j, l, st);

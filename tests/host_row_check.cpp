@@ -70,6 +70,25 @@ int64_t hc_move_costs(int32_t acc64, int32_t nw, int32_t T, const int32_t* D,
                : move_costs<int32_t, 2>(T, D, R, costs, gM, gR, j, out, steps);
 }
 
+// Local N3 indices of the non-null swaps of a row, by rank; returns their
+// number.
+int32_t hc_swaps(int32_t nw, int32_t T, const uint8_t* gM, const uint8_t* gR,
+                 int32_t* out) {
+  RowBits b{0, 0, 0, 0};
+  for (int t = 0; t < T; ++t) {
+    if (gM[t]) flip(b.m0, b.m1, t);
+    if (gR[t]) flip(b.r0, b.r1, t);
+  }
+  if (nw == 1) {
+    const SwapMasks s = swap_masks<1>(b, T);
+    for (int i = 0; i < s.n; ++i) out[i] = swap_of_rank<1>(s, T, i);
+    return s.n;
+  }
+  const SwapMasks s = swap_masks<2>(b, T);
+  for (int i = 0; i < s.n; ++i) out[i] = swap_of_rank<2>(s, T, i);
+  return s.n;
+}
+
 uint64_t hc_shake_draw(uint64_t seed, uint64_t it, uint64_t k, uint64_t j) {
   return shake_draw(seed, it, k, j);
 }

@@ -32,6 +32,8 @@ def hc(tmp_path_factory):
     lib.hc_move_costs.restype = ctypes.c_int64
     lib.hc_move_costs.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                   P, P, P, P, P, ctypes.c_int32, P, P]
+    lib.hc_swaps.restype = ctypes.c_int32
+    lib.hc_swaps.argtypes = [ctypes.c_int32, ctypes.c_int32, P, P, P]
     lib.hc_shake_draw.restype = ctypes.c_uint64
     lib.hc_shake_draw.argtypes = [ctypes.c_uint64] * 4
     return lib
@@ -156,3 +158,28 @@ def test_deficits_fixed_through_the_stock_difference(hc, T):
                 if len(changed) and changed.max() < bad and out[m] < oracle.INF:
                     fixed_late += 1
     assert fixed_late >= 3, "no move fixed a later deficit; the case is not exercised"
+
+
+@pytest.mark.parametrize("T", [1, 2, 3, 31, 32, 33, 63, 64, 65, 96, 127, 128])
+def test_non_null_swaps_by_rank(hc, T):
+    """The N3 moves that change a row, listed by rank as the kernels take
+    them: every swap of two differing neighbouring bits, gM row first, in
+    index order; a null swap leaves the row (and its cost) unchanged."""
+    rng = np.random.default_rng(T)
+    g = gen.make_instance(70 + T, 3, K=1, T=T)
+    inst = oracle.Instance.from_arrays(g)
+    for nw in (1, 2):
+        if nw == 1 and T > 64:
+            continue
+        for gm, gr in _random_states(rng, T, 12):
+            out = np.zeros(max(2 * T, 1), np.int32)
+            n = hc.hc_swaps(nw, T, _p(gm), _p(gr), _p(out))
+            ref = [l for l in range(oracle.row_moves(T, 3))
+                   if (l < T - 1 and gm[l] != gm[l + 1]) or
+                   (l >= T - 1 and gr[l - T + 1] != gr[l - T + 2])]
+            assert list(out[:n]) == ref
+            if T > 1:
+                costs = oracle.move_costs(inst, gm[None, :], gr[None, :], 3)
+                cur = oracle.decode_row(inst, 0, gm, gr)[0]
+                null = sorted(set(range(oracle.row_moves(T, 3))) - set(ref))
+                assert all(costs[l] == cur for l in null)
