@@ -1,13 +1,14 @@
 """Autotuner for the persistent GVNS launch shape.
 
 Knobs (none changes a result; only speed):
-  lanes    -- lanes of a sub-warp that share one product row (4..32): each
-              lane evaluates ceil(|row moves| / lanes) candidates per sweep,
-              a warp holds 32 / lanes rows;
+  lanes    -- lanes that share one product row (4..32 within a warp; 64 or
+              128 = a row group of 2 or 4 warps, mode P): each lane evaluates
+              about |row moves| / lanes candidates per sweep;
   threads  -- threads per CTA (rows in flight per CTA = threads / lanes);
   cluster  -- CTAs that share one run (1 for batches of small instances;
               larger clusters split a big instance's rows over several SMs);
-  teams    -- speculative teams for a single run.
+  teams    -- speculative teams for a single run (0: as many as are
+              resident, up to 16).
 A probe runs each candidate for a few iterations of the real workload and
 times it with CUDA events; the best moves/s wins.  Choices are cached per
 workload signature (bucketed K, T and batch size) in memory and, optionally,
@@ -47,8 +48,8 @@ def _timed(fn):
 
 
 BATCH_CANDIDATES = [dict(lanes=l, threads=t, cluster=1) for l in (8, 16, 32)
-                    for t in (256, 512)]
-SINGLE_CANDIDATES = [dict(lanes=32, cluster=c, teams=s) for c in (4, 8, 16) for s in (1, 16)]
+                    for t in (512, 1024)]
+SINGLE_CANDIDATES = [dict(lanes=l, cluster=c, teams=0) for l in (32, 64) for c in (6, 8, 10)]
 
 
 def tune_batch(insts, probe_iters: int = 10, candidates=None, cache_file: str | None = None):

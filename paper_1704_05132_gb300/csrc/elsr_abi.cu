@@ -105,7 +105,7 @@ int check_instance(int32_t K, int32_t T, const int32_t* D, const int32_t* R,
 // over more lanes; batches are throughput-bound and keep more rows in flight.
 int default_lanes(int T, bool single) {
   if (single) return T <= 8 ? 4 : (T <= 16 ? 8 : (T <= 24 ? 16 : (T <= 40 ? 32 : 64)));
-  return T <= 8 ? 4 : (T <= 24 ? 8 : (T <= 64 ? 16 : 32));
+  return T <= 8 ? 4 : (T <= 24 ? 8 : 16);
 }
 
 }  // namespace
@@ -319,7 +319,12 @@ int vns_shape(elsr_batch* b, LaunchShape* ls) {
   if (ls->G > 32 && any_g) ls->G = 32;  // rows wider than a warp: mode P only
   const int kc = (maxK + C - 1) / C;
   int thr = b->threads;
-  if (!thr) thr = std::min(single && ls->G <= 32 ? 256 : 512, std::max(64, ((kc * ls->G + 31) / 32) * 32));
+  // Default block: one CTA per SM; a single run keeps its CTAs small (its
+  // rows are few and its sweeps latency-bound), many runs fill the SM with
+  // 1024 threads (more warps to hide the decode's dependent latencies).
+  if (!thr)
+    thr = std::min(single ? (ls->G <= 32 ? 256 : 512) : 1024,
+                   std::max(64, ((kc * ls->G + 31) / 32) * 32));
   if (ls->G > 32) {
     thr = std::max(thr, ls->G);
     thr -= thr % ls->G;

@@ -291,7 +291,8 @@ def test_batch_with_global_tables(E):
 
 SHAPES = [(4, 64, 1), (8, 256, 1), (16, 512, 1), (32, 512, 1), (16, 384, 1),
           (32, 64, 2), (16, 128, 3), (32, 224, 8), (8, 64, 16), (32, 32, 16),
-          (64, 128, 1), (64, 448, 8), (128, 256, 4), (128, 512, 2), (64, 64, 16)]
+          (64, 128, 1), (64, 448, 8), (128, 256, 4), (128, 512, 2), (64, 64, 16),
+          (16, 1024, 1), (32, 768, 2), (64, 960, 1), (8, 1024, 3)]
 
 
 @pytest.mark.parametrize("T", [40, 90])
