@@ -399,33 +399,78 @@ ELSR_HD Acc eval_move(const int2* tab, int T, const RowCosts& rc,
   const uint64_t u0 = nb.m0 | nb.r0, u1 = nb.m1 | nb.r1;
   const int s0 = other ? t1 : prv<NW>(u0, u1, t1);
   int s;
-  int2 ts;
   int32_t avail;
   Acc S;
-  if (s0 >= 0) {
-    if (s0 > cur.bad) return Inf<Acc>::value;  // unchanged prefix falls short
-    s = s0;
-    ts = tab[s];
-    avail = A[s];
-    S = C[s];
-  } else {
+  if (cur.bad < 0) {
+    // Nothing cached (demand precedes the row's first setup): the moved row
+    // is feasible only if the move adds a setup before all demand, and is
+    // then decoded to its end.
+    if (s0 >= 0) return Inf<Acc>::value;
     s = nxt<NW>(u0, u1, -1, T);
-    ts = tab[s];
+    int2 ts = tab[s];
     if (ts.x != 0) return Inf<Acc>::value;
     avail = ts.y;
     S = 0;
+    while (s < T) {
+      const int n = nxt<NW>(u0, u1, s, T);
+      const int2 tn = tab[n];
+      ++steps;
+      if (!seg_step<Acc>(s, bitat<NW>(nb.m0, nb.m1, s), bitat<NW>(nb.r0, nb.r1, s),
+                         ts, tn, T, rc, avail, S))
+        return Inf<Acc>::value;
+      s = n;
+      ts = tn;
+    }
+    return S;
   }
-  // changed region (and the whole rest when nothing is cached)
-  while (s < T && (s <= t2 || cur.bad < 0)) {
-    const int n = nxt<NW>(u0, u1, s, T);
-    const int2 tn = tab[n];
+  if (s0 > cur.bad) return Inf<Acc>::value;  // unchanged prefix falls short
+  // The changed region has at most three segments of the moved row, starting
+  // at a0 (s0, or the row's first setup), t1 and t1 + 1 (when they hold
+  // setups of the moved row after a0), and ends at s1, the first setup after
+  // t2 (the same in both rows).  Their bounds come from the bits alone, so
+  // every table entry they need is loaded up front.
+  const int s1 = nxt<NW>(u0, u1, t2, T);
+  int a0;
+  if (s0 >= 0) {
+    a0 = s0;
+  } else {
+    a0 = nxt<NW>(u0, u1, -1, T);
+  }
+  const int2 ta0 = tab[a0];
+  const int2 tt1 = tab[t1];
+  const int2 tt2 = tab[t2];
+  const int2 ts1 = tab[s1];
+  if (s0 >= 0) {
+    avail = A[s0];
+    S = C[s0];
+  } else {
+    if (ta0.x != 0) return Inf<Acc>::value;  // demand before the first setup
+    avail = ta0.y;
+    S = 0;
+  }
+  const bool v0 = a0 <= t2;
+  const bool v1 = t1 > a0 && bitat<NW>(u0, u1, t1);
+  const bool v2 = j == 3 && t2 > a0 && bitat<NW>(u0, u1, t2);
+  if (v0) {
     ++steps;
-    if (!seg_step<Acc>(s, bitat<NW>(nb.m0, nb.m1, s), bitat<NW>(nb.r0, nb.r1, s),
-                       ts, tn, T, rc, avail, S))
+    const int2 te = v1 ? tt1 : (v2 ? tt2 : ts1);
+    if (!seg_step<Acc>(a0, bitat<NW>(nb.m0, nb.m1, a0), bitat<NW>(nb.r0, nb.r1, a0), ta0,
+                       te, T, rc, avail, S))
       return Inf<Acc>::value;
-    s = n;
-    ts = tn;
   }
+  if (v1) {
+    ++steps;
+    if (!seg_step<Acc>(t1, bitat<NW>(nb.m0, nb.m1, t1), bitat<NW>(nb.r0, nb.r1, t1), tt1,
+                       v2 ? tt2 : ts1, T, rc, avail, S))
+      return Inf<Acc>::value;
+  }
+  if (v2) {
+    ++steps;
+    if (!seg_step<Acc>(t2, bitat<NW>(nb.m0, nb.m1, t2), bitat<NW>(nb.r0, nb.r1, t2), tt2,
+                       ts1, T, rc, avail, S))
+      return Inf<Acc>::value;
+  }
+  s = s1;
   if (s >= T) return S;
   // suffix: cached cost plus the effect of the stock difference delta
   int32_t delta = avail - A[s];
