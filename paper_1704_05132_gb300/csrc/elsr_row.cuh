@@ -157,7 +157,8 @@ ELSR_HD bool seg_step(int s, int gm, int gr, int2 ts, int2 tn, int T,
 // stock falls short still takes xR = avail and its deficit is treated as
 // manufactured.  For a feasible row this is the decode itself.
 //   A[s], C[s]  at every setup s: stock entering s and S accumulated before s
-//   L[0..nR)    the row's gR setups in period order: {need(s), s | gM(s)<<16}
+//   L[0..nR)    the row's gR setups in period order:
+//               {surplus(s) = A[s] - need(s), s | gM(s)<<16}
 //   P, Q[0..nR] exclusive prefix sums over L of room = max(0, need - A) and
 //               hR*(T-s)*room
 // bad = T when the row is feasible; else its first setup that falls short
@@ -330,7 +331,7 @@ ELSR_HD Acc build_row(const int2* tab, int T, const RowCosts& rc,
     ++segs;
     if (gr) {
       int2 e;
-      e.x = need;
+      e.x = avail - need;
       e.y = s | (gm << 16);
       L[nR] = e;
       const int32_t room = need > avail ? need - avail : 0;
@@ -440,6 +441,11 @@ ELSR_HD Acc eval_move(const int2* tab, int T, const RowCosts& rc,
   const int2 tt1 = tab[t1];
   const int2 tt2 = tab[t2];
   const int2 ts1 = tab[s1];
+  // cache entries at s1, issued together with the region's (s1 = T reads an
+  // unused in-range entry)
+  const int sc = s1 < T ? s1 : T - 1;
+  const int32_t A1 = A[sc];
+  const Acc C1 = C[sc];
   if (s0 >= 0) {
     avail = A[s0];
     S = C[s0];
@@ -470,12 +476,11 @@ ELSR_HD Acc eval_move(const int2* tab, int T, const RowCosts& rc,
                        ts1, T, rc, avail, S))
       return Inf<Acc>::value;
   }
-  s = s1;
-  if (s >= T) return S;
+  if (s1 >= T) return S;
   // suffix: cached cost plus the effect of the stock difference delta
-  int32_t delta = avail - A[s];
-  S += cur.S - C[s];
-  const int r0 = rank_below<NW>(cur.b.r0, cur.b.r1, s);
+  int32_t delta = avail - A1;
+  S += cur.S - C1;
+  const int r0 = rank_below<NW>(cur.b.r0, cur.b.r1, s1);
   if (delta == 0) return cur.ld >= r0 ? Inf<Acc>::value : S;
   if (delta > 0) {
     // More stock: each later gR setup absorbs up to its room (need minus the
@@ -485,32 +490,39 @@ ELSR_HD Acc eval_move(const int2* tab, int T, const RowCosts& rc,
     // form.  The step count is that of the walk: z - r0 + 1 setups (or all
     // remaining ones when delta is never used up).  A deficit setup after z,
     // or at z with room left over, still falls short.
-    const int32_t target = P[r0] + delta;
-    if (P[cur.nR] < target) {
+    const int32_t P0 = P[r0], Pn = P[cur.nR];
+    const Acc Q0 = Q[r0], Qn = Q[cur.nR];
+    const int32_t target = P0 + delta;
+    if (Pn < target) {
       steps += cur.nR - r0;
-      return S - (Q[cur.nR] - Q[r0]);
+      return S - (Qn - Q0);
     }
-    int lo = r0, hi = cur.nR - 1;  // smallest z with P[z+1] >= target
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      if (P[mid + 1] >= target) hi = mid; else lo = mid + 1;
+    // smallest z in [r0, nR) with P[z+1] >= target: the answer stays in
+    // [lo, lo + n) with P[lo + n] >= target while n halves
+    int lo = r0, n = cur.nR - r0;
+    while (n > 1) {
+      const int half = n >> 1;
+      lo = P[lo + half] < target ? lo + half : lo;
+      n -= half;
     }
     steps += lo - r0 + 1;
-    if (cur.ld > lo || (cur.ld == lo && P[lo + 1] != target)) return Inf<Acc>::value;
+    const int32_t Pz = P[lo], Pz1 = P[lo + 1];
+    const Acc Qz = Q[lo];
     const int sz = L[lo].y & 0xFFFF;
-    return S - (Q[lo] - Q[r0]) -
-           (Acc)rc.hR * (Acc)(T - sz) * (Acc)(target - P[lo]);
+    if (cur.ld > lo || (cur.ld == lo && Pz1 != target)) return Inf<Acc>::value;
+    return S - (Qz - Q0) - (Acc)rc.hR * (Acc)(T - sz) * (Acc)(target - Pz);
   }
   // Less stock: walk the gR setups while delta < 0 (a shortfall at a
   // remanufacture-only setup is infeasible, and so is any deficit left).
+  // With surplus sg = A - need, xR = need + min(sg, 0), so the change of xR
+  // is min(sg + delta, 0) - min(sg, 0).
   for (int r = r0; r < cur.nR; ++r) {
     const int2 e = L[r];
     const int sr = e.y & 0xFFFF;
-    const int32_t a = A[sr];
-    const int32_t an = a + delta;
+    const int32_t sg = e.x, sn = sg + delta;
     ++steps;
-    if (!(e.y >> 16) && an < e.x) return Inf<Acc>::value;
-    const int32_t dx = (an < e.x ? an : e.x) - (a < e.x ? a : e.x);
+    if (!(e.y >> 16) && sn < 0) return Inf<Acc>::value;
+    const int32_t dx = (sn < 0 ? sn : 0) - (sg < 0 ? sg : 0);
     S -= (Acc)rc.hR * (Acc)(T - sr) * (Acc)dx;
     delta -= dx;
     if (delta == 0) break;

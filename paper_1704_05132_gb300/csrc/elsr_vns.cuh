@@ -323,7 +323,7 @@ __device__ __forceinline__ void rebuild_row(const Rows<Acc>& m, int q, int lane,
               ((Acc)rc.hM * (Acc)need - (Acc)rc.hR * (Acc)xr) * (Acc)(T - t);
       if (gr) {
         int2 en;
-        en.x = need;
+        en.x = avail - need;
         en.y = t | (gm << 16);
         L[r] = en;
         Pr[r] = lroom;
