@@ -14,6 +14,8 @@ Sifaleras (2017) that the C function follows:
 * ``vnd``                            -- Algorithm 1 (pipe VND)
 * ``shake`` / ``draw``               -- Algorithm 2, Shake(x, k)
 * ``vns`` / ``multistart``           -- Algorithm 2 (GVNS) and the best-of of Section 3
+* ``shake_worker`` / ``vns_forkjoin`` -- Algorithm 2 as the paper runs it: P
+  workers shake and descend from the same x, the minimum is kept (Section 3)
 """
 from __future__ import annotations
 
@@ -87,6 +89,8 @@ def _load():
                 "orc_draw": (u64, [u64, u64, u64, u64]),
                 "orc_shake": (None, [i32, i32, P, P, u64, i64, i32]),
                 "orc_vns": (i32, [P, P, P, u64, i32, i32, i32, P, P, P, P]),
+                "orc_shake_worker": (None, [i32, i32, P, P, u64, i64, i32, i32]),
+                "orc_vns_forkjoin": (i32, [P, P, P, u64, i32, i32, i32, i32, P, P, P, P]),
                 "orc_initial_solution": (None, [i32, i32, P, P]),
                 "orc_move_window": (i64, [P, i32, P, P, i32, i64]),
             }
@@ -272,6 +276,33 @@ def vns(inst: Instance, seed: int, iters: int, kmax: int = 3, mode: int = 0,
                      iters, kmax, mode, ctypes.byref(cnt), _ptr(log), _ptr(bc), _ptr(h))
     if rc != 0:
         raise RuntimeError("oracle VNS hit a VND cycle cap")
+    return VnsResult(int(bc[0]), gm, gr, _counters_dict(cnt), log[:iters], int(h[0]))
+
+
+def shake_worker(K, T, gM, gR, seed, it, k, worker):
+    """Shake(x, k) of fork-join worker p, in place (draws keyed p << 8 | j)."""
+    _load().orc_shake_worker(K, T, _ptr(gM), _ptr(gR), seed, it, k, worker)
+
+
+def vns_forkjoin(inst: Instance, seed: int, iters: int, kmax: int = 3, mode: int = 0,
+                 workers: int = 2, gM=None, gR=None) -> VnsResult:
+    """Algorithm 2 with P workers per iteration (Section 3's fork-join model):
+    every worker shakes the incumbent with its own draws and runs VND, the
+    least (f, worker) is kept when it improves.  traj["pad"] = the winner."""
+    lib = _load()
+    if gM is None or gR is None:
+        gM, gR = initial_solution(inst.K, inst.T)
+    gm = _bits(gM, inst.K, inst.T).copy()
+    gr = _bits(gR, inst.K, inst.T).copy()
+    cnt = _Counters()
+    log = np.zeros(max(iters, 1), TRAJ_DTYPE)
+    bc = np.zeros(1, np.int64)
+    h = np.zeros(1, np.uint64)
+    rc = lib.orc_vns_forkjoin(inst.cref, _ptr(gm), _ptr(gr), seed & 0xFFFFFFFFFFFFFFFF,
+                              iters, kmax, mode, workers, ctypes.byref(cnt), _ptr(log),
+                              _ptr(bc), _ptr(h))
+    if rc != 0:
+        raise RuntimeError("oracle fork-join GVNS hit a VND cycle cap")
     return VnsResult(int(bc[0]), gm, gr, _counters_dict(cnt), log[:iters], int(h[0]))
 
 

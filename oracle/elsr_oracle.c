@@ -520,6 +520,102 @@ int32_t orc_vns(const orc_instance *in, uint8_t *gM, uint8_t *gR, uint64_t seed,
     return rc;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Hybrid GVNS of Algorithm 2 (fork-join over workers, reading).             */
+/* ------------------------------------------------------------------------ */
+
+/* Shake(x, k) of worker p: as orc_shake, with move j drawn as
+ * draw(seed, it, k, p << 8 | j).  Worker 0 draws exactly as the sequential
+ * GVNS does. */
+void orc_shake_worker(int32_t K, int32_t T, uint8_t *gM, uint8_t *gR, uint64_t seed,
+                      int64_t it, int32_t k, int32_t worker)
+{
+    int64_t size = orc_nb_size(K, T, k);
+    if (size <= 0) return;
+    for (int32_t j = 0; j < k; ++j) {
+        uint64_t key = ((uint64_t)worker << 8) | (uint64_t)j;
+        uint64_t m = orc_draw(seed, (uint64_t)it, (uint64_t)k, key) % (uint64_t)size;
+        orc_apply_move(K, T, k, (int64_t)m, gM, gR);
+    }
+}
+
+/*
+ * Algorithm 2 as the paper runs it on two GPUs: every OpenMP thread (one per
+ * GPU) shakes the same incumbent x with the same k and runs VND on its own
+ * copy; the threads' objective values are compared and the minimum is kept
+ * (Section 3, fork-join model).  Reading, for P workers:
+ *   x = VND(start); k = 1
+ *   for it = 0 .. iters-1:
+ *       for p = 0 .. P-1:  x''_p = VND(Shake_p(x, k, it))
+ *       p* = the p with the least (f(x''_p), p)
+ *       if f(x''_p*) < f(x): x = x''_p*, k = 1
+ *       else:                k = k+1, back to 1 after kmax
+ * The log holds (it, k, f(x''_p*), accepted) with p* in its spare field; the
+ * trajectory hash folds the same values as the sequential GVNS.  Counters
+ * add up every worker's VND.  With one worker this is orc_vns.
+ */
+int32_t orc_vns_forkjoin(const orc_instance *in, uint8_t *gM, uint8_t *gR, uint64_t seed,
+                         int32_t iters, int32_t kmax, int32_t mode, int32_t workers,
+                         orc_counters *cnt, orc_traj *log, int64_t *best_cost,
+                         uint64_t *traj_hash)
+{
+    const int32_t K = in->K, T = in->T;
+    const size_t n = (size_t)K * T;
+    uint8_t *pM = malloc(n ? n : 1), *pR = malloc(n ? n : 1);
+    uint8_t *bM = malloc(n ? n : 1), *bR = malloc(n ? n : 1);
+    uint64_t h = 0;
+    int32_t rc = 0;
+
+    memset(cnt, 0, sizeof(*cnt));
+    if (orc_vnd(in, gM, gR, mode, cnt) != 0) rc = -1;
+    int64_t fx = orc_total_cost(in, gM, gR, NULL);
+    int32_t k = 1;
+    for (int32_t it = 0; it < iters && rc == 0; ++it) {
+        int64_t fbest = ORC_INF;
+        int32_t pbest = -1;
+        for (int32_t p = 0; p < workers; ++p) {
+            memcpy(pM, gM, n);
+            memcpy(pR, gR, n);
+            orc_shake_worker(K, T, pM, pR, seed, it, k, p);
+            if (orc_vnd(in, pM, pR, mode, cnt) != 0) rc = -1;
+            int64_t f2 = orc_total_cost(in, pM, pR, NULL);
+            if (pbest < 0 || f2 < fbest) { /* strict: the lowest worker wins ties */
+                fbest = f2;
+                pbest = p;
+                memcpy(bM, pM, n);
+                memcpy(bR, pR, n);
+            }
+        }
+        int32_t acc = fbest < fx;
+        if (log) {
+            log[it].it = it;
+            log[it].k = k;
+            log[it].cost = fbest;
+            log[it].accepted = acc;
+            log[it].pad = pbest;
+        }
+        h = traj_hash_step(h, it, k, fbest, acc);
+        cnt->iterations += 1;
+        if (acc) {
+            memcpy(gM, bM, n);
+            memcpy(gR, bR, n);
+            fx = fbest;
+            k = 1;
+            cnt->accepted += 1;
+        } else {
+            k = k + 1;
+            if (k > kmax) k = 1;
+        }
+    }
+    if (best_cost) *best_cost = fx;
+    if (traj_hash) *traj_hash = h;
+    free(pM);
+    free(pR);
+    free(bM);
+    free(bR);
+    return rc;
+}
+
 /* Initial solution (reading; the paper omits it): every setup open. */
 void orc_initial_solution(int32_t K, int32_t T, uint8_t *gM, uint8_t *gR)
 {

@@ -333,3 +333,93 @@ def test_eval_neighbourhood_matches_move_costs():
     for k in range(3):
         row = np.concatenate([c[k] for c in allc])
         assert pc[k] == row.min() and pm[k] == int(np.argmin(row))
+
+
+# ---------------------------------------------------------------------------
+# Fork-join GVNS (Algorithm 2 with one shake + VND per worker, the minimum
+# kept: the paper's two-GPU scheme of Section 3).
+# ---------------------------------------------------------------------------
+
+def test_shake_worker_follows_draws():
+    """Worker p's shake applies the moves drawn with key p << 8 | j (the
+    generator module's own splitmix64 recomputes them); worker 0 is the
+    sequential shake."""
+    K, T = 4, 11
+    mix = gen._mix_int
+    for seed, it, k, p in [(0, 0, 1, 0), (5, 3, 2, 1), (77, 40, 3, 6), (1, 9, 3, 255)]:
+        gm = np.zeros((K, T), np.uint8)
+        gr = np.zeros((K, T), np.uint8)
+        gm[:, ::3] = 1
+        gr[:, 1::2] = 1
+        a, b = gm.copy(), gr.copy()
+        oracle.shake_worker(K, T, a, b, seed, it, k, p)
+        size = oracle.nb_size(K, T, k)
+        for j in range(k):
+            d = mix(mix(mix(seed) ^ it) ^ ((k << 32) | (p << 8) | j))
+            oracle.apply_move(K, T, k, d % size, gm, gr)
+        assert (a == gm).all() and (b == gr).all()
+        if p == 0:
+            c, d2 = a.copy(), b.copy()
+            oracle.shake(K, T, a, b, seed, it, k)
+            oracle.shake_worker(K, T, c, d2, seed, it, k, 0)
+            assert (a == c).all() and (b == d2).all()
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_forkjoin_one_worker_is_sequential_gvns(mode):
+    inst = oracle.Instance.from_arrays(gen.plain_small())
+    a = oracle.vns(inst, seed=4, iters=150, kmax=3, mode=mode)
+    b = oracle.vns_forkjoin(inst, seed=4, iters=150, kmax=3, mode=mode, workers=1)
+    assert a.best_cost == b.best_cost and a.traj_hash == b.traj_hash
+    assert a.counters == b.counters
+    assert (a.gM == b.gM).all() and (a.gR == b.gR).all()
+    assert (a.traj["cost"] == b.traj["cost"]).all() and (b.traj["pad"] == 0).all()
+
+
+@pytest.mark.parametrize("mode,workers", [(0, 3), (1, 2), (0, 5)])
+def test_forkjoin_iterations_recomposed(mode, workers):
+    """Each logged iteration equals the minimum over workers of
+    f(VND(Shake_p(x, k))), recomputed here from the separately pinned
+    shake, VND and objective; acceptance, k and the incumbent follow the
+    rules of Algorithm 2."""
+    inst = oracle.Instance.from_arrays(gen.make_instance(31, 2, K=4, T=10))
+    iters = 25
+    res = oracle.vns_forkjoin(inst, seed=8, iters=iters, kmax=3, mode=mode, workers=workers)
+    gm, gr = oracle.initial_solution(inst.K, inst.T)
+    gm, gr, cnt0 = oracle.vnd(inst, gm, gr, mode)
+    fx = oracle.total_cost(inst, gm, gr)[0]
+    k = 1
+    moves = cnt0["moves_evaluated"]
+    for it in range(iters):
+        cands = []
+        for p in range(workers):
+            a, b = gm.copy(), gr.copy()
+            oracle.shake_worker(inst.K, inst.T, a, b, 8, it, k, p)
+            a, b, c = oracle.vnd(inst, a, b, mode)
+            moves += c["moves_evaluated"]
+            cands.append((oracle.total_cost(inst, a, b)[0], p, a, b))
+        f2, p, a, b = min(cands, key=lambda c: (c[0], c[1]))
+        e = res.traj[it]
+        assert (e["it"], e["k"], e["cost"], e["pad"]) == (it, k, f2, p)
+        assert bool(e["accepted"]) == (f2 < fx)
+        if f2 < fx:
+            gm, gr, fx, k = a, b, f2, 1
+        else:
+            k = k + 1 if k < 3 else 1
+    assert res.best_cost == fx
+    assert (res.gM == gm).all() and (res.gR == gr).all()
+    assert res.counters["moves_evaluated"] == moves
+    assert res.counters["iterations"] == iters
+
+
+@pytest.mark.parametrize("seed", range(2))
+def test_forkjoin_not_below_brute_force(seed):
+    g = gen.make_instance(40 + seed, 0, K=2, T=5)
+    inst = oracle.Instance.from_arrays(g)
+    opt = sum(_brute_force_row(inst, k) for k in range(inst.K))
+    for mode in (0, 1):
+        res = oracle.vns_forkjoin(inst, seed=seed, iters=20, kmax=3, mode=mode, workers=4)
+        assert res.best_cost >= opt
+        assert oracle.total_cost(inst, res.gM, res.gR)[0] == res.best_cost
+        acc = res.traj["cost"][res.traj["accepted"] == 1]
+        assert (np.diff(acc) < 0).all()
