@@ -133,13 +133,17 @@ void elsr_destroy(elsr_t *h);
 int elsr_set_stream(elsr_t *h, void *stream);
 
 /* Kernel launch shape: lanes per product row (4, 8, 16 or 32 lanes of one
- * warp; 64 or 128 = a row spread over 2 or 4 warps, mode P only) and threads
+ * warp; 64 or 128 = a row spread over 2 or 4 warps) and threads
  * per block (multiple of 32 and of the lanes, <= 1024); 0 keeps the default. */
 int elsr_set_launch(elsr_t *h, int32_t lanes_per_row, int32_t threads);
 
 /* CTAs of one thread-block cluster that share a GVNS run of this handle
- * (1..16; 0 = automatic).  Mode G runs always use one CTA.  Results do not
- * depend on it. */
+ * (1..16; 0 = automatic).  In mode G the CTAs' best keys meet through
+ * distributed shared memory once per neighbourhood, so the single argmin
+ * spans the whole cluster.  The cluster grows beyond the request until the
+ * run's rows fit the CTAs' shared memory (K = 300 x T = 104 needs at least
+ * 4 CTAs).
+ * Results do not depend on it. */
 int elsr_set_cluster(elsr_t *h, int32_t cluster);
 
 /* Speculative execution of one mode-P GVNS run: up to `teams` clusters run

@@ -282,19 +282,16 @@ struct LaunchShape {
 int vns_shape(elsr_batch* b, LaunchShape* ls) {
   const int acc = b->acc64 ? 8 : 4;
   int maxK = 0, maxT = 0;
-  bool any_g = false;
   for (const RunDesc& r : b->h_runs) {
     maxK = std::max(maxK, b->insts[r.inst].K);
     maxT = std::max(maxT, b->insts[r.inst].T);
-    any_g = any_g || r.mode != ELSR_MODE_P;
   }
   int C = b->cluster;
   if (C <= 0) C = b->h_runs.size() == 1 ? std::min(8, std::max(1, maxK / 6)) : 1;
-  if (any_g) C = 1;  // the global argmin of mode G runs inside one CTA
   C = std::min(C, maxK);
   size_t need_s = 0, need_g = 0;
   // Grow the cluster until the largest run's rows fit the CTAs' shared
-  // memory (mode P only; mode G needs its rows in one CTA).
+  // memory.
   for (;;) {
     need_s = need_g = 0;
     for (const RunDesc& r : b->h_runs) {
@@ -303,7 +300,7 @@ int vns_shape(elsr_batch* b, LaunchShape* ls) {
       need_s = std::max<size_t>(need_s, vns_layout(kc, d.T, acc, true).total);
       need_g = std::max<size_t>(need_g, vns_layout(kc, d.T, acc, false).total);
     }
-    if (need_g <= (size_t)kSmemLimit || any_g || C >= 16 || C >= maxK) break;
+    if (need_g <= (size_t)kSmemLimit || C >= 16 || C >= maxK) break;
     ++C;
   }
   ls->nw = maxT <= 64 ? 1 : 2;
@@ -316,7 +313,6 @@ int vns_shape(elsr_batch* b, LaunchShape* ls) {
   }
   const bool single = b->h_runs.size() == 1;
   ls->G = b->lanes ? b->lanes : default_lanes(maxT, single);
-  if (ls->G > 32 && any_g) ls->G = 32;  // rows wider than a warp: mode P only
   const int kc = (maxK + C - 1) / C;
   int thr = b->threads;
   // Default block: one CTA per SM; a single run keeps its CTAs small (its

@@ -421,7 +421,7 @@ struct Team {
   }
 };
 
-// Row groups wider than a warp (G = 64 or 128 lanes, mode P): the group's
+// Row groups wider than a warp (G = 64 or 128 lanes): the group's
 // warps meet at named barrier 1 + group index.
 template <typename Acc>
 __device__ __forceinline__ void group_sync(const Team<Acc>& t) {
@@ -553,9 +553,10 @@ __device__ __forceinline__ void write_failed_run(const VnsParams& p, const RunDe
   p.out[rd.out] = o;
 }
 
-// Saturating objective of the team (sum of row costs over the cluster).
+// Objective of the team: F = sum of the feasible rows' costs and ninf = the
+// number of infeasible rows over the cluster (every thread gets both).
 template <typename Acc>
-__device__ int64_t team_total(Team<Acc>& t) {
+__device__ void team_sums(Team<Acc>& t, int64_t& F, int& ninf) {
   CtlShared* sh = t.sh;
   const int tp = t.tp;
   if (t.lane == 0) {
@@ -569,9 +570,9 @@ __device__ int64_t team_total(Team<Acc>& t) {
     if (ni) atomicAdd(&sh->ninf[tp], ni);
   }
   __syncthreads();
-  int64_t tot;
   if (t.C == 1) {
-    tot = sh->ninf[tp] ? INT64_MAX : (int64_t)sh->acc[tp];
+    F = (int64_t)sh->acc[tp];
+    ninf = sh->ninf[tp];
   } else {
     cg::cluster_group cl = cg::this_cluster();
     cl.sync();
@@ -585,14 +586,23 @@ __device__ int64_t team_total(Team<Acc>& t) {
       a += __shfl_xor_sync(kFull, a, o);
       ni += __shfl_xor_sync(kFull, ni, o);
     }
-    tot = ni ? INT64_MAX : (int64_t)a;
+    F = (int64_t)a;
+    ninf = ni;
   }
   if (t.tid == 0) {
     sh->acc[tp ^ 1] = 0ull;
     sh->ninf[tp ^ 1] = 0;
   }
   t.tp ^= 1;
-  return tot;
+}
+
+// Saturating objective of the team (sum of row costs over the cluster).
+template <typename Acc>
+__device__ int64_t team_total(Team<Acc>& t) {
+  int64_t F;
+  int ni;
+  team_sums(t, F, ni);
+  return ni ? INT64_MAX : F;
 }
 
 // VND of Algorithm 1 (pipe form), mode P: every product takes its best
@@ -661,43 +671,36 @@ __device__ int vnd_p(Team<Acc>& t, const int* stop = nullptr, int my_index = 0) 
   return cycles;
 }
 
-// VND, mode G (single-CTA teams): one best move of the whole neighbourhood by
-// (new objective, global index), applied when it lowers the objective.
+// VND, mode G: one best move of the whole neighbourhood by (new objective,
+// global index), applied when it lowers the objective.  Every CTA of the
+// team evaluates its own rows; the CTAs' minima meet through distributed
+// shared memory, so all CTAs hold the same winning key.  A winning key's cost
+// is the new objective itself (the other rows plus the moved row), which
+// every CTA adopts without a further exchange.
 template <typename Acc, int NW>
 __device__ int vnd_g(Team<Acc>& t) {
   CtlShared* sh = t.sh;
-  const int T = t.T;
-  if (t.tid == 0) {
-    sh->F = 0;
-    sh->Finf = 0;
-    sh->gkey[0] = sh->gkey[1] = ~0ull;
-  }
-  __syncthreads();
-  if (t.lane == 0) {
-    long long s = 0;
-    int ni = 0;
-    for (int q = t.sub; q < t.Kc; q += t.nsub) {
-      const int64_t c = t.m.cost(q);
-      if (c == INT64_MAX) ++ni; else s += c;
-    }
-    if (s) atomicAdd((unsigned long long*)&sh->F, (unsigned long long)s);
-    if (ni) atomicAdd(&sh->Finf, ni);
-  }
-  __syncthreads();
+  const int T = t.T, C = t.C;
+  int64_t F;    // sum of the feasible rows' costs (team-wide)
+  int Finf;     // infeasible rows (team-wide)
+  team_sums(t, F, Finf);
+  if (t.tid == 0) sh->gkey[0] = sh->gkey[1] = ~0ull;
+  team_sync(C);
+  const int GW = t.G < 32 ? t.G : 32;  // lanes of the group inside one warp
   int cycles = 0, e = 0;
   for (;;) {
     bool improved = false;
     for (int j = 1; j <= 3; ++j) {
       const int M = row_moves(T, j);
       if (M <= 0) continue;
-      const int64_t F = sh->F;
-      const int Finf = sh->Finf;
       const int64_t total = Finf ? INT64_MAX : F;
+      // every warp runs the same number of row iterations (the sub-warp
+      // minimum below is a full-warp shuffle)
       for (int qq = t.sub; qq < t.Kcr; qq += t.nsub) {
-        const bool valid = qq < t.Kc;
-        const int q = valid ? qq : 0;
         uint64_t best = ~0ull;
-        if (valid) {
+        if (qq < t.Kc) {
+          const int q = qq;
+          const int kg = q * C + t.crank;  // global row index
           const RowState<Acc> cur = t.m.state(q);
           const int64_t rck = t.m.cost(q);
           const int infk = rck == INT64_MAX;
@@ -714,42 +717,43 @@ __device__ int vnd_g(Team<Acc>& t) {
                                              t.m.L + q * T, t.m.P + q * (T + 1),
                                              t.m.Q + q * (T + 1), j, l, st);
             const int64_t nc = row_cost<Acc>(S, c0);
-            const int64_t nt = (others == INT64_MAX || nc == INT64_MAX) ? INT64_MAX : others + nc;
-            best = umin64(best, pack_key(nt, (uint32_t)(q * M + l)));
+            const int64_t nt =
+                (others == INT64_MAX || nc == INT64_MAX) ? INT64_MAX : others + nc;
+            best = umin64(best, pack_key(nt, (uint32_t)(kg * M + l)));
           }
           t.steps += (uint32_t)st;
         }
-        best = subwarp_min(best, t.G);
-        if (valid && t.lane == 0 && best != ~0ull) atomicMin(&sh->gkey[e], best);
+        best = subwarp_min(best, GW);
+        if ((t.tid & (GW - 1)) == 0 && best != ~0ull) atomicMin(&sh->gkey[e], best);
       }
-      __syncthreads();
-      const uint64_t gk = sh->gkey[e];
+      uint64_t gk;
+      if (C == 1) {
+        __syncthreads();
+        gk = sh->gkey[e];
+      } else {
+        cg::cluster_group cl = cg::this_cluster();
+        cl.sync();
+        uint64_t v = t.wlane < C ? *cl.map_shared_rank(&sh->gkey[e], t.wlane) : ~0ull;
+        gk = subwarp_min(v, 32);
+      }
       if (t.tid == 0) sh->gkey[e ^ 1] = ~0ull;
       if (gk != ~0ull && key_cost(gk) < total) {
         const int gi = key_index(gk);
-        const int qw = gi / M, lw = gi - qw * M;
-        if ((qw % t.nsub) == t.sub) {
-          int64_t old = 0;
+        const int kw = gi / M, lw = gi - kw * M;
+        const int qw = kw / C;
+        if ((kw % C) == t.crank && (qw % t.nsub) == t.sub) {
           if (t.lane == 0) {
-            old = t.m.cost(qw);
             RowBits nb = t.m.bits[qw];
             apply_row_move(nb, T, j, lw);
             t.m.bits[qw] = nb;
             ++t.applied;
           }
-          __syncwarp(t.smask);
-          rebuild_row<Acc, NW>(t.m, qw, t.lane, t.G, t.smask);
-          __syncwarp(t.smask);
-          if (t.lane == 0) {
-            const int64_t nw = t.m.cost(qw);
-            if (old == INT64_MAX) {
-              sh->Finf = Finf - 1;
-              sh->F = F + nw;
-            } else {
-              sh->F = F - old + nw;
-            }
-          }
+          group_sync(t);
+          group_rebuild<Acc, NW>(t, qw);
         }
+        // the new objective is finite, so every row is feasible now
+        F = key_cost(gk);
+        Finf = 0;
         improved = true;
       }
       __syncthreads();
@@ -768,13 +772,15 @@ __device__ __forceinline__ int vnd(Team<Acc>& t, int mode) {
 }
 
 // Shake(x, k) of Algorithm 2: k moves of N_k from splitmix64 draws keyed by
-// (seed, iteration, k, move); `first` marks a row's first hit.
+// (seed, iteration, k, move j); a fork-join worker p draws with move key
+// p << 8 | j (key_hi = p << 8).  `first` marks a row's first hit.
 struct ShakePlan {
   int rows[kMaxShake], locs[kMaxShake];
   bool first[kMaxShake];
 };
 
-__device__ __forceinline__ ShakePlan plan_shake(uint64_t seed, int it, int ks, int K, int T) {
+__device__ __forceinline__ ShakePlan plan_shake(uint64_t seed, int it, int ks, int K, int T,
+                                                uint64_t key_hi = 0) {
   ShakePlan pl;
   const int per = row_moves(T, ks);
   const int64_t size = per > 0 ? (int64_t)K * per : 0;
