@@ -33,6 +33,13 @@ WORKLOAD = {
                 "2000 shaking iterations, kmax=3, mode P",
     "K": 50, "T": 52, "gen_seed": 1, "vns_seed": 1, "iters": 2000, "kmax": 3, "mode": "P",
 }
+# Paper-shaped instance (the size of the paper's benchmark set: K=300
+# products, T=52 periods), secondary measurement via --instance paper.
+WORKLOAD_PAPER = {
+    "workload": "plain GVNS, one instance K=300 products x T=52 periods (paper-shaped), "
+                "seed 3, 1000 shaking iterations, kmax=3, mode P",
+    "K": 300, "T": 52, "gen_seed": 3, "vns_seed": 1, "iters": 1000, "kmax": 3, "mode": "P",
+}
 METRIC = "candidate moves evaluated/s"
 UNIT = "moves/s"
 INT_OPS_PER_SEGMENT = 16      # algorithmic integer operations per decode segment
@@ -174,18 +181,29 @@ def run_gpu(args):
     if world > 1:
         dist.barrier()
 
-    g = gen.plain_medium()
+    wl = dict(WORKLOAD_PAPER if args.instance == "paper" else WORKLOAD)
+    g = gen.paper_shaped() if args.instance == "paper" else gen.plain_medium()
+    mode = 1 if args.mode == "G" else 0
+    wl["mode"] = args.mode
+    wl["workload"] = wl["workload"].replace("mode P", f"mode {args.mode}")
+    if args.workers:
+        wl["workload"] = ("fork-join " + wl["workload"] +
+                          f", {args.workers} workers per iteration (Algorithm 2, Section 3)")
+        wl["workers"] = args.workers
     K, T = g.K, g.T
-    seed = WORKLOAD["vns_seed"] + rank  # replicas: one seed per rank
+    seed = wl["vns_seed"] + rank  # replicas: one seed per rank
     stream = torch.cuda.current_stream(dev)
     solver = elsr.Solver(g, stream=stream, lanes=args.lanes, threads=args.threads,
                          cluster=args.cluster, speculation=args.speculation)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
 
-    iters = args.iters if args.iters is not None else WORKLOAD["iters"]
+    iters = args.iters if args.iters is not None else wl["iters"]
 
     def step():
-        solver.vns_run(seed, iters, WORKLOAD["kmax"], 0)
+        if args.workers:
+            solver.vns_forkjoin_run(seed, iters, wl["kmax"], mode, args.workers)
+        else:
+            solver.vns_run(seed, iters, wl["kmax"], mode)
 
     for _ in range(args.warmup):
         step()
@@ -257,7 +275,10 @@ def run_gpu(args):
         t0 = time.perf_counter()
         s2 = elsr.Solver(host, stream=stream, lanes=args.lanes, threads=args.threads,
                          cluster=args.cluster, speculation=args.speculation)
-        s2.vns_run(seed, iters, WORKLOAD["kmax"], 0)
+        if args.workers:
+            s2.vns_forkjoin_run(seed, iters, wl["kmax"], mode, args.workers)
+        else:
+            s2.vns_run(seed, iters, wl["kmax"], mode)
         r2 = s2.result(solution=True, traj=False)
         s2.close()
         dt = time.perf_counter() - t0
@@ -280,9 +301,9 @@ def run_gpu(args):
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": dict(WORKLOAD, iters=iters, parallelism=f"replicas x{world}",
+        "config": dict(wl, iters=iters, parallelism=f"replicas x{world}",
                        l2="flushed between steps (256 MiB device write, untimed)",
-                       launch="one persistent thread-block cluster per GVNS run"),
+                       launch="one persistent launch per GVNS run"),
         "instances_per_s": world * args.steps / t_max,
         "moves_per_step": moves_per_step,
         "eval_launch": eval_launch,
@@ -297,7 +318,8 @@ def run_gpu(args):
                              f"{segs_per_step} segments per launch; peak = {SMS} SMs x "
                              f"{LANES_PER_SM} lanes x {SM_MAX_MHZ:.0f} MHz"},
     }
-    if not args.no_cpu_baseline and world == 1:
+    if not args.no_cpu_baseline and world == 1 and args.instance == "medium" \
+            and not args.workers and mode == 0:
         line["cpu_baseline"] = cpu_baseline(args.cpu_iters)
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -423,6 +445,13 @@ def main():
     ap.add_argument("--cluster", type=int, default=0, help="CTAs per run (0: automatic)")
     ap.add_argument("--speculation", type=int, default=0,
                     help="speculative teams for the single run (0: automatic, 1: off)")
+    ap.add_argument("--instance", default="medium", choices=["medium", "paper"],
+                    help="plain workload instance: K=50 x T=52 (default) or the paper-shaped "
+                         "K=300 x T=52")
+    ap.add_argument("--mode", default="P", choices=["P", "G"],
+                    help="VND mode of the plain workload (P: Algorithm 1, G: single argmin)")
+    ap.add_argument("--workers", type=int, default=0,
+                    help="fork-join workers per iteration (0: the sequential GVNS)")
     ap.add_argument("--workload", default="plain",
                     choices=["plain", "batch", "multistart", "serve"])
     ap.add_argument("--rate", type=float, default=2000.0, help="serving arrivals per second")

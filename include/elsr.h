@@ -205,7 +205,28 @@ int elsr_vns_run(elsr_t *h, uint64_t seed, int32_t iters, int32_t kmax,
                  int32_t mode);
 
 /*
- * Results of the last elsr_vns_run (waits for it).  stats (nullable); gM,
+ * Algorithm 2 as the paper runs it on two GPUs (Section 3, fork-join model),
+ * with `workers` workers on this GPU.  In every iteration each worker p
+ * shakes the incumbent x with the iteration's k and its own draws (move j
+ * of worker p is drawn as draw(seed, it, k, p << 8 | j), so worker 0 draws
+ * exactly as elsr_vns_run does) and runs VND (mode P or G) on its copy; the
+ * least (f(x''_p), p) replaces x when it is below f(x), and k goes back to 1,
+ * else k+1, wrapping after kmax.  x starts as VND of the current solution.
+ * Each worker is one team of CTAs (the handle's cluster and launch
+ * settings) and all workers run at once, so `workers` may not exceed the
+ * teams the device holds resident for this instance (ELSR_E_RANGE, with the
+ * number in elsr_last_error) nor ELSR_FJ_WORKERS_MAX (ELSR_E_ARG).  Every
+ * worker's VND counts in the statistics.  elsr_result() returns x, the
+ * statistics and the trajectory; an entry's `reserved` field holds the
+ * winning worker.  With one worker the run equals elsr_vns_run's.
+ * Asynchronous, like elsr_vns_run.
+ */
+#define ELSR_FJ_WORKERS_MAX 4096
+int elsr_vns_forkjoin_run(elsr_t *h, uint64_t seed, int32_t iters,
+                          int32_t kmax, int32_t mode, int32_t workers);
+
+/*
+ * Results of the last elsr_vns_run or elsr_vns_forkjoin_run (waits for it).  stats (nullable); gM,
  * gR (nullable, host [K][T] 0/1) receive x; plan (nullable, host int32
  * [4][K][T]) receives xM, xR, yM, yR of x; traj (nullable, host
  * [traj_capacity]) receives the first min(iters, traj_capacity) entries.

@@ -65,6 +65,7 @@ SIGNATURES = {
     "elsr_eval_neighbourhood": (ctypes.c_int, [P, u32, i32, P, P, P, P]),
     "elsr_move_costs": (ctypes.c_int, [P, i32, P, P]),
     "elsr_vns_run": (ctypes.c_int, [P, u64, i32, i32, i32]),
+    "elsr_vns_forkjoin_run": (ctypes.c_int, [P, u64, i32, i32, i32, i32]),
     "elsr_result": (ctypes.c_int, [P, P, P, P, P, P, i32]),
     "elsr_multistart_run": (ctypes.c_int, [P, u64, i32, i32, i32, i32, P, P, P]),
     "elsr_counters": (ctypes.c_int, [P, P]),

@@ -1,7 +1,10 @@
 """Build the in-tree C-ABI library ``_build/libelsr.so`` with nvcc (sm_103a).
 
-Two translation units (kernels, ABI) compile in parallel, then link into one
-shared library.  Only nvcc and the host compiler are needed; no cmake.
+The translation units compile in parallel, then link into one shared
+library.  The persistent GVNS kernels are compiled once per instantiation
+(accumulator width x bit-row words x table placement x block bound = 24
+objects from elsr_vns_inst.cu), so no single object carries all of them.
+Only nvcc and the host compiler are needed; no cmake.
 """
 from __future__ import annotations
 
@@ -15,9 +18,14 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libelsr.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["elsr_vns_i32_w1.cu", "elsr_vns_i32_w2.cu", "elsr_vns_i64_w1.cu",
-           "elsr_vns_i64_w2.cu", "elsr_kernels.cu", "elsr_abi.cu", "elsr_static.cu"]
+SOURCES = ["elsr_vns_dispatch.cu", "elsr_kernels.cu", "elsr_abi.cu", "elsr_static.cu"]
 HEADERS = ["elsr_row.cuh", "elsr_internal.h", "elsr_vns.cuh"]
+# (object suffix, defines) of each GVNS kernel instantiation
+VNS_INST = [(f"i{acc[3:5]}_w{nw}_{'s' if ts else 'g'}{maxt}",
+             [f"-DELSR_INST_ACC={acc}", f"-DELSR_INST_NW={nw}", f"-DELSR_INST_TS={ts}",
+              f"-DELSR_INST_MAXT={maxt}"])
+            for acc in ("int32_t", "int64_t") for nw in (1, 2) for ts in (1, 0)
+            for maxt in (256, 512, 1024)]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
@@ -44,12 +52,14 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     deps_common = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(INCLUDE, "elsr.h")]
     objs = []
     jobs = []
-    for src in SOURCES:
+    units = [(src, src.replace(".cu", ".o"), []) for src in SOURCES]
+    units += [("elsr_vns_inst.cu", f"elsr_vns_{suf}.o", defs) for suf, defs in VNS_INST]
+    for src, obj, defs in units:
         s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD, src.replace(".cu", ".o"))
+        o = os.path.join(BUILD, obj)
         objs.append(o)
         if force or ptxas_info or _stale(o, [s] + deps_common):
-            cmd = [nvcc()] + NVCC_FLAGS + ["-c", s, "-o", o]
+            cmd = [nvcc()] + NVCC_FLAGS + defs + ["-c", s, "-o", o]
             if ptxas_info:
                 cmd += ["-Xptxas", "-v"]
             jobs.append(cmd)
@@ -61,7 +71,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         return r.stdout + r.stderr
 
     logs = []
-    workers = max(1, min(len(SOURCES), os.cpu_count() or 1))
+    workers = max(1, min(len(units), os.cpu_count() or 1))
     with cf.ThreadPoolExecutor(max_workers=workers) as ex:
         logs = list(ex.map(run, jobs))
     if verbose or ptxas_info:

@@ -355,9 +355,28 @@ int vns_shape(elsr_batch* b, LaunchShape* ls) {
   return ELSR_OK;
 }
 
-// Queue the runs of b->h_runs (already ordered) on b->stream.
+// Room for `teams` speculative teams or fork-join workers: their result
+// slots and published rows (two round parities each), the grid-barrier
+// words and the speculative decision words.
+int ensure_spec(elsr_batch* b, int teams) {
+  if (teams <= (int)b->spec_cap) return ELSR_OK;
+  dev_free(b->d_spec_slots, b->stream);
+  dev_free(b->d_spec_rows, b->stream);
+  dev_free(b->d_spec_bar, b->stream);
+  dev_free(b->d_spec_dec, b->stream);
+  b->spec_cap = 0;
+  ELSR_TRY_CUDA(b, dev_alloc(&b->d_spec_slots, (size_t)2 * teams, b->stream));
+  ELSR_TRY_CUDA(b, dev_alloc(&b->d_spec_rows, (size_t)2 * teams * kMaxShake, b->stream));
+  ELSR_TRY_CUDA(b, dev_alloc(&b->d_spec_bar, 2, b->stream));
+  ELSR_TRY_CUDA(b, dev_alloc(&b->d_spec_dec, 2, b->stream));
+  b->spec_cap = teams;
+  return ELSR_OK;
+}
+
+// Queue the runs of b->h_runs (already ordered) on b->stream.  fj_workers > 0
+// runs the single run of b->h_runs as that many fork-join workers.
 int launch_runs(elsr_batch* b, const RowBits* start_bits, bool with_traj,
-                int64_t traj_entries, bool allow_spec = false) {
+                int64_t traj_entries, bool allow_spec = false, int fj_workers = 0) {
   LaunchShape ls;
   int rc = vns_shape(b, &ls);
   if (rc != ELSR_OK) return rc;
@@ -403,6 +422,38 @@ int launch_runs(elsr_batch* b, const RowBits* start_bits, bool with_traj,
   p.spec_rows = nullptr;
   p.spec_bar = nullptr;
   p.spec_dec = nullptr;
+  p.fj_workers = 0;
+  p.pad2 = 0;
+  if (fj_workers > 0) {
+    const int resident = ls.cluster == 1 ? ls.active * b->sms : ls.active;
+    if (nr != 1 || fj_workers > resident) {
+      b->err = "fork-join workers (" + std::to_string(fj_workers) +
+               ") exceed the teams that can be resident at once (" +
+               std::to_string(resident) + " with " + std::to_string(ls.cluster) +
+               " CTAs per worker)";
+      return ELSR_E_RANGE;
+    }
+    if ((rc = ensure_spec(b, fj_workers)) != ELSR_OK) return rc;
+    ELSR_TRY_CUDA(b, cudaMemsetAsync(b->d_spec_bar, 0, 2 * sizeof(int32_t), b->stream));
+    p.fj_workers = fj_workers;
+    p.spec_slots = b->d_spec_slots;
+    p.spec_rows = b->d_spec_rows;
+    p.spec_bar = b->d_spec_bar;
+    ls.blocks = fj_workers * ls.cluster;
+    ELSR_TRY_CUDA(b, vns_launch(b->acc64, ls.nw, ls.ts, ls.maxt, p, ls.blocks, ls.threads,
+                                ls.smem, ls.cluster, b->stream));
+    b->last_shape[7] = fj_workers;
+    b->last_shape[0] = ls.G;
+    b->last_shape[1] = ls.threads;
+    b->last_shape[2] = ls.cluster;
+    b->last_shape[3] = ls.blocks;
+    b->last_shape[4] = (int)ls.smem;
+    b->last_shape[5] = ls.ts;
+    b->last_shape[6] = ls.nw;
+    b->nruns = 1;
+    b->have_result = true;
+    return ELSR_OK;
+  }
   // A single mode-P run may be spread over several teams that speculate on
   // consecutive iterations (exact: the committed trajectory is the
   // sequential one).
@@ -415,18 +466,7 @@ int launch_runs(elsr_batch* b, const RowBits* start_bits, bool with_traj,
   }
   cudaError_t le = cudaErrorUnknown;
   if (teams > 1) {
-    if (teams > (int)b->spec_cap) {
-      dev_free(b->d_spec_slots, b->stream);
-      dev_free(b->d_spec_rows, b->stream);
-      dev_free(b->d_spec_bar, b->stream);
-      dev_free(b->d_spec_dec, b->stream);
-      b->spec_cap = 0;
-      ELSR_TRY_CUDA(b, dev_alloc(&b->d_spec_slots, (size_t)2 * teams, b->stream));
-      ELSR_TRY_CUDA(b, dev_alloc(&b->d_spec_rows, (size_t)2 * teams * kMaxShake, b->stream));
-      ELSR_TRY_CUDA(b, dev_alloc(&b->d_spec_bar, 2, b->stream));
-      ELSR_TRY_CUDA(b, dev_alloc(&b->d_spec_dec, 2, b->stream));
-      b->spec_cap = teams;
-    }
+    if ((rc = ensure_spec(b, teams)) != ELSR_OK) return rc;
     ELSR_TRY_CUDA(b, cudaMemsetAsync(b->d_spec_bar, 0, 2 * sizeof(int32_t), b->stream));
     // decision words start undecided; slot round tags start at -1
     ELSR_TRY_CUDA(b, cudaMemsetAsync(b->d_spec_dec, 0x7f, 2 * sizeof(int32_t), b->stream));
@@ -574,7 +614,7 @@ int refresh_rowcost(elsr_ctx* h) { return eval_launch(h, 0u, 0, 0, true); }
 
 extern "C" {
 
-int elsr_version(void) { return 10000; }
+int elsr_version(void) { return 10100; }
 
 int elsr_run_footprint(int32_t K, int32_t T, int32_t* smem_one_cta, int64_t* device_bytes) {
   if (K < 1 || T < 1 || T > ELSR_T_MAX) return ELSR_E_ARG;
@@ -811,6 +851,37 @@ int elsr_vns_run(elsr_t* h, uint64_t seed, int32_t iters, int32_t kmax, int32_t 
   r.traj_off = 0;
   b->h_runs.assign(1, r);
   int rc = launch_runs(b, h->d_state, true, iters, true);
+  if (rc != ELSR_OK) return rc;
+  h->last_kind = 1;
+  h->last_iters = iters;
+  h->best_out = 0;
+  h->counted = false;
+  return ELSR_OK;
+}
+
+int elsr_vns_forkjoin_run(elsr_t* h, uint64_t seed, int32_t iters, int32_t kmax,
+                          int32_t mode, int32_t workers) {
+  if (!h) return ELSR_E_ARG;
+  if (iters < 0 || kmax < 1 || kmax > 3 || (mode != ELSR_MODE_P && mode != ELSR_MODE_G) ||
+      workers < 1 || workers > ELSR_FJ_WORKERS_MAX) {
+    h->b.err = "need iters >= 0, 1 <= kmax <= 3, mode P or G, 1 <= workers <= " +
+               std::to_string(ELSR_FJ_WORKERS_MAX);
+    return ELSR_E_ARG;
+  }
+  elsr_batch* b = &h->b;
+  RunDesc r;
+  r.inst = 0;
+  r.iters = iters;
+  r.kmax = kmax;
+  r.mode = mode;
+  r.seed = seed;
+  r.out = 0;
+  r.pad = 0;
+  r.bits_off = 0;
+  r.start_off = 0;
+  r.traj_off = 0;
+  b->h_runs.assign(1, r);
+  int rc = launch_runs(b, h->d_state, true, iters, false, workers);
   if (rc != ELSR_OK) return rc;
   h->last_kind = 1;
   h->last_iters = iters;

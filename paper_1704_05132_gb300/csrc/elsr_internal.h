@@ -97,6 +97,10 @@ struct VnsParams {
   RowBits* spec_rows;    // [2][spec_teams][3]
   int32_t* spec_bar;     // [2]: arrivals, generation; zero at launch
   int32_t* spec_dec;     // [2]: per round parity, first accepting team once known
+  // fork-join launches (Algorithm 2 with one shake + VND per worker): the
+  // fj_workers teams share spec_slots, spec_rows and spec_bar (0: off)
+  int32_t fj_workers;
+  int32_t pad2;
 };
 
 struct StageParams {
@@ -190,40 +194,24 @@ size_t eval_smem_bytes(int rows, int T, bool acc64);
 cudaError_t launch_bestof(const BestofParams& p, cudaStream_t s);
 cudaError_t launch_plan(const PlanParams& p, int K, cudaStream_t s);
 
-// Persistent GVNS kernel variants: accumulator width, 64-bit words per bit
-// row (nw = 1 when T <= 64), prefix tables in shared memory (ts), block size
-// bound (maxt = 256, 512 or 1024).  cluster = CTAs per run (1 = no cluster).
-// prepare sets the kernel attributes and returns the resident blocks per SM
-// (cluster == 1) or the resident clusters on the device (cluster > 1).
-cudaError_t vns_prepare_i32_w1(bool ts, int maxt, size_t smem, int threads, int cluster, int* active);
-cudaError_t vns_prepare_i32_w2(bool ts, int maxt, size_t smem, int threads, int cluster, int* active);
-cudaError_t vns_prepare_i64_w1(bool ts, int maxt, size_t smem, int threads, int cluster, int* active);
-cudaError_t vns_prepare_i64_w2(bool ts, int maxt, size_t smem, int threads, int cluster, int* active);
-cudaError_t vns_launch_i32_w1(bool ts, int maxt, const VnsParams& p, int blocks, int threads,
-                              size_t smem, int cluster, cudaStream_t s);
-cudaError_t vns_launch_i32_w2(bool ts, int maxt, const VnsParams& p, int blocks, int threads,
-                              size_t smem, int cluster, cudaStream_t s);
-cudaError_t vns_launch_i64_w1(bool ts, int maxt, const VnsParams& p, int blocks, int threads,
-                              size_t smem, int cluster, cudaStream_t s);
-cudaError_t vns_launch_i64_w2(bool ts, int maxt, const VnsParams& p, int blocks, int threads,
-                              size_t smem, int cluster, cudaStream_t s);
+// Persistent GVNS kernels (elsr_vns.cuh), one instantiation per accumulator
+// width (Acc), 64-bit words per bit row (NW = 1 when T <= 64), prefix tables
+// in shared memory (TS) and block size bound (MAXT = 256, 512 or 1024); each
+// combination is compiled in a translation unit of its own
+// (elsr_vns_inst.cu).  prepare sets the kernel attributes and returns the
+// resident blocks per SM (cluster == 1) or the resident clusters on the
+// device (cluster > 1).  launch starts the batched kernel, the speculative
+// one (p.spec_teams > 1) or the fork-join one (p.fj_workers > 0).
+template <typename Acc, int NW, bool TS, int MAXT>
+cudaError_t vns_prepare_t(size_t smem, int threads, int cluster, int* active);
+template <typename Acc, int NW, bool TS, int MAXT>
+cudaError_t vns_launch_t(const VnsParams& p, int blocks, int threads, size_t smem,
+                         int cluster, cudaStream_t s);
 
-inline cudaError_t vns_prepare(bool acc64, int nw, bool ts, int maxt, size_t smem, int threads,
-                               int cluster, int* active) {
-  if (acc64)
-    return nw == 1 ? vns_prepare_i64_w1(ts, maxt, smem, threads, cluster, active)
-                   : vns_prepare_i64_w2(ts, maxt, smem, threads, cluster, active);
-  return nw == 1 ? vns_prepare_i32_w1(ts, maxt, smem, threads, cluster, active)
-                 : vns_prepare_i32_w2(ts, maxt, smem, threads, cluster, active);
-}
-
-inline cudaError_t vns_launch(bool acc64, int nw, bool ts, int maxt, const VnsParams& p,
-                              int blocks, int threads, size_t smem, int cluster, cudaStream_t s) {
-  if (acc64)
-    return nw == 1 ? vns_launch_i64_w1(ts, maxt, p, blocks, threads, smem, cluster, s)
-                   : vns_launch_i64_w2(ts, maxt, p, blocks, threads, smem, cluster, s);
-  return nw == 1 ? vns_launch_i32_w1(ts, maxt, p, blocks, threads, smem, cluster, s)
-                 : vns_launch_i32_w2(ts, maxt, p, blocks, threads, smem, cluster, s);
-}
+// Run-time choice of the instantiation (elsr_vns_dispatch.cu).
+cudaError_t vns_prepare(bool acc64, int nw, bool ts, int maxt, size_t smem, int threads,
+                        int cluster, int* active);
+cudaError_t vns_launch(bool acc64, int nw, bool ts, int maxt, const VnsParams& p,
+                       int blocks, int threads, size_t smem, int cluster, cudaStream_t s);
 
 }  // namespace elsr

@@ -790,7 +790,7 @@ __device__ __forceinline__ ShakePlan plan_shake(uint64_t seed, int it, int ks, i
     pl.locs[j] = 0;
     pl.first[j] = false;
     if (j < ks && size > 0) {
-      const uint64_t d = shake_draw(seed, (uint64_t)it, (uint64_t)ks, (uint64_t)j);
+      const uint64_t d = shake_draw(seed, (uint64_t)it, (uint64_t)ks, key_hi | (uint64_t)j);
       const int64_t mv = (int64_t)(d % (uint64_t)size);
       pl.rows[j] = (int)(mv / per);
       pl.locs[j] = (int)(mv - (int64_t)pl.rows[j] * per);
@@ -1243,19 +1243,182 @@ __global__ void __launch_bounds__(MAXT, 1) spec_kernel(const VnsParams p) {
   team_sync(t.C);
 }
 
+// ---------------------------------------------------------------------------
+// fj_kernel: Algorithm 2 as the paper runs it (Section 3, fork-join model):
+// W teams (clusters), the workers, hold the same incumbent x.  In every
+// iteration worker p shakes x with the iteration's k and its own draws (move
+// key p << 8 | j), runs VND (mode P or G), and publishes f(x''_p) and the
+// rows it changed (only shaken rows can change: the others stay locally
+// optimal).  After a bounded grid barrier every worker takes the least
+// (f(x''_p), p); when it is below f(x), every worker undoes its own shake and
+// adopts the winner's rows, else all undo.  All workers' VND work counts.
+// ---------------------------------------------------------------------------
+template <typename Acc, int NW, bool TS, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) fj_kernel(const VnsParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ CtlShared sh;
+  Team<Acc> t;
+  team_init(t, p.G);
+  cg::cluster_group cl = cg::this_cluster();
+  const int W = p.fj_workers;
+  const int team = blockIdx.x / t.C;
+  const RunDesc rd = p.runs[0];
+  if (W < 1 || (int)gridDim.x != W * t.C || !team_begin<Acc, NW, TS>(t, smem, &sh, p, rd)) {
+    if (blockIdx.x == 0 && t.tid == 0) write_failed_run(p, rd, kStatusLaunch);
+    return;
+  }
+  const int K = t.K, T = t.T;
+  const int64_t moves_per_cycle = (int64_t)K * (2 * T + (T > 1 ? 2 * (T - 1) : 0));
+  int status = 0;
+  int64_t cycles_total = 0;
+  int cyc = vnd<Acc, NW>(t, rd.mode);  // every worker descends from the start; counted once
+  if (cyc < 0) status = kStatusCap; else cycles_total += cyc;
+  int64_t fx = team_total(t);
+  flush_counters(t, &sh.steps, &sh.applied);
+  unsigned long long c_steps = 0, c_applied = 0;  // the workers' iterations (leader)
+  uint64_t h = 0;
+  int64_t accepted = 0;
+  int it = 0, kk = 1;
+  const bool leader = team == 0 && t.crank == 0 && t.tid == 0;
+  for (; it < rd.iters && status == 0; ++it) {
+    const int par = it & 1;
+    SpecSlot* slot = p.spec_slots + par * W + team;
+    if (t.crank == 0 && t.tid == 0) {
+      slot->applied = 0ull;
+      slot->steps = 0ull;
+    }
+    const ShakePlan pl = plan_shake(rd.seed, it, kk, K, T, (uint64_t)team << 8);
+    apply_shake<Acc, NW>(t, pl, kk, par);
+    cyc = vnd<Acc, NW>(t, rd.mode);
+    const int64_t f2 = team_total(t);  // cluster barrier: the slot reset is visible
+    flush_counters(t, &slot->steps, &slot->applied);
+#pragma unroll
+    for (int j = 0; j < kMaxShake; ++j)
+      if (t.owns(pl.rows[j]) && pl.first[j] && t.lane == 0)
+        p.spec_rows[(par * W + team) * kMaxShake + j] = t.m.bits[pl.rows[j] / t.C];
+    if (t.crank == 0 && t.tid == 0) {
+      slot->f2 = f2;
+      slot->cycles = cyc;
+    }
+    if (!grid_barrier(t, p.spec_bar, W)) {
+      status = kStatusTimeout;
+      break;
+    }
+    // least (f(x''_p), p) over the workers; VND caps; committed work
+    const SpecSlot* slots = p.spec_slots + par * W;
+    uint64_t best = ~0ull;
+    int capped = 0, cs = 0;
+    for (int base = 0; base < W; base += 32) {
+      const int i = base + t.wlane;
+      if (i < W) {
+        best = umin64(best, pack_key(__ldcg(&slots[i].f2), (uint32_t)i));
+        const int c = __ldcg(&slots[i].cycles);
+        capped |= c < 0;
+        cs += c > 0 ? c : 0;
+      }
+    }
+    best = subwarp_min(best, 32);
+    capped = __any_sync(kFull, capped);
+    for (int o = 16; o > 0; o >>= 1) cs += __shfl_xor_sync(kFull, cs, o);
+    cycles_total += cs;
+    const int a = key_index(best);
+    const int64_t fa = key_cost(best);
+    const int acc = fa < fx;
+    if (team == 0 && t.crank == 0 && t.warp == 0) {
+      unsigned long long st = 0ull, ap = 0ull;
+      for (int i = t.wlane; i < W; i += 32) {
+        st += __ldcg(&slots[i].steps);
+        ap += __ldcg(&slots[i].applied);
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        st += __shfl_xor_sync(kFull, st, o);
+        ap += __shfl_xor_sync(kFull, ap, o);
+      }
+      if (t.wlane == 0) {
+        c_steps += st;
+        c_applied += ap;
+        if (rd.traj_off >= 0) {
+          TrajEntry te;
+          te.it = it;
+          te.k = kk;
+          te.cost = fa;
+          te.accepted = acc;
+          te.reserved = a;
+          p.traj[rd.traj_off + it] = te;
+        }
+        h = splitmix64(h ^ (uint64_t)fa);
+        h = splitmix64(h ^ (((uint64_t)it << 32) | ((uint64_t)kk << 1) | (uint64_t)acc));
+      }
+    }
+    if (capped) {
+      status = kStatusCap;
+      break;
+    }
+    // every worker moves to the new incumbent
+    if (!(acc && team == a)) undo_shake<Acc>(t, pl, par);
+    if (acc && team != a) {
+      const ShakePlan pw = plan_shake(rd.seed, it, kk, K, T, (uint64_t)a << 8);
+#pragma unroll
+      for (int j = 0; j < kMaxShake; ++j) {
+        const int k = pw.rows[j];
+        if (t.owns(k) && pw.first[j]) {
+          if (t.lane == 0)
+            t.m.bits[k / t.C] = ldcg_bits(p.spec_rows + (par * W + a) * kMaxShake + j);
+          group_sync(t);
+          group_rebuild<Acc, NW>(t, k / t.C);
+        }
+        if (t.G <= 32) __syncwarp();
+      }
+    }
+    if (acc) {
+      fx = fa;
+      kk = 1;
+      ++accepted;
+    } else {
+      kk = kk % rd.kmax + 1;
+    }
+  }
+  // outputs (worker 0)
+  __syncthreads();  // undo / adoption of the last iteration are complete
+  if (team == 0) {
+    for (int q = t.tid; q < t.Kc; q += t.nthr)
+      p.out_bits[rd.bits_off + q * t.C + t.crank] = t.m.bits[q];
+  }
+  team_sync(t.C);
+  if (leader) {
+    unsigned long long steps = c_steps, applied = c_applied;
+    for (int c = 0; c < t.C; ++c) {
+      steps += t.C == 1 ? sh.steps : *cl.map_shared_rank(&sh.steps, c);
+      applied += t.C == 1 ? sh.applied : *cl.map_shared_rank(&sh.applied, c);
+    }
+    RunOut o;
+    o.best_cost = fx;
+    o.traj_hash = h;
+    o.moves_evaluated = cycles_total * moves_per_cycle;
+    o.evals = cycles_total * 3;
+    o.vnd_cycles = cycles_total;
+    o.applied = (int64_t)applied;
+    o.iterations = it;
+    o.accepted = accepted;
+    o.segments = (int64_t)steps;
+    o.status = status;
+    o.reserved = W;
+    p.out[rd.out] = o;
+  }
+  team_sync(t.C);
+}
+
 }  // namespace vns
 
 template <typename Acc, int NW, bool TS, int MAXT>
 cudaError_t vns_prepare_t(size_t smem, int threads, int cluster, int* active) {
   auto kern = vns::vns_kernel<Acc, NW, TS, MAXT>;
-  auto spec = vns::spec_kernel<Acc, NW, TS, MAXT>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(spec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  if (cluster > 8) {
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(spec, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  void (*const all[3])(const VnsParams) = {kern, vns::spec_kernel<Acc, NW, TS, MAXT>,
+                                            vns::fj_kernel<Acc, NW, TS, MAXT>};
+  for (auto f : all) {
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess && cluster > 8)
+      e = cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
   }
   if (cluster <= 1)
@@ -1274,11 +1437,11 @@ cudaError_t vns_prepare_t(size_t smem, int threads, int cluster, int* active) {
   return cudaOccupancyMaxActiveClusters(active, kern, &cfg);
 }
 
-// Launch the batched kernel, or the speculative one when p.spec_teams > 1
-// (then blocks = teams x cluster; the host sizes the teams to what the
-// occupancy query reports resident, and the grid barrier's waits are
-// bounded, so teams that could not all be resident end with a timeout
-// status instead of waiting forever).
+// Launch the batched kernel, the fork-join one when p.fj_workers > 0, or the
+// speculative one when p.spec_teams > 1.  The last two take blocks = teams x
+// cluster; the host sizes the teams to what the occupancy query reports
+// resident, and the grid barrier's waits are bounded, so teams that could
+// not all be resident end with a timeout status instead of waiting forever.
 template <typename Acc, int NW, bool TS, int MAXT>
 cudaError_t vns_launch_t(const VnsParams& p, int blocks, int threads, size_t smem,
                          int cluster, cudaStream_t s) {
@@ -1297,11 +1460,9 @@ cudaError_t vns_launch_t(const VnsParams& p, int blocks, int threads, size_t sme
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cfg.attrs = attr;
-  if (p.spec_teams <= 1) {
-    cfg.numAttrs = na;
-    return cudaLaunchKernelEx(&cfg, vns::vns_kernel<Acc, NW, TS, MAXT>, p);
-  }
   cfg.numAttrs = na;
+  if (p.fj_workers > 0) return cudaLaunchKernelEx(&cfg, vns::fj_kernel<Acc, NW, TS, MAXT>, p);
+  if (p.spec_teams <= 1) return cudaLaunchKernelEx(&cfg, vns::vns_kernel<Acc, NW, TS, MAXT>, p);
   return cudaLaunchKernelEx(&cfg, vns::spec_kernel<Acc, NW, TS, MAXT>, p);
 }
 

@@ -150,6 +150,19 @@ class Solver:
         self._chk(self._lib.elsr_vns_run(self._h, seed & ((1 << 64) - 1), iters, kmax, mode))
         self._last_iters = iters
 
+    def vns_forkjoin_run(self, seed: int, iters: int, kmax: int = 3, mode: int = nat.MODE_P,
+                         workers: int = 2):
+        """Queue a fork-join GVNS run (Algorithm 2 with `workers` shakes +
+        VNDs per iteration, the least result kept) on the stream."""
+        self._chk(self._lib.elsr_vns_forkjoin_run(self._h, seed & ((1 << 64) - 1), iters, kmax,
+                                                  mode, workers))
+        self._last_iters = iters
+
+    def vns_forkjoin(self, seed: int, iters: int, kmax: int = 3, mode: int = nat.MODE_P,
+                     workers: int = 2, **kw):
+        self.vns_forkjoin_run(seed, iters, kmax, mode, workers)
+        return self.result(**kw)
+
     def result(self, solution: bool = True, plan: bool = False, traj: bool = True):
         st = nat.Stats()
         gm = np.zeros((self.K, self.T), np.uint8) if solution else None
@@ -170,9 +183,11 @@ class Solver:
         if plan:
             out["plan"] = pl
         if n:
-            out["traj"] = np.array([(e.it, e.k, e.cost, e.accepted) for e in tr[:n]],
+            out["traj"] = np.array([(e.it, e.k, e.cost, e.accepted, e.reserved)
+                                    for e in tr[:n]],
                                    dtype=[("it", np.int32), ("k", np.int32),
-                                          ("cost", np.int64), ("accepted", np.int32)])
+                                          ("cost", np.int64), ("accepted", np.int32),
+                                          ("worker", np.int32)])
         return out
 
     def vns(self, seed: int, iters: int, kmax: int = 3, mode: int = nat.MODE_P, **kw):
