@@ -55,7 +55,8 @@ extern "C" {
 #define ELSR_E_NOMEM (-3) /* device or host allocation failed */
 #define ELSR_E_CUDA (-4)  /* a CUDA runtime call or kernel failed */
 #define ELSR_E_CAP (-5)   /* a VND exceeded its sweep cap (2^20 sweeps) */
-#define ELSR_E_STATE (-6) /* call out of order (e.g. no result yet) */
+#define ELSR_E_STATE (-6) /* call out of order (e.g. no result yet), or a
+                             resumed state that does not match its checkpoint */
 #define ELSR_E_TIMEOUT (-7) /* a device-side wait exceeded its limit */
 
 #define ELSR_T_MAX 128 /* periods per product */
@@ -92,6 +93,25 @@ typedef struct {
     int32_t accepted;
     int32_t reserved;
 } elsr_traj_t;
+
+/* State of a GVNS run between two iterations: Algorithm 2's loop variables
+ * plus the running totals, enough to continue the run exactly where it
+ * stopped (elsr_checkpoint, elsr_vns_resume).  The incumbent x itself is
+ * passed beside it as two K x T 0/1 arrays.  Plain data: it may be stored
+ * and loaded byte for byte. */
+typedef struct {
+    uint64_t seed;       /* the run's seed */
+    int32_t kmax;        /* the run's kmax (1..3) */
+    int32_t mode;        /* ELSR_MODE_P or ELSR_MODE_G */
+    int32_t workers;     /* fork-join workers (0: the sequential GVNS) */
+    int32_t next_it;     /* iterations run so far = index of the next one */
+    int32_t k;           /* neighbourhood index k of the next iteration */
+    int32_t status;      /* status of the run that produced it (ELSR_OK to resume) */
+    int64_t cost;        /* f(x) of the incumbent */
+    uint64_t traj_hash;  /* trajectory hash over iterations 0 .. next_it-1 */
+    int64_t moves_evaluated, evals, vnd_cycles, applied, accepted, segments;
+                         /* totals over iterations 0 .. next_it-1 and the initial VND */
+} elsr_checkpoint_t;
 
 /* Version of this ABI (major * 10000 + minor * 100 + patch). */
 int elsr_version(void);
@@ -226,7 +246,45 @@ int elsr_vns_forkjoin_run(elsr_t *h, uint64_t seed, int32_t iters,
                           int32_t kmax, int32_t mode, int32_t workers);
 
 /*
- * Results of the last elsr_vns_run or elsr_vns_forkjoin_run (waits for it).  stats (nullable); gM,
+ * Wall-clock budget of the handle's next single runs (elsr_vns_run,
+ * elsr_vns_forkjoin_run, elsr_vns_resume), in microseconds from the start
+ * of each run on the device; 0 (the default) = none.  This is Algorithm 2's
+ * "until t > t_max": the run stops after the first iteration whose VND ends
+ * past the budget (iters stays an upper bound), so its trajectory is a
+ * prefix of the unbudgeted run's and elsr_checkpoint / elsr_vns_resume can
+ * continue it.  A budgeted sequential run uses one team (no speculation).
+ */
+int elsr_set_time_limit(elsr_t *h, int64_t time_limit_us);
+
+/*
+ * Checkpoint of the last single run (elsr_vns_run, elsr_vns_forkjoin_run or
+ * elsr_vns_resume; waits for it): *ck receives the loop state after its last
+ * iteration, gM, gR (nullable together, host [K][T] 0/1) the incumbent x.
+ * Returns the run's status (ELSR_OK, ELSR_E_CAP, ELSR_E_TIMEOUT,
+ * ELSR_E_STATE) or an error; only an ELSR_OK checkpoint can be resumed.
+ */
+int elsr_checkpoint(elsr_t *h, elsr_checkpoint_t *ck, uint8_t *gM, uint8_t *gR);
+
+/*
+ * Continue a checkpointed run for `iters` more iterations (iterations
+ * ck->next_it .. ck->next_it + iters - 1) from x = (gM, gR), host [K][T]
+ * 0/1, with the checkpoint's seed, kmax, mode, k, trajectory hash and
+ * workers (0: sequential GVNS, else fork-join).  There is no initial VND (x
+ * is already VND's output), so a run of N iterations, a checkpoint and a
+ * resume of M give exactly the run of N + M iterations: trajectory, x, hash
+ * and totals.  x becomes the handle's current solution (as elsr_set_state;
+ * this part waits for the device).  The handle may be a fresh one on the
+ * same instance.  If f(x) differs from ck->cost the run stops before its
+ * first iteration with status ELSR_E_STATE.  Then asynchronous, like
+ * elsr_vns_run; elsr_result reports totals since iteration 0 and the
+ * trajectory entries of this part.
+ */
+int elsr_vns_resume(elsr_t *h, const elsr_checkpoint_t *ck, const uint8_t *gM,
+                    const uint8_t *gR, int32_t iters);
+
+/*
+ * Results of the last elsr_vns_run, elsr_vns_forkjoin_run or
+ * elsr_vns_resume (waits for it).  stats (nullable); gM,
  * gR (nullable, host [K][T] 0/1) receive x; plan (nullable, host int32
  * [4][K][T]) receives xM, xR, yM, yR of x; traj (nullable, host
  * [traj_capacity]) receives the first min(iters, traj_capacity) entries.

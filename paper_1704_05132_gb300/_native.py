@@ -39,6 +39,27 @@ class Stats(ctypes.Structure):
         return {n: int(getattr(self, n)) for n, _ in self._fields_ if n != "reserved"}
 
 
+class Checkpoint(ctypes.Structure):
+    """elsr_checkpoint_t: Algorithm 2's loop state between two iterations."""
+    _fields_ = [("seed", ctypes.c_uint64), ("kmax", ctypes.c_int32), ("mode", ctypes.c_int32),
+                ("workers", ctypes.c_int32), ("next_it", ctypes.c_int32), ("k", ctypes.c_int32),
+                ("status", ctypes.c_int32), ("cost", ctypes.c_int64),
+                ("traj_hash", ctypes.c_uint64), ("moves_evaluated", ctypes.c_int64),
+                ("evals", ctypes.c_int64), ("vnd_cycles", ctypes.c_int64),
+                ("applied", ctypes.c_int64), ("accepted", ctypes.c_int64),
+                ("segments", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {n: int(getattr(self, n)) for n, _ in self._fields_}
+
+    @classmethod
+    def from_dict(cls, d: dict) -> "Checkpoint":
+        c = cls()
+        for n, _ in cls._fields_:
+            setattr(c, n, int(d[n]))
+        return c
+
+
 class Traj(ctypes.Structure):
     _fields_ = [("it", ctypes.c_int32), ("k", ctypes.c_int32), ("cost", ctypes.c_int64),
                 ("accepted", ctypes.c_int32), ("reserved", ctypes.c_int32)]
@@ -66,6 +87,9 @@ SIGNATURES = {
     "elsr_move_costs": (ctypes.c_int, [P, i32, P, P]),
     "elsr_vns_run": (ctypes.c_int, [P, u64, i32, i32, i32]),
     "elsr_vns_forkjoin_run": (ctypes.c_int, [P, u64, i32, i32, i32, i32]),
+    "elsr_set_time_limit": (ctypes.c_int, [P, i64]),
+    "elsr_checkpoint": (ctypes.c_int, [P, P, P, P]),
+    "elsr_vns_resume": (ctypes.c_int, [P, P, P, P, i32]),
     "elsr_result": (ctypes.c_int, [P, P, P, P, P, P, i32]),
     "elsr_multistart_run": (ctypes.c_int, [P, u64, i32, i32, i32, i32, P, P, P]),
     "elsr_counters": (ctypes.c_int, [P, P]),

@@ -557,10 +557,16 @@ struct elsr_ctx {
   int32_t* d_movewin = nullptr;
   int32_t* d_plan = nullptr;
   int64_t moves_total = 0;
-  int last_kind = 0;  // 1: vns_run, 2: multistart
+  int last_kind = 0;  // 1: vns_run / forkjoin / resume, 2: multistart
   int32_t last_iters = 0;
   int32_t best_out = 0;
   bool counted = true;
+  int64_t time_limit_ns = 0;  // wall-clock budget of the next runs (0: none)
+  // the last single run (for checkpoints): its parameters and, for a resumed
+  // run, the checkpoint it continued (iterations and counters before it)
+  uint64_t run_seed = 0;
+  int32_t run_kmax = 0, run_mode = 0, run_workers = 0;
+  elsr_checkpoint_t base = {};
 
   ~elsr_ctx() {
     if (b.d_insts) cudaStreamSynchronize(b.stream);
@@ -831,13 +837,36 @@ int elsr_move_costs(elsr_t* h, int32_t nb, int64_t* costs, int32_t* window) {
   return ELSR_OK;
 }
 
-int elsr_vns_run(elsr_t* h, uint64_t seed, int32_t iters, int32_t kmax, int32_t mode) {
+int elsr_set_time_limit(elsr_t* h, int64_t time_limit_us) {
   if (!h) return ELSR_E_ARG;
-  if (iters < 0 || kmax < 1 || kmax > 3 || (mode != ELSR_MODE_P && mode != ELSR_MODE_G)) {
-    h->b.err = "need iters >= 0, 1 <= kmax <= 3, mode P or G";
+  if (time_limit_us < 0 || time_limit_us > (int64_t)1e12) {
+    h->b.err = "time_limit_us must be 0 (none) or a positive budget below 10^12";
     return ELSR_E_ARG;
   }
-  elsr_batch* b = &h->b;
+  h->time_limit_ns = time_limit_us * 1000;
+  return ELSR_OK;
+}
+
+namespace {
+
+// Bookkeeping of a queued single run for elsr_result / elsr_checkpoint.
+void note_single_run(elsr_t* h, const RunDesc& r, int32_t workers, const elsr_checkpoint_t* from) {
+  h->last_kind = 1;
+  h->last_iters = r.iters;
+  h->best_out = 0;
+  h->counted = false;
+  h->run_seed = r.seed;
+  h->run_kmax = r.kmax;
+  h->run_mode = r.mode;
+  h->run_workers = workers;
+  if (from) {
+    h->base = *from;
+  } else {
+    h->base = elsr_checkpoint_t{};
+  }
+}
+
+RunDesc single_run(uint64_t seed, int32_t iters, int32_t kmax, int32_t mode) {
   RunDesc r;
   r.inst = 0;
   r.iters = iters;
@@ -849,13 +878,25 @@ int elsr_vns_run(elsr_t* h, uint64_t seed, int32_t iters, int32_t kmax, int32_t 
   r.bits_off = 0;
   r.start_off = 0;
   r.traj_off = 0;
+  return r;
+}
+
+}  // namespace
+
+int elsr_vns_run(elsr_t* h, uint64_t seed, int32_t iters, int32_t kmax, int32_t mode) {
+  if (!h) return ELSR_E_ARG;
+  if (iters < 0 || kmax < 1 || kmax > 3 || (mode != ELSR_MODE_P && mode != ELSR_MODE_G)) {
+    h->b.err = "need iters >= 0, 1 <= kmax <= 3, mode P or G";
+    return ELSR_E_ARG;
+  }
+  elsr_batch* b = &h->b;
+  RunDesc r = single_run(seed, iters, kmax, mode);
+  r.time_limit_ns = h->time_limit_ns;
   b->h_runs.assign(1, r);
-  int rc = launch_runs(b, h->d_state, true, iters, true);
+  // a budgeted run is one team: speculative rounds cannot stop mid-way
+  int rc = launch_runs(b, h->d_state, true, iters, h->time_limit_ns == 0);
   if (rc != ELSR_OK) return rc;
-  h->last_kind = 1;
-  h->last_iters = iters;
-  h->best_out = 0;
-  h->counted = false;
+  note_single_run(h, r, 0, nullptr);
   return ELSR_OK;
 }
 
@@ -869,24 +910,79 @@ int elsr_vns_forkjoin_run(elsr_t* h, uint64_t seed, int32_t iters, int32_t kmax,
     return ELSR_E_ARG;
   }
   elsr_batch* b = &h->b;
-  RunDesc r;
-  r.inst = 0;
-  r.iters = iters;
-  r.kmax = kmax;
-  r.mode = mode;
-  r.seed = seed;
-  r.out = 0;
-  r.pad = 0;
-  r.bits_off = 0;
-  r.start_off = 0;
-  r.traj_off = 0;
+  RunDesc r = single_run(seed, iters, kmax, mode);
+  r.time_limit_ns = h->time_limit_ns;
   b->h_runs.assign(1, r);
   int rc = launch_runs(b, h->d_state, true, iters, false, workers);
   if (rc != ELSR_OK) return rc;
-  h->last_kind = 1;
-  h->last_iters = iters;
-  h->best_out = 0;
-  h->counted = false;
+  note_single_run(h, r, workers, nullptr);
+  return ELSR_OK;
+}
+
+int elsr_checkpoint(elsr_t* h, elsr_checkpoint_t* ck, uint8_t* gM, uint8_t* gR) {
+  if (!h || !ck || ((gM == nullptr) != (gR == nullptr))) return ELSR_E_ARG;
+  elsr_batch* b = &h->b;
+  if (h->last_kind != 1) {
+    b->err = "no single GVNS run (elsr_vns_run, elsr_vns_forkjoin_run, elsr_vns_resume) to checkpoint";
+    return ELSR_E_STATE;
+  }
+  ELSR_TRY_CUDA(b, cudaStreamSynchronize(b->stream));
+  RunOut o;
+  ELSR_TRY_CUDA(b, cudaMemcpyAsync(&o, b->d_out, sizeof(RunOut), cudaMemcpyDeviceToHost,
+                                   b->stream));
+  ELSR_TRY_CUDA(b, cudaStreamSynchronize(b->stream));
+  elsr_checkpoint_t c = h->base;
+  c.seed = h->run_seed;
+  c.kmax = h->run_kmax;
+  c.mode = h->run_mode;
+  c.workers = h->run_workers;
+  c.next_it = h->base.next_it + (int32_t)o.iterations;
+  c.k = o.k_next;
+  c.status = o.status;
+  c.cost = o.best_cost;
+  c.traj_hash = o.traj_hash;
+  c.moves_evaluated += o.moves_evaluated;
+  c.evals += o.evals;
+  c.vnd_cycles += o.vnd_cycles;
+  c.applied += o.applied;
+  c.accepted += o.accepted;
+  c.segments += o.segments;
+  *ck = c;
+  if (gM) {
+    std::vector<RowBits> rb(h->K);
+    ELSR_TRY_CUDA(b, cudaMemcpyAsync(rb.data(), b->d_bits, h->K * sizeof(RowBits),
+                                     cudaMemcpyDeviceToHost, b->stream));
+    ELSR_TRY_CUDA(b, cudaStreamSynchronize(b->stream));
+    unpack_bits(rb, h->K, h->T, gM, gR);
+  }
+  return o.status;
+}
+
+int elsr_vns_resume(elsr_t* h, const elsr_checkpoint_t* ck, const uint8_t* gM,
+                    const uint8_t* gR, int32_t iters) {
+  if (!h || !ck || !gM || !gR) return ELSR_E_ARG;
+  elsr_batch* b = &h->b;
+  if (iters < 0 || ck->kmax < 1 || ck->kmax > 3 ||
+      (ck->mode != ELSR_MODE_P && ck->mode != ELSR_MODE_G) || ck->workers < 0 ||
+      ck->workers > ELSR_FJ_WORKERS_MAX || ck->next_it < 0 || ck->k < 1 || ck->k > ck->kmax ||
+      (int64_t)ck->next_it + iters > INT32_MAX || ck->status != ELSR_OK) {
+    b->err = "invalid checkpoint (kmax, mode, workers, next_it, k or status) or iters";
+    return ELSR_E_ARG;
+  }
+  int rc = elsr_set_state(h, gM, gR);  // x becomes the handle's current solution
+  if (rc != ELSR_OK) return rc;
+  RunDesc r = single_run(ck->seed, iters, ck->kmax, ck->mode);
+  r.it0 = ck->next_it;
+  r.k0 = ck->k;
+  r.h0 = ck->traj_hash;
+  r.f0 = ck->cost;
+  r.resume = 1;
+  r.time_limit_ns = h->time_limit_ns;
+  b->h_runs.assign(1, r);
+  rc = launch_runs(b, h->d_state, true, iters, h->time_limit_ns == 0 && ck->workers == 0,
+                   ck->workers);
+  if (rc != ELSR_OK) return rc;
+  note_single_run(h, r, ck->workers, ck);
   return ELSR_OK;
 }
 
@@ -908,7 +1004,18 @@ int elsr_result(elsr_t* h, elsr_stats_t* stats, uint8_t* gM, uint8_t* gR,
     h->moves_total += o.moves_evaluated;
     h->counted = true;
   }
-  if (stats) to_stats(o, stats);
+  if (stats) {
+    to_stats(o, stats);
+    if (h->last_kind == 1) {  // a resumed run reports totals since its first iteration
+      stats->moves_evaluated += h->base.moves_evaluated;
+      stats->evals += h->base.evals;
+      stats->vnd_cycles += h->base.vnd_cycles;
+      stats->applied += h->base.applied;
+      stats->iterations += h->base.next_it;
+      stats->accepted += h->base.accepted;
+      stats->segments += h->base.segments;
+    }
+  }
   const RowBits* sol = b->d_bits + (int64_t)h->best_out * h->K;
   if (gM || gR) {
     std::vector<RowBits> rb(h->K);

@@ -14,6 +14,7 @@ constexpr int kMaxShake = 3;        // kmax <= 3: at most 3 shaken rows
 constexpr int kSmemLimit = 227 * 1024 - 1024;  // dynamic bytes; static control words (< 1 KB) take the rest
 constexpr int kStatusCap = -5;      // ELSR_E_CAP
 constexpr int kStatusTimeout = -7;  // ELSR_E_TIMEOUT
+constexpr int kStatusState = -6;    // ELSR_E_STATE: resumed state does not match
 constexpr int kStatusLaunch = -4;   // ELSR_E_CUDA: launch geometry mismatch
 
 // One instance of a batch: rows [row_off, row_off + K) of the per-row pools
@@ -37,6 +38,19 @@ struct RunDesc {
   int64_t bits_off;   // RowBits offset of this run's solution output
   int64_t start_off;  // RowBits offset of its start solution (-1: all open)
   int64_t traj_off;   // trajectory entry offset (-1: none)
+  // Continuation of a checkpointed run: iterations it0 .. it0 + iters - 1
+  // from the start solution (already VND's output, so no initial VND) with
+  // k = k0, trajectory hash h0, and the start's objective f0 (checked).
+  int32_t it0 = 0;
+  int32_t k0 = 1;
+  uint64_t h0 = 0;
+  int64_t f0 = 0;
+  int32_t resume = 0;
+  int32_t pad1 = 0;
+  // Wall-clock budget (Algorithm 2's time limit), nanoseconds from the
+  // run's start; 0 = none.  The run stops after the first iteration that
+  // ends past it.
+  int64_t time_limit_ns = 0;
 };
 
 struct RunOut {
@@ -46,6 +60,8 @@ struct RunOut {
   int64_t segments;
   int32_t status;
   int32_t reserved;
+  int32_t k_next;  // k of the iteration after the last one run
+  int32_t pad;
 };
 
 struct TrajEntry {

@@ -401,6 +401,7 @@ struct CtlShared {
   long long F;
   unsigned long long applied, steps;
   unsigned long long gmin[64];  // per row group and warp: partial minima (groups > 32 lanes)
+  int stopw[2];                 // wall-clock budget spent (CTA 0's word counts)
 };
 // kSmemLimit leaves 1 KB of the CTA's shared memory to static words.
 static_assert(sizeof(CtlShared) <= 768, "static control words outgrow their reserve");
@@ -553,12 +554,24 @@ __device__ __forceinline__ void write_failed_run(const VnsParams& p, const RunDe
   p.out[rd.out] = o;
 }
 
+__device__ __forceinline__ long long globaltimer_ns() {
+  unsigned long long v;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(v));
+  return (long long)v;
+}
+
 // Objective of the team: F = sum of the feasible rows' costs and ninf = the
 // number of infeasible rows over the cluster (every thread gets both).
+// With `stop` given (by every thread), thread 0 of CTA 0 also compares the
+// global timer with `deadline` (ns; 0 = none, and only that thread's value
+// matters) and every thread receives the verdict.
 template <typename Acc>
-__device__ void team_sums(Team<Acc>& t, int64_t& F, int& ninf) {
+__device__ void team_sums(Team<Acc>& t, int64_t& F, int& ninf, long long deadline = 0,
+                          int* stop = nullptr) {
   CtlShared* sh = t.sh;
   const int tp = t.tp;
+  if (stop && t.crank == 0 && t.tid == 0)
+    sh->stopw[tp] = deadline > 0 && globaltimer_ns() >= deadline;
   if (t.lane == 0) {
     int64_t s = 0;
     int ni = 0;
@@ -589,6 +602,7 @@ __device__ void team_sums(Team<Acc>& t, int64_t& F, int& ninf) {
     F = (int64_t)a;
     ninf = ni;
   }
+  if (stop) *stop = t.C == 1 ? sh->stopw[tp] : *cg::this_cluster().map_shared_rank(&sh->stopw[tp], 0);
   if (t.tid == 0) {
     sh->acc[tp ^ 1] = 0ull;
     sh->ninf[tp ^ 1] = 0;
@@ -596,12 +610,13 @@ __device__ void team_sums(Team<Acc>& t, int64_t& F, int& ninf) {
   t.tp ^= 1;
 }
 
-// Saturating objective of the team (sum of row costs over the cluster).
+// Saturating objective of the team (sum of row costs over the cluster);
+// deadline / stop as in team_sums.
 template <typename Acc>
-__device__ int64_t team_total(Team<Acc>& t) {
+__device__ int64_t team_total(Team<Acc>& t, long long deadline = 0, int* stop = nullptr) {
   int64_t F;
   int ni;
-  team_sums(t, F, ni);
+  team_sums(t, F, ni, deadline, stop);
   return ni ? INT64_MAX : F;
 }
 
@@ -902,23 +917,31 @@ __global__ void __launch_bounds__(MAXT, 1) vns_kernel(const VnsParams p) {
     }
     const int K = t.K, T = t.T;
     const int64_t moves_per_cycle = (int64_t)K * (2 * T + (T > 1 ? 2 * (T - 1) : 0));
-    int status = 0;
+    // wall-clock budget from the run's start (thread 0 of CTA 0 keeps time)
+    const long long deadline = rd.time_limit_ns > 0 && t.crank == 0 && t.tid == 0
+                                   ? globaltimer_ns() + rd.time_limit_ns : 0;
+    int status = 0, stop = 0;
     int64_t cycles_total = 0;
-    int cyc = vnd<Acc, NW>(t, rd.mode);
-    if (cyc < 0) status = kStatusCap; else cycles_total += cyc;
+    int cyc = 0;
+    if (!rd.resume) {  // a resumed run starts from VND's output
+      cyc = vnd<Acc, NW>(t, rd.mode);
+      if (cyc < 0) status = kStatusCap; else cycles_total += cyc;
+    }
     int64_t fx = team_total(t);
-    int kk = 1;  // neighbourhood index k of Algorithm 2
-    uint64_t h = 0;
+    if (rd.resume && fx != rd.f0) status = kStatusState;
+    int kk = rd.k0;  // neighbourhood index k of Algorithm 2
+    uint64_t h = rd.h0;
     int64_t iters_done = 0, accepted = 0;
     const bool log = rd.traj_off >= 0 && t.crank == 0 && t.tid == 0;
-    for (int it = 0; it < rd.iters && status == 0; ++it) {
+    const int it_end = rd.it0 + rd.iters;
+    for (int it = rd.it0; it < it_end && status == 0 && !stop; ++it) {
       const int par = it & 1;
       const int ks = kk;
       const ShakePlan pl = plan_shake(rd.seed, it, ks, K, T);
       apply_shake<Acc, NW>(t, pl, ks, par);
       cyc = vnd<Acc, NW>(t, rd.mode);
       if (cyc < 0) status = kStatusCap; else cycles_total += cyc;
-      const int64_t f2 = team_total(t);
+      const int64_t f2 = rd.time_limit_ns > 0 ? team_total(t, deadline, &stop) : team_total(t);
       const int acc = f2 < fx;
       if (t.crank == 0 && t.tid == 0) {
         if (log) {
@@ -928,7 +951,7 @@ __global__ void __launch_bounds__(MAXT, 1) vns_kernel(const VnsParams p) {
           te.cost = f2;
           te.accepted = acc;
           te.reserved = 0;
-          p.traj[rd.traj_off + it] = te;
+          p.traj[rd.traj_off + (it - rd.it0)] = te;
         }
         h = splitmix64(h ^ (uint64_t)f2);
         h = splitmix64(h ^ (((uint64_t)it << 32) | ((uint64_t)ks << 1) | (uint64_t)acc));
@@ -967,6 +990,8 @@ __global__ void __launch_bounds__(MAXT, 1) vns_kernel(const VnsParams p) {
       o.segments = (int64_t)steps;
       o.status = status;
       o.reserved = 0;
+      o.k_next = kk;
+      o.pad = 0;
       p.out[rd.out] = o;
     }
     team_sync(t.C);
@@ -1046,18 +1071,23 @@ __global__ void __launch_bounds__(MAXT, 1) spec_kernel(const VnsParams p) {
   const int64_t moves_per_cycle = (int64_t)K * (2 * T + (T > 1 ? 2 * (T - 1) : 0));
   int status = 0;
   int64_t cycles_total = 0;
-  int cyc = vnd_p<Acc, NW>(t);
-  if (cyc < 0) status = kStatusCap; else cycles_total += cyc;
+  int cyc = 0;
+  if (!rd.resume) {  // a resumed run starts from VND's output
+    cyc = vnd_p<Acc, NW>(t);
+    if (cyc < 0) status = kStatusCap; else cycles_total += cyc;
+  }
   int64_t fx = team_total(t);
+  if (rd.resume && fx != rd.f0) status = kStatusState;
   flush_counters(t, &sh.steps, &sh.applied);  // the initial VND counts once (team 0)
   unsigned long long c_steps = 0, c_applied = 0;  // committed speculative work
-  uint64_t h = 0;
+  uint64_t h = rd.h0;
   int64_t accepted = 0;
-  int it0 = 0, k0 = 1, round = 0;
+  int it0 = rd.it0, k0 = rd.k0, round = 0;
+  const int it_end = rd.it0 + rd.iters;
   const bool leader = team == 0 && t.crank == 0 && t.tid == 0;
-  while (it0 < rd.iters && status == 0) {
+  while (it0 < it_end && status == 0) {
     const int par = round & 1;
-    const int nact = (rd.iters - it0) < W ? (rd.iters - it0) : W;
+    const int nact = (it_end - it0) < W ? (it_end - it0) : W;
     const bool active = team < nact;
     const int ks = (k0 - 1 + team) % rd.kmax + 1;
     SpecSlot* slot = p.spec_slots + par * W + team;
@@ -1170,7 +1200,7 @@ __global__ void __launch_bounds__(MAXT, 1) spec_kernel(const VnsParams p) {
               te.cost = f2;
               te.accepted = acc;
               te.reserved = 0;
-              p.traj[rd.traj_off + it0 + ii] = te;
+              p.traj[rd.traj_off + (it0 + ii - rd.it0)] = te;
             }
             h = splitmix64(h ^ (uint64_t)f2);
             h = splitmix64(h ^ (((uint64_t)(it0 + ii) << 32) | ((uint64_t)ki << 1) | (uint64_t)acc));
@@ -1233,11 +1263,13 @@ __global__ void __launch_bounds__(MAXT, 1) spec_kernel(const VnsParams p) {
     o.evals = cycles_total * 3;
     o.vnd_cycles = cycles_total;
     o.applied = (int64_t)applied;
-    o.iterations = it0;
+    o.iterations = it0 - rd.it0;
     o.accepted = accepted;
     o.segments = (int64_t)steps;
     o.status = status;
     o.reserved = 0;
+    o.k_next = k0;
+    o.pad = 0;
     p.out[rd.out] = o;
   }
   team_sync(t.C);
@@ -1269,18 +1301,25 @@ __global__ void __launch_bounds__(MAXT, 1) fj_kernel(const VnsParams p) {
   }
   const int K = t.K, T = t.T;
   const int64_t moves_per_cycle = (int64_t)K * (2 * T + (T > 1 ? 2 * (T - 1) : 0));
-  int status = 0;
+  const bool leader = team == 0 && t.crank == 0 && t.tid == 0;
+  // wall-clock budget from the run's start (worker 0's leader keeps time)
+  const long long deadline = rd.time_limit_ns > 0 && leader ? globaltimer_ns() + rd.time_limit_ns : 0;
+  int status = 0, stop = 0;
   int64_t cycles_total = 0;
-  int cyc = vnd<Acc, NW>(t, rd.mode);  // every worker descends from the start; counted once
-  if (cyc < 0) status = kStatusCap; else cycles_total += cyc;
+  int cyc = 0;
+  if (!rd.resume) {  // every worker descends from the start; counted once
+    cyc = vnd<Acc, NW>(t, rd.mode);
+    if (cyc < 0) status = kStatusCap; else cycles_total += cyc;
+  }
   int64_t fx = team_total(t);
+  if (rd.resume && fx != rd.f0) status = kStatusState;
   flush_counters(t, &sh.steps, &sh.applied);
   unsigned long long c_steps = 0, c_applied = 0;  // the workers' iterations (leader)
-  uint64_t h = 0;
+  uint64_t h = rd.h0;
   int64_t accepted = 0;
-  int it = 0, kk = 1;
-  const bool leader = team == 0 && t.crank == 0 && t.tid == 0;
-  for (; it < rd.iters && status == 0; ++it) {
+  int it = rd.it0, kk = rd.k0;
+  const int it_end = rd.it0 + rd.iters;
+  for (; it < it_end && status == 0 && !stop; ++it) {
     const int par = it & 1;
     SpecSlot* slot = p.spec_slots + par * W + team;
     if (t.crank == 0 && t.tid == 0) {
@@ -1290,7 +1329,8 @@ __global__ void __launch_bounds__(MAXT, 1) fj_kernel(const VnsParams p) {
     const ShakePlan pl = plan_shake(rd.seed, it, kk, K, T, (uint64_t)team << 8);
     apply_shake<Acc, NW>(t, pl, kk, par);
     cyc = vnd<Acc, NW>(t, rd.mode);
-    const int64_t f2 = team_total(t);  // cluster barrier: the slot reset is visible
+    int spent = 0;  // worker 0: the budget is spent
+    const int64_t f2 = team_total(t, deadline, &spent);  // cluster barrier: the slot reset is visible
     flush_counters(t, &slot->steps, &slot->applied);
 #pragma unroll
     for (int j = 0; j < kMaxShake; ++j)
@@ -1299,6 +1339,7 @@ __global__ void __launch_bounds__(MAXT, 1) fj_kernel(const VnsParams p) {
     if (t.crank == 0 && t.tid == 0) {
       slot->f2 = f2;
       slot->cycles = cyc;
+      slot->done = spent;
     }
     if (!grid_barrier(t, p.spec_bar, W)) {
       status = kStatusTimeout;
@@ -1324,6 +1365,7 @@ __global__ void __launch_bounds__(MAXT, 1) fj_kernel(const VnsParams p) {
     const int a = key_index(best);
     const int64_t fa = key_cost(best);
     const int acc = fa < fx;
+    stop = __ldcg(&slots[0].done);  // worker 0's verdict on the budget
     if (team == 0 && t.crank == 0 && t.warp == 0) {
       unsigned long long st = 0ull, ap = 0ull;
       for (int i = t.wlane; i < W; i += 32) {
@@ -1344,7 +1386,7 @@ __global__ void __launch_bounds__(MAXT, 1) fj_kernel(const VnsParams p) {
           te.cost = fa;
           te.accepted = acc;
           te.reserved = a;
-          p.traj[rd.traj_off + it] = te;
+          p.traj[rd.traj_off + (it - rd.it0)] = te;
         }
         h = splitmix64(h ^ (uint64_t)fa);
         h = splitmix64(h ^ (((uint64_t)it << 32) | ((uint64_t)kk << 1) | (uint64_t)acc));
@@ -1398,11 +1440,13 @@ __global__ void __launch_bounds__(MAXT, 1) fj_kernel(const VnsParams p) {
     o.evals = cycles_total * 3;
     o.vnd_cycles = cycles_total;
     o.applied = (int64_t)applied;
-    o.iterations = it;
+    o.iterations = it - rd.it0;
     o.accepted = accepted;
     o.segments = (int64_t)steps;
     o.status = status;
     o.reserved = W;
+    o.k_next = kk;
+    o.pad = 0;
     p.out[rd.out] = o;
   }
   team_sync(t.C);

@@ -20,6 +20,11 @@ SHAPE_KEYS = ("lanes", "threads", "cluster", "blocks", "smem", "tables_in_smem",
               "teams")
 
 
+# elsr_traj_t; "worker" is the fork-join winner (the C field `reserved`)
+TRAJ_DTYPE = np.dtype([("it", np.int32), ("k", np.int32), ("cost", np.int64),
+                       ("accepted", np.int32), ("worker", np.int32)])
+
+
 def _p(a: np.ndarray):
     return a.ctypes.data_as(P)
 
@@ -67,6 +72,7 @@ class Solver:
         if speculation:
             self.set_speculation(speculation)
         self._last_iters = 0
+        self._base_it = 0
 
     # -- plumbing --
     def _chk(self, code):
@@ -149,6 +155,7 @@ class Solver:
         """Queue a GVNS run on the stream (asynchronous)."""
         self._chk(self._lib.elsr_vns_run(self._h, seed & ((1 << 64) - 1), iters, kmax, mode))
         self._last_iters = iters
+        self._base_it = 0
 
     def vns_forkjoin_run(self, seed: int, iters: int, kmax: int = 3, mode: int = nat.MODE_P,
                          workers: int = 2):
@@ -157,25 +164,60 @@ class Solver:
         self._chk(self._lib.elsr_vns_forkjoin_run(self._h, seed & ((1 << 64) - 1), iters, kmax,
                                                   mode, workers))
         self._last_iters = iters
+        self._base_it = 0
 
     def vns_forkjoin(self, seed: int, iters: int, kmax: int = 3, mode: int = nat.MODE_P,
                      workers: int = 2, **kw):
         self.vns_forkjoin_run(seed, iters, kmax, mode, workers)
         return self.result(**kw)
 
+    # -- checkpoint / resume and the wall-clock budget --
+    def set_time_limit(self, us: int = 0):
+        """Wall-clock budget of the next runs in microseconds (0: none)."""
+        self._chk(self._lib.elsr_set_time_limit(self._h, int(us)))
+
+    def checkpoint(self) -> dict:
+        """Loop state of the last run (waits for it) plus its incumbent x as
+        arrays "gM", "gR"; plain data (see save_checkpoint)."""
+        ck = nat.Checkpoint()
+        gm = np.zeros((self.K, self.T), np.uint8)
+        gr = np.zeros((self.K, self.T), np.uint8)
+        code = self._lib.elsr_checkpoint(self._h, ctypes.byref(ck), _p(gm), _p(gr))
+        if code not in (nat.ELSR_E_CAP, nat.ELSR_E_TIMEOUT, nat.ELSR_E_STATE):
+            self._chk(code)
+        d = ck.as_dict()
+        d["gM"], d["gR"] = gm, gr
+        return d
+
+    def vns_resume_run(self, ck: dict, iters: int):
+        """Queue iterations ck["next_it"] .. + iters - 1 of a checkpointed run."""
+        c = nat.Checkpoint.from_dict(ck)
+        gm, gr = _u8(ck["gM"]).reshape(self.K, self.T), _u8(ck["gR"]).reshape(self.K, self.T)
+        self._chk(self._lib.elsr_vns_resume(self._h, ctypes.byref(c), _p(gm), _p(gr), iters))
+        self._last_iters = iters
+        self._base_it = int(ck["next_it"])
+
+    def vns_resume(self, ck: dict, iters: int, **kw):
+        self.vns_resume_run(ck, iters)
+        return self.result(**kw)
+
     def result(self, solution: bool = True, plan: bool = False, traj: bool = True):
         st = nat.Stats()
+        st.status = 1  # stays 1 unless the library fills the statistics
         gm = np.zeros((self.K, self.T), np.uint8) if solution else None
         gr = np.zeros((self.K, self.T), np.uint8) if solution else None
         pl = np.zeros((4, self.K, self.T), np.int32) if plan else None
         n = self._last_iters if traj else 0
-        tr = (nat.Traj * max(n, 1))()
+        tr = np.zeros(max(n, 1), TRAJ_DTYPE)
         code = self._lib.elsr_result(self._h, ctypes.byref(st),
                                      _p(gm) if solution else None,
                                      _p(gr) if solution else None,
                                      _p(pl) if plan else None,
-                                     tr if n else None, n)
-        if code not in (nat.ELSR_E_CAP, nat.ELSR_E_TIMEOUT):
+                                     _p(tr) if n else None, n)
+        # a run that ended with a status (cap, timeout, mismatched resume)
+        # still reports its statistics
+        if not (code in (nat.ELSR_E_CAP, nat.ELSR_E_TIMEOUT, nat.ELSR_E_STATE)
+                and st.status == code):
             self._chk(code)
         out = st.as_dict()
         if solution:
@@ -183,11 +225,8 @@ class Solver:
         if plan:
             out["plan"] = pl
         if n:
-            out["traj"] = np.array([(e.it, e.k, e.cost, e.accepted, e.reserved)
-                                    for e in tr[:n]],
-                                   dtype=[("it", np.int32), ("k", np.int32),
-                                          ("cost", np.int64), ("accepted", np.int32),
-                                          ("worker", np.int32)])
+            ran = out["iterations"] - self._base_it  # entries this run wrote
+            out["traj"] = tr[:max(0, min(n, ran))].copy()
         return out
 
     def vns(self, seed: int, iters: int, kmax: int = 3, mode: int = nat.MODE_P, **kw):
@@ -202,6 +241,7 @@ class Solver:
         self._chk(self._lib.elsr_multistart_run(self._h, seed0, nstarts, iters, kmax, mode,
                                                 _p(bc), _p(bs), _p(cs) if costs else None))
         self._last_iters = 0
+        self._base_it = 0
         return int(bc[0]), int(bs[0]), cs
 
     def multistart_stats(self, n: int):
@@ -213,6 +253,16 @@ class Solver:
         v = np.zeros(1, np.int64)
         self._chk(self._lib.elsr_counters(self._h, _p(v)))
         return int(v[0])
+
+
+def save_checkpoint(path: str, ck: dict) -> None:
+    """Store a checkpoint (loop state and incumbent) in an .npz file."""
+    np.savez(path, **{k: np.asarray(v) for k, v in ck.items()})
+
+
+def load_checkpoint(path: str) -> dict:
+    with np.load(path) as z:
+        return {k: (z[k] if z[k].ndim else int(z[k])) for k in z.files}
 
 
 class Batch:

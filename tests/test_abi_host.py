@@ -68,3 +68,24 @@ def test_validation_rejects_bad_instances(lib):
     assert _create(lib, K, T, big, R, c)[0] == nat.ELSR_E_RANGE
     hm = [np.ones(K), np.ones(K), np.full(K, 2**30), np.ones(K)]
     assert _create(lib, K, T, np.full((K, T), 1000), R, hm)[0] == nat.ELSR_E_RANGE
+
+
+def test_checkpoint_struct_and_file_roundtrip(tmp_path):
+    """elsr_checkpoint_t as the binding lays it out (96 bytes: six 32-bit and
+    nine 64-bit fields), and a checkpoint survives an .npz round trip with
+    full 64-bit seed and hash values."""
+    from paper_1704_05132_gb300 import elsr
+    assert ctypes.sizeof(nat.Checkpoint) == 96
+    ck = {n: i + 1 for i, (n, _) in enumerate(nat.Checkpoint._fields_)}
+    ck["seed"] = (1 << 64) - 3
+    ck["traj_hash"] = 0x9E3779B97F4A7C15
+    ck["gM"] = np.eye(3, 5, dtype=np.uint8)
+    ck["gR"] = np.ones((3, 5), np.uint8)
+    path = str(tmp_path / "ck.npz")
+    elsr.save_checkpoint(path, ck)
+    back = elsr.load_checkpoint(path)
+    for n, _ in nat.Checkpoint._fields_:
+        assert back[n] == ck[n], n
+    assert (back["gM"] == ck["gM"]).all() and (back["gR"] == ck["gR"]).all()
+    c = nat.Checkpoint.from_dict(back)
+    assert c.seed == ck["seed"] and c.traj_hash == ck["traj_hash"]
