@@ -54,7 +54,8 @@ class _Instance(ctypes.Structure):
     _fields_ = [("K", ctypes.c_int32), ("T", ctypes.c_int32),
                 ("D", ctypes.c_void_p), ("R", ctypes.c_void_p),
                 ("kM", ctypes.c_void_p), ("kR", ctypes.c_void_p),
-                ("hM", ctypes.c_void_p), ("hR", ctypes.c_void_p)]
+                ("hM", ctypes.c_void_p), ("hR", ctypes.c_void_p),
+                ("pM", ctypes.c_void_p), ("pR", ctypes.c_void_p)]
 
 
 class _Counters(ctypes.Structure):
@@ -108,26 +109,34 @@ def _ptr(a: np.ndarray):
 
 @dataclass
 class Instance:
-    """Problem data of Section 2: D, R int32 [K][T]; kM, kR, hM, hR int32 [K]."""
+    """Problem data of Section 2: D, R int32 [K][T]; kM, kR, hM, hR int32 [K];
+    optional unit production costs pM, pR int32 [K] (Algorithm 1's p_M, p_R;
+    None = 0)."""
     D: np.ndarray
     R: np.ndarray
     kM: np.ndarray
     kR: np.ndarray
     hM: np.ndarray
     hR: np.ndarray
+    pM: np.ndarray | None = None
+    pR: np.ndarray | None = None
 
     def __post_init__(self):
-        for f in ("D", "R", "kM", "kR", "hM", "hR"):
+        fields = ["D", "R", "kM", "kR", "hM", "hR"]
+        fields += [f for f in ("pM", "pR") if getattr(self, f) is not None]
+        for f in fields:
             setattr(self, f, np.ascontiguousarray(getattr(self, f), dtype=np.int32))
         if self.D.ndim != 2 or self.D.shape != self.R.shape:
             raise ValueError("D and R must be [K][T]")
         K = self.D.shape[0]
-        for f in ("kM", "kR", "hM", "hR"):
+        for f in fields[2:]:
             if getattr(self, f).shape != (K,):
                 raise ValueError(f"{f} must have shape [K]")
+        ptr = lambda a: a.ctypes.data if a is not None else None
         self._c = _Instance(self.K, self.T, self.D.ctypes.data, self.R.ctypes.data,
                             self.kM.ctypes.data, self.kR.ctypes.data,
-                            self.hM.ctypes.data, self.hR.ctypes.data)
+                            self.hM.ctypes.data, self.hR.ctypes.data,
+                            ptr(self.pM), ptr(self.pR))
 
     @property
     def K(self) -> int:
@@ -139,14 +148,17 @@ class Instance:
 
     @classmethod
     def from_arrays(cls, arrs) -> "Instance":
-        """From any object with D, R, kM, kR, hM, hR attributes."""
-        return cls(arrs.D, arrs.R, arrs.kM, arrs.kR, arrs.hM, arrs.hR)
+        """From any object with D, R, kM, kR, hM, hR (and optionally pM, pR)
+        attributes."""
+        return cls(arrs.D, arrs.R, arrs.kM, arrs.kR, arrs.hM, arrs.hR,
+                   getattr(arrs, "pM", None), getattr(arrs, "pR", None))
 
     def row(self, k: int) -> "Instance":
         """The single-product instance made of product k alone."""
         s = slice(k, k + 1)
+        sub = lambda a: a[s] if a is not None else None
         return Instance(self.D[s], self.R[s], self.kM[s], self.kR[s],
-                        self.hM[s], self.hR[s])
+                        self.hM[s], self.hR[s], sub(self.pM), sub(self.pR))
 
     @property
     def cref(self):

@@ -40,11 +40,14 @@
 
 #define ORC_INF INT64_MAX
 
-/* Problem data of Section 2.  D and R are row-major [K][T]; costs are [K]. */
+/* Problem data of Section 2.  D and R are row-major [K][T]; costs are [K].
+ * pM, pR: unit manufacturing and remanufacturing costs [K] (Algorithm 1's
+ * p_M, p_R); NULL means 0. */
 typedef struct {
     int32_t K, T;
     const int32_t *D, *R;
     const int32_t *kM, *kR, *hM, *hR;
+    const int32_t *pM, *pR;
 } orc_instance;
 
 /* Per-run counters (Algorithm 1 / Algorithm 2 bookkeeping). */
@@ -84,7 +87,9 @@ static int64_t sat_add(int64_t a, int64_t b)
  * yR.  Reading (the formulation is in [SK2016], not in the paper):
  *   yM(t) = yM(t-1) + xM(t) + xR(t) - D(t),  yR(t) = yR(t-1) + R(t) - xR(t),
  *   yM(-1) = yR(-1) = 0, all quantities >= 0, holding charged on end-of-period
- *   stock, setup cost charged on the setup bit, unit production costs 0.
+ *   stock, setup cost charged on the setup bit, and the unit production
+ *   costs p_M, p_R of Algorithm 1's signature charged per unit of xM, xR
+ *   (0 unless the instance gives them).
  * Decode reading: at each period with a setup, cover the demand up to the
  * next setup; remanufacture first from the available recoverable stock when
  * gR(t) = 1, manufacture the rest when gM(t) = 1; a shortfall is infeasible.
@@ -100,6 +105,7 @@ int64_t orc_decode_row(const orc_instance *in, int32_t k,
     const int32_t *R = in->R + (int64_t)k * T;
     const int64_t kM = in->kM[k], kR = in->kR[k];
     const int64_t hM = in->hM[k], hR = in->hR[k];
+    const int64_t pM = in->pM ? in->pM[k] : 0, pR = in->pR ? in->pR[k] : 0;
     int64_t yM_prev = 0, yR_prev = 0, cost = 0;
 
     for (int32_t t = 0; t < T; ++t) {
@@ -120,7 +126,7 @@ int64_t orc_decode_row(const orc_instance *in, int32_t k,
         int64_t yM = yM_prev + xm + xr - D[t];
         if (yM < 0) return ORC_INF; /* demand not covered (e.g. before the first setup) */
         int64_t yR = avail - xr;
-        cost += kM * gM[t] + kR * gR[t] + hM * yM + hR * yR;
+        cost += kM * gM[t] + kR * gR[t] + hM * yM + hR * yR + pM * xm + pR * xr;
         if (plan) {
             plan[t] = xm;
             plan[T + t] = xr;

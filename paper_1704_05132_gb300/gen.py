@@ -67,13 +67,16 @@ class Stream:
 
 @dataclass
 class ElsrInstance:
-    """Problem data of Section 2 (int32 arrays, row-major D/R [K][T])."""
+    """Problem data of Section 2 (int32 arrays, row-major D/R [K][T]); pM, pR:
+    optional unit production costs [K] (None: none)."""
     D: np.ndarray
     R: np.ndarray
     kM: np.ndarray
     kR: np.ndarray
     hM: np.ndarray
     hR: np.ndarray
+    pM: np.ndarray | None = None
+    pR: np.ndarray | None = None
 
     @property
     def K(self) -> int:
@@ -136,3 +139,21 @@ def multistart_large() -> ElsrInstance:
 def serving_request(r: int, seed: int = 5) -> ElsrInstance:
     """Serving request r: K ~ U{5..200}, T ~ U{12..104}, keyed by request id."""
     return make_instance(seed, r, K_range=(5, 200), T_range=(12, 104))
+
+
+def with_production_costs(g: ElsrInstance, seed: int, ident: int = 0,
+                          pM_range=(10, 40), pR_range=(0, 60)) -> ElsrInstance:
+    """The instance g with unit production costs pM ~ U{pM_range},
+    pR ~ U{pR_range} per product, drawn (pM then pR for each product) from
+    the stream (seed, ident).  The paper names p_M, p_R in Algorithm 1's
+    signature without values; the default ranges make remanufacturing
+    cheaper for some products and dearer for others, so pR - pM takes both
+    signs and can outweigh the holding saving hR*(T-t)."""
+    s = Stream(seed, ident)
+    K = g.D.shape[0]
+    v = s.draws(2 * K).reshape(K, 2)
+    pM = pM_range[0] + (v[:, 0] % np.uint64(pM_range[1] - pM_range[0] + 1)).astype(np.int64)
+    pR = pR_range[0] + (v[:, 1] % np.uint64(pR_range[1] - pR_range[0] + 1)).astype(np.int64)
+    return ElsrInstance(g.D, g.R, g.kM, g.kR, g.hM, g.hR,
+                        np.ascontiguousarray(pM, dtype=np.int32),
+                        np.ascontiguousarray(pR, dtype=np.int32))

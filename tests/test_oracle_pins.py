@@ -423,3 +423,83 @@ def test_forkjoin_not_below_brute_force(seed):
         assert oracle.total_cost(inst, res.gM, res.gR)[0] == res.best_cost
         acc = res.traj["cost"][res.traj["accepted"] == 1]
         assert (np.diff(acc) < 0).all()
+
+
+# ---------------------------------------------------------------------------
+# Unit production costs p_M, p_R (Algorithm 1's signature).
+# ---------------------------------------------------------------------------
+
+def _worked_examples_production():
+    base = {r[0]: r for r in _worked_examples()}
+    rows = []
+    with open(os.path.join(GOLDEN, "worked_examples_production.txt")) as f:
+        for line in f:
+            if not line.strip() or line.startswith("#"):
+                continue
+            p = [c.strip() for c in line.split("|")]
+            rows.append((p, base[p[1]]))
+    return rows
+
+
+@pytest.mark.parametrize("row", _worked_examples_production(), ids=lambda r: r[0][0])
+def test_worked_examples_with_production_costs(row):
+    (name, _, pc, sxm, sxr, cost), b = row
+    pm, pr = _ints(pc)
+    kM, kR, hM, hR = _ints(b[3])
+    inst = oracle.Instance(np.array([_ints(b[1])]), np.array([_ints(b[2])]),
+                           [kM], [kR], [hM], [hR], [pm], [pr])
+    c, plan = oracle.decode_row(inst, 0, np.array(_ints(b[4])), np.array(_ints(b[5])))
+    if cost == "INF":
+        assert c == INF
+        return
+    assert c == int(cost)
+    assert int(plan[0].sum()) == int(sxm) and int(plan[1].sum()) == int(sxr)
+
+
+def test_closed_form_all_open_with_production_costs():
+    """Every setup open and R <= D: xR(t) = R(t), xM(t) = D(t) - R(t) and no
+    stock is held, so the cost is sum_k T(kM + kR) + pM sum D + (pR - pM) sum R."""
+    for seed in range(4):
+        g = gen.with_production_costs(gen.make_instance(seed, 5, K=6, T=13), seed, 9)
+        inst = oracle.Instance.from_arrays(g)
+        gm, gr = oracle.initial_solution(inst.K, inst.T)
+        total, _ = oracle.total_cost(inst, gm, gr)
+        i64 = lambda a: a.astype(np.int64)
+        want = (inst.T * (i64(inst.kM) + inst.kR) + i64(inst.pM) * i64(inst.D).sum(1)
+                + (i64(inst.pR) - inst.pM) * i64(inst.R).sum(1)).sum()
+        assert total == int(want)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_equal_production_costs_shift_every_feasible_cost(mode):
+    """pM = pR = p adds p * sum D to every feasible row whatever its setups
+    (xM + xR covers the demand), so GVNS takes the same steps and every
+    feasible trajectory cost moves by p * sum D."""
+    g = gen.make_instance(17, 1, K=6, T=16)
+    base = oracle.vns(oracle.Instance.from_arrays(g), seed=3, iters=60, kmax=3, mode=mode)
+    p = np.full(6, 23, np.int32)
+    inst = oracle.Instance(g.D, g.R, g.kM, g.kR, g.hM, g.hR, p, p)
+    res = oracle.vns(inst, seed=3, iters=60, kmax=3, mode=mode)
+    shift = 23 * int(g.D.astype(np.int64).sum())
+    assert (res.gM == base.gM).all() and (res.gR == base.gR).all()
+    assert res.best_cost == base.best_cost + shift
+    feas = base.traj["cost"] != INF
+    assert (res.traj["cost"][feas] == base.traj["cost"][feas] + shift).all()
+    assert (res.traj["cost"][~feas] == INF).all()
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_wagner_whitin_with_manufacturing_cost(seed):
+    """K=1, R=0: every unit is manufactured, so the best gM pattern costs the
+    Wagner-Whitin optimum plus pM * sum D (pR plays no part)."""
+    rng = np.random.default_rng(100 + seed)
+    T = 9
+    D = rng.integers(0, 30, T).astype(np.int32)
+    kM, hM, pm = int(rng.integers(20, 90)), int(rng.integers(1, 5)), int(rng.integers(1, 20))
+    ww = _wagner_whitin(D.tolist(), kM, hM)
+    inst = oracle.Instance(D[None, :], np.zeros((1, T), np.int32), [kM], [50], [hM], [1],
+                           [pm], [int(rng.integers(0, 50))])
+    zeros = np.zeros(T, np.uint8)
+    best = min(oracle.decode_row(inst, 0, np.array(p, np.uint8), zeros)[0]
+               for p in itertools.product((0, 1), repeat=T))
+    assert best == ww + pm * int(D.sum())
