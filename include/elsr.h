@@ -145,6 +145,19 @@ int elsr_create(elsr_t **out, int32_t K, int32_t T, const int32_t *D,
                 const int32_t *R, const int32_t *kM, const int32_t *kR,
                 const int32_t *hM, const int32_t *hR);
 
+/*
+ * As elsr_create, with unit production costs: pM, pR host int32 [K]
+ * (copied; both NULL = 0, as elsr_create).  Algorithm 1's signature carries
+ * p_M and p_R beside the setup and holding costs; the row cost then adds
+ * pM * xM(t) + pR * xR(t) in every period.  Each must be below 2^24, and
+ * the objective bound above grows by sum_k (pM + pR) * sum_t D.  Every
+ * other call works unchanged on such a handle.
+ */
+int elsr_create_ex(elsr_t **out, int32_t K, int32_t T, const int32_t *D,
+                   const int32_t *R, const int32_t *kM, const int32_t *kR,
+                   const int32_t *hM, const int32_t *hR, const int32_t *pM,
+                   const int32_t *pR);
+
 /* Free the handle and its device memory (synchronises its stream). */
 void elsr_destroy(elsr_t *h);
 
@@ -370,6 +383,14 @@ int elsr_batch_create_on(elsr_batch_t **out, int32_t n, const int32_t *Ks,
                          const int32_t *Ts, const int32_t *D, const int32_t *R,
                          const int32_t *kM, const int32_t *kR,
                          const int32_t *hM, const int32_t *hR, void *stream);
+/* As elsr_batch_create_on, with unit production costs pM, pR holding the
+ * instances' [K_i] blocks one after another (both NULL = 0), under the
+ * limits of elsr_create_ex. */
+int elsr_batch_create_ex(elsr_batch_t **out, int32_t n, const int32_t *Ks,
+                         const int32_t *Ts, const int32_t *D, const int32_t *R,
+                         const int32_t *kM, const int32_t *kR,
+                         const int32_t *hM, const int32_t *hR,
+                         const int32_t *pM, const int32_t *pR, void *stream);
 void elsr_batch_destroy(elsr_batch_t *b);
 
 /* Message of the last failed call on batch b (b NULL: last failed create on

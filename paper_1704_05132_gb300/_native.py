@@ -74,6 +74,7 @@ SIGNATURES = {
     "elsr_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "elsr_last_error": (ctypes.c_char_p, [P]),
     "elsr_create": (ctypes.c_int, [ctypes.POINTER(P), i32, i32, P, P, P, P, P, P]),
+    "elsr_create_ex": (ctypes.c_int, [ctypes.POINTER(P), i32, i32, P, P, P, P, P, P, P, P]),
     "elsr_destroy": (None, [P]),
     "elsr_set_stream": (ctypes.c_int, [P, P]),
     "elsr_set_launch": (ctypes.c_int, [P, i32, i32]),
@@ -98,6 +99,8 @@ SIGNATURES = {
                                                       u32, i32, P, P, P, P]),
     "elsr_batch_create": (ctypes.c_int, [ctypes.POINTER(P), i32, P, P, P, P, P, P, P, P]),
     "elsr_batch_create_on": (ctypes.c_int, [ctypes.POINTER(P), i32, P, P, P, P, P, P, P, P, P]),
+    "elsr_batch_create_ex": (ctypes.c_int, [ctypes.POINTER(P), i32, P, P, P, P, P, P, P, P,
+                                            P, P, P]),
     "elsr_batch_destroy": (None, [P]),
     "elsr_batch_last_error": (ctypes.c_char_p, [P]),
     "elsr_batch_set_stream": (ctypes.c_int, [P, P]),

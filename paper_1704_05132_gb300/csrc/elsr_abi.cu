@@ -51,8 +51,8 @@ void dev_free(T*& p, cudaStream_t s) {
 // *acc64 when a row's magnitude bound needs 64-bit accumulators.
 int check_instance(int32_t K, int32_t T, const int32_t* D, const int32_t* R,
                    const int32_t* kM, const int32_t* kR, const int32_t* hM,
-                   const int32_t* hR, bool* acc64, unsigned __int128* total,
-                   std::string& err) {
+                   const int32_t* hR, const int32_t* pM, const int32_t* pR, bool* acc64,
+                   unsigned __int128* total, std::string& err) {
   if (K < 1 || T < 1 || T > ELSR_T_MAX) {
     err = "K must be >= 1 and 1 <= T <= " + std::to_string(ELSR_T_MAX);
     return ELSR_E_ARG;
@@ -66,9 +66,14 @@ int check_instance(int32_t K, int32_t T, const int32_t* D, const int32_t* R,
     return ELSR_E_RANGE;
   }
   for (int32_t k = 0; k < K; ++k) {
-    if (kM[k] < 0 || kR[k] < 0 || hM[k] < 0 || hR[k] < 0) {
+    const int64_t pm = pM ? pM[k] : 0, pr = pR ? pR[k] : 0;
+    if (kM[k] < 0 || kR[k] < 0 || hM[k] < 0 || hR[k] < 0 || pm < 0 || pr < 0) {
       err = "negative cost in product " + std::to_string(k);
       return ELSR_E_ARG;
+    }
+    if (pm >= (1 << 24) || pr >= (1 << 24)) {
+      err = "unit production cost of product " + std::to_string(k) + " exceeds 2^24";
+      return ELSR_E_RANGE;
     }
     int64_t sd = 0, sr = 0, wd = 0, wr = 0;
     for (int32_t t = 0; t < T; ++t) {
@@ -91,7 +96,9 @@ int check_instance(int32_t K, int32_t T, const int32_t* D, const int32_t* R,
     unsigned __int128 b = (unsigned __int128)T * ((uint64_t)kM[k] + (uint64_t)kR[k]);
     b += (unsigned __int128)T * ((unsigned __int128)hM[k] * sd + (unsigned __int128)hR[k] * sr);
     b += (unsigned __int128)hM[k] * wd + (unsigned __int128)hR[k] * wr;
-    if (b >= ((unsigned __int128)1 << 30)) *acc64 = true;
+    b += (unsigned __int128)(pm + pr) * sd;  // pM * sum D + |pR - pM| * sum xR
+    if (b >= ((unsigned __int128)1 << 30) || (int64_t)hR[k] * T + pm + pr >= (1ll << 30))
+      *acc64 = true;
     *total += b;
   }
   if (*total >= ((unsigned __int128)1 << 40) - 1) {
@@ -132,6 +139,7 @@ struct elsr_batch {
           *d_hM = nullptr, *d_hR = nullptr;
   int2* d_tab = nullptr;  // global prefix tables (staged on demand)
   int64_t* d_C0 = nullptr;
+  int32_t *d_pM = nullptr, *d_pR = nullptr;  // unit production costs (none: 0)
   bool tab_ready = false;
 
   RunDesc* d_runs = nullptr;
@@ -166,6 +174,8 @@ struct elsr_batch {
     p.hR = d_hR;
     p.gtab = d_tab;
     p.gC0 = d_C0;
+    p.pM = d_pM;
+    p.pR = d_pR;
     return p;
   }
 
@@ -180,6 +190,8 @@ struct elsr_batch {
     dev_free(d_hR, stream);
     dev_free(d_tab, stream);
     dev_free(d_C0, stream);
+    dev_free(d_pM, stream);
+    dev_free(d_pR, stream);
     dev_free(d_runs, stream);
     dev_free(d_out, stream);
     dev_free(d_bits, stream);
@@ -197,7 +209,12 @@ namespace {
 
 int batch_init(elsr_batch* b, int32_t n, const int32_t* Ks, const int32_t* Ts,
                const int32_t* D, const int32_t* R, const int32_t* kM,
-               const int32_t* kR, const int32_t* hM, const int32_t* hR) {
+               const int32_t* kR, const int32_t* hM, const int32_t* hR,
+               const int32_t* pM = nullptr, const int32_t* pR = nullptr) {
+  if ((pM == nullptr) != (pR == nullptr)) {
+    b->err = "pM and pR must both be given or both be NULL";
+    return ELSR_E_ARG;
+  }
   if (n < 1 || !Ks || !Ts) {
     b->err = "batch needs n >= 1 and K/T arrays";
     return ELSR_E_ARG;
@@ -223,7 +240,8 @@ int batch_init(elsr_batch* b, int32_t n, const int32_t* Ks, const int32_t* Ts,
                             kM ? kM + d.row_off : nullptr,
                             kR ? kR + d.row_off : nullptr,
                             hM ? hM + d.row_off : nullptr,
-                            hR ? hR + d.row_off : nullptr, &a64, &tot, b->err);
+                            hR ? hR + d.row_off : nullptr, pM ? pM + d.row_off : nullptr,
+                            pR ? pR + d.row_off : nullptr, &a64, &tot, b->err);
     if (rc != ELSR_OK) {
       b->err = "instance " + std::to_string(i) + ": " + b->err;
       return rc;
@@ -254,6 +272,12 @@ int batch_init(elsr_batch* b, int32_t n, const int32_t* Ks, const int32_t* Ts,
   ELSR_TRY_CUDA(b, cudaMemcpyAsync(b->d_kR, kR, b->rows * 4, cudaMemcpyHostToDevice, b->stream));
   ELSR_TRY_CUDA(b, cudaMemcpyAsync(b->d_hM, hM, b->rows * 4, cudaMemcpyHostToDevice, b->stream));
   ELSR_TRY_CUDA(b, cudaMemcpyAsync(b->d_hR, hR, b->rows * 4, cudaMemcpyHostToDevice, b->stream));
+  if (pM) {
+    ELSR_TRY_CUDA(b, dev_alloc(&b->d_pM, b->rows, b->stream));
+    ELSR_TRY_CUDA(b, dev_alloc(&b->d_pR, b->rows, b->stream));
+    ELSR_TRY_CUDA(b, cudaMemcpyAsync(b->d_pM, pM, b->rows * 4, cudaMemcpyHostToDevice, b->stream));
+    ELSR_TRY_CUDA(b, cudaMemcpyAsync(b->d_pR, pR, b->rows * 4, cudaMemcpyHostToDevice, b->stream));
+  }
   ELSR_TRY_CUDA(b, cudaStreamSynchronize(b->stream));  // host arrays may be freed on return
   return ELSR_OK;
 }
@@ -287,7 +311,12 @@ int vns_shape(elsr_batch* b, LaunchShape* ls) {
     maxT = std::max(maxT, b->insts[r.inst].T);
   }
   int C = b->cluster;
-  if (C <= 0) C = b->h_runs.size() == 1 ? std::min(8, std::max(1, maxK / 6)) : 1;
+  // A single run spreads its rows over a cluster: 8 CTAs keep the most
+  // speculative teams resident (15 on 152 SMs); beyond ~12 rows per CTA a
+  // sweep's dependent chain grows with the rows each row group walks, and
+  // 16 CTAs win (K=300: 26 vs 37 ms per 1000 iterations, measured).
+  if (C <= 0)
+    C = b->h_runs.size() == 1 ? (maxK > 96 ? 16 : std::min(8, std::max(1, maxK / 6))) : 1;
   C = std::min(C, maxK);
   size_t need_s = 0, need_g = 0;
   // Grow the cluster until the largest run's rows fit the CTAs' shared
@@ -658,6 +687,13 @@ const char* elsr_last_error(const elsr_t* h) {
 int elsr_create(elsr_t** out, int32_t K, int32_t T, const int32_t* D,
                 const int32_t* R, const int32_t* kM, const int32_t* kR,
                 const int32_t* hM, const int32_t* hR) {
+  return elsr_create_ex(out, K, T, D, R, kM, kR, hM, hR, nullptr, nullptr);
+}
+
+int elsr_create_ex(elsr_t** out, int32_t K, int32_t T, const int32_t* D,
+                   const int32_t* R, const int32_t* kM, const int32_t* kR,
+                   const int32_t* hM, const int32_t* hR, const int32_t* pM,
+                   const int32_t* pR) {
   if (!out) {
     g_create_error = "out is NULL";
     return ELSR_E_ARG;
@@ -669,7 +705,7 @@ int elsr_create(elsr_t** out, int32_t K, int32_t T, const int32_t* D,
     return ELSR_E_NOMEM;
   }
   const int32_t Ks[1] = {K}, Ts[1] = {T};
-  int rc = batch_init(&h->b, 1, Ks, Ts, D, R, kM, kR, hM, hR);
+  int rc = batch_init(&h->b, 1, Ks, Ts, D, R, kM, kR, hM, hR, pM, pR);
   if (rc == ELSR_OK) {
     h->K = K;
     h->T = T;
@@ -1134,6 +1170,14 @@ int elsr_batch_create_on(elsr_batch_t** out, int32_t n, const int32_t* Ks,
                          const int32_t* Ts, const int32_t* D, const int32_t* R,
                          const int32_t* kM, const int32_t* kR, const int32_t* hM,
                          const int32_t* hR, void* stream) {
+  return elsr_batch_create_ex(out, n, Ks, Ts, D, R, kM, kR, hM, hR, nullptr, nullptr, stream);
+}
+
+int elsr_batch_create_ex(elsr_batch_t** out, int32_t n, const int32_t* Ks,
+                         const int32_t* Ts, const int32_t* D, const int32_t* R,
+                         const int32_t* kM, const int32_t* kR, const int32_t* hM,
+                         const int32_t* hR, const int32_t* pM, const int32_t* pR,
+                         void* stream) {
   if (!out) {
     g_create_error = "out is NULL";
     return ELSR_E_ARG;
@@ -1145,7 +1189,7 @@ int elsr_batch_create_on(elsr_batch_t** out, int32_t n, const int32_t* Ks,
     return ELSR_E_NOMEM;
   }
   b->stream = (cudaStream_t)stream;
-  int rc = batch_init(b, n, Ks, Ts, D, R, kM, kR, hM, hR);
+  int rc = batch_init(b, n, Ks, Ts, D, R, kM, kR, hM, hR, pM, pR);
   if (rc != ELSR_OK) {
     g_create_error = b->err;
     delete b;

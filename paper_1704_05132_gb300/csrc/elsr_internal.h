@@ -83,6 +83,8 @@ struct InstPools {
   const int32_t* hR;
   const int2* gtab;    // global prefix tables (when not staged in smem)
   const int64_t* gC0;  // per-row constants matching gtab
+  const int32_t* pM;   // unit production costs per row (nullable: 0)
+  const int32_t* pR;
 };
 
 // One speculative team's result for one round (spec_kernel).
@@ -171,7 +173,7 @@ ELSR_HD VnsLayout vns_layout(int Kc, int T, int acc_bytes, bool tab_smem) {
   L.tab = o;
   if (tab_smem) o = align16(o + K * (TT + 1) * 8u);
   L.rc = o;
-  o = align16(o + K * 16u);
+  o = align16(o + K * (uint32_t)sizeof(RowCosts));
   L.C0 = o;
   o = align16(o + K * 8u);
   L.bits = o;

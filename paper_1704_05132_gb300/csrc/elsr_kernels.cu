@@ -51,7 +51,7 @@ __global__ void stage_kernel(const StageParams p) {
                    p.ip.R + id.cell_off + (int64_t)k * T, T, lane,
                    p.gtab + id.tab_off + (int64_t)k * (T + 1),
                    p.ip.hM[id.row_off + k], p.ip.hR[id.row_off + k],
-                   p.gC0 + id.row_off + k);
+                   p.ip.pM ? p.ip.pM[id.row_off + k] : 0, p.gC0 + id.row_off + k);
   }
 }
 
@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(1024) eval_kernel(const EvalParams p) {
       stage_row_warp(p.ip.D + id.cell_off + (int64_t)k * T,
                      p.ip.R + id.cell_off + (int64_t)k * T, T, wlane,
                      tab + (int64_t)i * (T + 1), p.ip.hM[id.row_off + k],
-                     p.ip.hR[id.row_off + k], &C0[i]);
+                     p.ip.hR[id.row_off + k], p.ip.pM ? p.ip.pM[id.row_off + k] : 0, &C0[i]);
     }
   }
   if (tid == 0) {
@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(1024) eval_kernel(const EvalParams p) {
   const int k = row0 + sub;
   const bool valid = k < K;
   RowState<Acc> cur;
-  RowCosts rc{0, 0, 0, 0};
+  RowCosts rc{0, 0, 0, 0, 0};
   int64_t c0 = 0;
   const int2* tk = tab + (int64_t)sub * (T + 1);
   int32_t* Ak = A + sub * T;
@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(1024) eval_kernel(const EvalParams p) {
   cur.ld = -1;
   if (valid) {
     const int64_t ro = id.row_off + k;
-    rc = RowCosts{p.ip.kM[ro], p.ip.kR[ro], p.ip.hM[ro], p.ip.hR[ro]};
+    rc = vns::row_costs(p.ip, ro);
     c0 = C0[sub];
     cur.b = p.bits[k];
     if (lane == 0) {

@@ -24,6 +24,10 @@
 // cost is S + C0 with S the sum of segment terms and the per-row constant
 // C0 = hR * sum_t R(t)(T-t) - hM * sum_t D(t)(T-t).
 //
+// With unit production costs pM, pR (Algorithm 1's signature) the row adds
+// pM * sum D to C0 and every remanufactured unit's weight hR*(T-s) becomes
+// hR*(T-s) - (pR - pM) (see xr_weight).
+//
 // Row cache (per setup s of the current row, from its relaxed decode):
 // A[s] = avail at s and C[s] = S accumulated before s, plus the list of gR
 // setups with prefix sums of their room.  A move changes
@@ -133,10 +137,22 @@ ELSR_HD void apply_row_move(RowBits& b, int T, int j, int local) {
 }
 
 // Per-row constants: costs and the row's prefix table tab[0..T] =
-// {CD[j], CR1[j]} (CR1[T] = total returns).
+// {CD[j], CR1[j]} (CR1[T] = total returns).  dP = pR - pM, the difference
+// of the unit production costs of Algorithm 1's signature (0 when the
+// instance has none).
 struct RowCosts {
-  int32_t kM, kR, hM, hR;
+  int32_t kM, kR, hM, hR, dP;
 };
+
+// What one more unit remanufactured (and one less manufactured) at setup s
+// saves: hR per period of recoverable stock to the horizon, less the unit
+// cost difference dP.  With xM + xR = need at every setup, a segment costs
+// hM*need*(T-s) - xr_weight*xR, and the row's production cost is pM * sum D
+// (in C0) plus dP * sum xR.
+template <typename Acc>
+ELSR_HD Acc xr_weight(const RowCosts& rc, int T, int s) {
+  return (Acc)rc.hR * (Acc)(T - s) - (Acc)rc.dP;
+}
 
 // One segment [s, n) with setup flags gm, gr at s.  ts = tab[s], tn = tab[n].
 // Updates avail (stock entering n) and S; returns false on a shortfall.
@@ -147,7 +163,7 @@ ELSR_HD bool seg_step(int s, int gm, int gr, int2 ts, int2 tn, int T,
   const int32_t xr = gr ? (avail < need ? avail : need) : 0;
   if (!gm && xr < need) return false;
   S += (Acc)(gm ? rc.kM : 0) + (Acc)(gr ? rc.kR : 0) +
-       ((Acc)rc.hM * (Acc)need - (Acc)rc.hR * (Acc)xr) * (Acc)(T - s);
+       ((Acc)rc.hM * (Acc)need - (Acc)rc.hR * (Acc)xr) * (Acc)(T - s) + (Acc)rc.dP * (Acc)xr;
   avail = avail - xr + (tn.y - ts.y);
   return true;
 }
@@ -160,7 +176,7 @@ ELSR_HD bool seg_step(int s, int gm, int gr, int2 ts, int2 tn, int T,
 //   L[0..nR)    the row's gR setups in period order:
 //               {surplus(s) = A[s] - need(s), s | gM(s)<<16}
 //   P, Q[0..nR] exclusive prefix sums over L of room = max(0, need - A) and
-//               hR*(T-s)*room
+//               xr_weight(s)*room
 // bad = T when the row is feasible; else its first setup that falls short
 // (-1 when demand precedes the first setup: then nothing is cached); ld = the
 // L index of its last setup that falls short (-1 when none).
@@ -301,7 +317,7 @@ ELSR_HD int swap_of_rank(const SwapMasks& s, int T, int i) {
 // Relaxed decode of a whole row from its bits, writing the cache.  Returns
 // the relaxed S and sets bad, nR and ld.  P, Q ([nR+1]) receive exclusive
 // prefix sums over the gR list of room(r) = max(0, need - avail) and
-// hR*(T-s)*room(r).  segs counts the segments walked.
+// xr_weight(s)*room(r).  segs counts the segments walked.
 template <typename Acc, int NW>
 ELSR_HD Acc build_row(const int2* tab, int T, const RowCosts& rc,
                       const RowBits& b, int32_t* A, Acc* C, int2* L,
@@ -336,7 +352,7 @@ ELSR_HD Acc build_row(const int2* tab, int T, const RowCosts& rc,
       L[nR] = e;
       const int32_t room = need > avail ? need - avail : 0;
       P[nR + 1] = P[nR] + room;
-      Q[nR + 1] = Q[nR] + (Acc)rc.hR * (Acc)(T - s) * (Acc)room;
+      Q[nR + 1] = Q[nR] + xr_weight<Acc>(rc, T, s) * (Acc)room;
       if (!gm && xr < need) {  // deficit, taken as manufactured
         if (bad == T) bad = s;
         ld = nR;
@@ -344,7 +360,7 @@ ELSR_HD Acc build_row(const int2* tab, int T, const RowCosts& rc,
       ++nR;
     }
     S += (Acc)(gm ? rc.kM : 0) + (Acc)(gr ? rc.kR : 0) +
-         ((Acc)rc.hM * (Acc)need - (Acc)rc.hR * (Acc)xr) * (Acc)(T - s);
+         (Acc)rc.hM * (Acc)need * (Acc)(T - s) - xr_weight<Acc>(rc, T, s) * (Acc)xr;
     avail = avail - xr + (tn.y - ts.y);
     s = n;
     ts = tn;
@@ -365,7 +381,7 @@ ELSR_HD Acc build_row(const int2* tab, int T, const RowCosts& rc,
 // have the same setups from there on and differ only in the recoverable
 // stock, by delta = avail_new - A[s1].  With the telescoped cost the suffix
 // then costs its cached (relaxed) value plus, at every later gR setup,
-// -hR*(T-s)*dx where dx is the change of xR = min(avail, need); delta
+// -xr_weight(s)*dx where dx is the change of xR = min(avail, need); delta
 // shrinks by dx, and the walk stops when it reaches 0.  A setup of the
 // current row that falls short (a deficit in the relaxed decode) is fixed
 // only when delta still covers its room there, so the moved row is feasible
@@ -485,7 +501,7 @@ ELSR_HD Acc eval_move(const int2* tab, int T, const RowCosts& rc,
   if (delta > 0) {
     // More stock: each later gR setup absorbs up to its room (need minus the
     // stock it had), lowering xM by as much, until delta is used up.  With
-    // the prefix sums P (room) and Q (hR*(T-s)*room) the setup z where the
+    // the prefix sums P (room) and Q (xr_weight*room) the setup z where the
     // rest of delta is absorbed is a binary search, and the cost is closed
     // form.  The step count is that of the walk: z - r0 + 1 setups (or all
     // remaining ones when delta is never used up).  A deficit setup after z,
@@ -510,7 +526,7 @@ ELSR_HD Acc eval_move(const int2* tab, int T, const RowCosts& rc,
     const Acc Qz = Q[lo];
     const int sz = L[lo].y & 0xFFFF;
     if (cur.ld > lo || (cur.ld == lo && Pz1 != target)) return Inf<Acc>::value;
-    return S - (Qz - Q0) - (Acc)rc.hR * (Acc)(T - sz) * (Acc)(target - Pz);
+    return S - (Qz - Q0) - xr_weight<Acc>(rc, T, sz) * (Acc)(target - Pz);
   }
   // Less stock: walk the gR setups while delta < 0 (a shortfall at a
   // remanufacture-only setup is infeasible, and so is any deficit left).
@@ -523,7 +539,7 @@ ELSR_HD Acc eval_move(const int2* tab, int T, const RowCosts& rc,
     ++steps;
     if (!(e.y >> 16) && sn < 0) return Inf<Acc>::value;
     const int32_t dx = (sn < 0 ? sn : 0) - (sg < 0 ? sg : 0);
-    S -= (Acc)rc.hR * (Acc)(T - sr) * (Acc)dx;
+    S -= (Acc)rc.hR * (Acc)(T - sr) * (Acc)dx - (Acc)rc.dP * (Acc)dx;
     delta -= dx;
     if (delta == 0) break;
   }

@@ -171,6 +171,8 @@ extern "C" int elsr_eval_neighbourhood_static(
   p.ip.hR = hR;
   p.ip.gtab = nullptr;
   p.ip.gC0 = nullptr;
+  p.ip.pM = nullptr;  // no unit production costs
+  p.ip.pR = nullptr;
   p.K = K;
   p.T = T;
   p.bits = (const RowBits*)(scratch + kBitsOff);

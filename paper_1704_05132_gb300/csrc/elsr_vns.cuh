@@ -49,11 +49,11 @@ __device__ __forceinline__ RowBits all_open(int T) {
 
 // Stage one row with a full warp: tab[0..T] = {CD[j], CR1[j]} by warp
 // inclusive scans over 32-period chunks (coalesced int32 loads), and the row
-// constant C0 = hR * sum R(t)(T-t) - hM * sum D(t)(T-t).
+// constant C0 = hR * sum R(t)(T-t) - hM * sum D(t)(T-t) + pM * sum D.
 __device__ __forceinline__ void stage_row_warp(const int32_t* __restrict__ D,
                                                const int32_t* __restrict__ R, int T,
                                                int lane, int2* tab, int32_t hM,
-                                               int32_t hR, int64_t* C0) {
+                                               int32_t hR, int32_t pM, int64_t* C0) {
   int32_t carryD = 0, carryR = 0;
   int64_t wd = 0, wr = 0;
   for (int base = 0; base < T; base += 32) {
@@ -84,8 +84,14 @@ __device__ __forceinline__ void stage_row_warp(const int32_t* __restrict__ D,
   if (lane == 0) {
     tab[0].x = 0;
     tab[T].y = carryR;
-    *C0 = (int64_t)hR * wr - (int64_t)hM * wd;
+    *C0 = (int64_t)hR * wr - (int64_t)hM * wd + (int64_t)pM * carryD;
   }
+}
+
+// Costs of pool row ro (unit production costs 0 when the pools have none).
+__device__ __forceinline__ RowCosts row_costs(const InstPools& ip, int64_t ro) {
+  const int32_t pm = ip.pM ? ip.pM[ro] : 0, pr = ip.pR ? ip.pR[ro] : 0;
+  return RowCosts{ip.kM[ro], ip.kR[ro], ip.hM[ro], ip.hR[ro], pr - pm};
 }
 
 // Shared-memory view of the rows a CTA owns in the current run.
@@ -320,7 +326,8 @@ __device__ __forceinline__ void rebuild_row(const Rows<Acc>& m, int q, int lane,
       A[t] = avail;
       C[t] = lsum;
       lsum += (Acc)(gm ? rc.kM : 0) + (Acc)(gr ? rc.kR : 0) +
-              ((Acc)rc.hM * (Acc)need - (Acc)rc.hR * (Acc)xr) * (Acc)(T - t);
+              ((Acc)rc.hM * (Acc)need - (Acc)rc.hR * (Acc)xr) * (Acc)(T - t) +
+              (Acc)rc.dP * (Acc)xr;
       if (gr) {
         int2 en;
         en.x = avail - need;
@@ -330,7 +337,7 @@ __device__ __forceinline__ void rebuild_row(const Rows<Acc>& m, int q, int lane,
         Qr[r] = lwroom;
         const int32_t room = need > avail ? need - avail : 0;
         lroom += room;
-        lwroom += (Acc)rc.hR * (Acc)(T - t) * (Acc)room;
+        lwroom += xr_weight<Acc>(rc, T, t) * (Acc)room;
         ++r;
       }
       y = avail - xr;
@@ -520,12 +527,12 @@ __device__ bool team_begin(Team<Acc>& t, unsigned char* smem, CtlShared* sh,
       stage_row_warp(p.ip.D + id.cell_off + (int64_t)k * T,
                      p.ip.R + id.cell_off + (int64_t)k * T, T, t.wlane,
                      (int2*)(smem + Lay.tab) + (int64_t)q * (T + 1), p.ip.hM[ro],
-                     p.ip.hR[ro], &m.C0[q]);
+                     p.ip.hR[ro], p.ip.pM ? p.ip.pM[ro] : 0, &m.C0[q]);
     } else if (t.wlane == 0) {
       m.C0[q] = p.ip.gC0[ro];
     }
     if (t.wlane == 0) {
-      m.rc[q] = RowCosts{p.ip.kM[ro], p.ip.kR[ro], p.ip.hM[ro], p.ip.hR[ro]};
+      m.rc[q] = row_costs(p.ip, ro);
       m.bits[q] = rd.start_off >= 0 ? p.start_bits[rd.start_off + k] : all_open(T);
     }
   }

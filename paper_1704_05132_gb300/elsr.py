@@ -61,7 +61,14 @@ class Solver:
         arrs = [_i32(inst.D), _i32(inst.R), _i32(inst.kM), _i32(inst.kR),
                 _i32(inst.hM), _i32(inst.hR)]
         h = P()
-        check(lib.elsr_create(ctypes.byref(h), self.K, self.T, *[_p(a) for a in arrs]), None)
+        pm, pr = getattr(inst, "pM", None), getattr(inst, "pR", None)
+        if pm is None and pr is None:
+            check(lib.elsr_create(ctypes.byref(h), self.K, self.T, *[_p(a) for a in arrs]), None)
+        else:  # unit production costs (Algorithm 1's p_M, p_R)
+            arrs += [_i32(pm if pm is not None else np.zeros(self.K)),
+                     _i32(pr if pr is not None else np.zeros(self.K))]
+            check(lib.elsr_create_ex(ctypes.byref(h), self.K, self.T,
+                                     *[_p(a) for a in arrs]), None)
         self._h = h
         self._lib = lib
         self.set_stream(stream)
@@ -279,8 +286,17 @@ class Batch:
         arrs = [cat("D"), cat("R"), cat("kM"), cat("kR"), cat("hM"), cat("hR")]
         b = P()
         sh = _stream_handle(stream)
-        code = lib.elsr_batch_create_on(ctypes.byref(b), self.n, _p(self.Ks), _p(self.Ts),
-                                        *[_p(a) for a in arrs], P(sh) if sh else None)
+        if any(getattr(i, "pM", None) is not None or getattr(i, "pR", None) is not None
+               for i in insts):
+            pc = lambda f: _i32(np.concatenate([
+                np.ravel(getattr(i, f)) if getattr(i, f, None) is not None
+                else np.zeros(i.D.shape[0]) for i in insts]))
+            arrs += [pc("pM"), pc("pR")]
+            code = lib.elsr_batch_create_ex(ctypes.byref(b), self.n, _p(self.Ks), _p(self.Ts),
+                                            *[_p(a) for a in arrs], P(sh) if sh else None)
+        else:
+            code = lib.elsr_batch_create_on(ctypes.byref(b), self.n, _p(self.Ks), _p(self.Ts),
+                                            *[_p(a) for a in arrs], P(sh) if sh else None)
         check(code, None, batch=True)
         self._b = b
         if lanes or threads:

@@ -28,8 +28,9 @@ int64_t move_costs(int T, const int32_t* D, const int32_t* R,
   }
   tab[T].x = cd;
   tab[T].y = cr;
-  const RowCosts rc{costs[0], costs[1], costs[2], costs[3]};
-  const int64_t C0 = (int64_t)costs[3] * wr - (int64_t)costs[2] * wd;
+  // costs: kM, kR, hM, hR, pM, pR
+  const RowCosts rc{costs[0], costs[1], costs[2], costs[3], costs[5] - costs[4]};
+  const int64_t C0 = (int64_t)costs[3] * wr - (int64_t)costs[2] * wd + (int64_t)costs[4] * cd;
   RowState<Acc> st;
   st.b = RowBits{0, 0, 0, 0};
   for (int t = 0; t < T; ++t) {

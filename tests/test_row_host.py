@@ -72,7 +72,7 @@ def test_delta_decode_matches_oracle(hc, T, acc64, nw):
     if T % 3 == 0:
         g.D[0, : T // 3] = 0          # leading zero demand
     inst = oracle.Instance.from_arrays(g)
-    costs = np.array([inst.kM[0], inst.kR[0], inst.hM[0], inst.hR[0]], np.int32)
+    costs = np.array([inst.kM[0], inst.kR[0], inst.hM[0], inst.hR[0], 0, 0], np.int32)
     D, R = inst.D[0].copy(), inst.R[0].copy()
     for gm, gr in _random_states(rng, T, 40):
         for j in (1, 2, 3):
@@ -129,7 +129,7 @@ def test_deficits_fixed_through_the_stock_difference(hc, T):
     rng = np.random.default_rng(1000 + T)
     g = gen.make_instance(900 + T, 2, K=1, T=T)
     inst = oracle.Instance.from_arrays(g)
-    costs = np.array([inst.kM[0], inst.kR[0], inst.hM[0], inst.hR[0]], np.int32)
+    costs = np.array([inst.kM[0], inst.kR[0], inst.hM[0], inst.hR[0], 0, 0], np.int32)
     D, R = inst.D[0].copy(), inst.R[0].copy()
     fixed_late = 0
     for trial in range(30):
@@ -183,3 +183,32 @@ def test_non_null_swaps_by_rank(hc, T):
                 cur = oracle.decode_row(inst, 0, gm, gr)[0]
                 null = sorted(set(range(oracle.row_moves(T, 3))) - set(ref))
                 assert all(costs[l] == cur for l in null)
+
+
+@pytest.mark.parametrize("T", [3, 12, 52, 65, 104])
+@pytest.mark.parametrize("acc64,nw", [(0, 1), (1, 2), (0, 2)])
+def test_delta_decode_with_production_costs(hc, T, acc64, nw):
+    """Unit production costs pM, pR (Algorithm 1's p_M, p_R): the delta
+    re-decode against the oracle's per-period decode, with pR - pM of both
+    signs and large enough to outweigh the holding saving hR*(T-t)."""
+    if nw == 1 and T > 64:
+        pytest.skip("one 64-bit word holds at most 64 periods")
+    rng = np.random.default_rng(T * 11 + acc64 + 3 * nw)
+    g = gen.make_instance(70 + T, 2, K=1, T=T)
+    for pm, pr in [(10, 3), (3, 10), (0, 400), (500, 0), (37, 37)]:
+        inst = oracle.Instance(g.D, g.R, g.kM, g.kR, g.hM, g.hR,
+                               np.array([pm], np.int32), np.array([pr], np.int32))
+        costs = np.array([inst.kM[0], inst.kR[0], inst.hM[0], inst.hR[0], pm, pr], np.int32)
+        D, R = inst.D[0].copy(), inst.R[0].copy()
+        for gm, gr in _random_states(rng, T, 12):
+            for j in (1, 2, 3):
+                M = oracle.row_moves(T, j)
+                if M <= 0:
+                    continue
+                out = np.zeros(M, np.int64)
+                segs = np.zeros(M, np.int32)
+                cur = hc.hc_move_costs(acc64, nw, T, _p(D), _p(R), _p(costs), _p(gm), _p(gr),
+                                       j, _p(out), _p(segs))
+                assert cur == oracle.decode_row(inst, 0, gm, gr)[0]
+                np.testing.assert_array_equal(out, oracle.move_costs(inst, gm[None, :],
+                                                                     gr[None, :], j))
