@@ -137,6 +137,41 @@ def cpu_baseline(iters: int):
                       f"({r.counters['moves_evaluated']} moves, {dt:.2f} s)"}
 
 
+def _oracle_job(job):
+    """One oracle GVNS run (in a spawned worker): job = (kind, ident, seed, iters)."""
+    import oracle
+    from paper_1704_05132_gb300 import gen
+    kind, ident, seed, iters = job
+    if kind == "batch":
+        g = gen.make_instance(0, ident, K_range=(5, 100), T_range=(12, 52))
+    elif kind == "multistart":
+        g = gen.multistart_large()
+    else:
+        g = gen.serving_request(ident)
+    t0 = time.perf_counter()
+    r = oracle.vns(oracle.Instance.from_arrays(g), seed, iters, 3, 0)
+    return r.counters["moves_evaluated"], time.perf_counter() - t0
+
+
+def cpu_baseline_pool(jobs, sample: str):
+    """The oracle as it stands on every host core: one independent run per
+    worker process (spawned, so no CUDA state is inherited), on a bounded
+    sample of a batched workload."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    n = os.cpu_count() or 1
+    with mp.get_context("spawn").Pool(n) as pool:
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_job, jobs, chunksize=1)
+        wall = time.perf_counter() - t0
+    moves = sum(m for m, _ in res)
+    per_run = sorted(dt for _, dt in res)
+    return {"value": moves / wall, "unit": UNIT, "cores": n, "kind": "oracle",
+            "instances_per_s": len(jobs) / wall, "p50_run_s": per_run[len(per_run) // 2],
+            "sample": sample + f" ({len(jobs)} runs, {moves} moves, {wall:.1f} s wall)"}
+
+
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
@@ -399,6 +434,17 @@ def run_batched(args):
     line["segments_per_step"] = segs_step
     if args.workload == "multistart":
         line["best_of"] = box["best"][:2]
+    if not args.no_cpu_baseline:
+        if args.workload == "batch":
+            m = min(n, 64)
+            line["cpu_baseline"] = cpu_baseline_pool(
+                [("batch", i, i, iters) for i in range(m)],
+                f"the first {m} of the {n} instances, {iters} iterations each")
+        else:
+            m, it_s = min(n, 16), min(iters, 200)
+            line["cpu_baseline"] = cpu_baseline_pool(
+                [("multistart", 0, s, it_s) for s in range(m)],
+                f"starts 0..{m - 1}, {it_s} of the {iters} iterations each")
     print(json.dumps(line), flush=True)
 
 
@@ -430,6 +476,12 @@ def run_serve(args):
             "instances_per_s": s["instances_per_s"], "p50_ms": s["p50_ms"],
             "p99_ms": s["p99_ms"], "mean_ms": s["mean_ms"], "batches": s["batches"],
             "span_s": s["span_s"], "clocks": clk.summary()}
+    if not args.no_cpu_baseline:
+        m = min(n, 16)
+        line["cpu_baseline"] = cpu_baseline_pool(
+            [("serve", r, r, iters) for r in range(m)],
+            f"requests 0..{m - 1} solved one per core, {iters} iterations each "
+            "(p50_run_s is the oracle's per-request solve time)")
     print(json.dumps(line), flush=True)
 
 
