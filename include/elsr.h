@@ -179,7 +179,7 @@ int elsr_set_launch(elsr_t *h, int32_t lanes_per_row, int32_t threads);
  * Results do not depend on it. */
 int elsr_set_cluster(elsr_t *h, int32_t cluster);
 
-/* Speculative execution of one mode-P GVNS run: up to `teams` clusters run
+/* Speculative execution of one GVNS run (mode P or G): up to `teams` clusters run
  * consecutive iterations from the same incumbent and commit them in order up
  * to the first acceptance, so trajectory, solution and counters equal the
  * sequential run's.  0 = automatic (up to 16 teams), 1 = off. */

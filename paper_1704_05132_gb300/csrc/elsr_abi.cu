@@ -483,11 +483,11 @@ int launch_runs(elsr_batch* b, const RowBits* start_bits, bool with_traj,
     b->have_result = true;
     return ELSR_OK;
   }
-  // A single mode-P run may be spread over several teams that speculate on
+  // A single run may be spread over several teams that speculate on
   // consecutive iterations (exact: the committed trajectory is the
   // sequential one).
   int teams = 1;
-  if (allow_spec && nr == 1 && b->h_runs[0].mode == ELSR_MODE_P && b->h_runs[0].iters > 1 &&
+  if (allow_spec && nr == 1 && b->h_runs[0].iters > 1 &&
       b->spec != 1) {
     const int resident = ls.cluster == 1 ? ls.active * b->sms : ls.active;
     const int want = b->spec > 1 ? b->spec : 16;

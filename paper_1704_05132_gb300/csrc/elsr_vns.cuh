@@ -409,6 +409,7 @@ struct CtlShared {
   unsigned long long applied, steps;
   unsigned long long gmin[64];  // per row group and warp: partial minima (groups > 32 lanes)
   int stopw[2];                 // wall-clock budget spent (CTA 0's word counts)
+  int gstop[2];                 // mode-G speculative teams: CTA 0's verdict on the decision word
 };
 // kSmemLimit leaves 1 KB of the CTA's shared memory to static words.
 static_assert(sizeof(CtlShared) <= 768, "static control words outgrow their reserve");
@@ -699,8 +700,11 @@ __device__ int vnd_p(Team<Acc>& t, const int* stop = nullptr, int my_index = 0) 
 // shared memory, so all CTAs hold the same winning key.  A winning key's cost
 // is the new objective itself (the other rows plus the moved row), which
 // every CTA adopts without a further exchange.
+// `stop` (speculative teams), as in vnd_p: thread 0 of CTA 0 reads the
+// decision word during N3 and passes its verdict with the next sweep's N1
+// exchange, after which the whole team gives up (returns -2) at once.
 template <typename Acc, int NW>
-__device__ int vnd_g(Team<Acc>& t) {
+__device__ int vnd_g(Team<Acc>& t, const int* stop = nullptr, int my_index = 0) {
   CtlShared* sh = t.sh;
   const int T = t.T, C = t.C;
   int64_t F;    // sum of the feasible rows' costs (team-wide)
@@ -710,11 +714,16 @@ __device__ int vnd_g(Team<Acc>& t) {
   team_sync(C);
   const int GW = t.G < 32 ? t.G : 32;  // lanes of the group inside one warp
   int cycles = 0, e = 0;
+  int seen = 0x7fffffff;  // thread 0 of CTA 0: the decision word as read during N3
   for (;;) {
     bool improved = false;
+    int quit = 0;
     for (int j = 1; j <= 3; ++j) {
       const int M = row_moves(T, j);
       if (M <= 0) continue;
+      const bool lead = stop && t.crank == 0 && t.tid == 0;
+      if (lead && j == 3) seen = *(volatile const int*)stop;
+      if (lead && j == 1) sh->gstop[e] = seen < my_index;
       const int64_t total = Finf ? INT64_MAX : F;
       // every warp runs the same number of row iterations (the sub-warp
       // minimum below is a full-warp shuffle)
@@ -752,11 +761,13 @@ __device__ int vnd_g(Team<Acc>& t) {
       if (C == 1) {
         __syncthreads();
         gk = sh->gkey[e];
+        if (stop && j == 1) quit = sh->gstop[e];
       } else {
         cg::cluster_group cl = cg::this_cluster();
         cl.sync();
         uint64_t v = t.wlane < C ? *cl.map_shared_rank(&sh->gkey[e], t.wlane) : ~0ull;
         gk = subwarp_min(v, 32);
+        if (stop && j == 1) quit = *cl.map_shared_rank(&sh->gstop[e], 0);
       }
       if (t.tid == 0) sh->gkey[e ^ 1] = ~0ull;
       if (gk != ~0ull && key_cost(gk) < total) {
@@ -780,6 +791,7 @@ __device__ int vnd_g(Team<Acc>& t) {
       }
       __syncthreads();
       e ^= 1;
+      if (quit) return -2;  // uniform: every thread read CTA 0's verdict
     }
     ++cycles;
     if (!improved) break;
@@ -789,8 +801,9 @@ __device__ int vnd_g(Team<Acc>& t) {
 }
 
 template <typename Acc, int NW>
-__device__ __forceinline__ int vnd(Team<Acc>& t, int mode) {
-  return mode == 0 ? vnd_p<Acc, NW>(t) : vnd_g<Acc, NW>(t);
+__device__ __forceinline__ int vnd(Team<Acc>& t, int mode, const int* stop = nullptr,
+                                   int my_index = 0) {
+  return mode == 0 ? vnd_p<Acc, NW>(t, stop, my_index) : vnd_g<Acc, NW>(t, stop, my_index);
 }
 
 // Shake(x, k) of Algorithm 2: k moves of N_k from splitmix64 draws keyed by
@@ -1006,7 +1019,7 @@ __global__ void __launch_bounds__(MAXT, 1) vns_kernel(const VnsParams p) {
 }
 
 // ---------------------------------------------------------------------------
-// spec_kernel: one GVNS run (mode P) executed by W teams that speculate on
+// spec_kernel: one GVNS run (mode P or G) executed by W teams that speculate on
 // consecutive iterations.  In a round every team starts from the same
 // incumbent x; team i runs iteration it0 + i (its k assumes iterations it0 ..
 // it0 + i - 1 were rejected), publishes f(x'') and its changed rows, and
@@ -1080,7 +1093,7 @@ __global__ void __launch_bounds__(MAXT, 1) spec_kernel(const VnsParams p) {
   int64_t cycles_total = 0;
   int cyc = 0;
   if (!rd.resume) {  // a resumed run starts from VND's output
-    cyc = vnd_p<Acc, NW>(t);
+    cyc = vnd<Acc, NW>(t, rd.mode);
     if (cyc < 0) status = kStatusCap; else cycles_total += cyc;
   }
   int64_t fx = team_total(t);
@@ -1111,7 +1124,7 @@ __global__ void __launch_bounds__(MAXT, 1) spec_kernel(const VnsParams p) {
       }
       pl = plan_shake(rd.seed, it0 + team, ks, K, T);
       apply_shake<Acc, NW>(t, pl, ks, par);
-      cyc = vnd_p<Acc, NW>(t, dec, team);
+      cyc = vnd<Acc, NW>(t, rd.mode, dec, team);
       if (cyc != -2) {  // -2: an earlier team's iteration was accepted
         const int64_t f2 = team_total(t);
         flush_counters(t, &slot->steps, &slot->applied);

@@ -117,3 +117,30 @@ def test_mode_p_paper_scale_vnd(E, paper_scale):
         r = s.vns(seed=0, iters=0, kmax=3, mode=0)
     np.testing.assert_array_equal(r["gM"], sm)
     np.testing.assert_array_equal(r["gR"], sr)
+
+
+@pytest.mark.parametrize("teams,cluster", [(2, 1), (5, 2), (16, 4), (0, 0), (31, 1)])
+def test_mode_g_speculative_run_matches_oracle(E, teams, cluster):
+    """Mode-G runs speculate like mode-P ones: teams run consecutive
+    iterations and commit them in order up to the first acceptance, so the
+    trajectory, solution and counters equal the sequential run's."""
+    g = gen.make_instance(6, 1, K=20, T=30)
+    o = oracle.vns(oracle.Instance.from_arrays(g), seed=9, iters=150, kmax=3, mode=1)
+    with E.Solver(g, cluster=cluster, speculation=teams) as s:
+        r = s.vns(seed=9, iters=150, kmax=3, mode=1)
+        shape = s.launch_shape()
+    if teams != 1:
+        assert shape["teams"] > 1
+    _check(r, o)
+    assert r["segments"] > 0
+
+
+def test_mode_g_speculation_counts_committed_work_only(E):
+    g = gen.make_instance(6, 2, K=24, T=40)
+    res = []
+    for teams in (1, 12):
+        with E.Solver(g, speculation=teams) as s:
+            r = s.vns(seed=2, iters=120, kmax=3, mode=1)
+        res.append((r["best_cost"], r["traj_hash"], r["moves_evaluated"], r["segments"],
+                    r["applied"], r["vnd_cycles"], r["iterations"], r["accepted"]))
+    assert res[0] == res[1]
