@@ -452,7 +452,8 @@ int launch_runs(elsr_batch* b, const RowBits* start_bits, bool with_traj,
   p.spec_bar = nullptr;
   p.spec_dec = nullptr;
   p.fj_workers = 0;
-  p.pad2 = 0;
+  // several runs with automatic lanes: each run picks its own row groups
+  p.adaptive_G = (nr > 1 && b->lanes == 0) ? 1 : 0;
   if (fj_workers > 0) {
     const int resident = ls.cluster == 1 ? ls.active * b->sms : ls.active;
     if (nr != 1 || fj_workers > resident) {

@@ -118,7 +118,9 @@ struct VnsParams {
   // fork-join launches (Algorithm 2 with one shake + VND per worker): the
   // fj_workers teams share spec_slots, spec_rows and spec_bar (0: off)
   int32_t fj_workers;
-  int32_t pad2;
+  // batched launches: choose each run's lanes per row from its row count
+  // (wider groups for small instances); 0 = every run uses G
+  int32_t adaptive_G;
 };
 
 struct StageParams {

@@ -912,6 +912,22 @@ __device__ __forceinline__ void team_init(Team<Acc>& t, int G) {
   t.smask = G >= 32 ? kFull : (((1u << G) - 1u) << (t.wlane & ~(G - 1)));
 }
 
+// Lanes per row for a run of K products on teams of C CTAs of `threads`
+// threads: the widest group (G0 .. 128 lanes) that still leaves a group per
+// row, so a small instance spreads each row over more lanes instead of
+// leaving groups idle.  Groups wider than a warp must tile the block and use
+// at most the 15 named barriers.
+__device__ __forceinline__ int run_lanes(int G0, int K, int C, int threads) {
+  const int Kc = (K + C - 1) / C;
+  int G = G0;
+  for (int g = G0 * 2; g <= 128; g *= 2) {
+    if (threads / g < Kc) break;
+    if (g > 32 && (threads % g != 0 || threads / g > 15)) continue;
+    G = g;
+  }
+  return G;
+}
+
 // ---------------------------------------------------------------------------
 // vns_kernel: persistent batched GVNS, one team (cluster) per run, runs taken
 // from a device work queue.
@@ -930,6 +946,7 @@ __global__ void __launch_bounds__(MAXT, 1) vns_kernel(const VnsParams p) {
     team_sync(t.C);
     if (r >= p.nruns) return;
     const RunDesc rd = p.runs[r];
+    if (p.adaptive_G) team_init(t, run_lanes(p.G, p.ip.insts[rd.inst].K, t.C, t.nthr));
     if (!team_begin<Acc, NW, TS>(t, smem, &sh, p, rd)) {
       if (t.crank == 0 && t.tid == 0) write_failed_run(p, rd, kStatusLaunch);
       team_sync(t.C);

@@ -364,3 +364,25 @@ def test_invalid_state_rejected(E):
             s.set_state(bad, bad)
         with pytest.raises(Exception):
             s.vns_run(0, 10, kmax=4)
+
+
+def test_batch_small_instances_use_wide_row_groups(E):
+    """A batch with automatic lanes gives each run its own row-group width
+    (wider for instances with few products); every run still equals the
+    oracle's.  Sizes from 2 to 40 products cover 16-, 32- and 128-lane
+    groups in 1024-thread blocks."""
+    insts = [gen.make_instance(13, i, K=k, T=t)
+             for i, (k, t) in enumerate([(2, 12), (5, 40), (8, 52), (9, 20), (16, 33),
+                                         (31, 52), (33, 12), (40, 52), (3, 64), (7, 65)])]
+    b = E.Batch(insts, threads=1024)
+    seeds = np.arange(len(insts), dtype=np.uint64) + 100
+    b.run(seeds, iters=60, kmax=3, mode=0)
+    res = b.results()
+    for i, g in enumerate(insts):
+        o = oracle.vns(_inst(g), seed=100 + i, iters=60, kmax=3, mode=0)
+        assert res[i]["best_cost"] == o.best_cost, i
+        assert res[i]["traj_hash"] == o.traj_hash, i
+        assert res[i]["moves_evaluated"] == o.counters["moves_evaluated"], i
+        gm, gr = b.solution(i)
+        np.testing.assert_array_equal(gm, o.gM)
+    b.close()
