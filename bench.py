@@ -208,10 +208,10 @@ def run_gpu(args):
     import torch.distributed as dist
 
     world, rank, local = _dist()
-    if world > 1:
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
+    torch.cuda.set_device(local)  # before the process group: its barriers use this device
     dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
 
     from paper_1704_05132_gb300 import build, elsr, gen
     if rank == 0 or world == 1:
