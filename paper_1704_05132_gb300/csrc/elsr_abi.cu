@@ -581,8 +581,13 @@ struct elsr_ctx {
   int32_t K = 0, T = 0;
   RowBits* d_state = nullptr;
   int64_t* d_rowcost = nullptr;
-  uint64_t* d_ppkey = nullptr;
-  uint64_t* d_scratch = nullptr;
+  // one device buffer for the evaluation's reduction words [4] and
+  // per-product keys [K], mirrored by a pinned host buffer, so that an
+  // evaluation needs one asynchronous copy each way
+  uint64_t* d_evalbuf = nullptr;
+  uint64_t* h_evalbuf = nullptr;  // pinned, [4 + K]
+  uint64_t* d_ppkey = nullptr;    // d_evalbuf + 4
+  uint64_t* d_scratch = nullptr;  // d_evalbuf
   int64_t* d_movecost = nullptr;
   int32_t* d_movewin = nullptr;
   int32_t* d_plan = nullptr;
@@ -603,8 +608,8 @@ struct elsr_ctx {
     const cudaStream_t stream = b.stream;
     dev_free(d_state, stream);
     dev_free(d_rowcost, stream);
-    dev_free(d_ppkey, stream);
-    dev_free(d_scratch, stream);
+    dev_free(d_evalbuf, stream);
+    if (h_evalbuf) cudaFreeHost(h_evalbuf);
     dev_free(d_movecost, stream);
     dev_free(d_movewin, stream);
     dev_free(d_plan, stream);
@@ -637,8 +642,20 @@ int eval_launch(elsr_ctx* h, uint32_t mask, int32_t mode, int single_j,
   p.move_cost = single_j ? h->d_movecost : nullptr;
   p.move_win = single_j ? h->d_movewin : nullptr;
   p.scratch = h->d_scratch;
-  const uint64_t init[4] = {~0ull, 0ull, 0ull, 0ull};
-  ELSR_TRY_CUDA(b, cudaMemcpyAsync(h->d_scratch, init, sizeof(init), cudaMemcpyHostToDevice, b->stream));
+  // reduction words {gkey, sum after, infeasible after, improving}: staged
+  // in the pinned buffer (the previous evaluation's results were consumed
+  // before it returned)
+  h->h_evalbuf[0] = ~0ull;
+  h->h_evalbuf[1] = h->h_evalbuf[2] = h->h_evalbuf[3] = 0ull;
+  ELSR_TRY_CUDA(b, cudaMemcpyAsync(h->d_scratch, h->h_evalbuf, 4 * sizeof(uint64_t),
+                                   cudaMemcpyHostToDevice, b->stream));
+  // Few rows: one row per CTA with 128 threads on its moves (the default
+  // for a single run spreads a row over more than a warp); many rows: rows
+  // of G lanes packed four to a CTA.
+  if (G >= 32 && !b->lanes && (int64_t)h->K <= 2 * (int64_t)b->sms) {
+    ELSR_TRY_CUDA(b, launch_eval_wide(p, b->acc64, 128, b->stream));
+    return ELSR_OK;
+  }
   const int blocks = (h->K + nsub - 1) / nsub;
   ELSR_TRY_CUDA(b, launch_eval(p, b->acc64, blocks, threads, smem, b->stream));
   return ELSR_OK;
@@ -714,8 +731,12 @@ int elsr_create_ex(elsr_t** out, int32_t K, int32_t T, const int32_t* D,
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = dev_alloc(&h->d_state, K, b->stream);
     if (e == cudaSuccess) e = dev_alloc(&h->d_rowcost, K, b->stream);
-    if (e == cudaSuccess) e = dev_alloc(&h->d_ppkey, K, b->stream);
-    if (e == cudaSuccess) e = dev_alloc(&h->d_scratch, 4, b->stream);
+    if (e == cudaSuccess) e = dev_alloc(&h->d_evalbuf, (size_t)K + 4, b->stream);
+    if (e == cudaSuccess) e = cudaMallocHost(&h->h_evalbuf, ((size_t)K + 4) * sizeof(uint64_t));
+    if (e == cudaSuccess) {
+      h->d_scratch = h->d_evalbuf;
+      h->d_ppkey = h->d_evalbuf + 4;
+    }
     if (e == cudaSuccess) e = dev_alloc(&h->d_plan, (size_t)4 * K * T, b->stream);
     if (e != cudaSuccess) {
       b->err = std::string("device allocation: ") + cudaGetErrorString(e);
@@ -823,12 +844,11 @@ int elsr_eval_neighbourhood(elsr_t* h, uint32_t nb_mask, int32_t mode,
   }
   int rc = eval_launch(h, nb_mask, mode, 0, false);
   if (rc != ELSR_OK) return rc;
-  std::vector<uint64_t> keys(h->K);
-  uint64_t sc[4];
-  ELSR_TRY_CUDA(&h->b, cudaMemcpyAsync(keys.data(), h->d_ppkey, h->K * sizeof(uint64_t),
+  ELSR_TRY_CUDA(&h->b, cudaMemcpyAsync(h->h_evalbuf, h->d_evalbuf, (h->K + 4) * sizeof(uint64_t),
                                        cudaMemcpyDeviceToHost, h->b.stream));
-  ELSR_TRY_CUDA(&h->b, cudaMemcpyAsync(sc, h->d_scratch, sizeof(sc), cudaMemcpyDeviceToHost, h->b.stream));
   ELSR_TRY_CUDA(&h->b, cudaStreamSynchronize(h->b.stream));
+  const uint64_t* sc = h->h_evalbuf;
+  const uint64_t* keys = h->h_evalbuf + 4;
   for (int k = 0; k < h->K; ++k) {
     if (pp_cost) pp_cost[k] = keys[k] == ~0ull ? INT64_MAX : key_cost(keys[k]);
     if (pp_move) pp_move[k] = keys[k] == ~0ull ? -1 : key_index(keys[k]);

@@ -210,6 +210,9 @@ cudaError_t launch_stage(const StageParams& p, int total_rows, cudaStream_t s);
 cudaError_t launch_eval(const EvalParams& p, bool acc64, int blocks,
                         int threads, size_t smem, cudaStream_t s);
 cudaError_t eval_prepare(bool acc64, int T, size_t smem);
+// One row of instance 0 per CTA, `threads` (a multiple of 32, <= 128) on its
+// moves; grid = p.K.  Shared memory fits the default limit (T <= 128).
+cudaError_t launch_eval_wide(const EvalParams& p, bool acc64, int threads, cudaStream_t s);
 size_t eval_smem_bytes(int rows, int T, bool acc64);
 cudaError_t launch_bestof(const BestofParams& p, cudaStream_t s);
 cudaError_t launch_plan(const PlanParams& p, int K, cudaStream_t s);

@@ -209,6 +209,130 @@ __global__ void __launch_bounds__(1024) eval_kernel(const EvalParams p) {
 }
 
 // ---------------------------------------------------------------------------
+// eval_wide_kernel: one row of instance 0 per CTA, every thread of the block
+// on its moves (a neighbourhood of one row is 2T or 2(T-1) moves, so about
+// one or two per thread).  Warp 0 stages the row and builds its cache with
+// the lane-parallel rebuild; the block's minimum goes through shared memory.
+// Same outputs as eval_kernel.  Shared memory: the single-row layout of the
+// GVNS kernels without their save slots.
+// ---------------------------------------------------------------------------
+template <typename Acc, int NW>
+__global__ void __launch_bounds__(128, 1) eval_wide_kernel(const EvalParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ long long sh_F;
+  __shared__ int sh_Finf;
+  __shared__ unsigned long long sh_key[2][4];
+  const int tid = threadIdx.x, nthr = blockDim.x, wlane = tid & 31, warp = tid >> 5;
+  const int nwarps = nthr >> 5;
+  const int K = p.K, T = p.T, k = blockIdx.x;
+  const InstDesc id = p.ip.insts[0];
+  const VnsLayout lay = vns_layout(1, T, (int)sizeof(Acc), true);
+  vns::Rows<Acc> m;
+  m.tab = (const int2*)(smem + lay.tab);
+  m.rc = (RowCosts*)(smem + lay.rc);
+  m.C0 = (int64_t*)(smem + lay.C0);
+  m.bits = (RowBits*)(smem + lay.bits);
+  m.S = (Acc*)(smem + lay.S);
+  m.mark = (RowMark*)(smem + lay.mark);
+  m.nR = (int32_t*)(smem + lay.nR);
+  m.A = (int32_t*)(smem + lay.A);
+  m.C = (Acc*)(smem + lay.C);
+  m.L = (int2*)(smem + lay.L);
+  m.P = (int32_t*)(smem + lay.P);
+  m.Q = (Acc*)(smem + lay.Q);
+  m.save = nullptr;
+  m.slot = 0;
+  m.T = T;
+  m.C_ = 1;
+  m.crank = 0;
+  m.ts = true;
+  const int64_t ro = id.row_off + k;
+  if (warp == 0) {
+    stage_row_warp(p.ip.D + id.cell_off + (int64_t)k * T, p.ip.R + id.cell_off + (int64_t)k * T,
+                   T, wlane, (int2*)(smem + lay.tab), p.ip.hM[ro], p.ip.hR[ro],
+                   p.ip.pM ? p.ip.pM[ro] : 0, &m.C0[0]);
+    if (wlane == 0) {
+      m.rc[0] = vns::row_costs(p.ip, ro);
+      m.bits[0] = p.bits[k];
+    }
+  }
+  if (tid == 0) {
+    sh_F = 0;
+    sh_Finf = 0;
+  }
+  __syncthreads();
+  if (p.mode == 1 && p.rowcost_in) {
+    long long sf = 0;
+    int ni = 0;
+    for (int r = tid; r < K; r += nthr) {
+      const int64_t c = p.rowcost_in[r];
+      if (c == INT64_MAX) ++ni; else sf += c;
+    }
+    if (sf) atomicAdd((unsigned long long*)&sh_F, (unsigned long long)sf);
+    if (ni) atomicAdd(&sh_Finf, ni);
+  }
+  if (warp == 0) vns::rebuild_row<Acc, NW>(m, 0, wlane, 32, kFull);
+  __syncthreads();
+  const int64_t F = sh_F;
+  const int Finf = sh_Finf;
+  const RowState<Acc> cur = m.state(0);
+  const RowCosts rc = m.rc[0];
+  const int64_t c0 = m.C0[0];
+  const int64_t rck = m.cost(0);
+  if (tid == 0 && p.rowcost_out) p.rowcost_out[k] = rck;
+  const int infk = rck == INT64_MAX;
+  const int64_t others = (Finf - infk > 0) ? INT64_MAX : F - (infk ? 0 : rck);
+  uint64_t bestP = ~0ull, bestG = ~0ull;
+  for (int j = 1; j <= 3; ++j) {
+    if (!(p.mask & (1u << (j - 1)))) continue;
+    const int M = row_moves(T, j);
+    if (M <= 0) continue;
+    const uint32_t loff = j == 1 ? 0u : (j == 2 ? (uint32_t)T : 2u * T);
+    const uint32_t goff = j == 1 ? 0u : (j == 2 ? (uint32_t)(K * T) : 2u * K * T);
+    for (int l = tid; l < M; l += nthr) {
+      int st = 0;
+      const Acc S = eval_move<Acc, NW>(m.tab, T, rc, cur, m.A, m.C, m.L, m.P, m.Q, j, l, st);
+      const int64_t nc = row_cost<Acc>(S, c0);
+      bestP = umin64(bestP, pack_key(nc, loff + (uint32_t)l));
+      if (p.mode == 1) {
+        const int64_t nt = (others == INT64_MAX || nc == INT64_MAX) ? INT64_MAX : others + nc;
+        bestG = umin64(bestG, pack_key(nt, goff + (uint32_t)(k * M + l)));
+      }
+      if (j == p.single_j) {
+        if (p.move_cost) p.move_cost[(int64_t)k * M + l] = nc;
+        if (p.move_win) p.move_win[(int64_t)k * M + l] = st;
+      }
+    }
+  }
+  bestP = subwarp_min(bestP, 32);
+  bestG = subwarp_min(bestG, 32);
+  if (wlane == 0) {
+    sh_key[0][warp] = bestP;
+    sh_key[1][warp] = bestG;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int w = 1; w < nwarps; ++w) {
+      bestP = umin64(bestP, sh_key[0][w]);
+      bestG = umin64(bestG, sh_key[1][w]);
+    }
+    if (p.pp_key) p.pp_key[k] = bestP;
+    if (p.scratch) {
+      if (p.mode == 1 && bestG != ~0ull)
+        atomicMin((unsigned long long*)&p.scratch[0], (unsigned long long)bestG);
+      const bool imp = bestP != ~0ull && key_cost(bestP) < rck;
+      const int64_t after = imp ? key_cost(bestP) : rck;
+      if (after == INT64_MAX) {
+        atomicAdd((unsigned long long*)&p.scratch[2], 1ull);
+      } else {
+        atomicAdd((unsigned long long*)&p.scratch[1], (unsigned long long)after);
+      }
+      if (imp) atomicAdd((unsigned long long*)&p.scratch[3], 1ull);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // bestof_kernel: one block, lexicographic (cost, run) minimum.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024) bestof_kernel(const BestofParams p) {
@@ -267,13 +391,24 @@ __global__ void plan_kernel(const PlanParams p) {
   }
 }
 
+// Raise a kernel's dynamic shared-memory limit only when a launch needs more
+// than it was last given on this device (the attribute call is not free).
 template <typename Acc>
 cudaError_t eval_prepare_t(int T, size_t smem) {
-  if (T <= 64)
-    return cudaFuncSetAttribute(eval_kernel<Acc, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem);
-  return cudaFuncSetAttribute(eval_kernel<Acc, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)smem);
+  constexpr int kDevices = 64;
+  static int granted[2][kDevices];  // per word count and device; 0 = not yet set
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const int w = T <= 64 ? 0 : 1;
+  if (dev >= 0 && dev < kDevices && granted[w][dev] >= (int)smem) return cudaSuccess;
+  e = w == 0 ? cudaFuncSetAttribute(eval_kernel<Acc, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem)
+             : cudaFuncSetAttribute(eval_kernel<Acc, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem);
+  if (e == cudaSuccess && dev >= 0 && dev < kDevices && granted[w][dev] < (int)smem)
+    granted[w][dev] = (int)smem;
+  return e;
 }
 
 template <typename Acc>
@@ -284,7 +419,21 @@ void eval_launch_t(const EvalParams& p, int blocks, int threads, size_t smem, cu
     eval_kernel<Acc, 2><<<blocks, threads, smem, s>>>(p);
 }
 
+template <typename Acc>
+cudaError_t eval_wide_launch_t(const EvalParams& p, int threads, cudaStream_t s) {
+  const size_t smem = vns_layout(1, p.T, (int)sizeof(Acc), true).save;
+  if (p.T <= 64)
+    eval_wide_kernel<Acc, 1><<<p.K, threads, smem, s>>>(p);
+  else
+    eval_wide_kernel<Acc, 2><<<p.K, threads, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_eval_wide(const EvalParams& p, bool acc64, int threads, cudaStream_t s) {
+  return acc64 ? eval_wide_launch_t<int64_t>(p, threads, s) : eval_wide_launch_t<int32_t>(p, threads, s);
+}
 
 // ---------------------------------------------------------------------------
 // Launchers
