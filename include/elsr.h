@@ -232,7 +232,11 @@ int elsr_move_costs(elsr_t *h, int32_t nb, int64_t *costs, int32_t *window);
  * current solution, entirely on the device.  iters >= 0, 1 <= kmax <= 3,
  * mode ELSR_MODE_P or ELSR_MODE_G.  The current solution is not modified.
  * Asynchronous: the work is queued on the handle's stream; elsr_result()
- * waits for it.  iters = 0 runs VND alone.
+ * waits for it.  iters = 0 runs VND alone.  A run keeps its rows in the
+ * shared memory of one thread-block cluster of at most 16 CTAs (about 1,000
+ * products at T = 128, 2,500 at T = 52); a larger instance is refused with
+ * ELSR_E_RANGE before anything is launched.  The evaluation calls have no
+ * such limit.
  */
 int elsr_vns_run(elsr_t *h, uint64_t seed, int32_t iters, int32_t kmax,
                  int32_t mode);
