@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(128, 1) eval_wide_kernel(const EvalParams p) {
     if (sf) atomicAdd((unsigned long long*)&sh_F, (unsigned long long)sf);
     if (ni) atomicAdd(&sh_Finf, ni);
   }
-  if (warp == 0) vns::rebuild_row<Acc, NW>(m, 0, wlane, 32, kFull);
+  if (warp == 0) vns::rebuild_any<Acc, NW>(m, 0, wlane, 32, kFull);
   __syncthreads();
   const int64_t F = sh_F;
   const int Finf = sh_Finf;

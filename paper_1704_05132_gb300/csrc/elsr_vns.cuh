@@ -393,6 +393,186 @@ __device__ __forceinline__ void rebuild_row(const Rows<Acc>& m, int q, int lane,
   }
 }
 
+// Two-pass variant of rebuild_row for lanes holding at most PM periods: the
+// first pass keeps each period's returns, need and setup bits in registers,
+// so the second pass writes every cache entry once, with its offsets, and
+// reads no table entry again.  Same results as rebuild_row.
+template <typename Acc, int NW, int PM>
+__device__ __forceinline__ void rebuild_row_regs(const Rows<Acc>& m, int q, int lane, int G,
+                                                 unsigned smask) {
+  const int T = m.T;
+  const int2* tab = m.tab_row(q);
+  const RowBits b = m.bits[q];
+  const RowCosts rc = m.rc[q];
+  const uint64_t u0 = b.m0 | b.r0, u1 = b.m1 | b.r1;
+  int32_t* A = m.A + q * T;
+  Acc* C = m.C + q * T;
+  int2* L = m.L + q * T;
+  int32_t* Pr = m.P + q * (T + 1);
+  Acc* Qr = m.Q + q * (T + 1);
+  const int P = (T + G - 1) / G;
+  const int a = lane * P, e = a + P < T ? a + P : T;
+  // the first setup and the demand before it (lane 0 uses them last)
+  const int f = nxt<NW>(u0, u1, -1, T);
+  const int32_t dfirst = tab[f].x;
+  int32_t Rt[PM], need[PM];
+  int kind[PM];  // bit 0: setup, bit 1: gM, bit 2: gR
+  int64_t fp = 0, fq = kNegInf;
+#pragma unroll
+  for (int i = 0; i < PM; ++i) {
+    const int t = a + i;
+    Rt[i] = 0;
+    need[i] = 0;
+    kind[i] = 0;
+    if (t < e) {
+      const int2 tt = tab[t];
+      Rt[i] = tt.y - (t > 0 ? tab[t - 1].y : 0);
+      const int gm = bitat<NW>(b.m0, b.m1, t), gr = bitat<NW>(b.r0, b.r1, t);
+      kind[i] = (gm | gr) | (gm << 1) | (gr << 2);
+      if (gm | gr) need[i] = tab[nxt<NW>(u0, u1, t, T)].x - tt.x;
+      const int64_t pt = gr ? (int64_t)Rt[i] - (int64_t)need[i] : (int64_t)Rt[i];
+      const int64_t qt = gr ? 0 : kNegInf;
+      fq = (fq + pt > qt) ? fq + pt : qt;
+      fp += pt;
+    }
+  }
+  for (int o = 1; o < G; o <<= 1) {
+    const int64_t pp = __shfl_up_sync(smask, fp, o, G);
+    const int64_t qq = __shfl_up_sync(smask, fq, o, G);
+    if (lane >= o) {
+      const int64_t nq = qq + fp;
+      fq = nq > fq ? nq : fq;
+      fp += pp;
+    }
+  }
+  int64_t ep = __shfl_up_sync(smask, fp, 1, G);
+  int64_t eq = __shfl_up_sync(smask, fq, 1, G);
+  if (lane == 0) {
+    ep = 0;
+    eq = kNegInf;
+  }
+  const int32_t y0 = (int32_t)(ep > eq ? ep : eq);  // stock entering period a
+  // pass 1: this lane's totals
+  Acc lsum = 0, lwroom = 0;
+  int32_t lroom = 0;
+  int first_bad = T, last_def = -1, nr_lane = 0;
+  {
+    int32_t y = y0;
+#pragma unroll
+    for (int i = 0; i < PM; ++i) {
+      const int t = a + i;
+      const int32_t avail = y + Rt[i];
+      if (kind[i] & 1) {
+        const int gm = (kind[i] >> 1) & 1, gr = kind[i] >> 2;
+        const int32_t xr = gr ? (avail < need[i] ? avail : need[i]) : 0;
+        if (!gm && xr < need[i] && first_bad == T) first_bad = t;
+        lsum += (Acc)(gm ? rc.kM : 0) + (Acc)(gr ? rc.kR : 0) +
+                ((Acc)rc.hM * (Acc)need[i] - (Acc)rc.hR * (Acc)xr) * (Acc)(T - t) +
+                (Acc)rc.dP * (Acc)xr;
+        if (gr) {
+          const int32_t room = need[i] > avail ? need[i] - avail : 0;
+          lroom += room;
+          lwroom += xr_weight<Acc>(rc, T, t) * (Acc)room;
+          ++nr_lane;
+        }
+        y = avail - xr;
+      } else {
+        y = avail;
+      }
+    }
+  }
+  // exclusive offsets of C, P, Q over the lanes
+  Acc off = lsum, offQ = lwroom;
+  int32_t offP = lroom;
+  for (int o = 1; o < G; o <<= 1) {
+    const Acc v = __shfl_up_sync(smask, off, o, G);
+    const Acc vq = __shfl_up_sync(smask, offQ, o, G);
+    const int32_t vp = __shfl_up_sync(smask, offP, o, G);
+    if (lane >= o) {
+      off += v;
+      offQ += vq;
+      offP += vp;
+    }
+  }
+  const Acc total = __shfl_sync(smask, off, G - 1, G);
+  const Acc totQ = __shfl_sync(smask, offQ, G - 1, G);
+  const int32_t totP = __shfl_sync(smask, offP, G - 1, G);
+  off -= lsum;
+  offQ -= lwroom;
+  offP -= lroom;
+  // pass 2: the entries, written once
+  {
+    int32_t y = y0;
+    int r = rank_below<NW>(b.r0, b.r1, a);
+#pragma unroll
+    for (int i = 0; i < PM; ++i) {
+      const int t = a + i;
+      const int32_t avail = y + Rt[i];
+      if (kind[i] & 1) {
+        const int gm = (kind[i] >> 1) & 1, gr = kind[i] >> 2;
+        const int32_t xr = gr ? (avail < need[i] ? avail : need[i]) : 0;
+        A[t] = avail;
+        C[t] = off;
+        off += (Acc)(gm ? rc.kM : 0) + (Acc)(gr ? rc.kR : 0) +
+               ((Acc)rc.hM * (Acc)need[i] - (Acc)rc.hR * (Acc)xr) * (Acc)(T - t) +
+               (Acc)rc.dP * (Acc)xr;
+        if (gr) {
+          if (!gm && xr < need[i]) last_def = r;
+          L[r] = int2{avail - need[i], t | (gm << 16)};
+          Pr[r] = offP;
+          Qr[r] = offQ;
+          const int32_t room = need[i] > avail ? need[i] - avail : 0;
+          offP += room;
+          offQ += xr_weight<Acc>(rc, T, t) * (Acc)room;
+          ++r;
+        }
+        y = avail - xr;
+      } else {
+        y = avail;
+      }
+    }
+  }
+  if (G == 32) {
+    first_bad = (int)__reduce_min_sync(kFull, (unsigned)first_bad);
+    last_def = (int)__reduce_max_sync(kFull, (unsigned)(last_def + 1)) - 1;
+  } else {
+    for (int o = G >> 1; o > 0; o >>= 1) {
+      const int v = __shfl_xor_sync(smask, first_bad, o, G);
+      const int w = __shfl_xor_sync(smask, last_def, o, G);
+      first_bad = v < first_bad ? v : first_bad;
+      last_def = w > last_def ? w : last_def;
+    }
+  }
+  if (lane == 0) {
+    RowMark mk;
+    mk.bad = (int16_t)(dfirst != 0 ? -1 : first_bad);  // -1: demand before the first setup
+    mk.ld = (int16_t)last_def;
+    m.mark[q] = mk;
+    m.S[q] = total;
+    const int nr = popc64(b.r0) + (NW == 1 ? 0 : popc64(b.r1));
+    m.nR[q] = nr;
+    Pr[nr] = totP;
+    Qr[nr] = totQ;
+  }
+}
+
+// Row rebuild by a group of G <= 32 lanes: the two-pass variant when each
+// lane holds at most 4 periods, specialised for 2 (rows of at most 64
+// periods on 32 lanes, the single-run default).  Inlined: as a called
+// function its live registers spill around the call, which costs more than
+// its code size.
+template <typename Acc, int NW>
+__device__ __forceinline__ void rebuild_any(const Rows<Acc>& m, int q, int lane, int G,
+                                            unsigned smask) {
+  const int P = (m.T + G - 1) / G;
+  if (NW == 1 && P <= 2)
+    rebuild_row_regs<Acc, NW, 2>(m, q, lane, G, smask);
+  else if (P <= 4)
+    rebuild_row_regs<Acc, NW, 4>(m, q, lane, G, smask);
+  else
+    rebuild_row<Acc, NW>(m, q, lane, G, smask);
+}
+
 // ---------------------------------------------------------------------------
 // Team context: the CTA's view of the run its cluster executes.
 // ---------------------------------------------------------------------------
@@ -459,9 +639,9 @@ __device__ __forceinline__ uint64_t group_min(const Team<Acc>& t, uint64_t v) {
 template <typename Acc, int NW>
 __device__ __forceinline__ void group_rebuild(const Team<Acc>& t, int q) {
   if (t.G <= 32) {
-    rebuild_row<Acc, NW>(t.m, q, t.lane, t.G, t.smask);
+    rebuild_any<Acc, NW>(t.m, q, t.lane, t.G, t.smask);
   } else if (t.lane < 32) {
-    rebuild_row<Acc, NW>(t.m, q, t.lane, 32, kFull);
+    rebuild_any<Acc, NW>(t.m, q, t.lane, 32, kFull);
   }
   group_sync(t);
 }
