@@ -32,7 +32,9 @@
  * hand-derived worked examples, closed forms, plan invariants, a
  * Wagner-Whitin reduction and brute force.  The readings themselves (decode
  * rule, neighbourhoods, shake, acceptance) cannot be pinned against the
- * paper's unpublished [SK2016] rules: parity unpinned for those readings.
+ * paper's unpublished [SK2016] rules: parity unpinned for those readings,
+ * and likewise for the fork-join workers' draw keys (the paper gives no
+ * shaking rule).
  */
 #include <stdint.h>
 #include <stdlib.h>
