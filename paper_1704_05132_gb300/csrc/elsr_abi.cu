@@ -667,7 +667,7 @@ int refresh_rowcost(elsr_ctx* h) { return eval_launch(h, 0u, 0, 0, true); }
 
 extern "C" {
 
-int elsr_version(void) { return 10100; }
+int elsr_version(void) { return 10300; }
 
 int elsr_run_footprint(int32_t K, int32_t T, int32_t* smem_one_cta, int64_t* device_bytes) {
   if (K < 1 || T < 1 || T > ELSR_T_MAX) return ELSR_E_ARG;
@@ -1112,7 +1112,7 @@ int elsr_multistart_run(elsr_t* h, uint64_t seed0, int32_t nstarts, int32_t iter
     return ELSR_E_ARG;
   }
   elsr_batch* b = &h->b;
-  b->h_runs.resize(nstarts);
+  b->h_runs.assign(nstarts, RunDesc{});  // fresh descriptors: no resume, no budget
   for (int32_t s = 0; s < nstarts; ++s) {
     RunDesc& r = b->h_runs[s];
     r.inst = 0;
@@ -1277,7 +1277,7 @@ int elsr_batch_run(elsr_batch_t* b, const uint64_t* seeds, int32_t iters, int32_
   std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t c) {
     return (int64_t)b->insts[a].K * b->insts[a].T > (int64_t)b->insts[c].K * b->insts[c].T;
   });
-  b->h_runs.resize(b->n);
+  b->h_runs.assign(b->n, RunDesc{});  // fresh descriptors: no resume, no budget
   b->out_of_inst.assign(b->n, 0);
   for (int32_t q = 0; q < b->n; ++q) {
     const int32_t i = order[q];

@@ -119,3 +119,24 @@ def test_resume_rejects_a_state_that_does_not_match(E):
             s.vns_resume(dict(ck, k=4), 10)  # k beyond kmax: refused on the host
         r2 = s.vns_resume(ck, 10)
         assert r2["status"] == 0 and r2["iterations"] == 40
+
+
+def test_multistart_after_resume_and_budget_starts_fresh(E):
+    """Run descriptors of a resume or a budgeted run do not leak into a later
+    multi-start on the same handle: every start equals the oracle's run."""
+    g = gen.plain_small()
+    inst = oracle.Instance.from_arrays(g)
+    want = [oracle.vns(inst, seed=i, iters=40, kmax=3, mode=0).best_cost for i in range(8)]
+    with E.Solver(g) as s:
+        s.vns(seed=0, iters=30, kmax=3, mode=0)
+        ck = s.checkpoint()
+        for step in ("resume", "budget"):
+            if step == "resume":
+                s.vns_resume(ck, 10)
+            else:
+                s.set_time_limit(2000)
+                s.vns(seed=1, iters=50, kmax=3, mode=0)
+            s.set_state()  # back to every setup open
+            best, start, costs = s.multistart(0, 8, 40, 3, 0, costs=True)
+            np.testing.assert_array_equal(costs, want)
+            assert (best, start) == min((c, i) for i, c in enumerate(want))
