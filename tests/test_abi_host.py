@@ -89,3 +89,40 @@ def test_checkpoint_struct_and_file_roundtrip(tmp_path):
     assert (back["gM"] == ck["gM"]).all() and (back["gR"] == ck["gR"]).all()
     c = nat.Checkpoint.from_dict(back)
     assert c.seed == ck["seed"] and c.traj_hash == ck["traj_hash"]
+
+
+def _create_ex(lib, K, T, D, R, c, pm, pr):
+    h = ctypes.c_void_p()
+    arrs = [np.ascontiguousarray(a, np.int32) for a in (D, R, c[0], c[1], c[2], c[3])]
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+    pms = None if pm is None else np.ascontiguousarray(pm, np.int32)
+    prs = None if pr is None else np.ascontiguousarray(pr, np.int32)
+    code = lib.elsr_create_ex(ctypes.byref(h), K, T, *[p(a) for a in arrs], p(pms), p(prs))
+    return code, h
+
+
+def test_production_costs_validated_on_the_host(lib):
+    """Unit production costs: negative values, values from 2^24 on, and one
+    array without the other are refused before any device work."""
+    K, T = 3, 5
+    D = np.full((K, T), 7)
+    R = np.zeros((K, T))
+    c = [np.full(K, 100), np.full(K, 50), np.full(K, 2), np.full(K, 1)]
+    assert _create_ex(lib, K, T, D, R, c, [1, -1, 0], [0, 0, 0])[0] == nat.ELSR_E_ARG
+    assert _create_ex(lib, K, T, D, R, c, [0, 0, 0], [0, 1 << 24, 0])[0] == nat.ELSR_E_RANGE
+    code, h = _create_ex(lib, K, T, D, R, c, [1, 2, 3], None)
+    assert code == nat.ELSR_E_ARG and not h.value
+    assert b"pM and pR" in lib.elsr_last_error(None)
+
+
+def test_new_entry_points_reject_a_null_handle(lib):
+    """Fork-join, time budget, checkpoint and resume return ELSR_E_ARG for a
+    NULL handle (and touch nothing)."""
+    ck = nat.Checkpoint()
+    gm = np.zeros(4, np.uint8)
+    P = ctypes.c_void_p
+    assert lib.elsr_vns_forkjoin_run(None, 0, 10, 3, 0, 2) == nat.ELSR_E_ARG
+    assert lib.elsr_set_time_limit(None, 1000) == nat.ELSR_E_ARG
+    assert lib.elsr_checkpoint(None, ctypes.byref(ck), None, None) == nat.ELSR_E_ARG
+    assert lib.elsr_vns_resume(None, ctypes.byref(ck), gm.ctypes.data_as(P),
+                               gm.ctypes.data_as(P), 5) == nat.ELSR_E_ARG
