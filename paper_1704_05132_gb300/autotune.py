@@ -2,7 +2,8 @@
 
 Knobs (none changes a result; only speed):
   lanes    -- lanes that share one product row (4..32 within a warp; 64 or
-              128 = a row group of 2 or 4 warps, mode P): each lane evaluates
+              128 = a row group of 2 or 4 warps; 0 = automatic, which lets
+              each run of a batch pick its own): each lane evaluates
               about |row moves| / lanes candidates per sweep;
   threads  -- threads per CTA (rows in flight per CTA = threads / lanes);
   cluster  -- CTAs that share one run (1 for batches of small instances;
@@ -47,9 +48,11 @@ def _timed(fn):
     return e0.elapsed_time(e1), out
 
 
-BATCH_CANDIDATES = [dict(lanes=l, threads=t, cluster=1) for l in (8, 16, 32)
+# lanes = 0: every run of the batch picks its own row-group width
+BATCH_CANDIDATES = [dict(lanes=l, threads=t, cluster=1) for l in (0, 8, 16, 32)
                     for t in (512, 1024)]
-SINGLE_CANDIDATES = [dict(lanes=l, cluster=c, teams=0) for l in (32, 64) for c in (6, 8, 10)]
+SINGLE_CANDIDATES = [dict(lanes=l, cluster=c, teams=0) for l in (32, 64)
+                     for c in (6, 8, 9, 10, 12, 16)]
 
 
 def tune_batch(insts, probe_iters: int = 10, candidates=None, cache_file: str | None = None):
