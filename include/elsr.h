@@ -182,7 +182,13 @@ int elsr_set_cluster(elsr_t *h, int32_t cluster);
 /* Speculative execution of one GVNS run (mode P or G): up to `teams` clusters run
  * consecutive iterations from the same incumbent and commit them in order up
  * to the first acceptance, so trajectory, solution and counters equal the
- * sequential run's.  0 = automatic (up to 16 teams), 1 = off. */
+ * sequential run's.  0 = automatic (up to 16 teams), 1 = off.  The teams
+ * meet at a grid barrier every round, so all of them must be resident at
+ * once; their number is sized on an idle device.  When other long-running
+ * work occupies the device, teams that cannot start leave the others
+ * waiting, and after a few seconds the run ends with ELSR_E_TIMEOUT instead
+ * of hanging; set 1 (off) for runs that share a busy device.  Batches and
+ * multi-start runs have no such barrier. */
 int elsr_set_speculation(elsr_t *h, int32_t teams);
 
 /* Launch shape of the last GVNS launch: shape[8] = {lanes per row, threads
@@ -253,7 +259,9 @@ int elsr_vns_run(elsr_t *h, uint64_t seed, int32_t iters, int32_t kmax,
  * settings) and all workers run at once, so `workers` may not exceed the
  * teams the device holds resident for this instance (ELSR_E_RANGE, with the
  * number in elsr_last_error) nor ELSR_FJ_WORKERS_MAX (ELSR_E_ARG).  Every
- * worker's VND counts in the statistics.  elsr_result() returns x, the
+ * worker's VND counts in the statistics.  The workers meet at a grid
+ * barrier every iteration, so on a device busy with other work the run may
+ * end with ELSR_E_TIMEOUT (see elsr_set_speculation).  elsr_result() returns x, the
  * statistics and the trajectory; an entry's `reserved` field holds the
  * winning worker.  With one worker the run equals elsr_vns_run's.
  * Asynchronous, like elsr_vns_run.
