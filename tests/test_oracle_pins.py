@@ -503,3 +503,78 @@ def test_wagner_whitin_with_manufacturing_cost(seed):
     best = min(oracle.decode_row(inst, 0, np.array(p, np.uint8), zeros)[0]
                for p in itertools.product((0, 1), repeat=T))
     assert best == ww + pm * int(D.sum())
+
+
+# ---------------------------------------------------------------------------
+# Degenerate instances: closed forms that hold whatever the decode's steps.
+# ---------------------------------------------------------------------------
+
+def test_closed_form_returns_exceed_demand():
+    """R >= D in every period and every gR open: returns cover all demand,
+    nothing is manufactured (yM = 0), and the returns stock after period t is
+    sum_{i<=t} (R_i - D_i), so a row costs
+    kM * |gM| + T * kR + hR * sum_i (R_i - D_i) * (T - i), whatever gM is."""
+    rng = np.random.default_rng(7)
+    K, T = 4, 11
+    D = rng.integers(0, 60, (K, T))
+    R = D + rng.integers(0, 25, (K, T))
+    kM, kR = rng.integers(50, 300, K), rng.integers(50, 300, K)
+    hM, hR = rng.integers(1, 6, K), rng.integers(1, 4, K)
+    inst = oracle.Instance(D, R, kM, kR, hM, hR)
+    gr = np.ones((K, T), np.uint8)
+    w = np.arange(T, 0, -1)
+    for trial in range(6):
+        gm = (rng.random((K, T)) < 0.4).astype(np.uint8)
+        _, rc = oracle.total_cost(inst, gm, gr)
+        for k in range(K):
+            want = kM[k] * gm[k].sum() + T * kR[k] + hR[k] * ((R[k] - D[k]) * w).sum()
+            assert rc[k] == want, (trial, k)
+            _, plan = oracle.decode_row(inst, k, gm[k], gr[k])
+            assert (plan[0] == 0).all() and (plan[2] == 0).all()   # xM = yM = 0
+
+
+def test_zero_demand_and_returns():
+    """D = R = 0: every setup pattern is feasible and costs only its setups,
+    kM * |gM| + kR * |gR|; with positive setup costs the unique local optimum
+    of every neighbourhood is the empty pattern, so VND from all open and
+    GVNS end there at cost 0, in both modes."""
+    K, T = 3, 9
+    z = np.zeros((K, T), np.int64)
+    kM, kR = np.array([40, 7, 300]), np.array([1, 90, 33])
+    inst = oracle.Instance(z, z, kM, kR, [3, 1, 2], [1, 1, 1])
+    rng = np.random.default_rng(3)
+    for _ in range(5):
+        gm = (rng.random((K, T)) < 0.5).astype(np.uint8)
+        gr = (rng.random((K, T)) < 0.5).astype(np.uint8)
+        _, rc = oracle.total_cost(inst, gm, gr)
+        assert (rc == kM * gm.sum(1) + kR * gr.sum(1)).all()
+    gm0, gr0 = oracle.initial_solution(K, T)
+    for mode in (0, 1):
+        gm, gr, _ = oracle.vnd(inst, gm0, gr0, mode)
+        assert not gm.any() and not gr.any()
+        res = oracle.vns(inst, seed=5, iters=25, kmax=3, mode=mode)
+        assert res.best_cost == 0 and res.counters["accepted"] == 0
+
+
+def test_ties_go_to_the_lowest_index():
+    """Two identical products with D = R = 0 and gM = 0110: dropping either
+    open setup saves kM, every other N1 move costs more, so the per-product
+    best N1 move is t = 1 (not t = 2), and the global best is product 0's
+    (index 1, not product 1's index 5)."""
+    T, kM = 4, 100
+    z = np.zeros((2, T), np.int64)
+    inst = oracle.Instance(z, z, [kM, kM], [60, 60], [1, 1], [1, 1])
+    gm = np.array([[0, 1, 1, 0]] * 2, np.uint8)
+    gr = np.zeros((2, T), np.uint8)
+    _, _, pc, pm, _ = oracle.eval_neighbourhood(inst, gm, gr, 1, 0)
+    assert pc.tolist() == [kM, kM] and pm.tolist() == [1, 1]
+    bc, bm, _, _, _ = oracle.eval_neighbourhood(inst, gm, gr, 1, 1)
+    assert (bc, bm) == (kM + 2 * kM, 1)
+    # N3 alone: the swaps 01 -> 10 at t = 0 and 10 -> 01 at t = 2 keep the
+    # cost (2 kM); the null swap at t = 1 too, so N3's first move wins.  In
+    # the combined layouts it comes after N1 and N2: local index 2T, global
+    # index 2KT (product 0's).
+    _, _, pc3, pm3, _ = oracle.eval_neighbourhood(inst, gm, gr, 4, 0)
+    assert pc3.tolist() == [2 * kM, 2 * kM] and pm3.tolist() == [2 * T, 2 * T]
+    bc3, bm3, _, _, _ = oracle.eval_neighbourhood(inst, gm, gr, 4, 1)
+    assert (bc3, bm3) == (4 * kM, 2 * 2 * T)
