@@ -219,7 +219,12 @@ int elsr_cost(elsr_t *h, int64_t *rowcost, int64_t *total);
  *   mode ELSR_MODE_G: *best_cost, *best_move = lexicographic minimum of
  *     (new objective, combined global index); pp_* as in mode P.
  * Outputs are host pointers and may be NULL.  Adds the moves to the
- * handle's evaluation counter.  Synchronous.
+ * handle's evaluation counter.  Synchronous.  The first call for a (mode,
+ * nb_mask) pair records the call's device work (reset of the reduction
+ * words, the kernel, the copy of the results) as a CUDA graph owned by the
+ * handle, which allocates; later calls replay it on the handle's stream.
+ * Changing the lanes per row (elsr_set_launch) drops the graphs.  Callers
+ * that must not allocate use elsr_eval_neighbourhood_static.
  */
 int elsr_eval_neighbourhood(elsr_t *h, uint32_t nb_mask, int32_t mode,
                             int64_t *best_cost, int64_t *best_move,

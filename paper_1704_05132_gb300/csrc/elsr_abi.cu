@@ -585,9 +585,16 @@ struct elsr_ctx {
   // per-product keys [K], mirrored by a pinned host buffer, so that an
   // evaluation needs one asynchronous copy each way
   uint64_t* d_evalbuf = nullptr;
-  uint64_t* h_evalbuf = nullptr;  // pinned, [4 + K]
+  uint64_t* h_evalbuf = nullptr;  // pinned, [4 + K] results + [4] initial words
   uint64_t* d_ppkey = nullptr;    // d_evalbuf + 4
   uint64_t* d_scratch = nullptr;  // d_evalbuf
+  // elsr_eval_neighbourhood as one CUDA graph per (mode, mask): reset of the
+  // reduction words, the evaluation kernel and the copy of its results,
+  // captured on a private stream and replayed on the handle's stream; made
+  // again when the lanes per row change
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t eval_exec[2][8] = {};
+  int32_t eval_exec_lanes = 0;
   int64_t* d_movecost = nullptr;
   int32_t* d_movewin = nullptr;
   int32_t* d_plan = nullptr;
@@ -610,24 +617,43 @@ struct elsr_ctx {
     dev_free(d_rowcost, stream);
     dev_free(d_evalbuf, stream);
     if (h_evalbuf) cudaFreeHost(h_evalbuf);
+    drop_eval_graphs();
+    if (cap_stream) cudaStreamDestroy(cap_stream);
     dev_free(d_movecost, stream);
     dev_free(d_movewin, stream);
     dev_free(d_plan, stream);
+  }
+
+  void drop_eval_graphs() {
+    for (auto& row : eval_exec)
+      for (auto& ex : row)
+        if (ex) {
+          cudaGraphExecDestroy(ex);
+          ex = nullptr;
+        }
   }
 };
 
 namespace {
 
-int eval_launch(elsr_ctx* h, uint32_t mask, int32_t mode, int single_j,
-                bool write_rowcost) {
+// Launch geometry and parameters of one full-neighbourhood evaluation.
+struct EvalPlan {
+  EvalParams p;
+  int blocks = 0;
+  int threads = 128;
+  size_t smem = 0;
+  bool wide = false;  // one row per 128-thread CTA (eval_wide_kernel)
+};
+
+int eval_plan(elsr_ctx* h, uint32_t mask, int32_t mode, int single_j, bool write_rowcost,
+              EvalPlan& pl) {
   elsr_batch* b = &h->b;
   // the evaluation kernel reduces within a warp: at most 32 lanes per row
   const int G = std::min(32, b->lanes ? b->lanes : default_lanes(h->T, true));
-  const int threads = 128;
-  const int nsub = threads / G;
-  const size_t smem = eval_smem_bytes(nsub, h->T, b->acc64);
-  ELSR_TRY_CUDA(b, eval_prepare(b->acc64, h->T, smem));
-  EvalParams p;
+  const int nsub = pl.threads / G;
+  pl.smem = eval_smem_bytes(nsub, h->T, b->acc64);
+  ELSR_TRY_CUDA(b, eval_prepare(b->acc64, h->T, pl.smem));
+  EvalParams& p = pl.p;
   p.ip = b->pools();
   p.K = h->K;
   p.T = h->T;
@@ -642,22 +668,67 @@ int eval_launch(elsr_ctx* h, uint32_t mask, int32_t mode, int single_j,
   p.move_cost = single_j ? h->d_movecost : nullptr;
   p.move_win = single_j ? h->d_movewin : nullptr;
   p.scratch = h->d_scratch;
-  // reduction words {gkey, sum after, infeasible after, improving}: staged
-  // in the pinned buffer (the previous evaluation's results were consumed
-  // before it returned)
-  h->h_evalbuf[0] = ~0ull;
-  h->h_evalbuf[1] = h->h_evalbuf[2] = h->h_evalbuf[3] = 0ull;
-  ELSR_TRY_CUDA(b, cudaMemcpyAsync(h->d_scratch, h->h_evalbuf, 4 * sizeof(uint64_t),
-                                   cudaMemcpyHostToDevice, b->stream));
   // Few rows: one row per CTA with 128 threads on its moves (the default
   // for a single run spreads a row over more than a warp); many rows: rows
   // of G lanes packed four to a CTA.
-  if (G >= 32 && !b->lanes && (int64_t)h->K <= 2 * (int64_t)b->sms) {
-    ELSR_TRY_CUDA(b, launch_eval_wide(p, b->acc64, 128, b->stream));
-    return ELSR_OK;
+  pl.wide = G >= 32 && !b->lanes && (int64_t)h->K <= 2 * (int64_t)b->sms;
+  pl.blocks = (h->K + nsub - 1) / nsub;
+  return ELSR_OK;
+}
+
+// The evaluation's stream work: the reduction words {gkey, sum after,
+// infeasible after, improving} set to {~0, 0, 0, 0} from the fixed pinned
+// block after the results, then the kernel.
+cudaError_t eval_issue(elsr_ctx* h, const EvalPlan& pl, cudaStream_t s) {
+  cudaError_t e = cudaMemcpyAsync(h->d_scratch, h->h_evalbuf + 4 + h->K, 4 * sizeof(uint64_t),
+                                  cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  return pl.wide ? launch_eval_wide(pl.p, h->b.acc64, pl.threads, s)
+                 : launch_eval(pl.p, h->b.acc64, pl.blocks, pl.threads, pl.smem, s);
+}
+
+int eval_launch(elsr_ctx* h, uint32_t mask, int32_t mode, int single_j,
+                bool write_rowcost) {
+  EvalPlan pl;
+  const int rc = eval_plan(h, mask, mode, single_j, write_rowcost, pl);
+  if (rc != ELSR_OK) return rc;
+  ELSR_TRY_CUDA(&h->b, eval_issue(h, pl, h->b.stream));
+  return ELSR_OK;
+}
+
+// Graph of one elsr_eval_neighbourhood call (initial words, kernel, copy of
+// the reduction words and per-product keys into the pinned buffer), made on
+// first use of a (mode, mask) and kept until the lanes per row change.
+int eval_graph(elsr_ctx* h, uint32_t mask, int32_t mode, cudaGraphExec_t* out) {
+  elsr_batch* b = &h->b;
+  if (h->eval_exec_lanes != b->lanes) {
+    h->drop_eval_graphs();
+    h->eval_exec_lanes = b->lanes;
   }
-  const int blocks = (h->K + nsub - 1) / nsub;
-  ELSR_TRY_CUDA(b, launch_eval(p, b->acc64, blocks, threads, smem, b->stream));
+  cudaGraphExec_t& ex = h->eval_exec[mode][mask];
+  if (!ex) {
+    EvalPlan pl;
+    const int rc = eval_plan(h, mask, mode, 0, false, pl);
+    if (rc != ELSR_OK) return rc;
+    if (!h->cap_stream)
+      ELSR_TRY_CUDA(b, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    ELSR_TRY_CUDA(b, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = eval_issue(h, pl, h->cap_stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(h->h_evalbuf, h->d_evalbuf, ((size_t)h->K + 4) * sizeof(uint64_t),
+                          cudaMemcpyDeviceToHost, h->cap_stream);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e_end = cudaStreamEndCapture(h->cap_stream, &g);
+    if (e == cudaSuccess) e = e_end;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      ex = nullptr;
+      b->err = std::string("evaluation graph: ") + cudaGetErrorString(e);
+      return ELSR_E_CUDA;
+    }
+  }
+  *out = ex;
   return ELSR_OK;
 }
 
@@ -732,7 +803,12 @@ int elsr_create_ex(elsr_t** out, int32_t K, int32_t T, const int32_t* D,
     if (e == cudaSuccess) e = dev_alloc(&h->d_state, K, b->stream);
     if (e == cudaSuccess) e = dev_alloc(&h->d_rowcost, K, b->stream);
     if (e == cudaSuccess) e = dev_alloc(&h->d_evalbuf, (size_t)K + 4, b->stream);
-    if (e == cudaSuccess) e = cudaMallocHost(&h->h_evalbuf, ((size_t)K + 4) * sizeof(uint64_t));
+    if (e == cudaSuccess) e = cudaMallocHost(&h->h_evalbuf, ((size_t)K + 8) * sizeof(uint64_t));
+    if (e == cudaSuccess) {
+      uint64_t* init = h->h_evalbuf + 4 + K;
+      init[0] = ~0ull;
+      init[1] = init[2] = init[3] = 0ull;
+    }
     if (e == cudaSuccess) {
       h->d_scratch = h->d_evalbuf;
       h->d_ppkey = h->d_evalbuf + 4;
@@ -842,10 +918,10 @@ int elsr_eval_neighbourhood(elsr_t* h, uint32_t nb_mask, int32_t mode,
     h->b.err = "nb_mask must be within 0..7 and mode P or G";
     return ELSR_E_ARG;
   }
-  int rc = eval_launch(h, nb_mask, mode, 0, false);
+  cudaGraphExec_t ex = nullptr;
+  int rc = eval_graph(h, nb_mask, mode, &ex);
   if (rc != ELSR_OK) return rc;
-  ELSR_TRY_CUDA(&h->b, cudaMemcpyAsync(h->h_evalbuf, h->d_evalbuf, (h->K + 4) * sizeof(uint64_t),
-                                       cudaMemcpyDeviceToHost, h->b.stream));
+  ELSR_TRY_CUDA(&h->b, cudaGraphLaunch(ex, h->b.stream));
   ELSR_TRY_CUDA(&h->b, cudaStreamSynchronize(h->b.stream));
   const uint64_t* sc = h->h_evalbuf;
   const uint64_t* keys = h->h_evalbuf + 4;

@@ -142,13 +142,14 @@ class Solver:
 
     # -- Algorithm 1: one neighbourhood evaluation --
     def eval_neighbourhood(self, mask: int = 0b111, mode: int = nat.MODE_P):
-        bc = np.zeros(1, np.int64)
-        bm = np.zeros(1, np.int64)
-        pc = np.zeros(self.K, np.int64)
-        pm = np.zeros(self.K, np.int64)
-        self._chk(self._lib.elsr_eval_neighbourhood(self._h, mask, mode, _p(bc), _p(bm),
-                                                    _p(pc), _p(pm)))
-        return int(bc[0]), int(bm[0]), pc, pm
+        """(best cost, best move, per-product costs [K], per-product moves [K]);
+        the four outputs share one buffer, passed as raw addresses."""
+        K = self.K
+        out = np.empty(2 + 2 * K, np.int64)
+        a = out.__array_interface__["data"][0]
+        self._chk(self._lib.elsr_eval_neighbourhood(self._h, mask, mode, a, a + 8, a + 16,
+                                                    a + 16 + 8 * K))
+        return int(out[0]), int(out[1]), out[2:2 + K], out[2 + K:]
 
     def move_costs(self, j: int):
         n = self.K * (2 * (self.T - 1) if j == 3 else self.T)
