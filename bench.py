@@ -412,15 +412,16 @@ def run_batched(args):
         step()
     torch.cuda.synchronize()
     ms = []
-    moves = 0
-    for _ in range(args.steps):
-        flush.add_(1)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        step()
-        e1.record(stream)
-        e1.synchronize()
-        ms.append(e0.elapsed_time(e1))
+    with ClockSampler(0) as clk:
+        for _ in range(args.steps):
+            flush.add_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+    clocks = clk.summary()
     st = stats()
     moves_step = sum(r["moves_evaluated"] for r in st)
     segs_step = sum(r["segments"] for r in st)
@@ -429,7 +430,7 @@ def run_batched(args):
     line = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "dtype": "int32", "data": "synthetic", "config": cfg,
-            "instances_per_s": n * args.steps / t, "launch_shape": shape}
+            "instances_per_s": n * args.steps / t, "launch_shape": shape, "clocks": clocks}
     line["value"] = moves_step * args.steps / t
     line["segments_per_step"] = segs_step
     if args.workload == "multistart":

@@ -386,3 +386,30 @@ def test_batch_small_instances_use_wide_row_groups(E):
         gm, gr = b.solution(i)
         np.testing.assert_array_equal(gm, o.gM)
     b.close()
+
+
+def test_eval_graph_replay_follows_state_launch_and_stream(E):
+    """elsr_eval_neighbourhood replays a recorded CUDA graph per (mode, mask):
+    its results follow the solution set between calls, a change of lanes per
+    row records the graph again (both kernels of the evaluation), and a
+    replay on another stream stays ordered after that stream's state copy."""
+    import torch
+    g = gen.make_instance(5, 9, K=21, T=44)
+    inst = _inst(g)
+    rng = np.random.default_rng(17)
+    states = list(_states(rng, inst.K, inst.T, 4))
+    side = torch.cuda.Stream()
+    with E.Solver(g) as s:
+        for step, lanes in enumerate((0, 8, 32, 0)):
+            s.set_launch(lanes=lanes)
+            if step == 3:
+                s.set_stream(side)
+            for gm, gr in states:
+                s.set_state(gm, gr)
+                for mode in (0, 1):
+                    for mask in (7, 2, 7):
+                        got = s.eval_neighbourhood(mask, mode)
+                        bc, bm, pc, pm, _ = oracle.eval_neighbourhood(inst, gm, gr, mask, mode)
+                        assert got[:2] == (bc, bm), (lanes, mode, mask)
+                        np.testing.assert_array_equal(got[2], pc)
+                        np.testing.assert_array_equal(got[3], pm)
