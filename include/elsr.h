@@ -22,7 +22,9 @@
  *     where a call is documented as asynchronous; the library copies its
  *     inputs, so the caller keeps ownership of every buffer it passes;
  *   - device work is issued on the handle's CUDA stream (elsr_set_stream;
- *     default: the legacy default stream) on the device current at create.
+ *     default: the legacy default stream) on the device current at create;
+ *   - a handle or batch is used by one host thread at a time; different
+ *     handles may be used from different threads at once.
  *
  * Decode rule (the paper defers the formulation to [SK2016]; this is the
  * reading the library implements): at each period with a setup, cover the
@@ -162,7 +164,9 @@ int elsr_create_ex(elsr_t **out, int32_t K, int32_t T, const int32_t *D,
 void elsr_destroy(elsr_t *h);
 
 /* Issue the handle's device work on `stream` (a cudaStream_t; NULL = the
- * legacy default stream). */
+ * legacy default stream).  Work issued afterwards on the new stream is
+ * ordered after everything already issued on the previous one, which must
+ * therefore still exist when the call is made.  Asynchronous. */
 int elsr_set_stream(elsr_t *h, void *stream);
 
 /* Kernel launch shape: lanes per product row (4, 8, 16 or 32 lanes of one
@@ -413,6 +417,7 @@ void elsr_batch_destroy(elsr_batch_t *b);
 /* Message of the last failed call on batch b (b NULL: last failed create on
  * this thread). */
 const char *elsr_batch_last_error(const elsr_batch_t *b);
+/* As elsr_set_stream, for a batch. */
 int elsr_batch_set_stream(elsr_batch_t *b, void *stream);
 int elsr_batch_set_launch(elsr_batch_t *b, int32_t lanes_per_row,
                           int32_t threads);

@@ -834,8 +834,7 @@ void elsr_destroy(elsr_t* h) { delete h; }
 
 int elsr_set_stream(elsr_t* h, void* stream) {
   if (!h) return ELSR_E_ARG;
-  h->b.stream = (cudaStream_t)stream;
-  return ELSR_OK;
+  return elsr_batch_set_stream(&h->b, stream);
 }
 
 int elsr_set_launch(elsr_t* h, int32_t lanes, int32_t threads) {
@@ -1304,7 +1303,18 @@ const char* elsr_batch_last_error(const elsr_batch_t* b) {
 
 int elsr_batch_set_stream(elsr_batch_t* b, void* stream) {
   if (!b) return ELSR_E_ARG;
-  b->stream = (cudaStream_t)stream;
+  const cudaStream_t to = (cudaStream_t)stream;
+  if (to != b->stream) {
+    // work issued later on the new stream runs after everything issued so
+    // far on the old one (a run still in flight writes the same buffers)
+    cudaEvent_t ev = nullptr;
+    ELSR_TRY_CUDA(b, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    cudaError_t e = cudaEventRecord(ev, b->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(to, ev, 0);
+    cudaEventDestroy(ev);  // released once the recorded work completes
+    ELSR_TRY_CUDA(b, e);
+    b->stream = to;
+  }
   return ELSR_OK;
 }
 

@@ -18,6 +18,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "elsr_vns.cuh"
 
 namespace elsr {
@@ -396,18 +398,26 @@ __global__ void plan_kernel(const PlanParams p) {
 template <typename Acc>
 cudaError_t eval_prepare_t(int T, size_t smem) {
   constexpr int kDevices = 64;
-  static int granted[2][kDevices];  // per word count and device; 0 = not yet set
+  // per word count and device, the largest size granted so far (0: none);
+  // handles on several host threads may race here, which at worst repeats
+  // the attribute call
+  static std::atomic<int> granted[2][kDevices];
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   const int w = T <= 64 ? 0 : 1;
-  if (dev >= 0 && dev < kDevices && granted[w][dev] >= (int)smem) return cudaSuccess;
+  const bool cached = dev >= 0 && dev < kDevices;
+  if (cached && granted[w][dev].load(std::memory_order_relaxed) >= (int)smem) return cudaSuccess;
   e = w == 0 ? cudaFuncSetAttribute(eval_kernel<Acc, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem)
              : cudaFuncSetAttribute(eval_kernel<Acc, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem);
-  if (e == cudaSuccess && dev >= 0 && dev < kDevices && granted[w][dev] < (int)smem)
-    granted[w][dev] = (int)smem;
+  if (e == cudaSuccess && cached) {
+    int cur = granted[w][dev].load(std::memory_order_relaxed);
+    while (cur < (int)smem &&
+           !granted[w][dev].compare_exchange_weak(cur, (int)smem, std::memory_order_relaxed)) {
+    }
+  }
   return e;
 }
 

@@ -413,3 +413,19 @@ def test_eval_graph_replay_follows_state_launch_and_stream(E):
                         assert got[:2] == (bc, bm), (lanes, mode, mask)
                         np.testing.assert_array_equal(got[2], pc)
                         np.testing.assert_array_equal(got[3], pm)
+
+
+def test_stream_switch_waits_for_work_in_flight(E):
+    """A run queued on one stream, then the handle moved to another stream
+    before the run has finished: the results read on the new stream are the
+    finished run's (elsr_set_stream orders the new stream after the old)."""
+    import torch
+    g = gen.plain_medium()
+    o = oracle.vns(_inst(g), seed=1, iters=400, kmax=3, mode=0)
+    first, second = torch.cuda.Stream(), torch.cuda.Stream()
+    with E.Solver(g, stream=first, speculation=1) as s:
+        s.vns_run(1, 400, 3, 0)   # about 10 ms on one team: still running below
+        s.set_stream(second)
+        r = s.result()
+    np.testing.assert_array_equal(r["traj"]["cost"], o.traj["cost"])
+    _check_run(r, o)
