@@ -212,3 +212,46 @@ def test_delta_decode_with_production_costs(hc, T, acc64, nw):
                 assert cur == oracle.decode_row(inst, 0, gm, gr)[0]
                 np.testing.assert_array_equal(out, oracle.move_costs(inst, gm[None, :],
                                                                      gr[None, :], j))
+
+
+def _degenerate_rows(rng, T):
+    """(name, D, R, [kM, kR, hM, hR, pM, pR]) rows of the degenerate kinds:
+    no demand or returns, returns above demand, zero holding, zero setup
+    costs, no cost at all, and returns above demand with pR < pM."""
+    D = rng.integers(0, 101, T).astype(np.int32)
+    R = (D * rng.integers(200, 601, T) // 1000).astype(np.int32)
+    z = np.zeros(T, np.int32)
+    more = (D + rng.integers(0, 30, T)).astype(np.int32)
+    return [("empty", z, z, [310, 120, 3, 1, 0, 0]),
+            ("returns_above_demand", D, more, [250, 140, 4, 2, 0, 0]),
+            ("zero_holding", D, R, [260, 170, 0, 0, 0, 0]),
+            ("zero_setup", D, R, [0, 0, 5, 2, 0, 0]),
+            ("no_cost", D, R, [0, 0, 0, 0, 0, 0]),
+            ("returns_above_demand_pR_below_pM", D, more, [250, 140, 4, 2, 90, 35])]
+
+
+@pytest.mark.parametrize("T", [1, 12, 52, 64, 65, 104])
+def test_degenerate_rows_match_oracle(hc, T):
+    """The kernels' row arithmetic on degenerate rows (costs that tie, stock
+    that only grows, rows with nothing to produce) against the oracle's full
+    decode, per move, with 32- and 64-bit accumulators."""
+    rng = np.random.default_rng(5000 + T)
+    for name, D, R, c in _degenerate_rows(rng, T):
+        inst = oracle.Instance(D[None, :], R[None, :], [c[0]], [c[1]], [c[2]], [c[3]],
+                               [c[4]], [c[5]])
+        costs = np.array(c, np.int32)
+        for acc64, nw in [(0, 1), (1, 2)] if T <= 64 else [(0, 2), (1, 2)]:
+            for gm, gr in _random_states(rng, T, 10):
+                for j in (1, 2, 3):
+                    M = oracle.row_moves(T, j)
+                    if M <= 0:
+                        continue
+                    out = np.zeros(M, np.int64)
+                    segs = np.zeros(M, np.int32)
+                    cur = hc.hc_move_costs(acc64, nw, T, _p(D), _p(R), _p(costs), _p(gm),
+                                           _p(gr), j, _p(out), _p(segs))
+                    assert cur == oracle.decode_row(inst, 0, gm, gr)[0], name
+                    ref = oracle.move_costs(inst, gm[None, :], gr[None, :], j)
+                    np.testing.assert_array_equal(out, ref, err_msg=f"{name} j={j}")
+                    win = [oracle.move_window(inst, 0, gm, gr, j, m) for m in range(M)]
+                    np.testing.assert_array_equal(segs, win, err_msg=f"{name} j={j}")
