@@ -62,22 +62,24 @@ def tune_batch(insts, probe_iters: int = 10, candidates=None, cache_file: str | 
     if hit:
         return hit
     seeds = np.arange(len(insts), dtype=np.uint64)
-    best, best_rate = None, -1.0
+    best, best_rate, err = None, -1.0, None
     for cand in candidates or BATCH_CANDIDATES:
-        b = Batch(insts, lanes=cand["lanes"], threads=cand["threads"], cluster=cand["cluster"])
+        b = None
         try:
+            b = Batch(insts, lanes=cand["lanes"], threads=cand["threads"],
+                      cluster=cand["cluster"])
             b.run(seeds, 1, 3, 0)  # warm-up (kernel attributes, first touch)
             b.results()
             ms, _ = _timed(lambda: b.run(seeds, probe_iters, 3, 0))
             rate = sum(r["moves_evaluated"] for r in b.results()) / ms
-        except Exception:
-            rate = -1.0
+        except Exception as e:  # a shape this device or batch cannot run
+            rate, err = -1.0, e
         finally:
-            b.close()
+            if b is not None:
+                b.close()
         if rate > best_rate:
             best, best_rate = dict(cand), rate
-    _store(key, best, cache_file)
-    return best
+    return _chosen(key, best, err, cache_file)
 
 
 def tune_single(inst, probe_iters: int = 100, candidates=None, cache_file: str | None = None):
@@ -86,18 +88,29 @@ def tune_single(inst, probe_iters: int = 100, candidates=None, cache_file: str |
     hit = _lookup(key, cache_file)
     if hit:
         return hit
-    best, best_rate = None, -1.0
+    best, best_rate, err = None, -1.0, None
     for cand in candidates or SINGLE_CANDIDATES:
-        with Solver(inst, lanes=cand["lanes"], cluster=cand["cluster"],
-                    speculation=cand["teams"]) as s:
-            try:
-                s.vns(0, 2, 3, 0, traj=False, solution=False)
-                ms, _ = _timed(lambda: s.vns_run(0, probe_iters, 3, 0))
-                rate = s.result(traj=False, solution=False)["moves_evaluated"] / ms
-            except Exception:
-                rate = -1.0
+        s = None
+        try:
+            s = Solver(inst, lanes=cand["lanes"], cluster=cand["cluster"],
+                       speculation=cand["teams"])
+            s.vns(0, 2, 3, 0, traj=False, solution=False)
+            ms, _ = _timed(lambda: s.vns_run(0, probe_iters, 3, 0))
+            rate = s.result(traj=False, solution=False)["moves_evaluated"] / ms
+        except Exception as e:  # a shape this device or instance cannot run
+            rate, err = -1.0, e
+        finally:
+            if s is not None:
+                s.close()
         if rate > best_rate:
             best, best_rate = dict(cand), rate
+    return _chosen(key, best, err, cache_file)
+
+
+def _chosen(key, best, err, cache_file):
+    """Cache and return the winning shape; no shape that ran is an error."""
+    if best is None:
+        raise RuntimeError(f"autotune: no candidate launch shape ran for {key}") from err
     _store(key, best, cache_file)
     return best
 
