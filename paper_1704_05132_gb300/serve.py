@@ -130,6 +130,14 @@ class Server:
         resident = 0
         stats = ServeStats()
         sizes = {}
+        for r in requests:  # a request that can never be admitted is refused up front
+            key = (r.inst.K, r.inst.T)
+            if key not in sizes:
+                sizes[key] = footprint(*key)
+            if sizes[key][1] > self.mem_budget:
+                raise ValueError(f"request {r.rid} (K={key[0]}, T={key[1]}) needs "
+                                 f"{sizes[key][1]} device bytes, more than the budget of "
+                                 f"{self.mem_budget}")
         t0 = time.perf_counter()
         clock = (lambda: time.perf_counter() - t0) if realtime else (lambda: float("inf"))
         while pending or waiting or inflight:
@@ -158,10 +166,7 @@ class Server:
                 for r in list(waiting):
                     if r.iters != iters or len(take) >= self.max_batch:
                         continue
-                    key = (r.inst.K, r.inst.T)
-                    if key not in sizes:
-                        sizes[key] = footprint(*key)
-                    fb = sizes[key][1]
+                    fb = sizes[(r.inst.K, r.inst.T)][1]
                     if resident + nbytes + fb > self.mem_budget:
                         break
                     take.append(r)
