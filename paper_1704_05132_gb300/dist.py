@@ -70,6 +70,8 @@ def multistart(inst, seed0: int, nstarts: int, iters: int, kmax: int = 3, mode: 
     seeds seed0 .. seed0 + count - 1 and returns (best cost, best local start,
     gM, gR); by default the CUDA engine (Solver.multistart).  Returns
     (best cost, best global start, gM, gR) on every rank."""
+    if not 1 <= nstarts < (1 << KEY_INDEX_BITS):
+        raise ValueError(f"nstarts must be in 1 .. {(1 << KEY_INDEX_BITS) - 1}")
     import torch.distributed as dist
     rank, world = dist.get_rank(group), dist.get_world_size(group)
     lo, hi = shard(nstarts, rank, world)

@@ -35,6 +35,16 @@ def test_pack_shard_helpers():
         assert max(h - l for l, h in parts) - min(h - l for l, h in parts) <= 1
 
 
+def test_start_count_checked_before_any_collective():
+    """No starts (or more than the 24-bit start index holds) is refused on
+    the host, before a process group is even needed."""
+    from paper_1704_05132_gb300 import gen
+    inst = gen.plain_small()
+    for n in (0, -1, 1 << 24):
+        with pytest.raises(ValueError, match="nstarts"):
+            D.multistart(inst, 0, n, 10)
+
+
 def _oracle_solve(inst, seed0, count, iters, kmax, mode):
     import oracle
     best, res = oracle.multistart(oracle.Instance.from_arrays(inst),
