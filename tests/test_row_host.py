@@ -255,3 +255,44 @@ def test_degenerate_rows_match_oracle(hc, T):
                     np.testing.assert_array_equal(out, ref, err_msg=f"{name} j={j}")
                     win = [oracle.move_window(inst, 0, gm, gr, j, m) for m in range(M)]
                     np.testing.assert_array_equal(segs, win, err_msg=f"{name} j={j}")
+
+
+def _golden(name):
+    rows = []
+    with open(os.path.join(HERE, "golden", name)) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                rows.append([c.strip() for c in line.split("|")])
+    return rows
+
+
+def _golden_rows():
+    """(name, D, R, [kM, kR, hM, hR, pM, pR], gM, gR, cost) of every hand-derived
+    worked example, with and without unit production costs."""
+    base = {r[0]: r for r in _golden("worked_examples.txt")}
+    out = []
+    for name, D, R, c, gm, gr, cost, *_ in base.values():
+        out.append((name, D, R, c.split() + ["0", "0"], gm, gr, cost))
+    for name, b, pc, _, _, cost in _golden("worked_examples_production.txt"):
+        _, D, R, c, gm, gr, *_ = base[b]
+        out.append((name, D, R, c.split() + pc.split(), gm, gr, cost))
+    return out
+
+
+@pytest.mark.parametrize("row", _golden_rows(), ids=lambda r: r[0])
+def test_kernel_row_cost_equals_hand_derivation(hc, row):
+    """The kernels' row arithmetic gives each hand-derived example's cost
+    directly (no oracle in between), with 32- and 64-bit accumulators and one
+    or two words per bit row."""
+    name, D, R, c, gm, gr, cost = row
+    as_i32 = lambda s: np.array([int(v) for v in s.split()], np.int32)
+    D, R, gm, gr = as_i32(D), as_i32(R), as_i32(gm).astype(np.uint8), as_i32(gr).astype(np.uint8)
+    costs = np.array([int(v) for v in c], np.int32)
+    T = len(D)
+    want = oracle.INF if cost == "INF" else int(cost)
+    for acc64, nw in [(0, 1), (1, 1), (0, 2), (1, 2)]:
+        out = np.zeros(T, np.int64)
+        segs = np.zeros(T, np.int32)
+        got = hc.hc_move_costs(acc64, nw, T, _p(D), _p(R), _p(costs), _p(gm), _p(gr), 1,
+                               _p(out), _p(segs))
+        assert got == want, (name, acc64, nw)
