@@ -296,3 +296,56 @@ def test_kernel_row_cost_equals_hand_derivation(hc, row):
         got = hc.hc_move_costs(acc64, nw, T, _p(D), _p(R), _p(costs), _p(gm), _p(gr), 1,
                                _p(out), _p(segs))
         assert got == want, (name, acc64, nw)
+
+
+def test_random_rows_property(hc):
+    """Randomised rows (any T up to 128, zero or large costs, returns below
+    or above demand, production costs of either sign of pR - pM, any setup
+    pattern): the kernels' per-move costs and decode-step counts equal the
+    oracle's.  Runs where hypothesis is installed."""
+    hyp = pytest.importorskip("hypothesis")
+    st = pytest.importorskip("hypothesis.strategies")
+
+    @hyp.settings(max_examples=150, deadline=None, derandomize=True,
+                  suppress_health_check=list(hyp.HealthCheck))
+    @hyp.given(T=st.integers(1, 128), seed=st.integers(0, 2**32 - 1),
+               kind=st.sampled_from(["plain", "zero_costs", "returns_above", "production",
+                                     "sparse_demand"]))
+    def check(T, seed, kind):
+        rng = np.random.default_rng(seed)
+        D = rng.integers(0, 101, T).astype(np.int32)
+        if kind == "sparse_demand":
+            D[rng.random(T) < 0.7] = 0
+        R = (D * rng.integers(200, 601, T) // 1000).astype(np.int32)
+        if kind == "returns_above":
+            R = (D + rng.integers(0, 40, T)).astype(np.int32)
+        c = [int(rng.integers(0, 501)), int(rng.integers(0, 401)), int(rng.integers(0, 7)),
+             int(rng.integers(0, 4)), 0, 0]
+        if kind == "zero_costs":
+            c[int(rng.integers(0, 4))] = 0
+            c[int(rng.integers(0, 4))] = 0
+        if kind == "production":
+            c[4], c[5] = int(rng.integers(0, 200)), int(rng.integers(0, 200))
+        inst = oracle.Instance(D[None, :], R[None, :], [c[0]], [c[1]], [c[2]], [c[3]],
+                               [c[4]], [c[5]])
+        costs = np.array(c, np.int32)
+        gm = (rng.random(T) < rng.uniform(0.05, 0.9)).astype(np.uint8)
+        gr = (rng.random(T) < rng.uniform(0.05, 0.9)).astype(np.uint8)
+        if rng.random() < 0.6:
+            gm[0] = 1
+        acc64 = int(rng.integers(0, 2))
+        nw = 2 if T > 64 else int(rng.integers(1, 3))
+        for j in (1, 2, 3):
+            M = oracle.row_moves(T, j)
+            if M <= 0:
+                continue
+            out = np.zeros(M, np.int64)
+            segs = np.zeros(M, np.int32)
+            cur = hc.hc_move_costs(acc64, nw, T, _p(D), _p(R), _p(costs), _p(gm), _p(gr), j,
+                                   _p(out), _p(segs))
+            assert cur == oracle.decode_row(inst, 0, gm, gr)[0]
+            np.testing.assert_array_equal(out, oracle.move_costs(inst, gm[None, :], gr[None, :], j))
+            win = [oracle.move_window(inst, 0, gm, gr, j, m) for m in range(M)]
+            np.testing.assert_array_equal(segs, win)
+
+    check()
