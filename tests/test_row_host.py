@@ -21,10 +21,17 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(ROOT, "paper_1704_05132_gb300", "csrc")
 
 
+# Set by tests/test_row_host_sanitized.py, which reruns this file with the
+# harness built under AddressSanitizer and UBSan.
+SANITIZE = os.environ.get("ELSR_HC_SANITIZE") == "1"
+
+
 @pytest.fixture(scope="module")
 def hc(tmp_path_factory):
     out = str(tmp_path_factory.mktemp("hc") / "hc.so")
-    subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC",
+    opt = (["-O1", "-g", "-fno-omit-frame-pointer", "-fsanitize=address,undefined",
+            "-fno-sanitize-recover=all"] if SANITIZE else ["-O2"])
+    subprocess.check_call(["g++"] + opt + ["-std=c++17", "-shared", "-fPIC",
                            "-I", CSRC, os.path.join(HERE, "host_row_check.cpp"),
                            "-o", out])
     lib = ctypes.CDLL(out)
