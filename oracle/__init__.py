@@ -30,7 +30,10 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "elsr_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
-_LIB_PATH = os.path.join(_BUILD, "libelsr_oracle.so")
+# ELSR_ORACLE_SANITIZE=1 (set by tests/test_host_sanitized.py) builds and
+# loads a separate copy under AddressSanitizer and UBSan.
+_SANITIZE = os.environ.get("ELSR_ORACLE_SANITIZE") == "1"
+_LIB_PATH = os.path.join(_BUILD, "libelsr_oracle_san.so" if _SANITIZE else "libelsr_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
@@ -44,7 +47,9 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC",
+    opt = (["-O1", "-g", "-fno-omit-frame-pointer", "-fsanitize=address,undefined",
+            "-fno-sanitize-recover=all"] if _SANITIZE else ["-O2"])
+    subprocess.check_call(["gcc"] + opt + ["-std=c11", "-shared", "-fPIC",
                            "-Wall", "-Wextra", "-o", tmp, _SRC])
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH

@@ -21,7 +21,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(ROOT, "paper_1704_05132_gb300", "csrc")
 
 
-# Set by tests/test_row_host_sanitized.py, which reruns this file with the
+# Set by tests/test_host_sanitized.py, which reruns this file with the
 # harness built under AddressSanitizer and UBSan.
 SANITIZE = os.environ.get("ELSR_HC_SANITIZE") == "1"
 
