@@ -22,13 +22,15 @@ thread_local std::string g_create_error;
 
 const int kVndCap = 1 << 20;
 
-#define ELSR_TRY_CUDA(obj, call)                                          \
-  do {                                                                    \
-    cudaError_t e_ = (call);                                              \
-    if (e_ != cudaSuccess) {                                              \
-      (obj)->err = std::string(#call) + ": " + cudaGetErrorString(e_);    \
-      return ELSR_E_CUDA;                                                 \
-    }                                                                     \
+// A failed CUDA call sets the handle's message and returns ELSR_E_NOMEM for
+// a failed allocation, else ELSR_E_CUDA.
+#define ELSR_TRY_CUDA(obj, call)                                               \
+  do {                                                                         \
+    cudaError_t e_ = (call);                                                   \
+    if (e_ != cudaSuccess) {                                                   \
+      (obj)->err = std::string(#call) + ": " + cudaGetErrorString(e_);         \
+      return e_ == cudaErrorMemoryAllocation ? ELSR_E_NOMEM : ELSR_E_CUDA;     \
+    }                                                                          \
   } while (0)
 
 // Device memory is stream-ordered (cudaMallocAsync / cudaFreeAsync on the
