@@ -578,3 +578,18 @@ def test_ties_go_to_the_lowest_index():
     assert pc3.tolist() == [2 * kM, 2 * kM] and pm3.tolist() == [2 * T, 2 * T]
     bc3, bm3, _, _, _ = oracle.eval_neighbourhood(inst, gm, gr, 4, 1)
     assert (bc3, bm3) == (4 * kM, 2 * 2 * T)
+
+
+def test_multistart_best_is_lowest_start_among_ties():
+    """Repeated seeds give identical starts, so costs tie exactly; the
+    best-of must be the lexicographic (cost, start) minimum: never above any
+    start's cost, and the first of equal starts."""
+    inst = oracle.Instance.from_arrays(gen.make_instance(0, 3, K=6, T=14))
+    seeds = [7, 2, 7, 2, 9]
+    best, res = oracle.multistart(inst, seeds, iters=20, kmax=3, mode=0)
+    costs = [r.best_cost for r in res]
+    assert costs[0] == costs[2] and costs[1] == costs[3]
+    assert res[0].traj_hash == res[2].traj_hash
+    assert costs[best] == min(costs)
+    assert best == costs.index(min(costs))       # the first start of that cost
+    assert best in (0, 1, 4)
