@@ -1,8 +1,12 @@
-"""bench.py's reference arm on the CPU: the oracle, as it stands, timed on
-one host core on a bounded sample of the benchmark workload.  Its JSON line
-carries the same metric, unit, direction and workload as the GPU arm, a
-cpu_baseline describing the run and an e2e entry with no host-device bytes;
-under a multi-rank launch only rank 0 runs and prints."""
+"""bench.py host logic on the CPU.
+
+* The reference arm: the oracle, as it stands, timed on one host core on a
+  bounded sample of the benchmark workload.  Its JSON line carries the same
+  metric, unit, direction and workload as the GPU arm, a cpu_baseline
+  describing the run and an e2e entry with no host-device bytes; under a
+  multi-rank launch only rank 0 runs and prints.
+* The clock record: sampled nvidia-smi lines summarised into the line's
+  `clocks` entry (median SM clock, maximum, throttle reasons seen)."""
 import importlib.util
 import json
 import os
@@ -48,3 +52,26 @@ def test_reference_arm_other_ranks_exit_quietly():
              RANK="1", LOCAL_RANK="1", WORLD_SIZE="2")
     assert r.returncode == 0, r.stderr[-2000:]
     assert not [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+
+
+def test_clock_summary_parses_throttle_reasons(tmp_path):
+    """The sampled nvidia-smi lines become the line's `clocks` entry: median
+    SM clock under load, the maximum clock, and every throttle reason seen
+    active at any sample."""
+    b = _bench_module()
+    csv = tmp_path / "clocks.csv"
+    csv.write_text(
+        "0, 2070, 2070, 850.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n"
+        "0, 1980, 2070, 1390.5, 0x0000000000000004, Not Active, Not Active, Not Active, Active\n"
+        "0, 2070, 2070, 900.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n"
+        "0, 1500, 2070, 1400.0, 0x0000000000000008, Active, Not Active, Not Active, Not Active\n"
+        "garbage line\n")
+    s = b.ClockSampler(0)
+    s.proc, s.path = object(), str(csv)
+    out = s.summary()
+    assert out["samples"] == 4 and out["sm_max_mhz"] == 2070.0
+    assert out["sm_mhz"] == 2025.0                       # median of 2070, 1980, 2070, 1500
+    assert out["reasons"] == ["hw_slowdown", "sw_power_cap"]
+    assert not os.path.exists(csv)                       # the sample file is removed
+    empty = b.ClockSampler(0)
+    assert empty.summary()["reasons"] == ["unsampled"]   # nvidia-smi could not start
