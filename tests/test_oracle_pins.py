@@ -593,3 +593,77 @@ def test_multistart_best_is_lowest_start_among_ties():
     assert costs[best] == min(costs)
     assert best == costs.index(min(costs))       # the first start of that cost
     assert best in (0, 1, 4)
+
+
+def test_move_costs_recomposed_from_apply_and_decode():
+    """Each entry of move_costs is the decode of the row after that move,
+    through the separately pinned apply_move and decode_row, in the layout
+    k * |row moves| + local."""
+    rng = np.random.default_rng(21)
+    inst = oracle.Instance.from_arrays(gen.make_instance(13, 2, K=3, T=9))
+    K, T = inst.K, inst.T
+    for _ in range(4):
+        gm = (rng.random((K, T)) < 0.5).astype(np.uint8)
+        gr = (rng.random((K, T)) < 0.5).astype(np.uint8)
+        gm[:, 0] = 1
+        for j in (1, 2, 3):
+            c = oracle.move_costs(inst, gm, gr, j)
+            per = oracle.row_moves(T, j)
+            assert len(c) == oracle.nb_size(K, T, j) == K * per
+            for m in range(len(c)):
+                a, b = gm.copy(), gr.copy()
+                oracle.apply_move(K, T, j, m, a, b)
+                k = m // per
+                changed = np.flatnonzero((a != gm).any(1) | (b != gr).any(1))
+                assert set(changed.tolist()) <= {k}
+                assert c[m] == oracle.decode_row(inst, k, a[k], b[k])[0]
+
+
+def _sat(*xs):
+    s = 0
+    for x in xs:
+        s = INF if (s == INF or x == INF) else s + x
+    return s
+
+
+@pytest.mark.parametrize("mask", [1, 2, 4, 5, 7])
+def test_eval_neighbourhood_recomposed_from_move_costs(mask):
+    """Algorithm 1's best-neighbour search, recomposed: per product the
+    lexicographic (cost, combined local index) minimum; mode P's objective
+    after every strictly improving product applies its move, and the count
+    of such products; mode G's lexicographic (objective, combined global
+    index) minimum over all moves, the objective being the saturating sum of
+    the other rows plus the moved row."""
+    rng = np.random.default_rng(mask)
+    inst = oracle.Instance.from_arrays(gen.make_instance(14, mask, K=4, T=8))
+    K, T = inst.K, inst.T
+    for trial in range(5):
+        gm = (rng.random((K, T)) < 0.5).astype(np.uint8)
+        gr = (rng.random((K, T)) < 0.5).astype(np.uint8)
+        if trial % 2 == 0:
+            gm[:, 0] = 1
+        total, rc = oracle.total_cost(inst, gm, gr)
+        blocks, offs_local, offs_global, lo, go = [], [], [], 0, 0
+        for j in (1, 2, 3):
+            per = oracle.row_moves(T, j)
+            if mask & (1 << (j - 1)):
+                blocks.append((oracle.move_costs(inst, gm, gr, j).reshape(K, per), lo, go))
+            lo += per
+            go += K * per
+        want_pc, want_pm = [], []
+        for k in range(K):
+            cands = [(int(c[k, l]), off + l) for c, off, _ in blocks for l in range(c.shape[1])]
+            best = min(cands)
+            want_pc.append(best[0])
+            want_pm.append(best[1])
+        imp = [k for k in range(K) if want_pc[k] < rc[k]]
+        others = [[rc[q] for q in range(K) if q != k] for k in range(K)]
+        want_p = _sat(*[want_pc[k] if k in imp else rc[k] for k in range(K)])
+        gcands = [(_sat(int(c[k, l]), *others[k]), goff + k * c.shape[1] + l)
+                  for c, _, goff in blocks for k in range(K) for l in range(c.shape[1])]
+        bc_p, bm_p, pc, pm, n = oracle.eval_neighbourhood(inst, gm, gr, mask, 0)
+        assert pc.tolist() == want_pc and pm.tolist() == want_pm
+        assert (bc_p, bm_p) == (want_p, len(imp))
+        assert n == sum(c.size for c, _, _ in blocks)
+        bc_g, bm_g, _, _, _ = oracle.eval_neighbourhood(inst, gm, gr, mask, 1)
+        assert (bc_g, bm_g) == min(gcands)
