@@ -667,3 +667,85 @@ def test_eval_neighbourhood_recomposed_from_move_costs(mask):
         assert n == sum(c.size for c, _, _ in blocks)
         bc_g, bm_g, _, _, _ = oracle.eval_neighbourhood(inst, gm, gr, mask, 1)
         assert (bc_g, bm_g) == min(gcands)
+
+
+def _vnd_replay(inst, gm, gr, mode):
+    """Algorithm 1's pipe VND step by step from the pinned evaluation and
+    apply: for j = 1..3 evaluate N_j alone; mode P applies every product's
+    best move that strictly improves its row, mode G the single best move
+    when it lowers the objective; stop after a sweep without improvement."""
+    K, T = inst.K, inst.T
+    gm, gr = gm.copy(), gr.copy()
+    loff = {1: 0, 2: T, 3: 2 * T}                  # combined local offsets
+    goff = {1: 0, 2: K * T, 3: 2 * K * T}          # combined global offsets
+    cnt = dict(vnd_cycles=0, evals=0, moves_evaluated=0, applied=0)
+    while True:
+        cnt["vnd_cycles"] += 1
+        improved = False
+        for j in (1, 2, 3):
+            per = oracle.row_moves(T, j)
+            total, rc = oracle.total_cost(inst, gm, gr)
+            bc, bm, pc, pm, n = oracle.eval_neighbourhood(inst, gm, gr, 1 << (j - 1), mode)
+            cnt["evals"] += 1
+            cnt["moves_evaluated"] += n
+            if mode == 0:
+                for k in range(K):
+                    if pc[k] < rc[k]:
+                        oracle.apply_move(K, T, j, k * per + int(pm[k]) - loff[j], gm, gr)
+                        cnt["applied"] += 1
+                        improved = True
+            elif bc < total:
+                oracle.apply_move(K, T, j, bm - goff[j], gm, gr)
+                cnt["applied"] += 1
+                improved = True
+        if not improved:
+            return gm, gr, cnt
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_vnd_replayed_from_evaluation_and_apply(mode):
+    rng = np.random.default_rng(40 + mode)
+    inst = oracle.Instance.from_arrays(gen.make_instance(15, mode, K=4, T=11))
+    starts = [oracle.initial_solution(inst.K, inst.T)]
+    for _ in range(3):
+        gm = (rng.random((inst.K, inst.T)) < 0.5).astype(np.uint8)
+        gr = (rng.random((inst.K, inst.T)) < 0.5).astype(np.uint8)
+        gm[:, 0] = 1
+        starts.append((gm, gr))
+    for gm, gr in starts:
+        wm, wr, wc = _vnd_replay(inst, gm, gr, mode)
+        om, orr, oc = oracle.vnd(inst, gm, gr, mode)
+        np.testing.assert_array_equal(om, wm)
+        np.testing.assert_array_equal(orr, wr)
+        for key, v in wc.items():
+            assert oc[key] == v, key
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_gvns_replayed_from_shake_vnd_and_objective(mode):
+    """Algorithm 2 (reading 7) step by step from the pinned Shake, VND and
+    objective: every trajectory entry (k, f(x''), accepted), the final x and
+    f(x) equal the oracle's run."""
+    inst = oracle.Instance.from_arrays(gen.make_instance(16, mode, K=4, T=10))
+    K, T, seed, iters, kmax = inst.K, inst.T, 11, 60, 3
+    gm, gr = oracle.initial_solution(K, T)
+    gm, gr, _ = oracle.vnd(inst, gm, gr, mode)
+    fx, k = oracle.total_cost(inst, gm, gr)[0], 1
+    want = []
+    for it in range(iters):
+        a, b = gm.copy(), gr.copy()
+        oracle.shake(K, T, a, b, seed, it, k)
+        a, b, _ = oracle.vnd(inst, a, b, mode)
+        f = oracle.total_cost(inst, a, b)[0]
+        want.append((it, k, f, int(f < fx)))
+        if f < fx:
+            gm, gr, fx, k = a, b, f, 1
+        else:
+            k = k + 1 if k < kmax else 1
+    o = oracle.vns(inst, seed=seed, iters=iters, kmax=kmax, mode=mode)
+    got = [(int(e["it"]), int(e["k"]), int(e["cost"]), int(e["accepted"])) for e in o.traj]
+    assert got == want
+    assert o.best_cost == fx
+    np.testing.assert_array_equal(o.gM, gm)
+    np.testing.assert_array_equal(o.gR, gr)
+    assert any(w[3] for w in want) and not all(w[3] for w in want)
