@@ -749,3 +749,26 @@ def test_gvns_replayed_from_shake_vnd_and_objective(mode):
     np.testing.assert_array_equal(o.gM, gm)
     np.testing.assert_array_equal(o.gR, gr)
     assert any(w[3] for w in want) and not all(w[3] for w in want)
+
+
+def test_objective_is_the_saturating_sum_of_rows():
+    """Section 2's objective: the sum of the independent row costs, with any
+    infeasible row making the whole solution infeasible (INT64_MAX)."""
+    inst = oracle.Instance.from_arrays(gen.make_instance(17, 0, K=5, T=9))
+    K, T = inst.K, inst.T
+    rng = np.random.default_rng(8)
+    seen_inf = seen_fin = False
+    for _ in range(40):
+        gm = (rng.random((K, T)) < 0.5).astype(np.uint8)
+        gr = (rng.random((K, T)) < 0.5).astype(np.uint8)
+        gm[:, 0] = rng.random(K) < 0.85
+        total, rc = oracle.total_cost(inst, gm, gr)
+        rows = [oracle.decode_row(inst, k, gm[k], gr[k])[0] for k in range(K)]
+        assert rc.tolist() == rows
+        if INF in rows:
+            assert total == INF
+            seen_inf = True
+        else:
+            assert total == sum(rows)
+            seen_fin = True
+    assert seen_inf and seen_fin
