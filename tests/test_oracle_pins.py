@@ -758,10 +758,13 @@ def test_objective_is_the_saturating_sum_of_rows():
     K, T = inst.K, inst.T
     rng = np.random.default_rng(8)
     seen_inf = seen_fin = False
-    for _ in range(40):
+    for i in range(40):
         gm = (rng.random((K, T)) < 0.5).astype(np.uint8)
         gr = (rng.random((K, T)) < 0.5).astype(np.uint8)
         gm[:, 0] = rng.random(K) < 0.85
+        if i % 2:   # every row opens with manufacturing, no remanufacture-only setup
+            gm[:, 0] = 1
+            gr &= gm
         total, rc = oracle.total_cost(inst, gm, gr)
         rows = [oracle.decode_row(inst, k, gm[k], gr[k])[0] for k in range(K)]
         assert rc.tolist() == rows
