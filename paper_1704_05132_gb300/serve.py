@@ -130,7 +130,7 @@ class Server:
         resident = 0
         stats = ServeStats()
         sizes = {}
-        for r in requests:  # a request that can never be admitted is refused up front
+        for r in pending:  # a request that can never be admitted is refused up front
             key = (r.inst.K, r.inst.T)
             if key not in sizes:
                 sizes[key] = footprint(*key)

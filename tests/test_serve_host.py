@@ -112,7 +112,7 @@ def test_scheduler_invariants_with_fake_batches(monkeypatch):
     srv.torch = _FakeTorch
     srv.streams = [_FakeStream() for _ in range(3)]
     srv.max_batch = 7
-    stats = serve.Server.run(srv, reqs, realtime=False)
+    stats = serve.Server.run(srv, iter(reqs), realtime=False)   # any iterable
     got = {r.rid: r for r in stats.results}
     assert sorted(got) == list(range(60))
     for q in reqs:
