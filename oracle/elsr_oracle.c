@@ -13,7 +13,9 @@
  *   - Section 2 (problem statement): products k, periods t, setup costs
  *     kM(k), kR(k), holding costs hM(k), hR(k), demand D(k,t), returns
  *     R(k,t); decisions xM, xR (manufactured / remanufactured quantities) and
- *     yM, yR (serviceable / recoverable stock); objective = setup + holding.
+ *     yM, yR (serviceable / recoverable stock); objective = setup + holding,
+ *     plus unit production costs pM(k) * xM + pR(k) * xR when an instance
+ *     gives them (Algorithm 1's signature names p_M, p_R; 0 otherwise).
  *   - Section 3: products are uncoupled, so the objective is a sum of
  *     per-product row costs.
  *   - Algorithm 1 (parallel VND): for each neighbourhood N_k, find each
