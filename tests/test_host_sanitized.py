@@ -13,8 +13,8 @@ error:
   with buffers of exactly the kernels' shared-memory extents (A, C, L: T
   entries; P, Q and the prefix tables: T + 1), against the oracle.
 
-Device sanitizers are not available on the GPU pool; this covers the
-oracle that every parity test trusts and the row code every kernel inlines.
+No device-side sanitizer runs in this suite; this covers the oracle that
+every parity test trusts and the row code every kernel inlines.
 """
 import os
 import subprocess
