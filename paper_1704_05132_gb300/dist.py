@@ -18,21 +18,26 @@ import numpy as np
 KEY_COST_BITS = 40
 KEY_INDEX_BITS = 24
 INF_COST = (1 << KEY_COST_BITS) - 1
+_KEY_BIAS = 1 << 63  # the unsigned 64-bit key, shifted into the int64 range
 
 
 def pack_key(cost: int, start: int) -> int:
-    """(cost, start) -> int64 key ordered lexicographically (INF -> all ones)."""
+    """(cost, start) -> int64 key whose signed order is the lexicographic
+    order of (cost, start): the unsigned key cost << 24 | start (INF -> all
+    cost bits set) minus 2^63, so that every key, the INF sentinel included,
+    fits a signed 64-bit MIN all-reduce."""
     if not 0 <= start < (1 << KEY_INDEX_BITS):
         raise ValueError("start index out of range")
     c = INF_COST if cost >= INF_COST else int(cost)
     if c < 0:
         raise ValueError("negative cost")
-    return (c << KEY_INDEX_BITS) | int(start)
+    return ((c << KEY_INDEX_BITS) | int(start)) - _KEY_BIAS
 
 
 def unpack_key(key: int):
-    c = int(key) >> KEY_INDEX_BITS
-    return ((1 << 63) - 1 if c == INF_COST else c), int(key) & ((1 << KEY_INDEX_BITS) - 1)
+    u = int(key) + _KEY_BIAS
+    c = u >> KEY_INDEX_BITS
+    return ((1 << 63) - 1 if c == INF_COST else c), u & ((1 << KEY_INDEX_BITS) - 1)
 
 
 def shard(nstarts: int, rank: int, world: int):

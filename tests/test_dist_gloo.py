@@ -28,6 +28,13 @@ def test_pack_shard_helpers():
     assert D.unpack_key(D.pack_key(12345, 7)) == (12345, 7)
     assert D.pack_key(5, 9) < D.pack_key(5, 10) < D.pack_key(6, 0)
     assert D.unpack_key(D.pack_key(1 << 62, 3))[0] == (1 << 63) - 1
+    # every key, the empty-rank sentinel and the largest finite cost
+    # included, fits int64 and keeps its order there
+    lo, hi = -(1 << 63), (1 << 63) - 1
+    sentinel = D.pack_key(D.INF_COST, (1 << D.KEY_INDEX_BITS) - 1)
+    big = D.pack_key(D.INF_COST - 1, 0)
+    assert lo <= D.pack_key(0, 0) < big < sentinel <= hi
+    assert D.unpack_key(big) == (D.INF_COST - 1, 0)
     for n, w in [(10, 3), (4096, 8), (3, 4), (1, 2)]:
         parts = [D.shard(n, r, w) for r in range(w)]
         assert parts[0][0] == 0 and parts[-1][1] == n
@@ -88,14 +95,17 @@ def _run(world, nstarts, fail_rank=-1):
     return sorted(out)
 
 
-def test_sharded_bestof_equals_single_process():
+@pytest.mark.parametrize("world,nstarts", [(2, 7), (3, 2)])
+def test_sharded_bestof_equals_single_process(world, nstarts):
+    """Also with fewer starts than ranks: a rank without starts contributes
+    only the sentinel key and still receives the winner's solution."""
     import oracle
     from paper_1704_05132_gb300 import gen
-    nstarts = 7
     inst = gen.make_instance(4, 2, K=3, T=8)
     best, res = oracle.multistart(oracle.Instance.from_arrays(inst),
                                   [100 + i for i in range(nstarts)], 6, 3, 0)
-    out = _run(2, nstarts)
+    out = _run(world, nstarts)
+    assert len(out) == world
     for rank, status, cost, start, gm, gr in out:
         assert status == "ok"
         assert (cost, start) == (res[best].best_cost, best)
