@@ -65,6 +65,10 @@ class ServeStats:
     wall_s: float = 0.0
 
     def summary(self) -> dict:
+        if not self.results:  # an empty request stream
+            return {"requests": 0, "batches": self.batches, "p50_ms": None, "p99_ms": None,
+                    "mean_ms": None, "instances_per_s": 0.0, "moves_per_s": 0.0,
+                    "max_resident_bytes": self.max_resident_bytes, "span_s": 0.0}
         lat = np.array([r.latency for r in self.results]) * 1e3
         moves = sum(r.moves_evaluated for r in self.results)
         first = min(r.arrival for r in self.results)

@@ -128,3 +128,14 @@ def test_scheduler_invariants_with_fake_batches(monkeypatch):
     assert max(sizes) <= 7 and sum(sizes) == 60
     assert stats.batches >= 60 // 7
     assert _FakeBatch.open_max >= 2 and _FakeBatch.open_now == 0   # overlap, then drained
+
+
+def test_empty_request_stream():
+    """No requests: nothing is launched and the summary reports zero
+    throughput and no latency percentiles."""
+    srv = _server(budget=1 << 20)
+    srv.streams = [_FakeStream()]
+    stats = serve.Server.run(srv, [], realtime=False)
+    s = stats.summary()
+    assert stats.results == [] and stats.batches == 0
+    assert s["requests"] == 0 and s["p50_ms"] is None and s["instances_per_s"] == 0.0
