@@ -278,6 +278,9 @@ class Batch:
 
     def __init__(self, insts, stream=None, lanes: int = 0, threads: int = 0,
                  cluster: int = 0):
+        insts = list(insts)
+        if not insts:
+            raise ValueError("a batch needs at least one instance")
         lib = load()
         self._lib = lib
         self.n = len(insts)

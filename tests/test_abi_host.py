@@ -126,3 +126,11 @@ def test_new_entry_points_reject_a_null_handle(lib):
     assert lib.elsr_checkpoint(None, ctypes.byref(ck), None, None) == nat.ELSR_E_ARG
     assert lib.elsr_vns_resume(None, ctypes.byref(ck), gm.ctypes.data_as(P),
                                gm.ctypes.data_as(P), 5) == nat.ELSR_E_ARG
+
+
+def test_empty_batch_refused_before_any_call():
+    """A batch of no instances is refused by the binding with a clear error,
+    before the library is asked for anything."""
+    from paper_1704_05132_gb300 import elsr
+    with pytest.raises(ValueError, match="at least one instance"):
+        elsr.Batch([])
