@@ -37,6 +37,27 @@ def _u8(a) -> np.ndarray:
     return np.ascontiguousarray(a, dtype=np.uint8)
 
 
+def _instance_arrays(inst):
+    """The instance's arrays as contiguous int32, their shapes checked
+    against one another before any pointer reaches the library (which reads
+    K*T and K entries): D, R [K][T]; kM, kR, hM, hR [K]; pM, pR [K] or None."""
+    D, R = _i32(inst.D), _i32(inst.R)
+    if D.ndim != 2 or R.shape != D.shape:
+        raise ValueError(f"D and R must be [K][T] arrays of one shape, got {D.shape}, {R.shape}")
+    K = D.shape[0]
+    rows = []
+    for f in ("kM", "kR", "hM", "hR", "pM", "pR"):
+        v = getattr(inst, f, None)
+        if v is None and f in ("pM", "pR"):
+            rows.append(None)
+            continue
+        a = _i32(v)
+        if a.shape != (K,):
+            raise ValueError(f"{f} must have shape ({K},), got {a.shape}")
+        rows.append(a)
+    return [D, R] + rows[:4], rows[4], rows[5]
+
+
 def _stream_handle(stream) -> int | None:
     if stream is None:
         try:
@@ -56,12 +77,10 @@ class Solver:
 
     def __init__(self, inst, stream=None, lanes: int = 0, threads: int = 0,
                  cluster: int = 0, speculation: int = 0):
+        arrs, pm, pr = _instance_arrays(inst)
         lib = load()
-        self.K, self.T = int(inst.D.shape[0]), int(inst.D.shape[1])
-        arrs = [_i32(inst.D), _i32(inst.R), _i32(inst.kM), _i32(inst.kR),
-                _i32(inst.hM), _i32(inst.hR)]
+        self.K, self.T = int(arrs[0].shape[0]), int(arrs[0].shape[1])
         h = P()
-        pm, pr = getattr(inst, "pM", None), getattr(inst, "pR", None)
         if pm is None and pr is None:
             check(lib.elsr_create(ctypes.byref(h), self.K, self.T, *[_p(a) for a in arrs]), None)
         else:  # unit production costs (Algorithm 1's p_M, p_R)
@@ -281,6 +300,8 @@ class Batch:
         insts = list(insts)
         if not insts:
             raise ValueError("a batch needs at least one instance")
+        for i in insts:
+            _instance_arrays(i)
         lib = load()
         self._lib = lib
         self.n = len(insts)
@@ -325,7 +346,8 @@ class Batch:
 
     def run(self, seeds, iters: int, kmax: int = 3, mode: int = nat.MODE_P):
         s = np.ascontiguousarray(seeds, dtype=np.uint64)
-        assert s.shape == (self.n,)
+        if s.shape != (self.n,):
+            raise ValueError(f"one seed per instance: expected shape ({self.n},), got {s.shape}")
         self._seeds = s
         self._chk(self._lib.elsr_batch_run(self._b, _p(s), iters, kmax, mode))
 

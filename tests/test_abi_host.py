@@ -134,3 +134,22 @@ def test_empty_batch_refused_before_any_call():
     from paper_1704_05132_gb300 import elsr
     with pytest.raises(ValueError, match="at least one instance"):
         elsr.Batch([])
+
+
+def test_binding_checks_array_shapes_before_the_library_reads_them():
+    """The library reads K*T and K entries behind the pointers it is given;
+    the binding refuses arrays of other shapes instead of passing them on."""
+    from paper_1704_05132_gb300 import elsr, gen
+    g = gen.make_instance(1, 1, K=4, T=6)
+    bad = [
+        gen.ElsrInstance(g.D, g.R[:, :5], g.kM, g.kR, g.hM, g.hR),          # R shorter
+        gen.ElsrInstance(g.D[0], g.R[0], g.kM, g.kR, g.hM, g.hR),           # 1-D rows
+        gen.ElsrInstance(g.D, g.R, g.kM[:3], g.kR, g.hM, g.hR),             # kM too short
+        gen.ElsrInstance(g.D, g.R, g.kM, g.kR, g.hM, g.hR[:, None]),        # hR 2-D
+        gen.ElsrInstance(g.D, g.R, g.kM, g.kR, g.hM, g.hR, g.kM[:2], None),  # pM too short
+    ]
+    for b in bad:
+        with pytest.raises(ValueError):
+            elsr.Solver(b)
+        with pytest.raises(ValueError):
+            elsr.Batch([g, b])
