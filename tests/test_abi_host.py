@@ -153,3 +153,53 @@ def test_binding_checks_array_shapes_before_the_library_reads_them():
             elsr.Solver(b)
         with pytest.raises(ValueError):
             elsr.Batch([g, b])
+
+
+class _CaptureLib:
+    """Stands in for the library: records what elsr_create / elsr_create_ex
+    receive, reading the arrays behind the pointers during the call."""
+
+    def __init__(self):
+        self.calls = []
+
+    def _read(self, ptr, n):
+        buf = (ctypes.c_int32 * n).from_address(ptr.value if hasattr(ptr, "value") else ptr)
+        return np.frombuffer(buf, dtype=np.int32).copy()
+
+    def _create(self, name, out, K, T, *ptrs):
+        arrays = [self._read(ptrs[0], K * T).reshape(K, T), self._read(ptrs[1], K * T).reshape(K, T)]
+        arrays += [self._read(p, K) for p in ptrs[2:]]
+        self.calls.append((name, K, T, arrays))
+        return 0
+
+    def elsr_create(self, out, K, T, *ptrs):
+        return self._create("elsr_create", out, K, T, *ptrs)
+
+    def elsr_create_ex(self, out, K, T, *ptrs):
+        return self._create("elsr_create_ex", out, K, T, *ptrs)
+
+    def elsr_set_stream(self, h, s):
+        return 0
+
+    def elsr_destroy(self, h):
+        pass
+
+
+def test_binding_passes_the_instance_in_abi_order(monkeypatch):
+    """Solver hands elsr_create K, T and D, R, kM, kR, hM, hR (and pM, pR to
+    elsr_create_ex) in the order include/elsr.h declares, as int32 copies of
+    the instance's values."""
+    from paper_1704_05132_gb300 import elsr, gen
+    cap = _CaptureLib()
+    monkeypatch.setattr(elsr, "load", lambda: cap)
+    g = gen.make_instance(2, 5, K=3, T=7)
+    gp = gen.with_production_costs(g, 4)
+    for inst, name in ((g, "elsr_create"), (gp, "elsr_create_ex")):
+        s = elsr.Solver(inst)
+        s._h = None   # nothing to destroy in the stand-in
+        got_name, K, T, arrays = cap.calls[-1]
+        assert (got_name, K, T) == (name, 3, 7)
+        fields = ["D", "R", "kM", "kR", "hM", "hR"] + (["pM", "pR"] if inst.pM is not None else [])
+        assert len(arrays) == len(fields)
+        for f, a in zip(fields, arrays):
+            np.testing.assert_array_equal(a, getattr(inst, f), err_msg=f)
