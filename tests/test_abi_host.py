@@ -203,3 +203,49 @@ def test_binding_passes_the_instance_in_abi_order(monkeypatch):
         assert len(arrays) == len(fields)
         for f, a in zip(fields, arrays):
             np.testing.assert_array_equal(a, getattr(inst, f), err_msg=f)
+
+
+class _CaptureBatchLib(_CaptureLib):
+    def _batch(self, name, out, n, Ks_p, Ts_p, *rest):
+        Ks, Ts = self._read(Ks_p, n), self._read(Ts_p, n)
+        cells, rows = int((Ks.astype(np.int64) * Ts).sum()), int(Ks.sum())
+        ptrs = rest[:-1]  # the last argument is the stream
+        arrays = [self._read(ptrs[0], cells), self._read(ptrs[1], cells)]
+        arrays += [self._read(p, rows) for p in ptrs[2:]]
+        self.calls.append((name, n, Ks, Ts, arrays))
+        return 0
+
+    def elsr_batch_create_on(self, out, n, Ks, Ts, *rest):
+        return self._batch("elsr_batch_create_on", out, n, Ks, Ts, *rest)
+
+    def elsr_batch_create_ex(self, out, n, Ks, Ts, *rest):
+        return self._batch("elsr_batch_create_ex", out, n, Ks, Ts, *rest)
+
+    def elsr_batch_destroy(self, b):
+        pass
+
+
+def test_batch_passes_instances_back_to_back(monkeypatch):
+    """Batch hands the library n, Ks, Ts and the instances' arrays one after
+    another ([K_i][T_i] cell blocks, [K_i] row blocks), zeros for the
+    production costs of instances that have none."""
+    from paper_1704_05132_gb300 import elsr, gen
+    cap = _CaptureBatchLib()
+    monkeypatch.setattr(elsr, "load", lambda: cap)
+    insts = [gen.make_instance(3, i, K=k, T=t) for i, (k, t) in enumerate([(2, 5), (4, 3), (1, 9)])]
+    mixed = [insts[0], gen.with_production_costs(insts[1], 6), insts[2]]
+    for batch, name in ((insts, "elsr_batch_create_on"), (mixed, "elsr_batch_create_ex")):
+        b = elsr.Batch(batch)
+        b._b = None
+        got, n, Ks, Ts, arrays = cap.calls[-1]
+        assert (got, n) == (name, 3)
+        assert Ks.tolist() == [2, 4, 1] and Ts.tolist() == [5, 3, 9]
+        cells = ["D", "R"]
+        rows = ["kM", "kR", "hM", "hR"] + (["pM", "pR"] if name.endswith("_ex") else [])
+        for f, a in zip(cells + rows, arrays):
+            if f in cells:
+                want = np.concatenate([getattr(i, f).ravel() for i in batch])
+            else:
+                want = np.concatenate([getattr(i, f) if getattr(i, f) is not None
+                                       else np.zeros(i.K, np.int32) for i in batch])
+            np.testing.assert_array_equal(a, want, err_msg=f)
