@@ -412,6 +412,8 @@ int elsr_batch_create_ex(elsr_batch_t **out, int32_t n, const int32_t *Ks,
                          const int32_t *kM, const int32_t *kR,
                          const int32_t *hM, const int32_t *hR,
                          const int32_t *pM, const int32_t *pR, void *stream);
+/* Free the batch and its device memory (stream-ordered on the batch's
+ * stream, after the work already queued there).  NULL is ignored. */
 void elsr_batch_destroy(elsr_batch_t *b);
 
 /* Message of the last failed call on batch b (b NULL: last failed create on
@@ -419,6 +421,10 @@ void elsr_batch_destroy(elsr_batch_t *b);
 const char *elsr_batch_last_error(const elsr_batch_t *b);
 /* As elsr_set_stream, for a batch. */
 int elsr_batch_set_stream(elsr_batch_t *b, void *stream);
+/* As elsr_set_launch, for a batch: lanes_per_row 0 lets every run of the
+ * batch pick its own row-group width (wider for runs with few products);
+ * threads 0 = automatic (up to 1024 per CTA, one CTA per SM).  ELSR_E_ARG
+ * outside the values elsr_set_launch accepts. */
 int elsr_batch_set_launch(elsr_batch_t *b, int32_t lanes_per_row,
                           int32_t threads);
 
