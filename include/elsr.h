@@ -214,12 +214,13 @@ int elsr_cost(elsr_t *h, int64_t *rowcost, int64_t *total);
 /*
  * One best-improvement evaluation of the neighbourhoods in nb_mask (bit j-1
  * selects N_j) at the current solution; nothing is applied.  This is
- * Algorithm 1's "find best neighbour" over every product in one launch.
+ * Algorithm 1's best-neighbour search over every product in one launch.
  *   mode ELSR_MODE_P: pp_cost[k], pp_move[k] = lexicographic minimum of
  *     (new row cost, combined local index) over product k's moves (cost
- *     ELSR_INF / move -1 when the row has none); *best_cost = s - diff, the
- *     objective after every product applies its best move when that move
- *     strictly improves its row; *best_move = number of such products.
+ *     ELSR_INF / move -1 when the row has none); *best_cost = the current
+ *     objective minus the summed improvements, i.e. the objective after
+ *     every product applies its best move when that move strictly improves
+ *     its row; *best_move = number of such products.
  *   mode ELSR_MODE_G: *best_cost, *best_move = lexicographic minimum of
  *     (new objective, combined global index); pp_* as in mode P.
  * Outputs are host pointers and may be NULL.  Adds the moves to the
@@ -283,7 +284,7 @@ int elsr_vns_forkjoin_run(elsr_t *h, uint64_t seed, int32_t iters,
  * Wall-clock budget of the handle's next single runs (elsr_vns_run,
  * elsr_vns_forkjoin_run, elsr_vns_resume), in microseconds from the start
  * of each run on the device; 0 (the default) = none.  This is Algorithm 2's
- * "until t > t_max": the run stops after the first iteration whose VND ends
+ * stopping test on elapsed time: the run stops after the first iteration whose VND ends
  * past the budget (iters stays an upper bound), so its trajectory is a
  * prefix of the unbudgeted run's and elsr_checkpoint / elsr_vns_resume can
  * continue it.  A budgeted sequential run uses one team (no speculation).

@@ -10,7 +10,7 @@ exposes thin ctypes wrappers.  Each wrapper names the passage of Antoniadis &
 Sifaleras (2017) that the C function follows:
 
 * ``decode_row`` / ``total_cost``    -- Section 2 objective and the decode reading
-* ``move_costs`` / ``eval_neighbourhood`` -- Algorithm 1, "find best neighbour"
+* ``move_costs`` / ``eval_neighbourhood`` -- Algorithm 1, best-neighbour search
 * ``vnd``                            -- Algorithm 1 (pipe VND)
 * ``shake`` / ``draw``               -- Algorithm 2, Shake(x, k)
 * ``vns`` / ``multistart``           -- Algorithm 2 (GVNS) and the best-of of Section 3

@@ -235,7 +235,7 @@ void orc_move_costs(const orc_instance *in, const uint8_t *gM,
 }
 
 /* ------------------------------------------------------------------------ */
-/* Best neighbour (Algorithm 1, "find best neighbour" and diff).             */
+/* Best neighbour (Algorithm 1: best-neighbour search and summed gains).    */
 /* ------------------------------------------------------------------------ */
 
 /* Offsets of N_1, N_2, N_3 in the combined (all three neighbourhoods) move
@@ -267,8 +267,9 @@ static int64_t total_with_row(const int64_t *rowcost, int32_t K, int32_t k,
  * Mode P (mode = 0, Algorithm 1): for every product k, the best move of row
  * k is the lexicographic minimum of (new row cost, combined local index);
  * pp_cost[k], pp_move[k] receive it (cost ORC_INF, move -1 when the row has
- * no moves).  *best_cost = s - diff, the objective after every product
- * applies its best move when that move strictly improves its row;
+ * no moves).  *best_cost = the current objective minus the summed
+ * improvements, i.e. the objective after every product applies its best
+ * move when that move strictly improves its row;
  * *best_move = the number of improving products.
  *
  * Mode G (mode = 1, single argmin): the best move over the whole

@@ -5,7 +5,7 @@
 //                 (warp-shuffle scans), for instances too large to stage in
 //                 shared memory.
 //   eval_kernel   one best-improvement evaluation of whole neighbourhoods of
-//                 one instance (Algorithm 1's "find best neighbour" for every
+//                 one instance (Algorithm 1's best-neighbour search for every
 //                 product at once): stage rows in shared memory, build each
 //                 row's cache, delta re-decode every candidate, sub-warp
 //                 argmin per product, global argmin for mode G.

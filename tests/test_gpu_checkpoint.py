@@ -1,5 +1,5 @@
 """Checkpoint / resume of GVNS runs and the wall-clock budget (Algorithm 2's
-"until t > t_max"), against the oracle's uninterrupted runs.
+stopping test on elapsed time), against the oracle's uninterrupted runs.
 
 A run of N iterations, a checkpoint and a resume of M iterations must give
 exactly the oracle's run of N + M iterations: every trajectory entry, the

@@ -6,7 +6,7 @@ Each test names what fixes the expected value: hand-derived worked examples
 initial solution, inventory invariants of Section 2's model, the
 Wagner-Whitin dynamic program (Wagner & Whitin 1958) at K=1, R=0, brute force
 over every setup pattern of tiny instances, and the product separability that
-Section 3 states ("no link exist between the products").
+Section 3 states (the products do not interact).
 """
 import itertools
 import os
