@@ -79,7 +79,7 @@ typedef struct {
     int64_t applied;         /* moves applied by VND (all products) */
     int64_t iterations;      /* GVNS shaking iterations run */
     int64_t accepted;        /* iterations whose VND result replaced x */
-    int64_t segments;        /* decode-window setup segments walked (work) */
+    int64_t segments;        /* decode steps of every evaluated move (work measure) */
     int32_t status;          /* ELSR_OK, ELSR_E_CAP or ELSR_E_TIMEOUT */
     int32_t reserved;
 } elsr_stats_t;
@@ -236,8 +236,11 @@ int elsr_eval_neighbourhood(elsr_t *h, uint32_t nb_mask, int32_t mode,
                             int64_t *pp_cost, int64_t *pp_move);
 
 /* New cost of the moved row for every move of N_nb (global layout, host
- * costs[|N_nb|]); window (nullable, host int32[|N_nb|]) receives the setup
- * segments each delta evaluation walked.  Synchronous. */
+ * costs[|N_nb|]); window (nullable, host int32[|N_nb|]) receives each move's
+ * decode steps: the setup segments of the moved row that a re-decode visits
+ * before its stock on hand equals the row's (relaxed) decode again, up to
+ * the one where it falls short (a work measure, not part of the method).
+ * Synchronous. */
 int elsr_move_costs(elsr_t *h, int32_t nb, int64_t *costs, int32_t *window);
 
 /*

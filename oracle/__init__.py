@@ -98,7 +98,7 @@ def _load():
                 "orc_shake_worker": (None, [i32, i32, P, P, u64, i64, i32, i32]),
                 "orc_vns_forkjoin": (i32, [P, P, P, u64, i32, i32, i32, i32, P, P, P, P]),
                 "orc_initial_solution": (None, [i32, i32, P, P]),
-                "orc_move_window": (i64, [P, i32, P, P, i32, i64]),
+                "orc_decode_steps": (i64, [P, i32, P, P, i32, i64]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(lib, name)
@@ -331,8 +331,10 @@ def multistart(inst: Instance, seeds, iters: int, kmax: int = 3, mode: int = 0):
     return best, results
 
 
-def move_window(inst: Instance, k: int, gM_row, gR_row, j: int, local: int) -> int:
-    """Measurement helper: decode-window segments of one move (see C file)."""
+def decode_steps(inst: Instance, k: int, gM_row, gR_row, j: int, local: int) -> int:
+    """Work measure (not part of the method): setup segments of the moved row
+    that a re-decode visits before the rest of the row is known from the row
+    before the move (defined in ``orc_decode_steps``)."""
     gm = _bits(gM_row, 1, inst.T)
     gr = _bits(gR_row, 1, inst.T)
-    return int(_load().orc_move_window(inst.cref, k, _ptr(gm), _ptr(gr), j, local))
+    return int(_load().orc_decode_steps(inst.cref, k, _ptr(gm), _ptr(gr), j, local))

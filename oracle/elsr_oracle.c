@@ -635,76 +635,93 @@ void orc_initial_solution(int32_t K, int32_t T, uint8_t *gM, uint8_t *gR)
 }
 
 /* ------------------------------------------------------------------------ */
-/* Measurement helper (not part of the method): decode steps of a move.      */
+/* Work measure (not part of the method): decode steps of one move.          */
 /* ------------------------------------------------------------------------ */
 
-/* Per-period decode of one row (same rule as orc_decode_row) recording the
- * recoverable stock yR(t) and the first period where the row falls short
- * (T when feasible). */
 /*
- * Recoverable stock after every period under the decode rule; returns the
- * first period that falls short (T when none).  With `relaxed` set, a
- * remanufacture-only setup that falls short takes all the stock it has and
- * its deficit counts as manufactured, and the decode goes on (demand before
- * the first setup still ends it).
+ * Per-period decode of one row under the decode rule of orc_decode_row,
+ * recording avail[t] = yR(t-1) + R(t), the recoverable stock on hand at every
+ * period it reaches.  Returns the first period at which the row falls short
+ * (T when none).
+ *
+ * With `relaxed` set, a remanufacture-only setup whose stock cannot cover its
+ * need remanufactures all of it and the rest counts as manufactured, and the
+ * decode goes on; demand before the first setup still ends it (there is no
+ * setup to produce it).  For a feasible row both forms are the same decode.
  */
-static int32_t decode_stock_mode(const orc_instance *in, int32_t k, const uint8_t *gM,
-                                 const uint8_t *gR, int64_t *yR, int relaxed)
+static int32_t decode_avail(const orc_instance *in, int32_t k, const uint8_t *gM,
+                            const uint8_t *gR, int relaxed, int64_t *avail_at)
 {
     const int32_t T = in->T;
     const int32_t *D = in->D + (int64_t)k * T, *R = in->R + (int64_t)k * T;
-    int64_t yMp = 0, yRp = 0;
+    int64_t yM_prev = 0, yR_prev = 0;
     for (int32_t t = 0; t < T; ++t) {
-        int64_t avail = yRp + R[t], xm = 0, xr = 0;
+        int64_t avail = yR_prev + R[t], xm = 0, xr = 0;
+        avail_at[t] = avail;
         if (gM[t] || gR[t]) {
             int32_t n = t + 1;
             while (n < T && !(gM[n] || gR[n])) ++n;
-            int64_t need = -yMp;
+            int64_t need = -yM_prev;
             for (int32_t i = t; i < n; ++i) need += D[i];
             if (gR[t]) xr = avail < need ? avail : need;
-            if (gM[t]) xm = need - xr;
-            else if (xr < need) {
+            if (gM[t]) {
+                xm = need - xr;
+            } else if (xr < need) {
                 if (!relaxed) return t;
                 xm = need - xr;
             }
         }
-        int64_t yM = yMp + xm + xr - D[t];
+        int64_t yM = yM_prev + xm + xr - D[t];
         if (yM < 0) return t;
-        yR[t] = avail - xr;
-        yMp = yM;
-        yRp = yR[t];
+        yM_prev = yM;
+        yR_prev = avail - xr;
     }
     return T;
 }
 
-static int32_t decode_stock(const orc_instance *in, int32_t k, const uint8_t *gM,
-                            const uint8_t *gR, int64_t *yR)
+/* Next period after s holding a setup of the row (T when none). */
+static int32_t next_setup(const uint8_t *gM, const uint8_t *gR, int32_t s, int32_t T)
 {
-    return decode_stock_mode(in, k, gM, gR, yR, 0);
+    int32_t n = s + 1;
+    while (n < T && !(gM[n] || gR[n])) ++n;
+    return n;
 }
 
 /*
- * Decode steps an incremental evaluation of one move needs, a work measure
- * used to express throughput as integer operations per second:
- *   - 0 for a move that changes nothing, or whose unchanged prefix already
- *     falls short;
- *   - one step per setup segment of the moved row from s0 (the last period
- *     <= t1 holding a setup before and after the move; else the row's first
- *     setup) while the segment starts at or before t2 (t1..t2 = changed
- *     periods), or up to the end of the row when the row before the move has
- *     demand before its first setup;
- *   - then one step per later gR setup while the recoverable stock entering
- *     it differs between the moved row and the row before the move, the
- *     latter in its relaxed decode (a remanufacture-only setup that falls
- *     short counts its deficit as manufactured and the decode goes on);
- * stopping at the first segment that falls short.
+ * Decode steps of one move: the setup segments of the moved row x' that a
+ * re-decode must visit before the rest of x' is known from the row x before
+ * the move.  It measures work, to express throughput as integer operations
+ * per second; the decode, the objective and the search do not use it.
+ *
+ * Let t1..t2 be the periods the move changes.  Periods before t1 carry the
+ * same bits in x and x', so both decodes agree up to s0, the last period
+ * <= t1 that holds a setup in both rows (the segment starting there ends
+ * differently).  The re-decode starts at a0 = s0, or at the first setup of x'
+ * when there is no such period, and walks x' one setup segment per step:
+ *   - 0 steps when the move changes nothing, when x already falls short
+ *     before s0 (that prefix is common), or when x' has demand before a0;
+ *   - at a setup s > t2 (x and x' have the same setups from t2 on) the walk
+ *     stops without counting s when x' enters s with the recoverable stock
+ *     that x's decode has there: both rows then decode alike to the horizon;
+ *   - otherwise s counts one step, and the walk stops after it when x' falls
+ *     short in the segment starting at s, or at the end of the row.
+ * "x's decode" in the stopping test is its relaxed decode (decode_avail):
+ * it is the decode itself for a feasible x, and it also exists past the
+ * first shortfall of an infeasible x, where the plain decode has stopped.
+ * Once x' enters a setup with that decode's stock, x' repeats it from there
+ * (x' is feasible iff the relaxed decode has no shortfall after that setup),
+ * so no more decoding is needed; without the relaxed form every move of an
+ * infeasible row would be charged a re-decode to the end of the row.  This
+ * only lowers the count.  When x has demand before its first setup neither
+ * form exists, and x' is walked to its end or its first shortfall.
  */
-int64_t orc_move_window(const orc_instance *in, int32_t k, const uint8_t *gM,
-                        const uint8_t *gR, int32_t j, int64_t local)
+int64_t orc_decode_steps(const orc_instance *in, int32_t k, const uint8_t *gM,
+                         const uint8_t *gR, int32_t j, int64_t local)
 {
     const int32_t T = in->T;
-    uint8_t *nm = malloc(T), *nr = malloc(T);
-    int64_t *yo = malloc(sizeof(int64_t) * T), *yn = malloc(sizeof(int64_t) * T);
+    uint8_t *nm = malloc(T > 0 ? T : 1), *nr = malloc(T > 0 ? T : 1);
+    int64_t *ax = malloc(sizeof(int64_t) * (T > 0 ? T : 1));
+    int64_t *ay = malloc(sizeof(int64_t) * (T > 0 ? T : 1));
     int64_t count = 0;
     memcpy(nm, gM, T);
     memcpy(nr, gR, T);
@@ -716,50 +733,33 @@ int64_t orc_move_window(const orc_instance *in, int32_t k, const uint8_t *gM,
             if (t1 < 0) t1 = t;
             t2 = t;
         }
-    if (t1 < 0) goto done;
+    if (t1 < 0) goto done; /* nothing changes */
 
-    int32_t ofail = decode_stock(in, k, gM, gR, yn);
-    decode_stock_mode(in, k, gM, gR, yo, 1);
-    int32_t nfail = decode_stock(in, k, nm, nr, yn);
-    int32_t bad = ofail; /* setup of the failing segment, -1 before any setup */
-    if (ofail < T && !(gM[ofail] || gR[ofail])) bad = -1;
+    int32_t f = decode_avail(in, k, gM, gR, 0, ax);           /* x, plain */
+    int32_t x_alive = decode_avail(in, k, gM, gR, 1, ax) == T; /* x, relaxed */
+    int32_t f2 = decode_avail(in, k, nm, nr, 0, ay);          /* x' */
 
     int32_t s0 = -1;
-    if ((gM[t1] || gR[t1]) && (nm[t1] || nr[t1])) {
-        s0 = t1;
-    } else {
-        for (int32_t t = t1 - 1; t >= 0; --t)
-            if (gM[t] || gR[t]) { s0 = t; break; }
-    }
-    int32_t s;
-    if (s0 >= 0) {
-        if (s0 > bad) goto done;
-        s = s0;
-    } else {
-        s = 0;
-        while (s < T && !(nm[s] || nr[s])) ++s;
-        int64_t dsum = 0;
-        for (int32_t i = 0; i < s; ++i) dsum += in->D[(int64_t)k * T + i];
-        if (dsum > 0) goto done;
-    }
-    while (s < T && (s <= t2 || bad < 0)) {
+    for (int32_t t = t1; t >= 0; --t)
+        if ((gM[t] || gR[t]) && (nm[t] || nr[t])) {
+            s0 = t;
+            break;
+        }
+    if (s0 >= 0 && f < s0) goto done; /* the common prefix falls short */
+    int32_t a0 = s0 >= 0 ? s0 : next_setup(nm, nr, -1, T);
+    if (f2 < a0) goto done; /* demand before the first setup of x' */
+
+    for (int32_t s = a0; s < T;) {
+        if (s > t2 && x_alive && ay[s] == ax[s]) break; /* x' repeats x from s */
         ++count;
-        if (nfail == s) goto done;
-        int32_t n = s + 1;
-        while (n < T && !(nm[n] || nr[n])) ++n;
+        int32_t n = next_setup(nm, nr, s, T);
+        if (f2 >= s && f2 < n) break; /* x' falls short in this segment */
         s = n;
-    }
-    for (int32_t q = s; q < T; ++q) {
-        if (!gR[q]) continue;
-        int64_t d = (q > 0 ? yn[q - 1] : 0) - (q > 0 ? yo[q - 1] : 0);
-        if (d == 0) break;
-        ++count;
-        if (nfail == q) break;
     }
 done:
     free(nm);
     free(nr);
-    free(yo);
-    free(yn);
+    free(ax);
+    free(ay);
     return count;
 }

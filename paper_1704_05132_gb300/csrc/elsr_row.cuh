@@ -370,9 +370,11 @@ ELSR_HD Acc build_row(const int2* tab, int T, const RowCosts& rc,
 
 // Delta re-decode of the row after move `local` of N_j (Section 3's "find
 // the best neighbour" for one candidate).  Returns the new segment sum (Inf
-// when the moved row is infeasible).  steps counts the decode steps: the
-// segments of the changed region, then the gR setups that the stock
-// difference reaches (walked, or located by the binary search).
+// when the moved row is infeasible).  steps counts the decode steps of the
+// move, a work measure: the segments of the changed region, then every setup
+// from s1 on while the moved row enters it with other stock than the row
+// before the move (relaxed decode), up to the one where it falls short; the
+// closed forms below skip most of these setups, the count does not.
 //
 // Changed region: from s0 (the last period <= t1 that is a setup before and
 // after the move) segment by segment while the segment start is <= t2 (to
@@ -498,19 +500,21 @@ ELSR_HD Acc eval_move(const int2* tab, int T, const RowCosts& rc,
   S += cur.S - C1;
   const int r0 = rank_below<NW>(cur.b.r0, cur.b.r1, s1);
   if (delta == 0) return cur.ld >= r0 ? Inf<Acc>::value : S;
+  // setups from s1 through the last one the stock difference reaches
+  const int u_s1 = rank_below<NW>(u0, u1, s1);
   if (delta > 0) {
     // More stock: each later gR setup absorbs up to its room (need minus the
     // stock it had), lowering xM by as much, until delta is used up.  With
     // the prefix sums P (room) and Q (xr_weight*room) the setup z where the
     // rest of delta is absorbed is a binary search, and the cost is closed
-    // form.  The step count is that of the walk: z - r0 + 1 setups (or all
-    // remaining ones when delta is never used up).  A deficit setup after z,
+    // form.  The step count takes every setup from s1 through z (through
+    // the horizon when delta is never used up).  A deficit setup after z,
     // or at z with room left over, still falls short.
     const int32_t P0 = P[r0], Pn = P[cur.nR];
     const Acc Q0 = Q[r0], Qn = Q[cur.nR];
     const int32_t target = P0 + delta;
     if (Pn < target) {
-      steps += cur.nR - r0;
+      steps += rank_below<NW>(u0, u1, T) - u_s1;
       return S - (Qn - Q0);
     }
     // smallest z in [r0, nR) with P[z+1] >= target: the answer stays in
@@ -521,10 +525,10 @@ ELSR_HD Acc eval_move(const int2* tab, int T, const RowCosts& rc,
       lo = P[lo + half] < target ? lo + half : lo;
       n -= half;
     }
-    steps += lo - r0 + 1;
     const int32_t Pz = P[lo], Pz1 = P[lo + 1];
     const Acc Qz = Q[lo];
     const int sz = L[lo].y & 0xFFFF;
+    steps += rank_below<NW>(u0, u1, sz + 1) - u_s1;
     if (cur.ld > lo || (cur.ld == lo && Pz1 != target)) return Inf<Acc>::value;
     return S - (Qz - Q0) - xr_weight<Acc>(rc, T, sz) * (Acc)(target - Pz);
   }
@@ -532,17 +536,24 @@ ELSR_HD Acc eval_move(const int2* tab, int T, const RowCosts& rc,
   // remanufacture-only setup is infeasible, and so is any deficit left).
   // With surplus sg = A - need, xR = need + min(sg, 0), so the change of xR
   // is min(sg + delta, 0) - min(sg, 0).
+  int last = T - 1;  // the difference lasts to the horizon unless it ends
   for (int r = r0; r < cur.nR; ++r) {
     const int2 e = L[r];
     const int sr = e.y & 0xFFFF;
     const int32_t sg = e.x, sn = sg + delta;
-    ++steps;
-    if (!(e.y >> 16) && sn < 0) return Inf<Acc>::value;
+    if (!(e.y >> 16) && sn < 0) {
+      steps += rank_below<NW>(u0, u1, sr + 1) - u_s1;
+      return Inf<Acc>::value;
+    }
     const int32_t dx = (sn < 0 ? sn : 0) - (sg < 0 ? sg : 0);
     S -= (Acc)rc.hR * (Acc)(T - sr) * (Acc)dx - (Acc)rc.dP * (Acc)dx;
     delta -= dx;
-    if (delta == 0) break;
+    if (delta == 0) {
+      last = sr;
+      break;
+    }
   }
+  steps += rank_below<NW>(u0, u1, last + 1) - u_s1;
   return cur.ld >= r0 ? Inf<Acc>::value : S;
 }
 

@@ -1,7 +1,7 @@
 """GPU vs oracle parity through the C ABI (needs a GB300).
 
 Integer work, so every comparison is bit-exact: per-move row costs and
-decode windows, per-product and global argmins, VND results, whole GVNS
+decode steps, per-product and global argmins, VND results, whole GVNS
 trajectories (entry by entry), final solutions, plans and counters.
 """
 import numpy as np
@@ -67,7 +67,7 @@ CASES = [
 
 
 @pytest.mark.parametrize("name,mk", CASES, ids=[c[0] for c in CASES])
-def test_move_costs_and_windows(E, name, mk):
+def test_move_costs_and_decode_steps(E, name, mk):
     g = mk()
     inst = _inst(g)
     rng = np.random.default_rng(len(name))
@@ -84,10 +84,10 @@ def test_move_costs_and_windows(E, name, mk):
                 c, w = s.move_costs(j)
                 np.testing.assert_array_equal(c, oracle.move_costs(inst, gm, gr, j))
                 per = oracle.row_moves(inst.T, j)
-                # windows of a sample of moves, one by one through the oracle
+                # decode steps of a sample of moves, one by one through the oracle
                 for m in rng.choice(len(c), size=min(len(c), 40), replace=False):
                     k, l = divmod(int(m), per)
-                    assert w[m] == oracle.move_window(inst, k, gm[k], gr[k], j, l)
+                    assert w[m] == oracle.decode_steps(inst, k, gm[k], gr[k], j, l)
 
 
 @pytest.mark.parametrize("mode", [0, 1])
@@ -176,25 +176,25 @@ def test_vns_medium_full_trajectory(E):
         c, plan = oracle.decode_row(inst, k, o.gM[k], o.gR[k])
         assert c != INF
         np.testing.assert_array_equal(r["plan"][:, k, :], plan)
-    # windows walked: the sum of per-move decode windows of every evaluation
+    # the step counter: the sum of per-move decode steps of every evaluation
     assert r["segments"] > 0
 
 
-def test_segments_equal_oracle_windows(E):
-    """The kernel's segment counter equals the sum of the oracle's per-move
-    decode windows over every neighbourhood evaluation of a VND."""
+def test_segments_equal_oracle_decode_steps(E):
+    """The kernel's step counter equals the sum of the oracle's per-move
+    decode steps over every neighbourhood evaluation of a VND."""
     g = gen.make_instance(31, 0, K=6, T=20)
     inst = _inst(g)
     gm, gr = oracle.initial_solution(inst.K, inst.T)
     total = 0
-    # replay the oracle's mode-P VND, summing windows at each evaluation
+    # replay the oracle's mode-P VND, summing decode steps at each evaluation
     while True:
         imp = False
         for j in (1, 2, 3):
             per = oracle.row_moves(inst.T, j)
             for k in range(inst.K):
                 for l in range(per):
-                    total += oracle.move_window(inst, k, gm[k], gr[k], j, l)
+                    total += oracle.decode_steps(inst, k, gm[k], gr[k], j, l)
             c = oracle.move_costs(inst, gm, gr, j).reshape(inst.K, per)
             _, rc = oracle.total_cost(inst, gm, gr)
             for k in range(inst.K):

@@ -1,5 +1,5 @@
 """Unit production costs pM, pR (Algorithm 1's p_M, p_R) on the GPU vs the
-oracle, bit for bit: per-move row costs and decode windows, neighbourhood
+oracle, bit for bit: per-move row costs and decode steps, neighbourhood
 evaluations in modes P and G, VND, GVNS trajectories (speculative, cluster,
 fork-join and batched launches), with pR - pM of both signs and values large
 enough to need 64-bit row accumulators.

@@ -775,3 +775,90 @@ def test_objective_is_the_saturating_sum_of_rows():
             assert total == sum(rows)
             seen_fin = True
     assert seen_inf and seen_fin
+
+
+# ---------------------------------------------------------------------------
+# Work measure: decode steps of a move (tests/golden/decode_steps.txt).
+# ---------------------------------------------------------------------------
+
+def _decode_steps_rows():
+    rows = []
+    with open(os.path.join(GOLDEN, "decode_steps.txt")) as f:
+        for line in f:
+            if not line.strip() or line.startswith("#"):
+                continue
+            rows.append([c.strip() for c in line.split("|")])
+    return rows
+
+
+@pytest.mark.parametrize("row", _decode_steps_rows(), ids=lambda r: r[0])
+def test_decode_steps_hand_derived(row):
+    """Every N1, N2 and N3 move of the worked-example rows, step counts
+    derived by hand from the Section 2 decode (derivations in the file)."""
+    name, D, R, gM, gR, n1, n2, n3 = row
+    D, R = _ints(D), _ints(R)
+    T = len(D)
+    inst = oracle.Instance(np.array([D]), np.array([R]), [100], [50], [2], [1])
+    gm, gr = np.array(_ints(gM), np.uint8), np.array(_ints(gR), np.uint8)
+    for j, want in ((1, n1), (2, n2), (3, n3)):
+        got = [oracle.decode_steps(inst, 0, gm, gr, j, l) for l in range(oracle.row_moves(T, j))]
+        assert got == _ints(want), (name, j)
+
+
+def _setups(gm, gr, a0):
+    return [t for t in range(max(a0, 0), len(gm)) if gm[t] or gr[t]]
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_decode_steps_stop_where_the_decodes_coincide(seed):
+    """What the count means, checked on the pinned decode's plans: for a
+    feasible row and a feasible move, the walk covers the setups of the moved
+    row from a0 and stops at the first setup after the changed periods from
+    which the moved row's plan (xM, xR, yM, yR) repeats the row's plan; at every
+    counted setup after the changed periods the recoverable stock entering it
+    still differs.  Any move takes at most one step per setup of the moved
+    row from a0, and a move that changes nothing takes none."""
+    rng = np.random.default_rng(500 + seed)
+    checked = 0
+    for trial in range(12):
+        T = int(rng.integers(2, 24))
+        g = gen.make_instance(600 + seed, trial, K=1, T=T)
+        inst = oracle.Instance.from_arrays(g)
+        for _ in range(50):  # a feasible row, so that its plan exists
+            gm = (rng.random(T) < rng.uniform(0.2, 0.9)).astype(np.uint8)
+            gr = (rng.random(T) < rng.uniform(0.2, 0.9)).astype(np.uint8)
+            gm[0] = 1
+            c0, p0 = oracle.decode_row(inst, 0, gm, gr)
+            if c0 != INF:
+                break
+        for j in (1, 2, 3):
+            for l in range(oracle.row_moves(T, j)):
+                nm, nr = gm[None, :].copy(), gr[None, :].copy()
+                oracle.apply_move(1, T, j, l, nm, nr)
+                nm, nr = nm[0], nr[0]
+                steps = oracle.decode_steps(inst, 0, gm, gr, j, l)
+                changed = np.nonzero((nm != gm) | (nr != gr))[0]
+                if len(changed) == 0:
+                    assert steps == 0
+                    continue
+                t1, t2 = int(changed[0]), int(changed[-1])
+                both = [t for t in range(t1 + 1) if (gm[t] or gr[t]) and (nm[t] or nr[t])]
+                s0 = both[-1] if both else -1
+                su = _setups(nm, nr, s0 if s0 >= 0 else 0)
+                assert 0 <= steps <= len(su)
+                c1, p1 = oracle.decode_row(inst, 0, nm, nr)
+                if c0 == INF or c1 == INF or steps == 0:
+                    continue
+                stop = su[steps] if steps < len(su) else T
+                # from the stop on, the moved row's plan is the row's plan
+                assert stop == T or stop > t2
+                np.testing.assert_array_equal(p1[:, stop:], p0[:, stop:])
+                # before it, after the change, the entering stock differed
+                for s in su[:steps]:
+                    if s > t2:
+                        assert s > 0 and p1[3, s - 1] != p0[3, s - 1]
+                # and the stop is the first such setup: stock equal there
+                if stop < T:
+                    assert p1[3, stop - 1] == p0[3, stop - 1]
+                checked += 1
+    assert checked > 200

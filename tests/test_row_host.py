@@ -93,7 +93,7 @@ def test_delta_decode_matches_oracle(hc, T, acc64, nw):
             assert cur == oracle.decode_row(inst, 0, gm, gr)[0]
             ref = oracle.move_costs(inst, gm[None, :], gr[None, :], j)
             np.testing.assert_array_equal(out, ref)
-            win = [oracle.move_window(inst, 0, gm, gr, j, m) for m in range(M)]
+            win = [oracle.decode_steps(inst, 0, gm, gr, j, m) for m in range(M)]
             np.testing.assert_array_equal(segs, win)
 
 
@@ -157,7 +157,7 @@ def test_deficits_fixed_through_the_stock_difference(hc, T):
                 assert cur == oracle.INF
                 np.testing.assert_array_equal(out, oracle.move_costs(inst, gm[None, :], gr[None, :], j))
                 np.testing.assert_array_equal(
-                    segs, [oracle.move_window(inst, 0, gm, gr, j, m) for m in range(M)])
+                    segs, [oracle.decode_steps(inst, 0, gm, gr, j, m) for m in range(M)])
             for m in range(M):
                 nm, nr = gm[None, :].copy(), gr[None, :].copy()
                 oracle.apply_move(1, T, j, m, nm, nr)
@@ -260,7 +260,7 @@ def test_degenerate_rows_match_oracle(hc, T):
                     assert cur == oracle.decode_row(inst, 0, gm, gr)[0], name
                     ref = oracle.move_costs(inst, gm[None, :], gr[None, :], j)
                     np.testing.assert_array_equal(out, ref, err_msg=f"{name} j={j}")
-                    win = [oracle.move_window(inst, 0, gm, gr, j, m) for m in range(M)]
+                    win = [oracle.decode_steps(inst, 0, gm, gr, j, m) for m in range(M)]
                     np.testing.assert_array_equal(segs, win, err_msg=f"{name} j={j}")
 
 
@@ -352,7 +352,7 @@ def test_random_rows_property(hc):
                                    _p(out), _p(segs))
             assert cur == oracle.decode_row(inst, 0, gm, gr)[0]
             np.testing.assert_array_equal(out, oracle.move_costs(inst, gm[None, :], gr[None, :], j))
-            win = [oracle.move_window(inst, 0, gm, gr, j, m) for m in range(M)]
+            win = [oracle.decode_steps(inst, 0, gm, gr, j, m) for m in range(M)]
             np.testing.assert_array_equal(segs, win)
 
     check()
