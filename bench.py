@@ -1,6 +1,6 @@
 """Benchmark of the ELSR VNS hot path on GB300.
 
-Default workload: plain GVNS on one synthetic instance with K=50 products and
+Headline workload: plain GVNS on one synthetic instance with K=50 products and
 T=52 periods (generator seed 1), 2000 shaking iterations, kmax=3, mode P
 (Algorithm 1's product-parallel VND).  One step = one whole GVNS run through
 the C ABI (stage the instance, VND, 2000 x (shake, VND, accept)), i.e. every
@@ -8,11 +8,22 @@ step of the hot path.  Metric: candidate moves evaluated per second (the sum
 over neighbourhood evaluations of |N_j|, counted exactly as the oracle counts
 them); VNS instances/s is reported beside it.
 
+The same JSON line carries `workloads`: the batched forms measured in the same
+run, each with its own CUDA-event timing, clocks, integer roofline and CPU
+baseline on every host core -- `batch` (1024 instances K ~ U{5..100},
+T ~ U{12..52}, 500 iterations each, one persistent launch), `multistart`
+(K=100 x T=104, 4096 starts x 1000 iterations, device best-of) and `serve`
+(a Poisson stream of 2000 requests/s, K ~ U{5..200}, T ~ U{12..104}, 300
+iterations each, p50/p99 latency).  The integer roofline's peak is measured
+on the device (elsr_int_issue_probe) with the SM clock sampled.
+
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+  python bench.py --workload batch|multistart|serve   (one workload's record)
 
 ``--impl reference`` times the CPU oracle (plain single-threaded C) on a
-bounded sample of the same workload.  Under torchrun (N > 1) every rank runs
-independent replicas (one instance, its own seed) and rank 0 prints one line.
+bounded sample of the headline workload.  Under torchrun (N > 1) every rank
+runs independent replicas (one instance, its own seed) and rank 0 prints one
+line.
 """
 from __future__ import annotations
 
@@ -43,8 +54,8 @@ WORKLOAD_PAPER = {
 }
 METRIC = "candidate moves evaluated/s"
 UNIT = "moves/s"
-INT_OPS_PER_SEGMENT = 16      # algorithmic integer operations per decode segment
-SMS, LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
+INT_OPS_PER_STEP = 16         # algorithmic integer operations per decode step
+LANES_PER_SM = 128            # 32-bit integer lanes per SM (4 SMSPs x 32), for context
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -203,6 +214,205 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def measure_int_peak(torch, dev, stream):
+    """Integer-issue peak of this GPU, measured: elsr_int_issue_probe (eight
+    independent chains of add / min / xor / multiply-add per thread, 8 CTAs
+    of 256 threads per SM) timed with CUDA events on `stream` over about a
+    second, the SM clock sampled meanwhile."""
+    import ctypes
+    from paper_1704_05132_gb300 import _native as nat
+    lib = nat.load()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks, iters = sms * 8, 2048
+    src = torch.arange(3, 39, dtype=torch.int32, device=dev)
+    sink = torch.empty(blocks * 256, dtype=torch.int32, device=dev)
+    ops = ctypes.c_int64()
+
+    def launch():
+        nat.check(lib.elsr_int_issue_probe(ctypes.c_void_p(stream.cuda_stream), blocks, iters,
+                                           ctypes.c_void_p(src.data_ptr()),
+                                           ctypes.c_void_p(sink.data_ptr()), ctypes.byref(ops)))
+
+    for _ in range(3):
+        launch()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n = 0
+    with ClockSampler(dev.index or 0) as clk:
+        t_end = time.perf_counter() + 1.0
+        e0.record(stream)
+        while time.perf_counter() < t_end or n < 10:
+            launch()
+            n += 1
+            if n % 8 == 0:
+                stream.synchronize()
+        e1.record(stream)
+        e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    clocks = clk.summary()
+    tops = ops.value * n / (ms / 1e3) / 1e12
+    mhz = clocks.get("sm_mhz")
+    per_clk = tops * 1e12 / (sms * mhz * 1e6) if mhz else None
+    return {"value": tops, "unit": "Tintop/s", "sms": sms, "launches": n, "ms": ms,
+            "ops_per_launch": ops.value, "clocks": clocks,
+            "int_ops_per_sm_per_clock": per_clk,
+            "how": "elsr_int_issue_probe: 8 CTAs x 256 threads per SM, 8 independent chains "
+                   "of add, min, xor, multiply-add per thread; CUDA events over ~1 s"}
+
+
+def roofline_alu(steps, kernel_s, peak, traffic=None, note=""):
+    """Integer roofline of a launch: INT_OPS_PER_STEP ops per decode step."""
+    achieved = INT_OPS_PER_STEP * steps / kernel_s / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak["value"], "unit": "Tintop/s",
+            "frac": achieved / peak["value"], "traffic": traffic,
+            "peak_source": "measured on this GPU (elsr_int_issue_probe, median SM clock "
+                           f"{peak['clocks'].get('sm_mhz')} MHz)",
+            "note": f"{INT_OPS_PER_STEP} int ops per decode step x {steps} decode steps per "
+                    f"launch (device counter, equal to the oracle's definition, taken in a "
+                    f"warm-up launch of the same run; the timed launches, whose trajectory is "
+                    f"the same, run with the counter off) / launch time" +
+                    (f"; {note}" if note else "")}
+
+
+def _timed_steps(torch, stream, step, steps, warmup, flush, dev):
+    """CUDA-event time of each of `steps` calls after `warmup` untimed ones,
+    L2 flushed (untimed) before each, clocks sampled meanwhile."""
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    ms = []
+    with ClockSampler(dev.index or 0) as clk:
+        for _ in range(steps):
+            flush.add_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+    return ms, clk.summary()
+
+
+def bench_batch(torch, dev, stream, flush, peak, steps, warmup, args, cpu=True):
+    """1024 independent instances K ~ U{5..100}, T ~ U{12..52} (seed 0, ids
+    0..1023), 500 iterations each, in one persistent launch per step."""
+    from paper_1704_05132_gb300 import elsr, gen
+    n = args.n or 1024
+    iters = args.iters if args.iters is not None else 500
+    insts = gen.batch_uneven(n)
+    b = elsr.Batch(insts, stream=stream, lanes=args.lanes, threads=args.threads,
+                   cluster=args.cluster)
+    seeds = np.arange(n, dtype=np.uint64)
+    b.run(seeds, iters, 3, 0)          # decode steps counted once, untimed
+    counted = b.results()
+    segs = sum(r["segments"] for r in counted)
+    b.set_count_steps(False)           # the counting launch was the first warm-up
+    ms, clocks = _timed_steps(torch, stream, lambda: b.run(seeds, iters, 3, 0), steps,
+                              max(0, warmup - 1), flush, dev)
+    st = b.results()
+    assert all(r["status"] == 0 for r in st)
+    assert [r["traj_hash"] for r in st] == [r["traj_hash"] for r in counted]
+    moves = sum(r["moves_evaluated"] for r in st)
+    t = sum(ms) / 1e3
+    stage_bytes = sum(4 * (2 * g.K * g.T + 4 * g.K) for g in insts)
+    rec = {"metric": METRIC, "value": moves * steps / t, "unit": UNIT,
+           "instances_per_s": n * steps / t, "ms_per_step": 1e3 * t / steps,
+           "steps": steps, "warmup": warmup, "higher_is_better": True,
+           "config": {"workload": f"batch of {n} instances, K ~ U{{5..100}}, T ~ U{{12..52}}, "
+                                  f"{iters} iterations each, kmax=3, mode P, one persistent "
+                                  "launch", "instances": n, "iters": iters,
+                      "l2": "flushed between steps (256 MiB device write, untimed)"},
+           "moves_per_step": moves, "segments_per_step": segs,
+           "launch_shape": b.launch_shape(), "clocks": clocks, "gpu_launches": steps,
+           "staging": {"bytes": stage_bytes,
+                       "note": "instance bytes read from HBM by the launch (D, R, costs)"},
+           "roofline": roofline_alu(segs, t / steps, peak)}
+    b.close()
+    if cpu and not args.no_cpu_baseline:
+        m = min(n, 64)
+        rec["cpu_baseline"] = cpu_baseline_pool(
+            [("batch", i, i, iters) for i in range(m)],
+            f"the first {m} of the {n} instances, {iters} iterations each")
+    return rec
+
+
+def bench_multistart(torch, dev, stream, flush, peak, steps, warmup, args, cpu=True):
+    """One instance K=100, T=104 (seed 0, id 0), 4096 starts seeded 0..4095,
+    1000 iterations each, best-of reduced on the device; one launch per step."""
+    from paper_1704_05132_gb300 import elsr, gen
+    n = args.n or 4096
+    iters = args.iters if args.iters is not None else 1000
+    g = gen.multistart_large()
+    sv = elsr.Solver(g, stream=stream, lanes=args.lanes, threads=args.threads,
+                     cluster=args.cluster)
+    box = {}
+
+    def step():
+        box["best"] = sv.multistart(0, n, iters, 3, 0)
+
+    step()                             # decode steps counted once, untimed
+    counted = sv.multistart_stats(n)
+    segs = sum(r["segments"] for r in counted)
+    sv.set_count_steps(False)          # the counting launch was the first warm-up
+    ms, clocks = _timed_steps(torch, stream, step, steps, max(0, warmup - 1), flush, dev)
+    st = sv.multistart_stats(n)
+    assert all(r["status"] == 0 for r in st)
+    assert [r["traj_hash"] for r in st] == [r["traj_hash"] for r in counted]
+    moves = sum(r["moves_evaluated"] for r in st)
+    t = sum(ms) / 1e3
+    rec = {"metric": METRIC, "value": moves * steps / t, "unit": UNIT,
+           "instances_per_s": n * steps / t, "ms_per_step": 1e3 * t / steps,
+           "steps": steps, "warmup": warmup, "higher_is_better": True,
+           "config": {"workload": f"multi-start, one instance K=100 x T=104, {n} starts "
+                                  f"(seeds 0..{n - 1}), {iters} iterations each, device "
+                                  "best-of", "starts": n, "iters": iters,
+                      "l2": "flushed between steps (256 MiB device write, untimed)"},
+           "best_of": {"cost": box["best"][0], "start": box["best"][1]},
+           "moves_per_step": moves, "segments_per_step": segs,
+           "launch_shape": sv.launch_shape(), "clocks": clocks, "gpu_launches": 2 * steps,
+           "roofline": roofline_alu(segs, t / steps, peak)}
+    sv.close()
+    if cpu and not args.no_cpu_baseline:
+        m, it_s = 16, min(iters, 200)
+        rec["cpu_baseline"] = cpu_baseline_pool(
+            [("multistart", 0, s, it_s) for s in range(m)],
+            f"starts 0..{m - 1}, {it_s} of the {iters} iterations each")
+    return rec
+
+
+def bench_serve(torch, dev, peak, args, cpu=True):
+    """Poisson arrivals (mean `--rate` requests/s) of instances K ~ U{5..200},
+    T ~ U{12..104} (seed 5, id = request id), 300 iterations each; p50/p99
+    latency (completion - arrival on the host clock) and instances/s."""
+    from paper_1704_05132_gb300 import serve
+    n = args.requests
+    iters = args.iters if args.iters is not None else 300
+    warm = serve.poisson_requests(64, args.rate, iters, seed=5, id0=10 ** 6)
+    serve.Server(slots=args.slots).run(warm, realtime=False)
+    reqs = serve.poisson_requests(n, args.rate, iters, seed=5)
+    srv = serve.Server(slots=args.slots, max_batch=args.max_batch)
+    with ClockSampler(dev.index or 0) as clk:
+        stats = srv.run(reqs)
+    s = stats.summary()
+    rec = {"metric": METRIC, "value": s["moves_per_s"], "unit": UNIT,
+           "instances_per_s": s["instances_per_s"], "offered_per_s": args.rate,
+           "p50_ms": s["p50_ms"], "p99_ms": s["p99_ms"], "mean_ms": s["mean_ms"],
+           "higher_is_better": True,
+           "config": {"workload": f"serving, Poisson arrivals mean {args.rate:g} req/s, "
+                                  f"{n} requests K ~ U{{5..200}}, T ~ U{{12..104}}, "
+                                  f"{iters} iterations each", "requests": n, "iters": iters,
+                      "slots": args.slots, "max_batch": args.max_batch},
+           "batches": s["batches"], "span_s": s["span_s"], "clocks": clk.summary(),
+           "timing": "host clock, arrival to result on the host"}
+    if cpu and not args.no_cpu_baseline:
+        m = 16
+        rec["cpu_baseline"] = cpu_baseline_pool(
+            [("serve", r, r, iters) for r in range(m)],
+            f"requests 0..{m - 1} solved one per core, {iters} iterations each "
+            "(p50_run_s is the oracle's per-request solve time)")
+    return rec
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -247,7 +457,8 @@ def run_gpu(args):
         step()
     st = solver.result(solution=False, traj=False)
     moves_per_step = st["moves_evaluated"]
-    segs_per_step = st["segments"]
+    segs_per_step = st["segments"]       # decode steps, counted in the warm-up run
+    solver.set_count_steps(False)        # the timed runs skip that bookkeeping
 
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -267,6 +478,8 @@ def run_gpu(args):
     torch.cuda.synchronize()
     st2 = solver.result(solution=False, traj=False)
     assert st2["moves_evaluated"] == moves_per_step and st2["status"] == 0
+    assert st2["best_cost"] == st["best_cost"] and st2["traj_hash"] == st["traj_hash"]
+    solver.set_count_steps(True)
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     t_local = sum(step_ms) / 1e3
     t_max = t_local
@@ -313,6 +526,7 @@ def run_gpu(args):
         t0 = time.perf_counter()
         s2 = elsr.Solver(host, stream=stream, lanes=args.lanes, threads=args.threads,
                          cluster=args.cluster, speculation=args.speculation)
+        s2.set_count_steps(False)
         if args.workers:
             s2.vns_forkjoin_run(seed, iters, wl["kmax"], mode, args.workers)
         else:
@@ -330,10 +544,9 @@ def run_gpu(args):
             dist.destroy_process_group()
         return
 
-    peaks = _peaks()
     clocks = clk.summary()
-    peak_ops = SMS * LANES_PER_SM * SM_MAX_MHZ * 1e6
-    achieved_ops = INT_OPS_PER_SEGMENT * segs_per_step / kernel_s
+    peak = measure_int_peak(torch, dev, stream)
+    sms = peak["sms"]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
@@ -350,140 +563,55 @@ def run_gpu(args):
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": args.steps,
         "launch_shape": solver.launch_shape(),
-        "roofline": {"bound": "alu", "achieved": achieved_ops / 1e12, "peak": peak_ops / 1e12,
-                     "unit": "Tintop/s", "frac": achieved_ops / peak_ops, "traffic": None,
-                     "note": f"{INT_OPS_PER_SEGMENT} int ops per decode segment x "
-                             f"{segs_per_step} segments per launch; peak = {SMS} SMs x "
-                             f"{LANES_PER_SM} lanes x {SM_MAX_MHZ:.0f} MHz"},
+        "roofline": roofline_alu(segs_per_step, kernel_s, peak),
+        "int_peak": dict(peak, unit_count_tops=sms * LANES_PER_SM *
+                         (peak["clocks"].get("sm_mhz") or 0) * 1e6 / 1e12,
+                         unit_count_note=f"{sms} SMs x {LANES_PER_SM} lanes x median SM "
+                                         "clock, for context"),
     }
     if not args.no_cpu_baseline and world == 1 and args.instance == "medium" \
             and not args.workers and mode == 0:
         line["cpu_baseline"] = cpu_baseline(args.cpu_iters)
+    if world == 1 and not args.no_workloads and args.instance == "medium" \
+            and not args.workers and mode == 0 and args.iters is None:
+        sub = argparse.Namespace(**vars(args))
+        sub.n, sub.lanes, sub.threads, sub.cluster = 0, 0, 0, 0
+        wsteps, wwarm = max(1, args.steps // 2), min(args.warmup, 3)
+        line["workloads"] = {
+            "batch": bench_batch(torch, dev, stream, flush, peak, wsteps, wwarm, sub),
+            "multistart": bench_multistart(torch, dev, stream, flush, peak,
+                                           min(args.steps, 3), wwarm, sub),
+            "serve": bench_serve(torch, dev, peak, sub),
+        }
+        b, ms_ = line["workloads"]["batch"], line["workloads"]["multistart"]
+        line["workloads"]["note"] = (
+            "instances/s at the workloads' own budgets: plain one run at a time "
+            f"{line['instances_per_s']:.1f}/s (2000 iterations), batch "
+            f"{b['instances_per_s']:.1f}/s (500), multi-start {ms_['instances_per_s']:.1f}/s "
+            "(1000); moves/s compares the forms at equal work")
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
 
 
-def run_batched(args):
-    """Batched workloads (secondary measurements): 'batch' = independent
-    instances K ~ U{5..100}, T ~ U{12..52} (seed 0, ids 0..n-1), one GVNS run
-    each in one persistent launch; 'multistart' = one instance K=100, T=104
-    (seed 0, id 0) with independent starts seeded 0..n-1 and a device best-of.
-    One step = one launch over the whole batch."""
+def run_workload(args):
+    """One batched workload's record as a line of its own (profiling)."""
     import torch
-    from paper_1704_05132_gb300 import build, elsr, gen
+    from paper_1704_05132_gb300 import build
     build.build()
+    torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    peak = measure_int_peak(torch, dev, stream)
     if args.workload == "batch":
-        n = args.n or 1024
-        iters = args.iters if args.iters is not None else 500
-        insts = gen.batch_uneven(n)
-        b = elsr.Batch(insts, stream=stream, lanes=args.lanes, threads=args.threads,
-                       cluster=args.cluster)
-        seeds = np.arange(n, dtype=np.uint64)
-
-        def step():
-            b.run(seeds, iters, 3, 0)
-
-        def stats():
-            return b.results()
-        cfg = {"workload": f"batch of {n} instances, K ~ U{{5..100}}, T ~ U{{12..52}}, "
-                           f"{iters} iterations each, kmax=3, mode P", "instances": n,
-               "iters": iters}
+        rec = bench_batch(torch, dev, stream, flush, peak, args.steps, args.warmup, args)
+    elif args.workload == "multistart":
+        rec = bench_multistart(torch, dev, stream, flush, peak, args.steps, args.warmup, args)
     else:
-        n = args.n or 4096
-        iters = args.iters if args.iters is not None else 1000
-        g = gen.multistart_large()
-        sv = elsr.Solver(g, stream=stream, lanes=args.lanes, threads=args.threads,
-                         cluster=args.cluster)
-        box = {}
-
-        def step():
-            box["best"] = sv.multistart(0, n, iters, 3, 0)
-
-        def stats():
-            return sv.multistart_stats(n)
-        cfg = {"workload": f"multi-start, one instance K=100 x T=104, {n} starts "
-                           f"(seeds 0..{n - 1}), {iters} iterations each, device best-of",
-               "starts": n, "iters": iters}
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    ms = []
-    with ClockSampler(0) as clk:
-        for _ in range(args.steps):
-            flush.add_(1)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            step()
-            e1.record(stream)
-            e1.synchronize()
-            ms.append(e0.elapsed_time(e1))
-    clocks = clk.summary()
-    st = stats()
-    moves_step = sum(r["moves_evaluated"] for r in st)
-    segs_step = sum(r["segments"] for r in st)
-    shape = b.launch_shape() if args.workload == "batch" else sv.launch_shape()
-    t = sum(ms) / 1e3
-    line = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
-            "higher_is_better": True, "dtype": "int32", "data": "synthetic", "config": cfg,
-            "instances_per_s": n * args.steps / t, "launch_shape": shape, "clocks": clocks}
-    line["value"] = moves_step * args.steps / t
-    line["segments_per_step"] = segs_step
-    if args.workload == "multistart":
-        line["best_of"] = box["best"][:2]
-    if not args.no_cpu_baseline:
-        if args.workload == "batch":
-            m = min(n, 64)
-            line["cpu_baseline"] = cpu_baseline_pool(
-                [("batch", i, i, iters) for i in range(m)],
-                f"the first {m} of the {n} instances, {iters} iterations each")
-        else:
-            m, it_s = min(n, 16), min(iters, 200)
-            line["cpu_baseline"] = cpu_baseline_pool(
-                [("multistart", 0, s, it_s) for s in range(m)],
-                f"starts 0..{m - 1}, {it_s} of the {iters} iterations each")
-    print(json.dumps(line), flush=True)
-
-
-def run_serve(args):
-    """Serving workload (secondary measurement): Poisson arrivals (mean
-    `--rate` requests/s) of instances K ~ U{5..200}, T ~ U{12..104} (seed 5,
-    id = request id), 300 iterations each, continuous batching over CUDA
-    streams; p50/p99 latency and instances/s."""
-    import torch
-    from paper_1704_05132_gb300 import build, serve
-    build.build()
-    torch.cuda.set_device(0)
-    n = args.n or 2000
-    iters = args.iters if args.iters is not None else 300
-    warm = serve.poisson_requests(64, args.rate, iters, seed=5, id0=10 ** 6)
-    serve.Server(slots=args.slots).run(warm, realtime=False)
-    reqs = serve.poisson_requests(n, args.rate, iters, seed=5)
-    srv = serve.Server(slots=args.slots, max_batch=args.max_batch)
-    with ClockSampler(0) as clk:
-        stats = srv.run(reqs)
-    s = stats.summary()
-    line = {"metric": METRIC, "value": s["moves_per_s"], "unit": UNIT, "n_gpus": 1,
-            "higher_is_better": True, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": f"serving, Poisson arrivals mean {args.rate:g} req/s, "
-                                   f"{n} requests K ~ U{{5..200}}, T ~ U{{12..104}}, "
-                                   f"{iters} iterations each, {args.slots} stream slots, "
-                                   f"at most {args.max_batch} requests per batch",
-                       "requests": n, "iters": iters},
-            "instances_per_s": s["instances_per_s"], "p50_ms": s["p50_ms"],
-            "p99_ms": s["p99_ms"], "mean_ms": s["mean_ms"], "batches": s["batches"],
-            "span_s": s["span_s"], "clocks": clk.summary()}
-    if not args.no_cpu_baseline:
-        m = min(n, 16)
-        line["cpu_baseline"] = cpu_baseline_pool(
-            [("serve", r, r, iters) for r in range(m)],
-            f"requests 0..{m - 1} solved one per core, {iters} iterations each "
-            "(p50_run_s is the oracle's per-request solve time)")
-    print(json.dumps(line), flush=True)
+        rec = bench_serve(torch, dev, peak, args)
+    rec.update({"n_gpus": 1, "dtype": "int32", "data": "synthetic", "int_peak": peak})
+    print(json.dumps(rec), flush=True)
 
 
 def main():
@@ -496,6 +624,8 @@ def main():
     ap.add_argument("--ref-iters", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="skip the batch / multi-start / serving records of the default run")
     ap.add_argument("--lanes", type=int, default=0, help="lanes per row (0: automatic)")
     ap.add_argument("--threads", type=int, default=0, help="threads per CTA (0: automatic)")
     ap.add_argument("--cluster", type=int, default=0, help="CTAs per run (0: automatic)")
@@ -511,6 +641,7 @@ def main():
     ap.add_argument("--workload", default="plain",
                     choices=["plain", "batch", "multistart", "serve"])
     ap.add_argument("--rate", type=float, default=2000.0, help="serving arrivals per second")
+    ap.add_argument("--requests", type=int, default=2000, help="serving requests")
     ap.add_argument("--slots", type=int, default=4, help="serving stream slots")
     ap.add_argument("--max-batch", type=int, default=304, help="serving requests per batch")
     ap.add_argument("--n", type=int, default=0, help="instances / starts of a batched workload")
@@ -521,10 +652,8 @@ def main():
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         run_reference(args)
-    elif args.workload in ("batch", "multistart"):
-        run_batched(args)
-    elif args.workload == "serve":
-        run_serve(args)
+    elif args.workload != "plain":
+        run_workload(args)
     else:
         run_gpu(args)
 

@@ -195,6 +195,14 @@ int elsr_set_cluster(elsr_t *h, int32_t cluster);
  * multi-start runs have no such barrier. */
 int elsr_set_speculation(elsr_t *h, int32_t teams);
 
+/* Decode-step counter of the GVNS launches (elsr_stats_t.segments; a work
+ * measure with no counterpart in the paper): on = 1 (the default) counts
+ * the decode steps of every evaluated move, on = 0 skips that bookkeeping
+ * (a few population counts per move) and reports segments = 0, e.g. while a
+ * run is timed.  Results and every other counter are the same either way.
+ * ELSR_E_ARG unless on is 0 or 1. */
+int elsr_set_count_steps(elsr_t *h, int32_t on);
+
 /* Launch shape of the last GVNS launch: shape[8] = {lanes per row, threads
  * per block, CTAs per run, blocks, shared bytes per block, prefix tables in
  * shared memory (0/1), 64-bit words per bit row, speculative teams}. */
@@ -368,7 +376,11 @@ int elsr_multistart_run(elsr_t *h, uint64_t seed0, int32_t nstarts,
  * call on each device looks up the array's device address; make that first
  * call before any stream capture.  All calls share the array and it keeps
  * the last call's contents, so calls that may overlap on the device (other
- * streams, other host threads) race on it and must be serialised.
+ * streams, other host threads) race on it and must be serialised.  The
+ * stream and every buffer must belong to the current device (ELSR_E_ARG for
+ * a stream or a device buffer of another device).  A CUDA error that an
+ * earlier call of the caller left pending is reported as ELSR_E_CUDA before
+ * any work is queued, and left pending.
  */
 #define ELSR_STATIC_K_MAX 4096
 #define ELSR_STATIC_BYTES (512 + 48 * ELSR_STATIC_K_MAX)
@@ -437,6 +449,26 @@ int elsr_batch_set_launch(elsr_batch_t *b, int32_t lanes_per_row,
 int elsr_batch_set_cluster(elsr_batch_t *b, int32_t cluster);
 int elsr_batch_launch_shape(elsr_batch_t *b, int32_t *shape);
 
+/* As elsr_set_count_steps, for a batch. */
+int elsr_batch_set_count_steps(elsr_batch_t *b, int32_t on);
+
+/* Instances per CTA of the next batch runs (a launch-shape choice that
+ * changes no result; the paper's Algorithm 1 runs one instance per device).
+ * With runs_per_cta = P > 1, every CTA of the persistent launch first takes
+ * the runs whose rows need more than a P-th of its shared memory (longest
+ * first, one run per CTA), then splits its threads into P partitions, each
+ * running one of the remaining runs with its own barrier, so that small
+ * runs do not leave row groups idle.  Applies to launches of one CTA per run
+ * with at most 32 lanes per row, and when threads per CTA divide into P
+ * partitions of whole warps; otherwise one run per CTA.  0 = automatic
+ * (the library's choice), else a power of two <= 8; ELSR_E_ARG otherwise. */
+int elsr_batch_set_runs_per_cta(elsr_batch_t *b, int32_t runs_per_cta);
+
+/* Packing of the last launch: *runs_per_cta (1 when none) and
+ * *whole_cta_runs, the runs that took a whole CTA before the partitions. */
+int elsr_batch_packing(const elsr_batch_t *b, int32_t *runs_per_cta,
+                       int32_t *whole_cta_runs);
+
 /* Queue GVNS runs of every instance i with seeds[i] (host [n]), from the
  * initial solution.  Asynchronous, like elsr_vns_run. */
 int elsr_batch_run(elsr_batch_t *b, const uint64_t *seeds, int32_t iters,
@@ -448,6 +480,23 @@ int elsr_batch_results(elsr_batch_t *b, elsr_stats_t *stats);
 
 /* Solution of instance i of the last batch run: gM, gR host [K_i][T_i]. */
 int elsr_batch_solution(elsr_batch_t *b, int32_t i, uint8_t *gM, uint8_t *gR);
+
+/*
+ * Integer-issue probe, a measurement aid with no counterpart in the paper:
+ * it measures the denominator of the integer roofline that throughput
+ * figures of the GVNS kernels are compared with.  Queues one launch on
+ * `stream` (a cudaStream_t; NULL = legacy default stream) of `blocks` CTAs
+ * of 256 threads; every thread runs `iters` x 16 steps of eight independent
+ * chains, one step being one 32-bit add, minimum, exclusive-or and
+ * multiply-add.  src: caller-owned device int32[36] of operands (any
+ * values); sink: caller-owned device int32[blocks * 256], overwritten.
+ * *ops (host) receives the integer operations the launch performs, to be
+ * divided by its duration measured on the stream.  Returns without waiting;
+ * ELSR_E_ARG for non-positive sizes or NULL pointers, ELSR_E_CUDA when the
+ * launch fails.
+ */
+int elsr_int_issue_probe(void *stream, int32_t blocks, int32_t iters,
+                         const int32_t *src, int32_t *sink, int64_t *ops);
 
 #ifdef __cplusplus
 }

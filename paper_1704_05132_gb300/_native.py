@@ -107,9 +107,14 @@ SIGNATURES = {
     "elsr_batch_set_launch": (ctypes.c_int, [P, i32, i32]),
     "elsr_batch_set_cluster": (ctypes.c_int, [P, i32]),
     "elsr_batch_launch_shape": (ctypes.c_int, [P, P]),
+    "elsr_batch_set_runs_per_cta": (ctypes.c_int, [P, i32]),
+    "elsr_batch_set_count_steps": (ctypes.c_int, [P, i32]),
+    "elsr_set_count_steps": (ctypes.c_int, [P, i32]),
+    "elsr_batch_packing": (ctypes.c_int, [P, P, P]),
     "elsr_batch_run": (ctypes.c_int, [P, P, i32, i32, i32]),
     "elsr_batch_results": (ctypes.c_int, [P, P]),
     "elsr_batch_solution": (ctypes.c_int, [P, i32, P, P]),
+    "elsr_int_issue_probe": (ctypes.c_int, [P, i32, i32, P, P, P]),
 }
 
 _lock = threading.Lock()

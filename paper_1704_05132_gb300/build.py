@@ -18,7 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libelsr.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["elsr_vns_dispatch.cu", "elsr_kernels.cu", "elsr_abi.cu", "elsr_static.cu"]
+SOURCES = ["elsr_vns_dispatch.cu", "elsr_kernels.cu", "elsr_abi.cu", "elsr_static.cu",
+           "elsr_probe.cu"]
 HEADERS = ["elsr_row.cuh", "elsr_internal.h", "elsr_vns.cuh"]
 # (object suffix, defines) of each GVNS kernel instantiation
 VNS_INST = [(f"i{acc[3:5]}_w{nw}_{'s' if ts else 'g'}{maxt}",

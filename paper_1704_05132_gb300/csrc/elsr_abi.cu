@@ -132,6 +132,9 @@ struct elsr_batch {
   int maxK = 0, maxT = 0;
   bool acc64 = false;
   int lanes = 0, threads = 0, cluster = 0;  // 0 = defaults
+  int parts = 0;                             // runs per CTA (0: automatic)
+  int count_steps = 1;                       // decode-step counter on (1) or off
+  int last_parts = 1, last_whole = 0;        // packing of the last launch
   int spec = 0;                              // speculative teams (0 auto, 1 off)
   int last_shape[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   int sms = 0;
@@ -209,6 +212,15 @@ struct elsr_batch {
 
 namespace {
 
+int default_parts(const elsr_batch* b, int threads, int G) {
+  // Measured on the 1024-instance batch (K ~ U{5..100}, T ~ U{12..52}, 1024
+  // threads): 2 runs per CTA 226 ms, 1 run 260 ms, 4 runs 267 ms, 8 runs
+  // 326 ms.  Packing only pays when there are runs enough to keep every
+  // partition busy.
+  const int64_t nr = (int64_t)b->h_runs.size();
+  return (threads >= 512 && G <= 32 && nr >= 4ll * std::max(1, b->sms)) ? 2 : 1;
+}
+
 int batch_init(elsr_batch* b, int32_t n, const int32_t* Ks, const int32_t* Ts,
                const int32_t* D, const int32_t* R, const int32_t* kM,
                const int32_t* kR, const int32_t* hM, const int32_t* hR,
@@ -265,7 +277,7 @@ int batch_init(elsr_batch* b, int32_t n, const int32_t* Ks, const int32_t* Ts,
   ELSR_TRY_CUDA(b, dev_alloc(&b->d_kR, b->rows, b->stream));
   ELSR_TRY_CUDA(b, dev_alloc(&b->d_hM, b->rows, b->stream));
   ELSR_TRY_CUDA(b, dev_alloc(&b->d_hR, b->rows, b->stream));
-  ELSR_TRY_CUDA(b, dev_alloc(&b->d_queue, 1, b->stream));
+  ELSR_TRY_CUDA(b, dev_alloc(&b->d_queue, 2, b->stream));
   ELSR_TRY_CUDA(b, dev_alloc(&b->d_bestkey, 1, b->stream));
   ELSR_TRY_CUDA(b, cudaMemcpyAsync(b->d_insts, b->insts.data(), n * sizeof(InstDesc), cudaMemcpyHostToDevice, b->stream));
   ELSR_TRY_CUDA(b, cudaMemcpyAsync(b->d_D, D, b->cells * 4, cudaMemcpyHostToDevice, b->stream));
@@ -300,7 +312,51 @@ struct LaunchShape {
   size_t smem;
   int threads, G, cluster, blocks;
   int active;  // resident blocks per SM (cluster 1) or clusters on the device
+  int parts = 1;            // runs per CTA in the partitioned phase
+  int n_whole = 0;          // runs [0, n_whole) take a whole CTA (or cluster)
+  uint32_t part_bytes = 0;  // dynamic shared bytes per partition
 };
+
+// Runs per CTA when the caller leaves it to the library: small runs of a
+// large batch share a CTA, so that few rows do not leave most of its row
+// groups idle at every sweep barrier.
+int default_parts(const elsr_batch* b, int threads, int G);
+
+// Instances per CTA: split the CTA's threads into P partitions for the runs
+// whose rows fit P-th of the shared memory.  Reorders b->h_runs (stably:
+// runs that need the whole CTA first, each class in its longest-first
+// order) and sets ls->parts, n_whole, part_bytes and the launch's dynamic
+// shared memory.  Leaves one team per CTA when packing does not apply.
+void pack_runs(elsr_batch* b, LaunchShape* ls, int acc, int P) {
+  const int nr = (int)b->h_runs.size();
+  ls->parts = 1;
+  ls->n_whole = nr;
+  ls->part_bytes = 0;
+  if (P <= 1 || ls->cluster != 1 || nr < 2 || ls->G > 32 || ls->threads % (32 * P) != 0 ||
+      ls->threads / P < ls->G)
+    return;
+  const uint32_t lim = ((uint32_t)kSmemLimit / (uint32_t)P) & ~15u;
+  std::vector<RunDesc> whole, small;
+  uint32_t need_whole = 0, need_part = 0;
+  for (const RunDesc& r : b->h_runs) {
+    const InstDesc& d = b->insts[r.inst];
+    const uint32_t lay = vns_layout(d.K, d.T, acc, ls->ts).total;
+    if (lay + kPartCtlBytes <= lim) {
+      small.push_back(r);
+      need_part = std::max(need_part, align16(lay + kPartCtlBytes));
+    } else {
+      whole.push_back(r);
+      need_whole = std::max(need_whole, lay);
+    }
+  }
+  if (small.size() < 2) return;
+  b->h_runs = whole;
+  b->h_runs.insert(b->h_runs.end(), small.begin(), small.end());
+  ls->parts = P;
+  ls->n_whole = (int)whole.size();
+  ls->part_bytes = need_part;
+  ls->smem = std::max<size_t>(need_whole, (size_t)P * need_part);
+}
 
 // Launch shape of the persistent kernel for the runs in b->h_runs: 64-bit
 // words per bit row, table placement, sub-warp width, block size, CTAs per
@@ -360,6 +416,7 @@ int vns_shape(elsr_batch* b, LaunchShape* ls) {
   ls->threads = thr;
   ls->maxt = thr <= 256 ? 256 : (thr <= 512 ? 512 : 1024);
   ls->cluster = C;
+  pack_runs(b, ls, acc, b->parts > 0 ? b->parts : default_parts(b, thr, ls->G));
   int active = 0;
   cudaError_t pe = vns_prepare(b->acc64, ls->nw, ls->ts, ls->maxt, ls->smem, thr, C, &active);
   if ((pe != cudaSuccess || active < 1) && !b->threads && thr > 256) {
@@ -434,14 +491,14 @@ int launch_runs(elsr_batch* b, const RowBits* start_bits, bool with_traj,
   }
   ELSR_TRY_CUDA(b, cudaMemcpyAsync(b->d_runs, b->h_runs.data(), nr * sizeof(RunDesc),
                                    cudaMemcpyHostToDevice, b->stream));
-  ELSR_TRY_CUDA(b, cudaMemsetAsync(b->d_queue, 0, sizeof(int32_t), b->stream));
+  ELSR_TRY_CUDA(b, cudaMemsetAsync(b->d_queue, 0, 2 * sizeof(int32_t), b->stream));
   VnsParams p;
   p.ip = b->pools();
   p.runs = b->d_runs;
   p.nruns = (int32_t)nr;
   p.G = ls.G;
   p.vnd_cap = kVndCap;
-  p.pad = 0;
+  p.count_steps = b->count_steps;
   p.start_bits = start_bits;
   p.out_bits = b->d_bits;
   p.out = b->d_out;
@@ -456,6 +513,12 @@ int launch_runs(elsr_batch* b, const RowBits* start_bits, bool with_traj,
   p.fj_workers = 0;
   // several runs with automatic lanes: each run picks its own row groups
   p.adaptive_G = (nr > 1 && b->lanes == 0) ? 1 : 0;
+  p.parts = ls.parts;
+  p.n_whole = ls.n_whole;
+  p.part_bytes = ls.part_bytes;
+  p.pad2 = 0;
+  b->last_parts = ls.parts;
+  b->last_whole = ls.n_whole;
   if (fj_workers > 0) {
     const int resident = ls.cluster == 1 ? ls.active * b->sms : ls.active;
     if (nr != 1 || fj_workers > resident) {
@@ -1343,6 +1406,36 @@ int elsr_batch_set_cluster(elsr_batch_t* b, int32_t cluster) {
     return ELSR_E_ARG;
   }
   b->cluster = cluster;
+  return ELSR_OK;
+}
+
+int elsr_batch_set_count_steps(elsr_batch_t* b, int32_t on) {
+  if (!b || (on != 0 && on != 1)) return ELSR_E_ARG;
+  b->count_steps = on;
+  return ELSR_OK;
+}
+
+int elsr_set_count_steps(elsr_t* h, int32_t on) {
+  if (!h) return ELSR_E_ARG;
+  return elsr_batch_set_count_steps(&h->b, on);
+}
+
+int elsr_batch_set_runs_per_cta(elsr_batch_t* b, int32_t runs_per_cta) {
+  if (!b) return ELSR_E_ARG;
+  if (runs_per_cta < 0 || runs_per_cta > kMaxParts ||
+      (runs_per_cta & (runs_per_cta - 1)) != 0) {
+    b->err = "runs per CTA must be 0 (automatic) or a power of two up to " +
+             std::to_string(kMaxParts);
+    return ELSR_E_ARG;
+  }
+  b->parts = runs_per_cta;
+  return ELSR_OK;
+}
+
+int elsr_batch_packing(const elsr_batch_t* b, int32_t* runs_per_cta, int32_t* whole_cta_runs) {
+  if (!b || !runs_per_cta || !whole_cta_runs) return ELSR_E_ARG;
+  *runs_per_cta = b->last_parts;
+  *whole_cta_runs = b->last_whole;
   return ELSR_OK;
 }
 

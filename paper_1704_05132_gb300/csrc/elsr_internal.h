@@ -16,6 +16,10 @@ constexpr int kStatusCap = -5;      // ELSR_E_CAP
 constexpr int kStatusTimeout = -7;  // ELSR_E_TIMEOUT
 constexpr int kStatusState = -6;    // ELSR_E_STATE: resumed state does not match
 constexpr int kStatusLaunch = -4;   // ELSR_E_CUDA: launch geometry mismatch
+// Control words at the start of each partition's shared memory when a CTA
+// holds several runs (the kernels check that they fit).
+constexpr uint32_t kPartCtlBytes = 768;
+constexpr int kMaxParts = 8;        // runs per CTA: partitions of >= 128 threads
 
 // One instance of a batch: rows [row_off, row_off + K) of the per-row pools
 // and cells [cell_off, cell_off + K*T) of the D/R pools.
@@ -102,12 +106,12 @@ struct VnsParams {
   int32_t nruns;
   int32_t G;  // sub-warp lanes per row
   int32_t vnd_cap;
-  int32_t pad;
+  int32_t count_steps;  // 1: count decode steps (RunOut.segments), 0: skip (timing)
   const RowBits* start_bits;
   RowBits* out_bits;
   RunOut* out;
   TrajEntry* traj;
-  int32_t* queue;  // work counter, zero at launch
+  int32_t* queue;  // [2] work counters (whole-CTA runs, partition runs), zero at launch
   // speculative single-run launches (spec_teams > 1)
   int32_t spec_teams;
   int32_t cluster;       // CTAs per team the launch was configured with
@@ -121,6 +125,14 @@ struct VnsParams {
   // batched launches: choose each run's lanes per row from its row count
   // (wider groups for small instances); 0 = every run uses G
   int32_t adaptive_G;
+  // instances per CTA: runs [0, n_whole) take a whole team each; with
+  // parts > 1 (cluster size 1, G <= 32) the CTA then splits into `parts`
+  // partitions of its threads, each a team with part_bytes of dynamic shared
+  // memory, for runs [n_whole, nruns)
+  int32_t parts;
+  int32_t n_whole;
+  uint32_t part_bytes;
+  int32_t pad2;
 };
 
 struct StageParams {

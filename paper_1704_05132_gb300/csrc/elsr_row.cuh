@@ -392,7 +392,7 @@ template <typename Acc, int NW>
 ELSR_HD Acc eval_move(const int2* tab, int T, const RowCosts& rc,
                       const RowState<Acc>& cur, const int32_t* A,
                       const Acc* C, const int2* L, const int32_t* P,
-                      const Acc* Q, int j, int local, int& steps) {
+                      const Acc* Q, int j, int local, int& steps, bool count = true) {
   RowBits nb = cur.b;
   int t1, other;
   if (j == 1) {
@@ -500,8 +500,12 @@ ELSR_HD Acc eval_move(const int2* tab, int T, const RowCosts& rc,
   S += cur.S - C1;
   const int r0 = rank_below<NW>(cur.b.r0, cur.b.r1, s1);
   if (delta == 0) return cur.ld >= r0 ? Inf<Acc>::value : S;
-  // setups from s1 through the last one the stock difference reaches
-  const int u_s1 = rank_below<NW>(u0, u1, s1);
+  // the step count takes the setups from s1 through the last one the stock
+  // difference reaches; from s1 on the current row has the moved row's
+  // setups, and its bits stay live in the caller anyway.  Callers that time
+  // the search pass count = false and skip these population counts.
+  const uint64_t w0 = cur.b.m0 | cur.b.r0, w1 = cur.b.m1 | cur.b.r1;
+  const int u_s1 = count ? rank_below<NW>(w0, w1, s1) : 0;
   if (delta > 0) {
     // More stock: each later gR setup absorbs up to its room (need minus the
     // stock it had), lowering xM by as much, until delta is used up.  With
@@ -514,7 +518,7 @@ ELSR_HD Acc eval_move(const int2* tab, int T, const RowCosts& rc,
     const Acc Q0 = Q[r0], Qn = Q[cur.nR];
     const int32_t target = P0 + delta;
     if (Pn < target) {
-      steps += rank_below<NW>(u0, u1, T) - u_s1;
+      if (count) steps += rank_below<NW>(w0, w1, T) - u_s1;
       return S - (Qn - Q0);
     }
     // smallest z in [r0, nR) with P[z+1] >= target: the answer stays in
@@ -528,7 +532,7 @@ ELSR_HD Acc eval_move(const int2* tab, int T, const RowCosts& rc,
     const int32_t Pz = P[lo], Pz1 = P[lo + 1];
     const Acc Qz = Q[lo];
     const int sz = L[lo].y & 0xFFFF;
-    steps += rank_below<NW>(u0, u1, sz + 1) - u_s1;
+    if (count) steps += rank_below<NW>(w0, w1, sz + 1) - u_s1;
     if (cur.ld > lo || (cur.ld == lo && Pz1 != target)) return Inf<Acc>::value;
     return S - (Qz - Q0) - xr_weight<Acc>(rc, T, sz) * (Acc)(target - Pz);
   }
@@ -542,7 +546,7 @@ ELSR_HD Acc eval_move(const int2* tab, int T, const RowCosts& rc,
     const int sr = e.y & 0xFFFF;
     const int32_t sg = e.x, sn = sg + delta;
     if (!(e.y >> 16) && sn < 0) {
-      steps += rank_below<NW>(u0, u1, sr + 1) - u_s1;
+      if (count) steps += rank_below<NW>(w0, w1, sr + 1) - u_s1;
       return Inf<Acc>::value;
     }
     const int32_t dx = (sn < 0 ? sn : 0) - (sg < 0 ? sg : 0);
@@ -553,7 +557,7 @@ ELSR_HD Acc eval_move(const int2* tab, int T, const RowCosts& rc,
       break;
     }
   }
-  steps += rank_below<NW>(u0, u1, last + 1) - u_s1;
+  if (count) steps += rank_below<NW>(w0, w1, last + 1) - u_s1;
   return cur.ld >= r0 ? Inf<Acc>::value : S;
 }
 

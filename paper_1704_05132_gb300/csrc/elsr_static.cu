@@ -40,6 +40,9 @@ constexpr size_t kKeyOff = kCostOff + 8ull * ELSR_STATIC_K_MAX;
 constexpr size_t kBitsOff = kKeyOff + 8ull * ELSR_STATIC_K_MAX;
 constexpr size_t kScratchBytes = kBitsOff + 32ull * ELSR_STATIC_K_MAX;
 static_assert(kScratchBytes == ELSR_STATIC_BYTES, "scratch size must match elsr.h");
+static_assert(sizeof(InstDesc) <= kRedOff, "the instance descriptor overlaps the reduction words");
+static_assert(kRedOff + 4 * sizeof(uint64_t) <= kCostOff, "reduction words overlap the row costs");
+static_assert(sizeof(RowBits) == 32, "packed setup bits are 32 bytes per row");
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
@@ -151,6 +154,25 @@ extern "C" int elsr_eval_neighbourhood_static(
   if (!D || !R || !kM || !kR || !hM || !hR || !gM || !gR || !best) return ELSR_E_ARG;
   if ((nb_mask & ~7u) || (mode != ELSR_MODE_P && mode != ELSR_MODE_G)) return ELSR_E_ARG;
   const cudaStream_t s = (cudaStream_t)stream;
+  // An error an earlier call of the caller left pending is reported, and left
+  // pending: the launch checks below would otherwise clear it as their own.
+  if (cudaPeekAtLastError() != cudaSuccess) return ELSR_E_CUDA;
+  // The array's address is per device: the stream and the caller's buffers
+  // must belong to the current device.
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return ELSR_E_CUDA;
+  if (s) {
+    int sdev = -1;
+    if (cudaStreamGetDevice(s, &sdev) != cudaSuccess) return ELSR_E_CUDA;
+    if (sdev != dev) return ELSR_E_ARG;
+  }
+  const void* bufs[] = {D, R, kM, kR, hM, hR, gM, gR, best, pp_cost, pp_move};
+  for (const void* b : bufs) {
+    if (!b) continue;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, b) != cudaSuccess) return ELSR_E_CUDA;
+    if (a.type == cudaMemoryTypeDevice && a.device != dev) return ELSR_E_ARG;
+  }
   unsigned char* scratch = nullptr;
   if (scratch_address(&scratch) != cudaSuccess) return ELSR_E_CUDA;
 

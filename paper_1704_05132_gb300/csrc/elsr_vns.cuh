@@ -213,7 +213,8 @@ __device__ __forceinline__ void restore_row(const Rows<Acc>& m, int q,
 template <typename Acc, int NW>
 __device__ __forceinline__ uint64_t row_best(const Rows<Acc>& m, int q,
                                              const RowState<Acc>& cur, int j, int M,
-                                             int lane, int G, uint32_t& steps) {
+                                             int lane, int G, uint32_t& steps,
+                                             bool count) {
   const int T = m.T;
   const int2* tk = m.tab_row(q);
   const int32_t* Aq = m.A + q * T;
@@ -231,12 +232,12 @@ __device__ __forceinline__ uint64_t row_best(const Rows<Acc>& m, int q,
     const SwapMasks sw = swap_masks<NW>(cur.b, T);
     for (int i = lane; i < sw.n; i += G) {
       const int l = swap_of_rank<NW>(sw, T, i);
-      const Acc S = eval_move<Acc, NW>(tk, T, rc, cur, Aq, Cq, Lq, Pq, Qq, 3, l, st);
+      const Acc S = eval_move<Acc, NW>(tk, T, rc, cur, Aq, Cq, Lq, Pq, Qq, 3, l, st, count);
       best = umin64(best, pack_key(row_cost<Acc>(S, c0), (uint32_t)l));
     }
   } else {
     for (int l = lane; l < M; l += G) {
-      const Acc S = eval_move<Acc, NW>(tk, T, rc, cur, Aq, Cq, Lq, Pq, Qq, j, l, st);
+      const Acc S = eval_move<Acc, NW>(tk, T, rc, cur, Aq, Cq, Lq, Pq, Qq, j, l, st, count);
       best = umin64(best, pack_key(row_cost<Acc>(S, c0), (uint32_t)l));
     }
   }
@@ -604,6 +605,11 @@ struct Team {
   int tp, fp;
   uint32_t steps, applied;
   int vnd_cap;
+  // A CTA may hold several runs at once, one per partition of its threads
+  // (instances per CTA): bar = 0 for a team that owns the whole CTA, else
+  // the partition's named barrier (1 + partition index) over its nthr threads.
+  int bar;
+  bool count;  // count decode steps (off while a run is timed)
 
   __device__ __forceinline__ bool owns(int k) const {
     return k >= 0 && (k % C) == crank && ((k / C) % nsub) == sub;
@@ -646,9 +652,36 @@ __device__ __forceinline__ void group_rebuild(const Team<Acc>& t, int q) {
   group_sync(t);
 }
 
-__device__ __forceinline__ void team_sync(int C) {
-  if (C == 1) {
+// Barrier over the threads of this CTA that belong to the team: the whole
+// CTA, or the team's partition of it.
+template <typename Acc>
+__device__ __forceinline__ void cta_sync(const Team<Acc>& t) {
+  if (t.bar == 0) {
     __syncthreads();
+  } else {
+    asm volatile("bar.sync %0, %1;" ::"r"(t.bar), "r"(t.nthr) : "memory");
+  }
+}
+
+// cta_sync that also returns whether `pred` was non-zero on any thread.
+template <typename Acc>
+__device__ __forceinline__ int cta_sync_or(const Team<Acc>& t, int pred) {
+  if (t.bar == 0) return __syncthreads_or(pred);
+  int r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.s32 p, %1, 0;\n\t"
+      "bar.red.or.pred q, %2, %3, p;\n\tselp.s32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"(pred), "r"(t.bar), "r"(t.nthr)
+      : "memory");
+  return r;
+}
+
+// Barrier over the whole team: its CTA share, or every CTA of its cluster.
+template <typename Acc>
+__device__ __forceinline__ void team_sync(const Team<Acc>& t) {
+  if (t.C == 1) {
+    cta_sync(t);
   } else {
     cg::this_cluster().sync();
   }
@@ -664,10 +697,11 @@ __device__ __forceinline__ uint32_t dynamic_smem_bytes() {
 }
 
 // Returns false (uniformly over the team) when the launch does not match
-// what the run needs: another cluster size than configured, or less dynamic
-// shared memory than the run's layout; nothing is touched then.
+// what the run needs: another cluster size than configured, or less shared
+// memory in the team's region (`region` bytes from `smem`) than the run's
+// layout; nothing is touched then.
 template <typename Acc, int NW, bool TS>
-__device__ bool team_begin(Team<Acc>& t, unsigned char* smem, CtlShared* sh,
+__device__ bool team_begin(Team<Acc>& t, unsigned char* smem, uint32_t region, CtlShared* sh,
                            const VnsParams& p, const RunDesc& rd) {
   const InstDesc id = p.ip.insts[rd.inst];
   const int K = id.K, T = id.T, C = t.C, crank = t.crank;
@@ -679,9 +713,10 @@ __device__ bool team_begin(Team<Acc>& t, unsigned char* smem, CtlShared* sh,
   t.tp = t.fp = 0;
   t.steps = t.applied = 0;
   t.vnd_cap = p.vnd_cap;
+  t.count = p.count_steps != 0;
   const int Kmax = (K + C - 1) / C;
   const VnsLayout Lay = vns_layout(Kmax, T, (int)sizeof(Acc), TS);
-  if (C != p.cluster || Lay.total > dynamic_smem_bytes()) return false;
+  if (C != p.cluster || Lay.total > region) return false;
   Rows<Acc>& m = t.m;
   m.tab = TS ? (const int2*)(smem + Lay.tab) : (p.ip.gtab + id.tab_off);
   m.rc = (RowCosts*)(smem + Lay.rc);
@@ -726,7 +761,7 @@ __device__ bool team_begin(Team<Acc>& t, unsigned char* smem, CtlShared* sh,
     sh->steps = 0ull;
     sh->abort = 0;
   }
-  __syncthreads();
+  cta_sync(t);
   for (int qq = t.sub; qq < t.Kcr; qq += t.nsub) {
     if (qq < t.Kc) group_rebuild<Acc, NW>(t, qq);
     if (t.G <= 32) __syncwarp();
@@ -770,7 +805,7 @@ __device__ void team_sums(Team<Acc>& t, int64_t& F, int& ninf, long long deadlin
     if (s) atomicAdd(&sh->acc[tp], (unsigned long long)s);
     if (ni) atomicAdd(&sh->ninf[tp], ni);
   }
-  __syncthreads();
+  cta_sync(t);
   if (t.C == 1) {
     F = (int64_t)sh->acc[tp];
     ninf = sh->ninf[tp];
@@ -829,7 +864,7 @@ __device__ int vnd_p(Team<Acc>& t, const int* stop = nullptr, int my_index = 0) 
         uint64_t best = ~0ull;
         if (valid) {
           const RowState<Acc> cur = t.m.state(q);
-          best = row_best<Acc, NW>(t.m, q, cur, j, M, t.lane, t.G, t.steps);
+          best = row_best<Acc, NW>(t.m, q, cur, j, M, t.lane, t.G, t.steps, t.count);
         }
         best = group_min(t, best);
         const bool imp = valid && key_cost(best) < t.m.cost(q);
@@ -849,7 +884,7 @@ __device__ int vnd_p(Team<Acc>& t, const int* stop = nullptr, int my_index = 0) 
     }
     ++cycles;
     if (stop && t.C == 1 && t.tid == 0) t.sh->flag[t.fp] = *(volatile const int*)stop < my_index;
-    int any = __syncthreads_or(improved);
+    int any = cta_sync_or(t, improved);
     int quit = 0;
     if (t.C > 1) {
       cg::cluster_group cl = cg::this_cluster();
@@ -891,7 +926,7 @@ __device__ int vnd_g(Team<Acc>& t, const int* stop = nullptr, int my_index = 0) 
   int Finf;     // infeasible rows (team-wide)
   team_sums(t, F, Finf);
   if (t.tid == 0) sh->gkey[0] = sh->gkey[1] = ~0ull;
-  team_sync(C);
+  team_sync(t);
   const int GW = t.G < 32 ? t.G : 32;  // lanes of the group inside one warp
   int cycles = 0, e = 0;
   int seen = 0x7fffffff;  // thread 0 of CTA 0: the decision word as read during N3
@@ -926,7 +961,7 @@ __device__ int vnd_g(Team<Acc>& t, const int* stop = nullptr, int my_index = 0) 
             const int l = j == 3 ? swap_of_rank<NW>(sw, T, i) : i;
             const Acc S = eval_move<Acc, NW>(tk, T, rc, cur, t.m.A + q * T, t.m.C + q * T,
                                              t.m.L + q * T, t.m.P + q * (T + 1),
-                                             t.m.Q + q * (T + 1), j, l, st);
+                                             t.m.Q + q * (T + 1), j, l, st, t.count);
             const int64_t nc = row_cost<Acc>(S, c0);
             const int64_t nt =
                 (others == INT64_MAX || nc == INT64_MAX) ? INT64_MAX : others + nc;
@@ -939,7 +974,7 @@ __device__ int vnd_g(Team<Acc>& t, const int* stop = nullptr, int my_index = 0) 
       }
       uint64_t gk;
       if (C == 1) {
-        __syncthreads();
+        cta_sync(t);
         gk = sh->gkey[e];
         if (stop && j == 1) quit = sh->gstop[e];
       } else {
@@ -969,7 +1004,7 @@ __device__ int vnd_g(Team<Acc>& t, const int* stop = nullptr, int my_index = 0) 
         Finf = 0;
         improved = true;
       }
-      __syncthreads();
+      cta_sync(t);
       e ^= 1;
       if (quit) return -2;  // uniform: every thread read CTA 0's verdict
     }
@@ -1075,21 +1110,32 @@ __device__ void flush_counters(Team<Acc>& t, unsigned long long* steps_dst,
   t.applied = 0;
 }
 
+// Row groups of G lanes over the team's threads.
 template <typename Acc>
-__device__ __forceinline__ void team_init(Team<Acc>& t, int G) {
-  cg::cluster_group cl = cg::this_cluster();
-  t.C = (int)cl.num_blocks();
-  t.crank = (int)cl.block_rank();
-  t.tid = threadIdx.x;
-  t.nthr = blockDim.x;
+__device__ __forceinline__ void team_set_lanes(Team<Acc>& t, int G) {
   t.G = G;
   t.lane = t.tid & (G - 1);
   t.sub = t.tid / G;
   t.nsub = t.nthr / G;
+  t.smask = G >= 32 ? kFull : (((1u << G) - 1u) << (t.wlane & ~(G - 1)));
+}
+
+// The team of this thread: its cluster (every thread of the CTA), or with
+// np > 1 one of np equal partitions of the CTA's threads (cluster size 1,
+// G <= 32; each partition is a team of its own with its own barrier).
+template <typename Acc>
+__device__ __forceinline__ void team_init(Team<Acc>& t, int G, int np = 1) {
+  cg::cluster_group cl = cg::this_cluster();
+  t.C = (int)cl.num_blocks();
+  t.crank = (int)cl.block_rank();
+  t.nthr = blockDim.x / np;
+  const int part = (int)threadIdx.x / t.nthr;
+  t.bar = np > 1 ? 1 + part : 0;
+  t.tid = threadIdx.x - part * t.nthr;
   t.wlane = t.tid & 31;
   t.warp = t.tid >> 5;
   t.nwarps = t.nthr >> 5;
-  t.smask = G >= 32 ? kFull : (((1u << G) - 1u) << (t.wlane & ~(G - 1)));
+  team_set_lanes(t, G);
 }
 
 // Lanes per row for a run of K products on teams of C CTAs of `threads`
@@ -1097,10 +1143,10 @@ __device__ __forceinline__ void team_init(Team<Acc>& t, int G) {
 // row, so a small instance spreads each row over more lanes instead of
 // leaving groups idle.  Groups wider than a warp must tile the block and use
 // at most the 15 named barriers.
-__device__ __forceinline__ int run_lanes(int G0, int K, int C, int threads) {
+__device__ __forceinline__ int run_lanes(int G0, int K, int C, int threads, int gmax = 128) {
   const int Kc = (K + C - 1) / C;
   int G = G0;
-  for (int g = G0 * 2; g <= 128; g *= 2) {
+  for (int g = G0 * 2; g <= gmax; g *= 2) {
     if (threads / g < Kc) break;
     if (g > 32 && (threads % g != 0 || threads / g > 15)) continue;
     G = g;
@@ -1109,27 +1155,39 @@ __device__ __forceinline__ int run_lanes(int G0, int K, int C, int threads) {
 }
 
 // ---------------------------------------------------------------------------
-// vns_kernel: persistent batched GVNS, one team (cluster) per run, runs taken
-// from a device work queue.
+// vns_kernel: persistent batched GVNS, runs taken from a device work queue.
+//
+// Phase 1: every team is a whole cluster (or CTA) and takes runs
+// [0, p.n_whole) from queue 0.  Phase 2 (p.parts > 1, cluster size 1): each
+// CTA splits into p.parts partitions of its threads, and each partition is a
+// team that takes runs [p.n_whole, p.nruns) from queue 1, in its own
+// p.part_bytes of dynamic shared memory (control words first, then the
+// run's rows).  The host puts the runs too large for a partition first, so
+// small runs share a CTA instead of leaving most of its row groups idle.
 // ---------------------------------------------------------------------------
-template <typename Acc, int NW, bool TS, int MAXT>
-__global__ void __launch_bounds__(MAXT, 1) vns_kernel(const VnsParams p) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ CtlShared sh;
-  Team<Acc> t;
-  team_init(t, p.G);
+constexpr uint32_t kCtlBytes = kPartCtlBytes;
+static_assert(sizeof(CtlShared) <= kCtlBytes, "partition control words outgrow their room");
+
+// One team's run loop: runs [first, end) from `queue`, in `region` bytes of
+// shared memory from `base`, control words in `sh`.  Inlined into each phase
+// of vns_kernel, so neither phase keeps the other's state live.
+template <typename Acc, int NW, bool TS>
+__device__ __forceinline__ void run_loop(Team<Acc>& t, unsigned char* base, uint32_t region,
+                                         CtlShared* sh, const VnsParams& p, int* queue,
+                                         int first, int end, int gmax) {
   cg::cluster_group cl = cg::this_cluster();
   for (;;) {
-    if (t.crank == 0 && t.tid == 0) sh.run = atomicAdd(p.queue, 1);
-    team_sync(t.C);
-    const int r = t.C == 1 ? sh.run : *cl.map_shared_rank(&sh.run, 0);
-    team_sync(t.C);
-    if (r >= p.nruns) return;
+    if (t.crank == 0 && t.tid == 0) sh->run = first + atomicAdd(queue, 1);
+    team_sync(t);
+    const int r = t.C == 1 ? sh->run : *cl.map_shared_rank(&sh->run, 0);
+    team_sync(t);
+    if (r >= end) return;
     const RunDesc rd = p.runs[r];
-    if (p.adaptive_G) team_init(t, run_lanes(p.G, p.ip.insts[rd.inst].K, t.C, t.nthr));
-    if (!team_begin<Acc, NW, TS>(t, smem, &sh, p, rd)) {
+    team_set_lanes(t, p.adaptive_G ? run_lanes(p.G, p.ip.insts[rd.inst].K, t.C, t.nthr, gmax)
+                                   : p.G);
+    if (!team_begin<Acc, NW, TS>(t, base, region, sh, p, rd)) {
       if (t.crank == 0 && t.tid == 0) write_failed_run(p, rd, kStatusLaunch);
-      team_sync(t.C);
+      team_sync(t);
       continue;
     }
     const int K = t.K, T = t.T;
@@ -1182,18 +1240,18 @@ __global__ void __launch_bounds__(MAXT, 1) vns_kernel(const VnsParams p) {
         undo_shake<Acc>(t, pl, par);
         kk = kk % rd.kmax + 1;
       }
-      if ((it & 255) == 255) flush_counters(t, &sh.steps, &sh.applied);
+      if ((it & 255) == 255) flush_counters(t, &sh->steps, &sh->applied);
     }
-    __syncthreads();  // restores of the last iteration are complete
+    cta_sync(t);  // restores of the last iteration are complete
     for (int q = t.tid; q < t.Kc; q += t.nthr)
       p.out_bits[rd.bits_off + q * t.C + t.crank] = t.m.bits[q];
-    flush_counters(t, &sh.steps, &sh.applied);
-    team_sync(t.C);
+    flush_counters(t, &sh->steps, &sh->applied);
+    team_sync(t);
     if (t.tid == 0 && t.crank == 0) {
       unsigned long long steps = 0, applied = 0;
       for (int c = 0; c < t.C; ++c) {
-        steps += t.C == 1 ? sh.steps : *cl.map_shared_rank(&sh.steps, c);
-        applied += t.C == 1 ? sh.applied : *cl.map_shared_rank(&sh.applied, c);
+        steps += t.C == 1 ? sh->steps : *cl.map_shared_rank(&sh->steps, c);
+        applied += t.C == 1 ? sh->applied : *cl.map_shared_rank(&sh->applied, c);
       }
       RunOut o;
       o.best_cost = fx;
@@ -1211,7 +1269,32 @@ __global__ void __launch_bounds__(MAXT, 1) vns_kernel(const VnsParams p) {
       o.pad = 0;
       p.out[rd.out] = o;
     }
-    team_sync(t.C);
+    team_sync(t);
+  }
+}
+
+template <typename Acc, int NW, bool TS, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) vns_kernel(const VnsParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ CtlShared sh;
+  Team<Acc> t;
+  team_init(t, p.G);
+  // phase 1: whole teams
+  run_loop<Acc, NW, TS>(t, smem, dynamic_smem_bytes(), &sh, p, p.queue, 0, p.n_whole, 128);
+  if (p.n_whole >= p.nruns) return;
+  // phase 2: every thread of the CTA left phase 1 together (queue 0 was
+  // empty), so its named barriers are complete
+  __syncthreads();
+  const int np = p.parts;
+  if (np > 1 && t.C == 1 && (int)blockDim.x % (32 * np) == 0 && p.G <= 32 &&
+      (uint32_t)np * p.part_bytes <= dynamic_smem_bytes() && p.part_bytes > kCtlBytes) {
+    team_init(t, p.G, np);
+    unsigned char* base = smem + (size_t)((int)threadIdx.x / t.nthr) * p.part_bytes;
+    run_loop<Acc, NW, TS>(t, base + kCtlBytes, p.part_bytes - kCtlBytes, (CtlShared*)base, p,
+                          p.queue + 1, p.n_whole, p.nruns, 32);
+  } else {  // not a shape the host launches: the whole team takes these runs
+    run_loop<Acc, NW, TS>(t, smem, dynamic_smem_bytes(), &sh, p, p.queue + 1, p.n_whole,
+                          p.nruns, 128);
   }
 }
 
@@ -1234,7 +1317,7 @@ constexpr long kSpinLimit = 1l << 24;  // grid-barrier polls (x ~200 ns) before 
 template <typename Acc>
 __device__ bool grid_barrier(Team<Acc>& t, int* bar, int W) {
   __threadfence();
-  team_sync(t.C);
+  team_sync(t);
   if (t.crank == 0 && t.tid == 0) {
     volatile int* vgen = bar + 1;
     const int gen = *vgen;
@@ -1255,7 +1338,7 @@ __device__ bool grid_barrier(Team<Acc>& t, int* bar, int W) {
     }
     __threadfence();
   }
-  team_sync(t.C);
+  team_sync(t);
   cg::cluster_group cl = cg::this_cluster();
   const int ab = t.C == 1 ? t.sh->abort : *cl.map_shared_rank(&t.sh->abort, 0);
   return ab == 0;
@@ -1280,7 +1363,7 @@ __global__ void __launch_bounds__(MAXT, 1) spec_kernel(const VnsParams p) {
   const int W = p.spec_teams;
   const int team = blockIdx.x / t.C;
   const RunDesc rd = p.runs[0];
-  if (W < 2 || (int)gridDim.x != W * t.C || !team_begin<Acc, NW, TS>(t, smem, &sh, p, rd)) {
+  if (W < 2 || (int)gridDim.x != W * t.C || !team_begin<Acc, NW, TS>(t, smem, dynamic_smem_bytes(), &sh, p, rd)) {
     if (blockIdx.x == 0 && t.tid == 0) write_failed_run(p, rd, kStatusLaunch);
     return;
   }
@@ -1330,7 +1413,7 @@ __global__ void __launch_bounds__(MAXT, 1) spec_kernel(const VnsParams p) {
           if (t.owns(pl.rows[j]) && pl.first[j] && t.lane == 0)
             p.spec_rows[(par * W + team) * kMaxShake + j] = t.m.bits[pl.rows[j] / t.C];
         __threadfence();
-        team_sync(t.C);
+        team_sync(t);
         if (t.crank == 0 && t.warp == 0) {
           if (t.wlane == 0) {
             slot->f2 = f2;
@@ -1461,12 +1544,12 @@ __global__ void __launch_bounds__(MAXT, 1) spec_kernel(const VnsParams p) {
     ++round;
   }
   // outputs (team 0)
-  __syncthreads();  // undo / adoption of the last round are complete
+  cta_sync(t);  // undo / adoption of the last round are complete
   if (team == 0) {
     for (int q = t.tid; q < t.Kc; q += t.nthr)
       p.out_bits[rd.bits_off + q * t.C + t.crank] = t.m.bits[q];
   }
-  team_sync(t.C);
+  team_sync(t);
   if (leader) {
     unsigned long long steps = c_steps, applied = c_applied;
     for (int c = 0; c < t.C; ++c) {
@@ -1489,7 +1572,7 @@ __global__ void __launch_bounds__(MAXT, 1) spec_kernel(const VnsParams p) {
     o.pad = 0;
     p.out[rd.out] = o;
   }
-  team_sync(t.C);
+  team_sync(t);
 }
 
 // ---------------------------------------------------------------------------
@@ -1512,7 +1595,7 @@ __global__ void __launch_bounds__(MAXT, 1) fj_kernel(const VnsParams p) {
   const int W = p.fj_workers;
   const int team = blockIdx.x / t.C;
   const RunDesc rd = p.runs[0];
-  if (W < 1 || (int)gridDim.x != W * t.C || !team_begin<Acc, NW, TS>(t, smem, &sh, p, rd)) {
+  if (W < 1 || (int)gridDim.x != W * t.C || !team_begin<Acc, NW, TS>(t, smem, dynamic_smem_bytes(), &sh, p, rd)) {
     if (blockIdx.x == 0 && t.tid == 0) write_failed_run(p, rd, kStatusLaunch);
     return;
   }
@@ -1638,12 +1721,12 @@ __global__ void __launch_bounds__(MAXT, 1) fj_kernel(const VnsParams p) {
     }
   }
   // outputs (worker 0)
-  __syncthreads();  // undo / adoption of the last iteration are complete
+  cta_sync(t);  // undo / adoption of the last iteration are complete
   if (team == 0) {
     for (int q = t.tid; q < t.Kc; q += t.nthr)
       p.out_bits[rd.bits_off + q * t.C + t.crank] = t.m.bits[q];
   }
-  team_sync(t.C);
+  team_sync(t);
   if (leader) {
     unsigned long long steps = c_steps, applied = c_applied;
     for (int c = 0; c < t.C; ++c) {
@@ -1666,7 +1749,7 @@ __global__ void __launch_bounds__(MAXT, 1) fj_kernel(const VnsParams p) {
     o.pad = 0;
     p.out[rd.out] = o;
   }
-  team_sync(t.C);
+  team_sync(t);
 }
 
 }  // namespace vns

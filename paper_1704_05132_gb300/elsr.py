@@ -117,6 +117,10 @@ class Solver:
     def set_speculation(self, teams: int = 0):
         self._chk(self._lib.elsr_set_speculation(self._h, teams))
 
+    def set_count_steps(self, on: bool = True):
+        """Decode-step counter of the next runs (off while timing)."""
+        self._chk(self._lib.elsr_set_count_steps(self._h, 1 if on else 0))
+
     def launch_shape(self) -> dict:
         v = np.zeros(8, np.int32)
         self._chk(self._lib.elsr_launch_shape(self._h, _p(v)))
@@ -296,7 +300,7 @@ class Batch:
     """Many instances of uneven size solved by one persistent launch."""
 
     def __init__(self, insts, stream=None, lanes: int = 0, threads: int = 0,
-                 cluster: int = 0):
+                 cluster: int = 0, runs_per_cta: int = 0):
         insts = list(insts)
         if not insts:
             raise ValueError("a batch needs at least one instance")
@@ -328,6 +332,8 @@ class Batch:
             self.set_launch(lanes, threads)
         if cluster:
             self._chk(self._lib.elsr_batch_set_cluster(self._b, cluster))
+        if runs_per_cta:
+            self.set_runs_per_cta(runs_per_cta)
 
     def _chk(self, code):
         return check(code, self._b, batch=True)
@@ -335,7 +341,19 @@ class Batch:
     def launch_shape(self) -> dict:
         v = np.zeros(8, np.int32)
         self._chk(self._lib.elsr_batch_launch_shape(self._b, _p(v)))
-        return dict(zip(SHAPE_KEYS, v.tolist()))
+        out = dict(zip(SHAPE_KEYS, v.tolist()))
+        pk = np.zeros(2, np.int32)
+        self._chk(self._lib.elsr_batch_packing(self._b, _p(pk[:1]), _p(pk[1:])))
+        out["runs_per_cta"], out["whole_cta_runs"] = int(pk[0]), int(pk[1])
+        return out
+
+    def set_count_steps(self, on: bool = True):
+        """Decode-step counter of the next runs (off while timing)."""
+        self._chk(self._lib.elsr_batch_set_count_steps(self._b, 1 if on else 0))
+
+    def set_runs_per_cta(self, runs_per_cta: int = 0):
+        """Instances per CTA (0: the library's choice)."""
+        self._chk(self._lib.elsr_batch_set_runs_per_cta(self._b, runs_per_cta))
 
     def set_stream(self, stream=None):
         s = _stream_handle(stream)

@@ -429,3 +429,34 @@ def test_stream_switch_waits_for_work_in_flight(E):
         r = s.result()
     np.testing.assert_array_equal(r["traj"]["cost"], o.traj["cost"])
     _check_run(r, o)
+
+
+def test_step_counter_switch_changes_no_result(E):
+    """Runs timed with the decode-step counter off give the same trajectory,
+    solution and every other counter, and report no steps; switched back on,
+    the count is the oracle's again (single run and batch)."""
+    g = gen.make_instance(8, 8, K=12, T=30)
+    inst = _inst(g)
+    with E.Solver(g) as s:
+        on = s.vns(seed=4, iters=60, kmax=3, mode=0)
+        s.set_count_steps(False)
+        off = s.vns(seed=4, iters=60, kmax=3, mode=0)
+        s.set_count_steps(True)
+        again = s.vns(seed=4, iters=60, kmax=3, mode=0)
+    keys = ("best_cost", "traj_hash", "moves_evaluated", "applied", "accepted", "vnd_cycles")
+    assert [on[k] for k in keys] == [off[k] for k in keys] == [again[k] for k in keys]
+    assert off["segments"] == 0 and on["segments"] == again["segments"] > 0
+    np.testing.assert_array_equal(on["gM"], off["gM"])
+    insts = gen.batch_uneven(12, seed=4)
+    b = E.Batch(insts)
+    seeds = np.arange(12, dtype=np.uint64)
+    b.run(seeds, 20, 3, 0)
+    r_on = b.results()
+    b.set_count_steps(False)
+    b.run(seeds, 20, 3, 0)
+    r_off = b.results()
+    assert [r["traj_hash"] for r in r_on] == [r["traj_hash"] for r in r_off]
+    assert all(r["segments"] == 0 for r in r_off) and all(r["segments"] > 0 for r in r_on)
+    b.close()
+    o = oracle.vns(inst, seed=4, iters=60, kmax=3, mode=0)
+    assert on["traj_hash"] == o.traj_hash

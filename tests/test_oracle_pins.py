@@ -862,3 +862,22 @@ def test_decode_steps_stop_where_the_decodes_coincide(seed):
                     assert p1[3, stop - 1] == p0[3, stop - 1]
                 checked += 1
     assert checked > 200
+
+
+def test_gvns_from_the_initial_vnd_output_is_the_same_run():
+    """Algorithm 2 applies VND to the start before its first shake, so a run
+    from the all-open start and one from that VND's output follow the same
+    trajectory; their counters differ by exactly the initial descent against
+    one sweep that moves nothing.  (The workload-scale GPU tests start the
+    oracle there.)  Shown on the multi-start instance, K=100, T=104."""
+    inst = oracle.Instance.from_arrays(gen.multistart_large())
+    r0 = oracle.vns(inst, seed=0, iters=0, kmax=3, mode=0)
+    a = oracle.vns(inst, seed=7, iters=3, kmax=3, mode=0)
+    b = oracle.vns(inst, seed=7, iters=3, kmax=3, mode=0, gM=r0.gM, gR=r0.gR)
+    assert (a.best_cost, a.traj_hash) == (b.best_cost, b.traj_hash)
+    np.testing.assert_array_equal(a.traj, b.traj)
+    sweep = inst.K * (2 * inst.T + 2 * (inst.T - 1))
+    assert a.counters["moves_evaluated"] == \
+        b.counters["moves_evaluated"] - sweep + r0.counters["moves_evaluated"]
+    assert a.counters["applied"] == b.counters["applied"] + r0.counters["applied"]
+    assert a.counters["accepted"] == b.counters["accepted"]

@@ -66,7 +66,7 @@ def _states(g, seed):
         yield gm, gr
 
 
-@pytest.mark.parametrize("shape", [(5, 12), (50, 52), (13, 100)])
+@pytest.mark.parametrize("shape", [(5, 12), (50, 52), (13, 100), (7, 8), (9, 20), (11, 33)])
 def test_static_eval_matches_allocating_entry_point(env, shape):
     torch, lib, elsr = env
     K, T = shape
@@ -75,7 +75,7 @@ def test_static_eval_matches_allocating_entry_point(env, shape):
         for gm, gr in _states(g, K):
             s.set_state(gm, gr)
             for mode in (0, 1):
-                for mask in (7, 1, 6):
+                for mask in (7, 1, 6, 0):
                     ref = s.eval_neighbourhood(mask, mode)
                     for _ in range(2):  # two calls in a row share the array
                         got = _static_eval(torch, lib, g, gm, gr, mask, mode)
