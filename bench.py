@@ -388,9 +388,9 @@ def bench_serve(torch, dev, peak, args, cpu=True):
     n = args.requests
     iters = args.iters if args.iters is not None else 300
     warm = serve.poisson_requests(64, args.rate, iters, seed=5, id0=10 ** 6)
-    serve.Server(slots=args.slots).run(warm, realtime=False)
+    serve.Server(slots=args.slots, max_runs=args.max_runs).run(warm, realtime=False)
     reqs = serve.poisson_requests(n, args.rate, iters, seed=5)
-    srv = serve.Server(slots=args.slots, max_batch=args.max_batch)
+    srv = serve.Server(slots=args.slots, max_runs=args.max_runs)
     with ClockSampler(dev.index or 0) as clk:
         stats = srv.run(reqs)
     s = stats.summary()
@@ -401,9 +401,11 @@ def bench_serve(torch, dev, peak, args, cpu=True):
            "config": {"workload": f"serving, Poisson arrivals mean {args.rate:g} req/s, "
                                   f"{n} requests K ~ U{{5..200}}, T ~ U{{12..104}}, "
                                   f"{iters} iterations each", "requests": n, "iters": iters,
-                      "slots": args.slots, "max_batch": args.max_batch},
-           "batches": s["batches"], "span_s": s["span_s"], "clocks": clk.summary(),
-           "timing": "host clock, arrival to result on the host"}
+                      "slots": args.slots, "max_runs_per_team": args.max_runs,
+                      "batching": "continuous: requests join running launches through "
+                                  "device queues and retire one by one"},
+           "launches": s["batches"], "max_inflight": s["max_inflight"], "span_s": s["span_s"],
+           "clocks": clk.summary(), "timing": "host clock, arrival to result on the host"}
     if cpu and not args.no_cpu_baseline:
         m = 16
         rec["cpu_baseline"] = cpu_baseline_pool(
@@ -642,8 +644,9 @@ def main():
                     choices=["plain", "batch", "multistart", "serve"])
     ap.add_argument("--rate", type=float, default=2000.0, help="serving arrivals per second")
     ap.add_argument("--requests", type=int, default=2000, help="serving requests")
-    ap.add_argument("--slots", type=int, default=4, help="serving stream slots")
-    ap.add_argument("--max-batch", type=int, default=304, help="serving requests per batch")
+    ap.add_argument("--slots", type=int, default=2048, help="serving requests in flight at most")
+    ap.add_argument("--max-runs", type=int, default=8,
+                    help="serving requests a team solves before it leaves its SMs")
     ap.add_argument("--n", type=int, default=0, help="instances / starts of a batched workload")
     ap.add_argument("--iters", type=int, default=None,
                     help="override the iteration budget (profiling of small cases only)")

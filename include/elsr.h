@@ -60,6 +60,7 @@ extern "C" {
 #define ELSR_E_STATE (-6) /* call out of order (e.g. no result yet), or a
                              resumed state that does not match its checkpoint */
 #define ELSR_E_TIMEOUT (-7) /* a device-side wait exceeded its limit */
+#define ELSR_E_BUSY (-8)  /* serving: no room for a request now (retry later) */
 
 #define ELSR_T_MAX 128 /* periods per product */
 #define ELSR_MODE_P 0  /* Algorithm 1: each product takes its best move */
@@ -480,6 +481,88 @@ int elsr_batch_results(elsr_batch_t *b, elsr_stats_t *stats);
 
 /* Solution of instance i of the last batch run: gM, gR host [K_i][T_i]. */
 int elsr_batch_solution(elsr_batch_t *b, int32_t i, uint8_t *gM, uint8_t *gR);
+
+/*
+ * Serving (the paper has one instance per run; serving requests of many
+ * instances as they arrive is this library's).  A server holds fixed-size
+ * device pools for the instances of the requests in flight and solves each
+ * request's GVNS run (Algorithm 2 with Algorithm 1's VND, mode P or G, from
+ * the all-open start) exactly as elsr_vns_run would: the same statistics
+ * and trajectory hash, whatever else is in flight.  Requests join the
+ * kernels already running and retire one by one, in any order.
+ *
+ * Requests are grouped by the CTAs (1..16) their rows need and by T <= 64 or
+ * not; each group has a queue in device memory.  A launch of a group runs
+ * one team per CTA cluster; a team takes the next queued request, solves
+ * it, writes its statistics into host memory and takes the next, and exits
+ * when the queue is empty or after max_runs requests (leaving its SMs to
+ * other groups).  Nothing on the device waits for the host; the host
+ * launches a group again while it has requests not yet retired.  Work is
+ * issued on streams the server owns; every call returns without waiting for
+ * the device.  A server uses the device that is current at creation; call it
+ * with that device current, from one host thread at a time.
+ */
+typedef struct elsr_server elsr_server_t;
+
+typedef struct {
+    int32_t slots;          /* requests in flight at most; 0: 2048 */
+    int32_t threads;        /* threads per CTA, a multiple of 32 <= 1024; 0: 1024 */
+    int64_t cells;          /* demand/return values the pools hold; 0: 8 Mi */
+    int64_t rows;           /* product rows the pools hold; 0: 512 Ki */
+    int32_t max_runs;       /* requests a team solves before it exits; 0: 8 */
+    int32_t acc64;          /* 1: 64-bit row accumulators (admits any instance);
+                               0: 32-bit (refuses instances that need 64) */
+    int32_t count_steps;    /* 1: count decode steps (stats.segments); 0: not */
+    int32_t keep_solutions; /* 1: a reported request keeps its solution until
+                               elsr_server_release; 0: freed when reported */
+} elsr_server_config_t;
+
+/* Create a server (cfg NULL: every default, steps not counted, solutions
+ * not kept).  Allocates its pools (device), staging buffers (pinned host)
+ * and result words (host memory mapped into the device).  ELSR_E_ARG for an
+ * invalid field, ELSR_E_NOMEM / ELSR_E_CUDA when an allocation fails. */
+int elsr_server_create(elsr_server_t **out, const elsr_server_config_t *cfg);
+
+/* Waits for the server's launches and copies, then frees everything. */
+void elsr_server_destroy(elsr_server_t *s);
+
+const char *elsr_server_last_error(const elsr_server_t *s);
+
+/*
+ * Submit one request: an instance as in elsr_create (host arrays D, R
+ * [K][T], kM, kR, hM, hR [K], copied: the caller keeps them) and a GVNS run
+ * (seed, iters, kmax <= 3, mode).  *ticket receives the request's ticket.
+ * Admission by footprint: the request needs a free slot, K*T cells and K
+ * rows of the pools; when they are not free now the call returns
+ * ELSR_E_BUSY (retry after elsr_server_poll reports completions).
+ * ELSR_E_RANGE when it can never be admitted: it exceeds the pools, its rows
+ * need more than 16 CTAs, or it needs 64-bit accumulators on a 32-bit
+ * server; ELSR_E_ARG / ELSR_E_RANGE as elsr_create for the instance.
+ */
+int elsr_server_submit(elsr_server_t *s, int32_t K, int32_t T, const int32_t *D,
+                       const int32_t *R, const int32_t *kM, const int32_t *kR,
+                       const int32_t *hM, const int32_t *hR, uint64_t seed,
+                       int32_t iters, int32_t kmax, int32_t mode, int64_t *ticket);
+
+/* Report up to max retired requests: tickets[i] (host) and, when stats is
+ * not NULL, their statistics as elsr_result reports them (status ELSR_OK,
+ * ELSR_E_CAP or ELSR_E_CUDA).  Returns how many (>= 0) or a negative error.
+ * Also launches groups that still have requests to solve; a caller polls
+ * until every ticket it submitted has been reported. */
+int elsr_server_poll(elsr_server_t *s, int32_t max, int64_t *tickets,
+                     elsr_stats_t *stats);
+
+/* Solution of a retired request (host gM, gR [K][T] 0/1): before the poll
+ * that reports it, or after it on a server that keeps solutions.
+ * ELSR_E_STATE when the ticket has not retired or is no longer held. */
+int elsr_server_solution(elsr_server_t *s, int64_t ticket, uint8_t *gM, uint8_t *gR);
+
+/* Free a reported request of a server that keeps solutions. */
+int elsr_server_release(elsr_server_t *s, int64_t ticket);
+
+/* Requests in flight (submitted, not yet freed) and kernel launches so far
+ * (either pointer may be NULL). */
+int elsr_server_info(const elsr_server_t *s, int64_t *inflight, int64_t *launches);
 
 /*
  * Integer-issue probe, a measurement aid with no counterpart in the paper:

@@ -21,6 +21,7 @@ ELSR_E_CUDA = -4
 ELSR_E_CAP = -5
 ELSR_E_STATE = -6
 ELSR_E_TIMEOUT = -7
+ELSR_E_BUSY = -8
 MODE_P = 0
 MODE_G = 1
 T_MAX = 128
@@ -115,7 +116,24 @@ SIGNATURES = {
     "elsr_batch_results": (ctypes.c_int, [P, P]),
     "elsr_batch_solution": (ctypes.c_int, [P, i32, P, P]),
     "elsr_int_issue_probe": (ctypes.c_int, [P, i32, i32, P, P, P]),
+    "elsr_server_create": (ctypes.c_int, [ctypes.POINTER(P), P]),
+    "elsr_server_destroy": (None, [P]),
+    "elsr_server_last_error": (ctypes.c_char_p, [P]),
+    "elsr_server_submit": (ctypes.c_int, [P, i32, i32, P, P, P, P, P, P, u64, i32, i32, i32,
+                                          P]),
+    "elsr_server_poll": (ctypes.c_int, [P, i32, P, P]),
+    "elsr_server_solution": (ctypes.c_int, [P, i64, P, P]),
+    "elsr_server_release": (ctypes.c_int, [P, i64]),
+    "elsr_server_info": (ctypes.c_int, [P, P, P]),
 }
+
+
+class ServerConfig(ctypes.Structure):
+    """elsr_server_config_t."""
+    _fields_ = [("slots", ctypes.c_int32), ("threads", ctypes.c_int32),
+                ("cells", ctypes.c_int64), ("rows", ctypes.c_int64),
+                ("max_runs", ctypes.c_int32), ("acc64", ctypes.c_int32),
+                ("count_steps", ctypes.c_int32), ("keep_solutions", ctypes.c_int32)]
 
 _lock = threading.Lock()
 _lib = None
@@ -150,10 +168,11 @@ class ElsrError(RuntimeError):
         self.code = code
 
 
-def check(code: int, handle=None, batch=False) -> int:
+def check(code: int, handle=None, batch=False, server=False) -> int:
     if code < 0:
         lib = load()
-        msg = (lib.elsr_batch_last_error(handle) if batch
+        msg = (lib.elsr_server_last_error(handle) if server
+               else lib.elsr_batch_last_error(handle) if batch
                else lib.elsr_last_error(handle))
         base = lib.elsr_strerror(code).decode()
         detail = msg.decode() if msg else ""

@@ -3,7 +3,8 @@
 The translation units compile in parallel, then link into one shared
 library.  The persistent GVNS kernels are compiled once per instantiation
 (accumulator width x bit-row words x table placement x block bound = 24
-objects from elsr_vns_inst.cu), so no single object carries all of them.
+objects from elsr_vns_inst.cu, and 4 of the serving kernel from
+elsr_srv_inst.cu), so no single object carries all of them.
 Only nvcc and the host compiler are needed; no cmake.
 """
 from __future__ import annotations
@@ -19,7 +20,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libelsr.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 SOURCES = ["elsr_vns_dispatch.cu", "elsr_kernels.cu", "elsr_abi.cu", "elsr_static.cu",
-           "elsr_probe.cu"]
+           "elsr_probe.cu", "elsr_serve.cu"]
 HEADERS = ["elsr_row.cuh", "elsr_internal.h", "elsr_vns.cuh"]
 # (object suffix, defines) of each GVNS kernel instantiation
 VNS_INST = [(f"i{acc[3:5]}_w{nw}_{'s' if ts else 'g'}{maxt}",
@@ -27,6 +28,10 @@ VNS_INST = [(f"i{acc[3:5]}_w{nw}_{'s' if ts else 'g'}{maxt}",
               f"-DELSR_INST_MAXT={maxt}"])
             for acc in ("int32_t", "int64_t") for nw in (1, 2) for ts in (1, 0)
             for maxt in (256, 512, 1024)]
+
+# (object suffix, defines) of each serving-kernel instantiation
+SRV_INST = [(f"i{acc[3:5]}_w{nw}", [f"-DELSR_INST_ACC={acc}", f"-DELSR_INST_NW={nw}"])
+            for acc in ("int32_t", "int64_t") for nw in (1, 2)]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
@@ -55,6 +60,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     jobs = []
     units = [(src, src.replace(".cu", ".o"), []) for src in SOURCES]
     units += [("elsr_vns_inst.cu", f"elsr_vns_{suf}.o", defs) for suf, defs in VNS_INST]
+    units += [("elsr_srv_inst.cu", f"elsr_srv_{suf}.o", defs) for suf, defs in SRV_INST]
     for src, obj, defs in units:
         s = os.path.join(CSRC, src)
         o = os.path.join(BUILD, obj)

@@ -119,6 +119,18 @@ int default_lanes(int T, bool single) {
 
 }  // namespace
 
+namespace elsr {
+
+int validate_instance(int32_t K, int32_t T, const int32_t* D, const int32_t* R,
+                      const int32_t* kM, const int32_t* kR, const int32_t* hM,
+                      const int32_t* hR, bool* acc64, std::string& err) {
+  unsigned __int128 total = 0;
+  *acc64 = false;
+  return check_instance(K, T, D, R, kM, kR, hM, hR, nullptr, nullptr, acc64, &total, err);
+}
+
+}  // namespace elsr
+
 // ---------------------------------------------------------------------------
 // Batch (a set of instances resident on the device)
 // ---------------------------------------------------------------------------
@@ -830,6 +842,7 @@ const char* elsr_strerror(int code) {
     case ELSR_E_CAP: return "VND sweep cap reached";
     case ELSR_E_STATE: return "call out of order";
     case ELSR_E_TIMEOUT: return "a device-side wait exceeded its limit";
+    case ELSR_E_BUSY: return "no room for the request now; retry after a completion";
     default: return "unknown error";
   }
 }
@@ -1071,7 +1084,7 @@ RunDesc single_run(uint64_t seed, int32_t iters, int32_t kmax, int32_t mode) {
   r.mode = mode;
   r.seed = seed;
   r.out = 0;
-  r.pad = 0;
+  r.tag = 0;
   r.bits_off = 0;
   r.start_off = 0;
   r.traj_off = 0;
@@ -1261,7 +1274,7 @@ int elsr_multistart_run(elsr_t* h, uint64_t seed0, int32_t nstarts, int32_t iter
     r.mode = mode;
     r.seed = seed0 + (uint64_t)s;
     r.out = s;
-    r.pad = 0;
+    r.tag = 0;
     r.bits_off = (int64_t)s * h->K;
     r.start_off = 0;
     r.traj_off = -1;
@@ -1469,7 +1482,7 @@ int elsr_batch_run(elsr_batch_t* b, const uint64_t* seeds, int32_t iters, int32_
     r.mode = mode;
     r.seed = seeds[i];
     r.out = i;
-    r.pad = 0;
+    r.tag = 0;
     r.bits_off = b->insts[i].row_off;
     r.start_off = -1;
     r.traj_off = -1;

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "elsr_row.cuh"
 
 namespace elsr {
@@ -38,7 +40,7 @@ struct RunDesc {
   int32_t mode;
   uint64_t seed;
   int32_t out;        // index into the per-run outputs
-  int32_t pad;
+  int32_t tag;        // echoed when a served request retires (serving: its ticket)
   int64_t bits_off;   // RowBits offset of this run's solution output
   int64_t start_off;  // RowBits offset of its start solution (-1: all open)
   int64_t traj_off;   // trajectory entry offset (-1: none)
@@ -135,6 +137,19 @@ struct VnsParams {
   int32_t pad2;
 };
 
+// Serving queue of one request class (CTAs per team, words per bit row):
+// the host appends slot numbers at slots[tail % cap] and then publishes the
+// new tail; teams claim positions head .. tail - 1.  A retired request's slot
+// gets done[slot] = its RunDesc tag + 1, in memory the host reads directly.
+struct SrvQueue {
+  const int32_t* slots;  // [cap] slot of each queue position (mod cap)
+  int32_t* head;         // positions claimed
+  const int32_t* tail;   // positions published
+  int32_t* done;         // [slots of the server] retire words (host-mapped)
+  int32_t cap;
+  int32_t max_runs;      // requests a team serves before it exits (yields its SMs)
+};
+
 struct StageParams {
   InstPools ip;
   int32_t ninst;
@@ -217,6 +232,12 @@ ELSR_HD VnsLayout vns_layout(int Kc, int T, int acc_bytes, bool tab_smem) {
   return L;
 }
 
+// Create-time checks of one instance without unit production costs (the
+// ranges of elsr.h); sets *acc64 when its rows need 64-bit accumulators.
+int validate_instance(int32_t K, int32_t T, const int32_t* D, const int32_t* R,
+                      const int32_t* kM, const int32_t* kR, const int32_t* hM,
+                      const int32_t* hR, bool* acc64, std::string& err);
+
 // Launchers.  Each returns the launch error.
 cudaError_t launch_stage(const StageParams& p, int total_rows, cudaStream_t s);
 cudaError_t launch_eval(const EvalParams& p, bool acc64, int blocks,
@@ -242,6 +263,17 @@ cudaError_t vns_prepare_t(size_t smem, int threads, int cluster, int* active);
 template <typename Acc, int NW, bool TS, int MAXT>
 cudaError_t vns_launch_t(const VnsParams& p, int blocks, int threads, size_t smem,
                          int cluster, cudaStream_t s);
+
+// Serving kernel (elsr_vns.cuh, prefix tables in shared memory, 1024-thread
+// bound), instantiated per accumulator width and words per bit row.
+template <typename Acc, int NW>
+cudaError_t srv_prepare_t(size_t smem, int threads, int cluster, int* active);
+template <typename Acc, int NW>
+cudaError_t srv_launch_t(const VnsParams& p, const SrvQueue& q, int blocks, int threads,
+                         size_t smem, int cluster, cudaStream_t s);
+cudaError_t srv_prepare(bool acc64, int nw, size_t smem, int threads, int cluster, int* active);
+cudaError_t srv_launch(bool acc64, int nw, const VnsParams& p, const SrvQueue& q, int blocks,
+                       int threads, size_t smem, int cluster, cudaStream_t s);
 
 // Run-time choice of the instantiation (elsr_vns_dispatch.cu).
 cudaError_t vns_prepare(bool acc64, int nw, bool ts, int maxt, size_t smem, int threads,

@@ -50,6 +50,15 @@ __device__ __forceinline__ RowBits all_open(int T) {
 // Stage one row with a full warp: tab[0..T] = {CD[j], CR1[j]} by warp
 // inclusive scans over 32-period chunks (coalesced int32 loads), and the row
 // constant C0 = hR * sum R(t)(T-t) - hM * sum D(t)(T-t) + pM * sum D.
+// Fresh: load through L2 only (ld.global.cg), for data the host may have
+// rewritten while the kernel was resident (the read-only and L1 paths are
+// not kept coherent with such writes).
+template <bool Fresh = false>
+__device__ __forceinline__ int32_t ld_in(const int32_t* p) {
+  return Fresh ? __ldcg(p) : __ldg(p);
+}
+
+template <bool Fresh = false>
 __device__ __forceinline__ void stage_row_warp(const int32_t* __restrict__ D,
                                                const int32_t* __restrict__ R, int T,
                                                int lane, int2* tab, int32_t hM,
@@ -58,8 +67,8 @@ __device__ __forceinline__ void stage_row_warp(const int32_t* __restrict__ D,
   int64_t wd = 0, wr = 0;
   for (int base = 0; base < T; base += 32) {
     const int t = base + lane;
-    const int32_t d = t < T ? __ldg(D + t) : 0;
-    const int32_t r = t < T ? __ldg(R + t) : 0;
+    const int32_t d = t < T ? ld_in<Fresh>(D + t) : 0;
+    const int32_t r = t < T ? ld_in<Fresh>(R + t) : 0;
     wd += (int64_t)d * (T - t);
     wr += (int64_t)r * (T - t);
     int32_t sd = d, sr = r;
@@ -89,9 +98,22 @@ __device__ __forceinline__ void stage_row_warp(const int32_t* __restrict__ D,
 }
 
 // Costs of pool row ro (unit production costs 0 when the pools have none).
+template <bool Fresh = false>
 __device__ __forceinline__ RowCosts row_costs(const InstPools& ip, int64_t ro) {
-  const int32_t pm = ip.pM ? ip.pM[ro] : 0, pr = ip.pR ? ip.pR[ro] : 0;
-  return RowCosts{ip.kM[ro], ip.kR[ro], ip.hM[ro], ip.hR[ro], pr - pm};
+  const int32_t pm = ip.pM ? ld_in<Fresh>(ip.pM + ro) : 0;
+  const int32_t pr = ip.pR ? ld_in<Fresh>(ip.pR + ro) : 0;
+  return RowCosts{ld_in<Fresh>(ip.kM + ro), ld_in<Fresh>(ip.kR + ro), ld_in<Fresh>(ip.hM + ro),
+                  ld_in<Fresh>(ip.hR + ro), pr - pm};
+}
+
+__device__ __forceinline__ InstDesc ldcg_inst(const InstDesc* d) {
+  static_assert(sizeof(InstDesc) == 32, "InstDesc is four 64-bit words");
+  InstDesc o;
+  unsigned long long* w = (unsigned long long*)&o;
+  const unsigned long long* s = (const unsigned long long*)d;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) w[i] = __ldcg(s + i);
+  return o;
 }
 
 // Shared-memory view of the rows a CTA owns in the current run.
@@ -700,10 +722,10 @@ __device__ __forceinline__ uint32_t dynamic_smem_bytes() {
 // what the run needs: another cluster size than configured, or less shared
 // memory in the team's region (`region` bytes from `smem`) than the run's
 // layout; nothing is touched then.
-template <typename Acc, int NW, bool TS>
+template <typename Acc, int NW, bool TS, bool Fresh = false>
 __device__ bool team_begin(Team<Acc>& t, unsigned char* smem, uint32_t region, CtlShared* sh,
                            const VnsParams& p, const RunDesc& rd) {
-  const InstDesc id = p.ip.insts[rd.inst];
+  const InstDesc id = Fresh ? ldcg_inst(p.ip.insts + rd.inst) : p.ip.insts[rd.inst];
   const int K = id.K, T = id.T, C = t.C, crank = t.crank;
   t.sh = sh;
   t.K = K;
@@ -740,15 +762,16 @@ __device__ bool team_begin(Team<Acc>& t, unsigned char* smem, uint32_t region, C
     const int k = q * C + crank;
     const int64_t ro = id.row_off + k;
     if (TS) {
-      stage_row_warp(p.ip.D + id.cell_off + (int64_t)k * T,
-                     p.ip.R + id.cell_off + (int64_t)k * T, T, t.wlane,
-                     (int2*)(smem + Lay.tab) + (int64_t)q * (T + 1), p.ip.hM[ro],
-                     p.ip.hR[ro], p.ip.pM ? p.ip.pM[ro] : 0, &m.C0[q]);
+      stage_row_warp<Fresh>(p.ip.D + id.cell_off + (int64_t)k * T,
+                            p.ip.R + id.cell_off + (int64_t)k * T, T, t.wlane,
+                            (int2*)(smem + Lay.tab) + (int64_t)q * (T + 1),
+                            ld_in<Fresh>(p.ip.hM + ro), ld_in<Fresh>(p.ip.hR + ro),
+                            p.ip.pM ? ld_in<Fresh>(p.ip.pM + ro) : 0, &m.C0[q]);
     } else if (t.wlane == 0) {
       m.C0[q] = p.ip.gC0[ro];
     }
     if (t.wlane == 0) {
-      m.rc[q] = row_costs(p.ip, ro);
+      m.rc[q] = row_costs<Fresh>(p.ip, ro);
       m.bits[q] = rd.start_off >= 0 ? p.start_bits[rd.start_off + k] : all_open(T);
     }
   }
@@ -1168,6 +1191,96 @@ __device__ __forceinline__ int run_lanes(int G0, int K, int C, int threads, int 
 constexpr uint32_t kCtlBytes = kPartCtlBytes;
 static_assert(sizeof(CtlShared) <= kCtlBytes, "partition control words outgrow their room");
 
+// One GVNS run of Algorithm 2 by a team whose rows are staged (team_begin):
+// VND from the start (unless resumed), then shake / VND / accept for the
+// run's iterations; the run's solution goes to p.out_bits + rd.bits_off and
+// its statistics to p.out[rd.out].  Ends with a team barrier.
+template <typename Acc, int NW>
+__device__ __forceinline__ void gvns_run(Team<Acc>& t, CtlShared* sh, const VnsParams& p,
+                                         const RunDesc& rd) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int K = t.K, T = t.T;
+  const int64_t moves_per_cycle = (int64_t)K * (2 * T + (T > 1 ? 2 * (T - 1) : 0));
+  // wall-clock budget from the run's start (thread 0 of CTA 0 keeps time)
+  const long long deadline = rd.time_limit_ns > 0 && t.crank == 0 && t.tid == 0
+                                 ? globaltimer_ns() + rd.time_limit_ns : 0;
+  int status = 0, stop = 0;
+  int64_t cycles_total = 0;
+  int cyc = 0;
+  if (!rd.resume) {  // a resumed run starts from VND's output
+    cyc = vnd<Acc, NW>(t, rd.mode);
+    if (cyc < 0) status = kStatusCap; else cycles_total += cyc;
+  }
+  int64_t fx = team_total(t);
+  if (rd.resume && fx != rd.f0) status = kStatusState;
+  int kk = rd.k0;  // neighbourhood index k of Algorithm 2
+  uint64_t h = rd.h0;
+  int64_t iters_done = 0, accepted = 0;
+  const bool log = rd.traj_off >= 0 && t.crank == 0 && t.tid == 0;
+  const int it_end = rd.it0 + rd.iters;
+  for (int it = rd.it0; it < it_end && status == 0 && !stop; ++it) {
+    const int par = it & 1;
+    const int ks = kk;
+    const ShakePlan pl = plan_shake(rd.seed, it, ks, K, T);
+    apply_shake<Acc, NW>(t, pl, ks, par);
+    cyc = vnd<Acc, NW>(t, rd.mode);
+    if (cyc < 0) status = kStatusCap; else cycles_total += cyc;
+    const int64_t f2 = rd.time_limit_ns > 0 ? team_total(t, deadline, &stop) : team_total(t);
+    const int acc = f2 < fx;
+    if (t.crank == 0 && t.tid == 0) {
+      if (log) {
+        TrajEntry te;
+        te.it = it;
+        te.k = ks;
+        te.cost = f2;
+        te.accepted = acc;
+        te.reserved = 0;
+        p.traj[rd.traj_off + (it - rd.it0)] = te;
+      }
+      h = splitmix64(h ^ (uint64_t)f2);
+      h = splitmix64(h ^ (((uint64_t)it << 32) | ((uint64_t)ks << 1) | (uint64_t)acc));
+    }
+    ++iters_done;
+    if (acc) {
+      fx = f2;
+      kk = 1;
+      ++accepted;
+    } else {
+      undo_shake<Acc>(t, pl, par);
+      kk = kk % rd.kmax + 1;
+    }
+    if ((it & 255) == 255) flush_counters(t, &sh->steps, &sh->applied);
+  }
+  cta_sync(t);  // restores of the last iteration are complete
+  for (int q = t.tid; q < t.Kc; q += t.nthr)
+    p.out_bits[rd.bits_off + q * t.C + t.crank] = t.m.bits[q];
+  flush_counters(t, &sh->steps, &sh->applied);
+  team_sync(t);
+  if (t.tid == 0 && t.crank == 0) {
+    unsigned long long steps = 0, applied = 0;
+    for (int c = 0; c < t.C; ++c) {
+      steps += t.C == 1 ? sh->steps : *cl.map_shared_rank(&sh->steps, c);
+      applied += t.C == 1 ? sh->applied : *cl.map_shared_rank(&sh->applied, c);
+    }
+    RunOut o;
+    o.best_cost = fx;
+    o.traj_hash = h;
+    o.moves_evaluated = cycles_total * moves_per_cycle;
+    o.evals = cycles_total * 3;
+    o.vnd_cycles = cycles_total;
+    o.applied = (int64_t)applied;
+    o.iterations = iters_done;
+    o.accepted = accepted;
+    o.segments = p.count_steps ? (int64_t)steps : 0;
+    o.status = status;
+    o.reserved = 0;
+    o.k_next = kk;
+    o.pad = 0;
+    p.out[rd.out] = o;
+  }
+  team_sync(t);
+}
+
 // One team's run loop: runs [first, end) from `queue`, in `region` bytes of
 // shared memory from `base`, control words in `sh`.  Inlined into each phase
 // of vns_kernel, so neither phase keeps the other's state live.
@@ -1190,86 +1303,7 @@ __device__ __forceinline__ void run_loop(Team<Acc>& t, unsigned char* base, uint
       team_sync(t);
       continue;
     }
-    const int K = t.K, T = t.T;
-    const int64_t moves_per_cycle = (int64_t)K * (2 * T + (T > 1 ? 2 * (T - 1) : 0));
-    // wall-clock budget from the run's start (thread 0 of CTA 0 keeps time)
-    const long long deadline = rd.time_limit_ns > 0 && t.crank == 0 && t.tid == 0
-                                   ? globaltimer_ns() + rd.time_limit_ns : 0;
-    int status = 0, stop = 0;
-    int64_t cycles_total = 0;
-    int cyc = 0;
-    if (!rd.resume) {  // a resumed run starts from VND's output
-      cyc = vnd<Acc, NW>(t, rd.mode);
-      if (cyc < 0) status = kStatusCap; else cycles_total += cyc;
-    }
-    int64_t fx = team_total(t);
-    if (rd.resume && fx != rd.f0) status = kStatusState;
-    int kk = rd.k0;  // neighbourhood index k of Algorithm 2
-    uint64_t h = rd.h0;
-    int64_t iters_done = 0, accepted = 0;
-    const bool log = rd.traj_off >= 0 && t.crank == 0 && t.tid == 0;
-    const int it_end = rd.it0 + rd.iters;
-    for (int it = rd.it0; it < it_end && status == 0 && !stop; ++it) {
-      const int par = it & 1;
-      const int ks = kk;
-      const ShakePlan pl = plan_shake(rd.seed, it, ks, K, T);
-      apply_shake<Acc, NW>(t, pl, ks, par);
-      cyc = vnd<Acc, NW>(t, rd.mode);
-      if (cyc < 0) status = kStatusCap; else cycles_total += cyc;
-      const int64_t f2 = rd.time_limit_ns > 0 ? team_total(t, deadline, &stop) : team_total(t);
-      const int acc = f2 < fx;
-      if (t.crank == 0 && t.tid == 0) {
-        if (log) {
-          TrajEntry te;
-          te.it = it;
-          te.k = ks;
-          te.cost = f2;
-          te.accepted = acc;
-          te.reserved = 0;
-          p.traj[rd.traj_off + (it - rd.it0)] = te;
-        }
-        h = splitmix64(h ^ (uint64_t)f2);
-        h = splitmix64(h ^ (((uint64_t)it << 32) | ((uint64_t)ks << 1) | (uint64_t)acc));
-      }
-      ++iters_done;
-      if (acc) {
-        fx = f2;
-        kk = 1;
-        ++accepted;
-      } else {
-        undo_shake<Acc>(t, pl, par);
-        kk = kk % rd.kmax + 1;
-      }
-      if ((it & 255) == 255) flush_counters(t, &sh->steps, &sh->applied);
-    }
-    cta_sync(t);  // restores of the last iteration are complete
-    for (int q = t.tid; q < t.Kc; q += t.nthr)
-      p.out_bits[rd.bits_off + q * t.C + t.crank] = t.m.bits[q];
-    flush_counters(t, &sh->steps, &sh->applied);
-    team_sync(t);
-    if (t.tid == 0 && t.crank == 0) {
-      unsigned long long steps = 0, applied = 0;
-      for (int c = 0; c < t.C; ++c) {
-        steps += t.C == 1 ? sh->steps : *cl.map_shared_rank(&sh->steps, c);
-        applied += t.C == 1 ? sh->applied : *cl.map_shared_rank(&sh->applied, c);
-      }
-      RunOut o;
-      o.best_cost = fx;
-      o.traj_hash = h;
-      o.moves_evaluated = cycles_total * moves_per_cycle;
-      o.evals = cycles_total * 3;
-      o.vnd_cycles = cycles_total;
-      o.applied = (int64_t)applied;
-      o.iterations = iters_done;
-      o.accepted = accepted;
-      o.segments = (int64_t)steps;
-      o.status = status;
-      o.reserved = 0;
-      o.k_next = kk;
-      o.pad = 0;
-      p.out[rd.out] = o;
-    }
-    team_sync(t);
+    gvns_run<Acc, NW>(t, sh, p, rd);
   }
 }
 
@@ -1295,6 +1329,72 @@ __global__ void __launch_bounds__(MAXT, 1) vns_kernel(const VnsParams p) {
   } else {  // not a shape the host launches: the whole team takes these runs
     run_loop<Acc, NW, TS>(t, smem, dynamic_smem_bytes(), &sh, p, p.queue + 1, p.n_whole,
                           p.nruns, 128);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// srv_kernel: serving.  Requests arrive while kernels run: the host stages a
+// request's instance into the pools, appends its slot to the queue of its
+// class (CTAs per team, words per bit row) and publishes the new tail.  Each
+// team (a cluster of the launch) claims the next published position, runs
+// that request's GVNS, writes its statistics and solution to host-mapped
+// memory and then its retire word, so every request retires on its own and
+// a request published after the launch began joins it.  Nothing waits: a
+// team whose claim finds the queue empty exits, and so does one that has
+// served q.max_runs requests (its SMs go to the launches of other classes);
+// the host launches again while published requests remain unclaimed.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int srv_claim(const SrvQueue& q) {
+  for (int tries = 0; tries < 64; ++tries) {  // bounded: another team won each race
+    const int h = *(volatile const int*)q.head;
+    const int tl = *(volatile const int*)q.tail;
+    if (h >= tl) return -1;
+    if (atomicCAS(q.head, h, h + 1) == h) return h;
+  }
+  return -1;
+}
+
+__device__ __forceinline__ RunDesc ldcg_run(const RunDesc* d) {
+  static_assert(sizeof(RunDesc) % 8 == 0, "RunDesc is whole 64-bit words");
+  RunDesc o;
+  unsigned long long* w = (unsigned long long*)&o;
+  const unsigned long long* s = (const unsigned long long*)d;
+#pragma unroll
+  for (int i = 0; i < (int)(sizeof(RunDesc) / 8); ++i) w[i] = __ldcg(s + i);
+  return o;
+}
+
+// Lanes per row of a batched run of T periods before any widening (the
+// host's batch default).
+__device__ __forceinline__ int batch_lanes(int T) { return T <= 8 ? 4 : (T <= 24 ? 8 : 16); }
+
+template <typename Acc, int NW, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) srv_kernel(const VnsParams p, const SrvQueue q) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ CtlShared sh;
+  Team<Acc> t;
+  team_init(t, 16);
+  cg::cluster_group cl = cg::this_cluster();
+  for (int served = 0; served < q.max_runs; ++served) {
+    if (t.crank == 0 && t.tid == 0) sh.run = srv_claim(q);
+    team_sync(t);
+    const int r = t.C == 1 ? sh.run : *cl.map_shared_rank(&sh.run, 0);
+    team_sync(t);
+    if (r < 0) return;
+    const int slot = __ldcg(q.slots + (r % q.cap));
+    const RunDesc rd = ldcg_run(p.runs + slot);
+    const InstDesc id = ldcg_inst(p.ip.insts + rd.inst);
+    team_set_lanes(t, run_lanes(batch_lanes(id.T), id.K, t.C, t.nthr, 128));
+    if (team_begin<Acc, NW, true, true>(t, smem, dynamic_smem_bytes(), &sh, p, rd)) {
+      gvns_run<Acc, NW>(t, &sh, p, rd);
+    } else {
+      if (t.crank == 0 && t.tid == 0) write_failed_run(p, rd, kStatusLaunch);
+      team_sync(t);
+    }
+    // every thread's solution words reach the host before the retire word
+    __threadfence_system();
+    team_sync(t);
+    if (t.crank == 0 && t.tid == 0) *(volatile int32_t*)(q.done + slot) = rd.tag + 1;
   }
 }
 
@@ -1565,7 +1665,7 @@ __global__ void __launch_bounds__(MAXT, 1) spec_kernel(const VnsParams p) {
     o.applied = (int64_t)applied;
     o.iterations = it0 - rd.it0;
     o.accepted = accepted;
-    o.segments = (int64_t)steps;
+    o.segments = p.count_steps ? (int64_t)steps : 0;
     o.status = status;
     o.reserved = 0;
     o.k_next = k0;
@@ -1742,7 +1842,7 @@ __global__ void __launch_bounds__(MAXT, 1) fj_kernel(const VnsParams p) {
     o.applied = (int64_t)applied;
     o.iterations = it - rd.it0;
     o.accepted = accepted;
-    o.segments = (int64_t)steps;
+    o.segments = p.count_steps ? (int64_t)steps : 0;
     o.status = status;
     o.reserved = W;
     o.k_next = kk;
@@ -1808,6 +1908,50 @@ cudaError_t vns_launch_t(const VnsParams& p, int blocks, int threads, size_t sme
   if (p.fj_workers > 0) return cudaLaunchKernelEx(&cfg, vns::fj_kernel<Acc, NW, TS, MAXT>, p);
   if (p.spec_teams <= 1) return cudaLaunchKernelEx(&cfg, vns::vns_kernel<Acc, NW, TS, MAXT>, p);
   return cudaLaunchKernelEx(&cfg, vns::spec_kernel<Acc, NW, TS, MAXT>, p);
+}
+
+template <typename Acc, int NW>
+cudaError_t srv_prepare_t(size_t smem, int threads, int cluster, int* active) {
+  auto kern = vns::srv_kernel<Acc, NW, 1024>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess && cluster > 8)
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e != cudaSuccess) return e;
+  if (cluster <= 1) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(active, kern, threads, smem);
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(cluster, 1, 1);
+  cfg.blockDim = dim3(threads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaOccupancyMaxActiveClusters(active, kern, &cfg);
+}
+
+template <typename Acc, int NW>
+cudaError_t srv_launch_t(const VnsParams& p, const SrvQueue& q, int blocks, int threads,
+                         size_t smem, int cluster, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  int na = 0;
+  if (cluster > 1) {
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    na = 1;
+  }
+  cfg.gridDim = dim3(blocks, 1, 1);
+  cfg.blockDim = dim3(threads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = na;
+  return cudaLaunchKernelEx(&cfg, vns::srv_kernel<Acc, NW, 1024>, p, q);
 }
 
 }  // namespace elsr

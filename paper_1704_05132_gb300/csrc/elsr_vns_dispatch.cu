@@ -1,5 +1,5 @@
 // elsr_vns_dispatch.cu -- run-time choice among the compiled instantiations
-// of the persistent GVNS kernels (each lives in its own object built from
+// of the persistent GVNS kernels and the serving kernel (each lives in its own object built from
 // elsr_vns_inst.cu; only their declarations are visible here).
 #include "elsr_internal.h"
 
@@ -54,6 +54,23 @@ cudaError_t vns_launch(bool acc64, int nw, bool ts, int maxt, const VnsParams& p
                        int blocks, int threads, size_t smem, int cluster, cudaStream_t s) {
   return acc64 ? launch_a<int64_t>(nw, ts, maxt, p, blocks, threads, smem, cluster, s)
                : launch_a<int32_t>(nw, ts, maxt, p, blocks, threads, smem, cluster, s);
+}
+
+cudaError_t srv_prepare(bool acc64, int nw, size_t smem, int threads, int cluster, int* active) {
+  if (acc64)
+    return nw == 1 ? srv_prepare_t<int64_t, 1>(smem, threads, cluster, active)
+                   : srv_prepare_t<int64_t, 2>(smem, threads, cluster, active);
+  return nw == 1 ? srv_prepare_t<int32_t, 1>(smem, threads, cluster, active)
+                 : srv_prepare_t<int32_t, 2>(smem, threads, cluster, active);
+}
+
+cudaError_t srv_launch(bool acc64, int nw, const VnsParams& p, const SrvQueue& q, int blocks,
+                       int threads, size_t smem, int cluster, cudaStream_t s) {
+  if (acc64)
+    return nw == 1 ? srv_launch_t<int64_t, 1>(p, q, blocks, threads, smem, cluster, s)
+                   : srv_launch_t<int64_t, 2>(p, q, blocks, threads, smem, cluster, s);
+  return nw == 1 ? srv_launch_t<int32_t, 1>(p, q, blocks, threads, smem, cluster, s)
+                 : srv_launch_t<int32_t, 2>(p, q, blocks, threads, smem, cluster, s);
 }
 
 }  // namespace elsr

@@ -1,18 +1,19 @@
-"""Continuous-batching server for GVNS solves of independent instances.
+"""Serving GVNS requests with continuous batching.
 
-Requests (an instance, a seed, an iteration budget) arrive over time.  The
-server keeps a pool of CUDA streams ("slots").  Whenever a slot is free, every
-waiting request that fits the device-memory budget is admitted (first come,
-first served) and solved by one persistent batched launch on that slot; while
-it runs, new arrivals queue up and are admitted by the next free slot, so the
-work of several batches overlaps on the device.  Requests whose rows do not
-fit one CTA's shared memory are launched separately (they use CTA clusters),
-so they do not force clusters on small instances.  A batch's device memory
-(instance data, tables, solutions) is held from admission until its results
-are read, and admission never lets the resident bytes exceed the budget.
+Requests (an instance, a seed, an iteration budget) arrive over time.  Each
+is submitted to the library's server (``elsr_server_*`` in the C ABI) as soon
+as it has arrived and fits: the server admits a request by its footprint in
+fixed-size device pools (a slot, K*T cells, K rows) and answers "busy" when
+they are full, in which case the request waits, in arrival order, for
+completions to free room.  On the device a submitted request joins the
+kernels already running: a team that finishes a request takes the next one
+queued for its size class, so requests of different sizes and arrival times
+are solved side by side, and each one retires on its own as soon as its run
+ends (its statistics land in host memory that the loop polls without
+synchronising any stream).
 
 Every request's result depends only on its instance, seed and budget, so it
-is the same whether it is solved alone or in any mix (tested).
+is the same whether it is served alone or in any mix (tested).
 
 Latency of a request = completion time - arrival time, on the host clock.
 """
@@ -26,9 +27,6 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from . import _native as nat
-from .elsr import Batch
-
-SMEM_ONE_CTA = 227 * 1024 - 1024  # dynamic shared bytes per CTA (static control words < 1 KB)
 
 
 @dataclass
@@ -50,7 +48,7 @@ class Result:
     arrival: float
     admitted: float
     done: float
-    batch: int
+    batch: int = 0        # kernel launches issued before it retired
 
     @property
     def latency(self) -> float:
@@ -60,15 +58,17 @@ class Result:
 @dataclass
 class ServeStats:
     results: list = field(default_factory=list)
-    batches: int = 0
+    batches: int = 0            # kernel launches of the server
     max_resident_bytes: int = 0
+    max_inflight: int = 0
     wall_s: float = 0.0
 
     def summary(self) -> dict:
         if not self.results:  # an empty request stream
             return {"requests": 0, "batches": self.batches, "p50_ms": None, "p99_ms": None,
                     "mean_ms": None, "instances_per_s": 0.0, "moves_per_s": 0.0,
-                    "max_resident_bytes": self.max_resident_bytes, "span_s": 0.0}
+                    "max_resident_bytes": self.max_resident_bytes,
+                    "max_inflight": self.max_inflight, "span_s": 0.0}
         lat = np.array([r.latency for r in self.results]) * 1e3
         moves = sum(r.moves_evaluated for r in self.results)
         first = min(r.arrival for r in self.results)
@@ -78,124 +78,168 @@ class ServeStats:
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                 "mean_ms": float(lat.mean()), "instances_per_s": len(self.results) / span,
                 "moves_per_s": moves / span, "max_resident_bytes": self.max_resident_bytes,
-                "span_s": span}
+                "max_inflight": self.max_inflight, "span_s": span}
 
 
-def footprint(K: int, T: int):
-    """(shared bytes per CTA at one CTA per run, device bytes while resident)."""
-    lib = nat.load()
-    sm = ctypes.c_int32()
-    dv = ctypes.c_int64()
-    nat.check(lib.elsr_run_footprint(K, T, ctypes.byref(sm), ctypes.byref(dv)))
-    return int(sm.value), int(dv.value)
+def footprint(K: int, T: int) -> int:
+    """Device bytes a request holds in the server's pools while in flight:
+    D and R (K*T int32 each) and four int32 costs per product."""
+    return 8 * K * T + 16 * K
+
+
+class NativeServer:
+    """The C ABI's server (argument marshalling only)."""
+
+    def __init__(self, slots: int = 0, cells: int = 0, rows: int = 0, threads: int = 0,
+                 max_runs: int = 0, acc64: bool = False, count_steps: bool = False,
+                 keep_solutions: bool = False):
+        self._lib = nat.load()
+        cfg = nat.ServerConfig(slots, threads, cells, rows, max_runs, int(acc64),
+                               int(count_steps), int(keep_solutions))
+        h = ctypes.c_void_p()
+        nat.check(self._lib.elsr_server_create(ctypes.byref(h), ctypes.byref(cfg)))
+        self._h = h
+        self.slots = slots or 2048
+        self.cells = cells or (8 << 20)
+        self.rows = rows or (512 << 10)
+        self._tk = np.zeros(1, np.int64)
+
+    def _chk(self, code):
+        return nat.check(code, self._h, server=True)
+
+    def submit(self, inst, seed: int, iters: int, kmax: int = 3, mode: int = nat.MODE_P):
+        """Ticket of the request, or None when the server is full now."""
+        arr = [np.ascontiguousarray(getattr(inst, f), dtype=np.int32)
+               for f in ("D", "R", "kM", "kR", "hM", "hR")]
+        K, T = arr[0].shape
+        p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        code = self._lib.elsr_server_submit(self._h, K, T, *[p(a) for a in arr],
+                                            seed & ((1 << 64) - 1), iters, kmax, mode,
+                                            self._tk.ctypes.data_as(ctypes.c_void_p))
+        if code == nat.ELSR_E_BUSY:
+            return None
+        self._chk(code)
+        return int(self._tk[0])
+
+    def poll(self, max_n: int = 1024):
+        """[(ticket, stats dict)] of requests retired since the last poll."""
+        tk = np.zeros(max_n, np.int64)
+        st = (nat.Stats * max_n)()
+        n = self._chk(self._lib.elsr_server_poll(self._h, max_n,
+                                                 tk.ctypes.data_as(ctypes.c_void_p), st))
+        return [(int(tk[i]), st[i].as_dict()) for i in range(n)]
+
+    def solution(self, ticket: int, K: int, T: int):
+        gm = np.zeros((K, T), np.uint8)
+        gr = np.zeros((K, T), np.uint8)
+        self._chk(self._lib.elsr_server_solution(self._h, ticket,
+                                                 gm.ctypes.data_as(ctypes.c_void_p),
+                                                 gr.ctypes.data_as(ctypes.c_void_p)))
+        return gm, gr
+
+    def release(self, ticket: int):
+        self._chk(self._lib.elsr_server_release(self._h, ticket))
+
+    def info(self):
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        self._chk(self._lib.elsr_server_info(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return int(a.value), int(b.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.elsr_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Server:
-    """Serve requests with `slots` concurrent batches under a device-memory
-    budget of `mem_budget` bytes."""
+    """Continuous-batching server over the library's device queues.
 
-    def __init__(self, slots: int = 4, mem_budget: int = 256 << 20, max_batch: int = 4096,
-                 kmax: int = 3, mode: int = nat.MODE_P):
-        import torch
-        self.torch = torch
-        self.streams = [torch.cuda.Stream() for _ in range(slots)]
-        self.mem_budget = mem_budget
-        self.max_batch = max_batch
+    slots / cells / rows size the device pools (requests in flight, demand
+    and return values, product rows); a request is admitted when its
+    footprint fits and waits otherwise."""
+
+    def __init__(self, slots: int = 2048, cells: int = 8 << 20, rows: int = 512 << 10,
+                 max_runs: int = 8, kmax: int = 3, mode: int = nat.MODE_P,
+                 acc64: bool = False, native=None):
+        self.slots, self.cells, self.rows = slots, cells, rows
+        self.max_runs = max_runs
         self.kmax = kmax
         self.mode = mode
+        self.acc64 = acc64
+        self._native = native  # a stand-in for NativeServer (tests)
 
-    def _launch(self, reqs, stream, now):
-        insts = [r.inst for r in reqs]
-        b = Batch(insts, stream=stream)
-        seeds = np.array([r.seed for r in reqs], dtype=np.uint64)
-        iters = reqs[0].iters
-        b.run(seeds, iters, self.kmax, self.mode)
-        ev = self.torch.cuda.Event()
-        ev.record(stream)
-        return b, ev
+    def _make(self):
+        if self._native is not None:
+            return self._native(self.slots, self.cells, self.rows)
+        return NativeServer(self.slots, self.cells, self.rows, max_runs=self.max_runs,
+                            acc64=self.acc64)
 
     def run(self, requests, realtime: bool = True) -> ServeStats:
         """Serve `requests` (arrival times relative to now when realtime, else
-        all available at once).  Requests of one batch share an iteration
-        budget, so batches are formed per budget.  On an error every slot is
-        drained before the error propagates (no work is left in flight)."""
-        try:
-            return self._run(requests, realtime)
-        finally:
-            for s in self.streams:
-                s.synchronize()
-
-    def _run(self, requests, realtime: bool) -> ServeStats:
-        torch = self.torch
+        all available at once) and return per-request results."""
         pending = collections.deque(sorted(requests, key=lambda r: (r.arrival, r.rid)))
-        waiting = collections.deque()
-        inflight = {}  # slot -> (list of (Batch, event, reqs)), admitted time, bytes
-        free = list(range(len(self.streams)))
-        resident = 0
-        stats = ServeStats()
-        sizes = {}
         for r in pending:  # a request that can never be admitted is refused up front
-            key = (r.inst.K, r.inst.T)
-            if key not in sizes:
-                sizes[key] = footprint(*key)
-            if sizes[key][1] > self.mem_budget:
-                raise ValueError(f"request {r.rid} (K={key[0]}, T={key[1]}) needs "
-                                 f"{sizes[key][1]} device bytes, more than the budget of "
-                                 f"{self.mem_budget}")
+            K, T = r.inst.D.shape
+            if K * T > self.cells or K > self.rows:
+                raise ValueError(f"request {r.rid} (K={K}, T={T}) needs {footprint(K, T)} "
+                                 f"pool bytes, more than the server's pools hold")
+        stats = ServeStats()
+        if not pending:
+            return stats
+        srv = self._make()
+        try:
+            return self._serve(srv, pending, realtime, stats)
+        finally:
+            srv.close()
+
+    def _serve(self, srv, pending, realtime, stats):
+        waiting = collections.deque()
+        inflight = {}  # ticket -> (request, admitted, bytes)
+        resident = 0
         t0 = time.perf_counter()
         clock = (lambda: time.perf_counter() - t0) if realtime else (lambda: float("inf"))
         while pending or waiting or inflight:
             now = clock()
             while pending and pending[0].arrival <= now:
                 waiting.append(pending.popleft())
-            # completions
-            for slot in list(inflight):
-                parts, admitted, nbytes = inflight[slot]
-                if all(ev.query() for _, ev, _ in parts):
-                    done = time.perf_counter() - t0
-                    for b, _, reqs in parts:
-                        for r, st in zip(reqs, b.results()):
-                            stats.results.append(Result(
-                                r.rid, st["best_cost"], st["traj_hash"], st["moves_evaluated"],
-                                st["status"], r.arrival if realtime else 0.0, admitted, done,
-                                stats.batches))
-                        b.close()
-                    resident -= nbytes
-                    del inflight[slot]
-                    free.append(slot)
-            # admissions
-            while free and waiting:
-                iters = waiting[0].iters
-                take, nbytes = [], 0
-                for r in list(waiting):
-                    if r.iters != iters or len(take) >= self.max_batch:
-                        continue
-                    fb = sizes[(r.inst.K, r.inst.T)][1]
-                    if resident + nbytes + fb > self.mem_budget:
-                        break
-                    take.append(r)
-                    nbytes += fb
-                if not take:
+            progressed = False
+            # admissions, in arrival order: stop at the first that does not fit
+            while waiting:
+                r = waiting[0]
+                tk = srv.submit(r.inst, r.seed, r.iters, self.kmax, self.mode)
+                if tk is None:
                     break
-                for r in take:
-                    waiting.remove(r)
-                slot = free.pop()
-                stream = self.streams[slot]
-                small = [r for r in take if sizes[(r.inst.K, r.inst.T)][0] <= SMEM_ONE_CTA]
-                large = [r for r in take if sizes[(r.inst.K, r.inst.T)][0] > SMEM_ONE_CTA]
-                parts = []
-                with torch.cuda.stream(stream):
-                    for grp in (small, large):
-                        if grp:
-                            b, ev = self._launch(grp, stream, now)
-                            parts.append((b, ev, grp))
-                resident += nbytes
+                waiting.popleft()
+                K, T = r.inst.D.shape
+                nb = footprint(K, T)
+                inflight[tk] = (r, time.perf_counter() - t0, nb)
+                resident += nb
                 stats.max_resident_bytes = max(stats.max_resident_bytes, resident)
-                inflight[slot] = (parts, time.perf_counter() - t0, nbytes)
-                stats.batches += 1
-            if not (free and waiting):
-                nxt = pending[0].arrival - clock() if pending else 0.0
-                time.sleep(min(max(nxt, 0.0), 2e-4) if nxt > 0 or inflight else 0.0)
+                stats.max_inflight = max(stats.max_inflight, len(inflight))
+                progressed = True
+            # retirements
+            done = srv.poll(1024)
+            if done:
+                t_done = time.perf_counter() - t0
+                launches = srv.info()[1]
+                for tk, st in done:
+                    r, admitted, nb = inflight.pop(tk)
+                    resident -= nb
+                    stats.results.append(Result(
+                        r.rid, st["best_cost"], st["traj_hash"], st["moves_evaluated"],
+                        st["status"], r.arrival if realtime else 0.0, admitted, t_done,
+                        launches))
+                progressed = True
+            if not progressed:
+                nxt = pending[0].arrival - clock() if pending and not waiting else 0.0
+                time.sleep(min(max(nxt, 0.0), 1e-4) if nxt > 0 else 2e-5)
+        stats.batches = srv.info()[1]
         stats.wall_s = time.perf_counter() - t0
         return stats
 

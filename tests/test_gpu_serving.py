@@ -1,7 +1,6 @@
 """Serving with continuous batching (needs a GB300): every request's result
-is the same as solving it alone, admission keeps resident device memory under
-the budget, and requests arriving while others run are batched as slots free
-up."""
+is the same as solving it alone (and the oracle's), admission waits for room
+in the server's pools, and requests arriving while others run join them."""
 import numpy as np
 import pytest
 
@@ -19,18 +18,18 @@ def E():
 
 
 def test_served_alone_equals_mixed(E):
+    """Requests of every size class (one that needs a cluster of CTAs rides
+    along) arrive while others run; each retires with exactly the result of
+    the same run solved alone, and a sample equals the oracle's run."""
+    import oracle
     elsr, serve = E
-    reqs = serve.poisson_requests(48, rate=4000.0, iters=25, seed=5)
-    # one oversize instance that needs a CTA cluster rides along
     from paper_1704_05132_gb300 import gen
+    reqs = serve.poisson_requests(48, rate=4000.0, iters=25, seed=5)
     big = gen.make_instance(5, 999, K=200, T=104)
     reqs.append(serve.Request(999, big, 999, 25, reqs[10].arrival))
-    budget = 6 * max(serve.footprint(r.inst.K, r.inst.T)[1] for r in reqs)
-    srv = serve.Server(slots=3, mem_budget=budget)
-    stats = srv.run(reqs)
+    stats = serve.Server(slots=64).run(reqs)
     assert len(stats.results) == len(reqs)
-    assert stats.batches > 3
-    assert stats.max_resident_bytes <= budget
+    assert stats.max_inflight > 3
     byid = {r.rid: r for r in stats.results}
     for q in reqs[:12] + [reqs[-1]]:
         with elsr.Solver(q.inst) as s:
@@ -39,8 +38,52 @@ def test_served_alone_equals_mixed(E):
         assert got.status == 0
         assert (got.best_cost, got.traj_hash, got.moves_evaluated) == \
             (alone["best_cost"], alone["traj_hash"], alone["moves_evaluated"]), q.rid
+    oracle.build()
+    for q in reqs[:4]:
+        o = oracle.vns(oracle.Instance.from_arrays(q.inst), q.seed, q.iters, 3, 0)
+        got = byid[q.rid]
+        assert (got.best_cost, got.traj_hash, got.moves_evaluated) == \
+            (o.best_cost, o.traj_hash, o.counters["moves_evaluated"]), q.rid
     summ = stats.summary()
     assert summ["p99_ms"] >= summ["p50_ms"] > 0
+
+
+def test_server_admits_by_footprint_and_keeps_solutions(E):
+    """A server with room for two requests at a time: the third waits
+    ("busy") until a retirement frees room; solutions are kept until
+    released and equal the oracle's; steps are counted when asked."""
+    import oracle
+    elsr, serve = E
+    from paper_1704_05132_gb300 import gen
+    insts = [gen.make_instance(41, i, K=9 + i, T=20 + 3 * i) for i in range(5)]
+    cells = max(g.K * g.T for g in insts) * 2
+    srv = serve.NativeServer(slots=8, cells=cells, rows=10_000, count_steps=True,
+                             keep_solutions=True)
+    tickets, waiting, busy_seen = {}, list(range(5)), 0
+    done = {}
+    while len(done) < 5:
+        while waiting:
+            i = waiting[0]
+            tk = srv.submit(insts[i], seed=100 + i, iters=15)
+            if tk is None:
+                busy_seen += 1
+                break
+            tickets[tk] = waiting.pop(0)
+        for tk, st in srv.poll():
+            done[tickets[tk]] = (tk, st)
+    assert busy_seen > 0
+    oracle.build()
+    for i, (tk, st) in sorted(done.items()):
+        g = insts[i]
+        o = oracle.vns(oracle.Instance.from_arrays(g), 100 + i, 15, 3, 0)
+        assert (st["best_cost"], st["traj_hash"]) == (o.best_cost, o.traj_hash)
+        assert st["segments"] > 0
+        gm, gr = srv.solution(tk, g.K, g.T)
+        np.testing.assert_array_equal(gm, o.gM)
+        np.testing.assert_array_equal(gr, o.gR)
+        srv.release(tk)
+    assert srv.info()[0] == 0
+    srv.close()
 
 
 def test_batched_beats_plain_at_equal_budget(E):
