@@ -300,6 +300,10 @@ def bench_batch(torch, dev, stream, flush, peak, steps, warmup, args, cpu=True):
     n = args.n or 1024
     iters = args.iters if args.iters is not None else 500
     insts = gen.batch_uneven(n)
+    tuned = None
+    if not (args.lanes or args.threads or args.cluster):
+        from paper_1704_05132_gb300 import autotune  # the Batch below takes its choice
+        tuned = autotune.tune_batch(insts, probe_iters=10)
     b = elsr.Batch(insts, stream=stream, lanes=args.lanes, threads=args.threads,
                    cluster=args.cluster)
     seeds = np.arange(n, dtype=np.uint64)
@@ -323,7 +327,8 @@ def bench_batch(torch, dev, stream, flush, peak, steps, warmup, args, cpu=True):
                                   "launch", "instances": n, "iters": iters,
                       "l2": "flushed between steps (256 MiB device write, untimed)"},
            "moves_per_step": moves, "segments_per_step": segs,
-           "launch_shape": b.launch_shape(), "clocks": clocks, "gpu_launches": steps,
+           "launch_shape": b.launch_shape(), "autotuned": tuned, "clocks": clocks,
+           "gpu_launches": steps,
            "staging": {"bytes": stage_bytes,
                        "note": "instance bytes read from HBM by the launch (D, R, costs)"},
            "roofline": roofline_alu(segs, t / steps, peak)}

@@ -460,8 +460,8 @@ int elsr_batch_set_count_steps(elsr_batch_t *b, int32_t on);
  * first, one run per CTA), then splits its threads into P partitions, each
  * running one of the remaining runs with its own barrier, so that small
  * runs do not leave row groups idle.  Applies to launches of one CTA per run
- * with at most 32 lanes per row, and when threads per CTA divide into P
- * partitions of whole warps; otherwise one run per CTA.  0 = automatic
+ * with at most 32 lanes per row and blocks of 512 threads or more that
+ * divide into P partitions of whole warps; otherwise one run per CTA.  0 = automatic
  * (the library's choice), else a power of two <= 8; ELSR_E_ARG otherwise. */
 int elsr_batch_set_runs_per_cta(elsr_batch_t *b, int32_t runs_per_cta);
 

@@ -8,12 +8,16 @@ Knobs (none changes a result; only speed):
   threads  -- threads per CTA (rows in flight per CTA = threads / lanes);
   cluster  -- CTAs that share one run (1 for batches of small instances;
               larger clusters split a big instance's rows over several SMs);
+  runs_per_cta -- instances per CTA of a batch (1, 2 or 4): small runs
+              share a CTA, each in a partition of its threads;
   teams    -- speculative teams for a single run (0: as many as are
               resident, up to 16).
 A probe runs each candidate for a few iterations of the real workload and
 times it with CUDA events; the best moves/s wins.  Choices are cached per
 workload signature (bucketed K, T and batch size) in memory and, optionally,
-in a JSON file.
+in a JSON file (``cache_file``, or the file named by ELSR_AUTOTUNE_CACHE).
+A Batch created with every knob left at 0 takes the cached choice for its
+signature when there is one (``lookup_batch``), without probing.
 """
 from __future__ import annotations
 
@@ -49,8 +53,8 @@ def _timed(fn):
 
 
 # lanes = 0: every run of the batch picks its own row-group width
-BATCH_CANDIDATES = [dict(lanes=l, threads=t, cluster=1) for l in (0, 8, 16, 32)
-                    for t in (512, 1024)]
+BATCH_CANDIDATES = [dict(lanes=l, threads=t, cluster=1, runs_per_cta=p) for l in (0, 8, 16)
+                    for t in (512, 1024) for p in (1, 2, 4)]
 SINGLE_CANDIDATES = [dict(lanes=l, cluster=c, teams=0) for l in (32, 64)
                      for c in (6, 8, 9, 10, 12, 16)]
 
@@ -67,7 +71,7 @@ def tune_batch(insts, probe_iters: int = 10, candidates=None, cache_file: str | 
         b = None
         try:
             b = Batch(insts, lanes=cand["lanes"], threads=cand["threads"],
-                      cluster=cand["cluster"])
+                      cluster=cand["cluster"], runs_per_cta=cand.get("runs_per_cta", 0))
             b.run(seeds, 1, 3, 0)  # warm-up (kernel attributes, first touch)
             b.results()
             ms, _ = _timed(lambda: b.run(seeds, probe_iters, 3, 0))
@@ -115,7 +119,14 @@ def _chosen(key, best, err, cache_file):
     return best
 
 
+def lookup_batch(insts, cache_file: str | None = None):
+    """The cached launch shape for this batch's signature, or None (no
+    probing)."""
+    return _lookup(signature(insts, "batch"), cache_file)
+
+
 def _lookup(key, cache_file):
+    cache_file = cache_file or os.environ.get("ELSR_AUTOTUNE_CACHE")
     if key in _cache:
         return _cache[key]
     if cache_file and os.path.exists(cache_file):
@@ -128,6 +139,7 @@ def _lookup(key, cache_file):
 
 
 def _store(key, value, cache_file):
+    cache_file = cache_file or os.environ.get("ELSR_AUTOTUNE_CACHE")
     _cache[key] = value
     if cache_file:
         disk = {}

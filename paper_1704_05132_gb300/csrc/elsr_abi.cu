@@ -344,8 +344,8 @@ void pack_runs(elsr_batch* b, LaunchShape* ls, int acc, int P) {
   ls->parts = 1;
   ls->n_whole = nr;
   ls->part_bytes = 0;
-  if (P <= 1 || ls->cluster != 1 || nr < 2 || ls->G > 32 || ls->threads % (32 * P) != 0 ||
-      ls->threads / P < ls->G)
+  if (P <= 1 || ls->cluster != 1 || nr < 2 || ls->G > 32 || ls->maxt < 512 ||
+      ls->threads % (32 * P) != 0 || ls->threads / P < ls->G)
     return;
   const uint32_t lim = ((uint32_t)kSmemLimit / (uint32_t)P) & ~15u;
   std::vector<RunDesc> whole, small;

@@ -58,20 +58,55 @@ __device__ __forceinline__ int32_t ld_in(const int32_t* p) {
   return Fresh ? __ldcg(p) : __ldg(p);
 }
 
+// Four consecutive periods t0 .. t0+3 of a row of T values (0 outside the
+// row): one 16-byte load when the four lie in the row and start on a 16-byte
+// boundary, else one load per period inside the row.
+template <bool Fresh>
+__device__ __forceinline__ void load4(const int32_t* __restrict__ row, int T, int t0,
+                                      int32_t v[4]) {
+  const int32_t* p = row + t0;
+  if (t0 >= 0 && t0 + 3 < T && ((uintptr_t)p & 15u) == 0) {
+    const int4 q = Fresh ? __ldcg((const int4*)p) : __ldg((const int4*)p);
+    v[0] = q.x;
+    v[1] = q.y;
+    v[2] = q.z;
+    v[3] = q.w;
+  } else {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[j] = (t0 + j >= 0 && t0 + j < T) ? ld_in<Fresh>(p + j) : 0;
+  }
+}
+
+// Stage one row with a full warp: tab[0..T] = {CD[j], CR1[j]} and the row
+// constant C0 = hR * sum R(t)(T-t) - hM * sum D(t)(T-t) + pM * sum D.  Lane w
+// takes the four periods of the w-th 16-byte window of D's row (from the
+// window holding period 0), so its loads are vector loads except at the
+// row's ends; a per-lane scan of its four values and a warp scan of the lane
+// totals give the prefix sums.  R's row is read at the same periods.
 template <bool Fresh = false>
 __device__ __forceinline__ void stage_row_warp(const int32_t* __restrict__ D,
                                                const int32_t* __restrict__ R, int T,
                                                int lane, int2* tab, int32_t hM,
                                                int32_t hR, int32_t pM, int64_t* C0) {
+  const int mis = (int)(((uintptr_t)D >> 2) & 3u);  // periods before D's first window
   int32_t carryD = 0, carryR = 0;
   int64_t wd = 0, wr = 0;
-  for (int base = 0; base < T; base += 32) {
-    const int t = base + lane;
-    const int32_t d = t < T ? ld_in<Fresh>(D + t) : 0;
-    const int32_t r = t < T ? ld_in<Fresh>(R + t) : 0;
-    wd += (int64_t)d * (T - t);
-    wr += (int64_t)r * (T - t);
-    int32_t sd = d, sr = r;
+  for (int base = -mis; base < T; base += 128) {
+    const int t0 = base + 4 * lane;
+    int32_t d[4], r[4];
+    load4<Fresh>(D, T, t0, d);
+    load4<Fresh>(R, T, t0, r);
+    int32_t sd = 0, sr = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int t = t0 + j;
+      wd += (int64_t)d[j] * (T - t);  // 0 outside the row
+      wr += (int64_t)r[j] * (T - t);
+      sd += d[j];
+      sr += r[j];
+      d[j] = sd;  // inclusive sums within the lane
+      r[j] = sr;
+    }
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const int32_t a = __shfl_up_sync(kFull, sd, o);
@@ -81,9 +116,14 @@ __device__ __forceinline__ void stage_row_warp(const int32_t* __restrict__ D,
         sr += b;
       }
     }
-    if (t < T) {
-      tab[t + 1].x = carryD + sd;  // CD[t+1]
-      tab[t].y = carryR + sr;      // CR1[t]
+    const int32_t offD = carryD + sd - d[3], offR = carryR + sr - r[3];  // before this lane
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int t = t0 + j;
+      if (t >= 0 && t < T) {
+        tab[t + 1].x = offD + d[j];  // CD[t+1]
+        tab[t].y = offR + r[j];      // CR1[t]
+      }
     }
     carryD += __shfl_sync(kFull, sd, 31);
     carryR += __shfl_sync(kFull, sr, 31);
@@ -613,6 +653,11 @@ struct CtlShared {
   unsigned long long gmin[64];  // per row group and warp: partial minima (groups > 32 lanes)
   int stopw[2];                 // wall-clock budget spent (CTA 0's word counts)
   int gstop[2];                 // mode-G speculative teams: CTA 0's verdict on the decision word
+  // a run's bookkeeping that only thread 0 of CTA 0 keeps (gvns_run): in
+  // shared memory rather than in every thread's registers
+  unsigned long long hash;      // trajectory hash
+  long long cycles, accepted;   // VND sweeps, accepted iterations
+  long long deadline;           // wall-clock budget's end (ns; 0 = none)
 };
 // kSmemLimit leaves 1 KB of the CTA's shared memory to static words.
 static_assert(sizeof(CtlShared) <= 768, "static control words outgrow their reserve");
@@ -1200,35 +1245,37 @@ __device__ __forceinline__ void gvns_run(Team<Acc>& t, CtlShared* sh, const VnsP
                                          const RunDesc& rd) {
   cg::cluster_group cl = cg::this_cluster();
   const int K = t.K, T = t.T;
-  const int64_t moves_per_cycle = (int64_t)K * (2 * T + (T > 1 ? 2 * (T - 1) : 0));
-  // wall-clock budget from the run's start (thread 0 of CTA 0 keeps time)
-  const long long deadline = rd.time_limit_ns > 0 && t.crank == 0 && t.tid == 0
-                                 ? globaltimer_ns() + rd.time_limit_ns : 0;
+  // Thread 0 of CTA 0 keeps the trajectory hash, the counters and the
+  // wall-clock budget in shared memory: no other thread needs them, and
+  // registers live across every VND call are the kernel's scarcest resource.
+  const bool lead = t.crank == 0 && t.tid == 0;
+  if (lead) {
+    sh->hash = rd.h0;
+    sh->cycles = 0;
+    sh->accepted = 0;
+    sh->deadline = rd.time_limit_ns > 0 ? globaltimer_ns() + rd.time_limit_ns : 0;
+  }
   int status = 0, stop = 0;
-  int64_t cycles_total = 0;
-  int cyc = 0;
   if (!rd.resume) {  // a resumed run starts from VND's output
-    cyc = vnd<Acc, NW>(t, rd.mode);
-    if (cyc < 0) status = kStatusCap; else cycles_total += cyc;
+    const int cyc = vnd<Acc, NW>(t, rd.mode);
+    if (cyc < 0) status = kStatusCap; else if (lead) sh->cycles += cyc;
   }
   int64_t fx = team_total(t);
   if (rd.resume && fx != rd.f0) status = kStatusState;
   int kk = rd.k0;  // neighbourhood index k of Algorithm 2
-  uint64_t h = rd.h0;
-  int64_t iters_done = 0, accepted = 0;
-  const bool log = rd.traj_off >= 0 && t.crank == 0 && t.tid == 0;
   const int it_end = rd.it0 + rd.iters;
-  for (int it = rd.it0; it < it_end && status == 0 && !stop; ++it) {
+  int it = rd.it0;
+  for (; it < it_end && status == 0 && !stop; ++it) {
     const int par = it & 1;
     const int ks = kk;
-    const ShakePlan pl = plan_shake(rd.seed, it, ks, K, T);
-    apply_shake<Acc, NW>(t, pl, ks, par);
-    cyc = vnd<Acc, NW>(t, rd.mode);
-    if (cyc < 0) status = kStatusCap; else cycles_total += cyc;
-    const int64_t f2 = rd.time_limit_ns > 0 ? team_total(t, deadline, &stop) : team_total(t);
+    apply_shake<Acc, NW>(t, plan_shake(rd.seed, it, ks, K, T), ks, par);
+    const int cyc = vnd<Acc, NW>(t, rd.mode);
+    if (cyc < 0) status = kStatusCap; else if (lead) sh->cycles += cyc;
+    const int64_t f2 =
+        rd.time_limit_ns > 0 ? team_total(t, lead ? sh->deadline : 0, &stop) : team_total(t);
     const int acc = f2 < fx;
-    if (t.crank == 0 && t.tid == 0) {
-      if (log) {
+    if (lead) {
+      if (rd.traj_off >= 0) {
         TrajEntry te;
         te.it = it;
         te.k = ks;
@@ -1237,16 +1284,18 @@ __device__ __forceinline__ void gvns_run(Team<Acc>& t, CtlShared* sh, const VnsP
         te.reserved = 0;
         p.traj[rd.traj_off + (it - rd.it0)] = te;
       }
+      uint64_t h = sh->hash;
       h = splitmix64(h ^ (uint64_t)f2);
       h = splitmix64(h ^ (((uint64_t)it << 32) | ((uint64_t)ks << 1) | (uint64_t)acc));
+      sh->hash = h;
+      sh->accepted += acc;
     }
-    ++iters_done;
     if (acc) {
       fx = f2;
       kk = 1;
-      ++accepted;
     } else {
-      undo_shake<Acc>(t, pl, par);
+      // the shake is drawn again from its keys rather than kept live across VND
+      undo_shake<Acc>(t, plan_shake(rd.seed, it, ks, K, T), par);
       kk = kk % rd.kmax + 1;
     }
     if ((it & 255) == 255) flush_counters(t, &sh->steps, &sh->applied);
@@ -1256,21 +1305,22 @@ __device__ __forceinline__ void gvns_run(Team<Acc>& t, CtlShared* sh, const VnsP
     p.out_bits[rd.bits_off + q * t.C + t.crank] = t.m.bits[q];
   flush_counters(t, &sh->steps, &sh->applied);
   team_sync(t);
-  if (t.tid == 0 && t.crank == 0) {
+  if (lead) {
     unsigned long long steps = 0, applied = 0;
     for (int c = 0; c < t.C; ++c) {
       steps += t.C == 1 ? sh->steps : *cl.map_shared_rank(&sh->steps, c);
       applied += t.C == 1 ? sh->applied : *cl.map_shared_rank(&sh->applied, c);
     }
+    const int64_t moves_per_cycle = (int64_t)K * (2 * T + (T > 1 ? 2 * (T - 1) : 0));
     RunOut o;
     o.best_cost = fx;
-    o.traj_hash = h;
-    o.moves_evaluated = cycles_total * moves_per_cycle;
-    o.evals = cycles_total * 3;
-    o.vnd_cycles = cycles_total;
+    o.traj_hash = sh->hash;
+    o.moves_evaluated = sh->cycles * moves_per_cycle;
+    o.evals = sh->cycles * 3;
+    o.vnd_cycles = sh->cycles;
     o.applied = (int64_t)applied;
-    o.iterations = iters_done;
-    o.accepted = accepted;
+    o.iterations = it - rd.it0;
+    o.accepted = sh->accepted;
     o.segments = p.count_steps ? (int64_t)steps : 0;
     o.status = status;
     o.reserved = 0;
@@ -1313,22 +1363,31 @@ __global__ void __launch_bounds__(MAXT, 1) vns_kernel(const VnsParams p) {
   __shared__ CtlShared sh;
   Team<Acc> t;
   team_init(t, p.G);
-  // phase 1: whole teams
-  run_loop<Acc, NW, TS>(t, smem, dynamic_smem_bytes(), &sh, p, p.queue, 0, p.n_whole, 128);
-  if (p.n_whole >= p.nruns) return;
-  // phase 2: every thread of the CTA left phase 1 together (queue 0 was
-  // empty), so its named barriers are complete
-  __syncthreads();
-  const int np = p.parts;
-  if (np > 1 && t.C == 1 && (int)blockDim.x % (32 * np) == 0 && p.G <= 32 &&
-      (uint32_t)np * p.part_bytes <= dynamic_smem_bytes() && p.part_bytes > kCtlBytes) {
-    team_init(t, p.G, np);
-    unsigned char* base = smem + (size_t)((int)threadIdx.x / t.nthr) * p.part_bytes;
-    run_loop<Acc, NW, TS>(t, base + kCtlBytes, p.part_bytes - kCtlBytes, (CtlShared*)base, p,
-                          p.queue + 1, p.n_whole, p.nruns, 32);
-  } else {  // not a shape the host launches: the whole team takes these runs
-    run_loop<Acc, NW, TS>(t, smem, dynamic_smem_bytes(), &sh, p, p.queue + 1, p.n_whole,
-                          p.nruns, 128);
+  if constexpr (MAXT < 512) {
+    // the host packs runs only into blocks of 512 threads or more
+    run_loop<Acc, NW, TS>(t, smem, dynamic_smem_bytes(), &sh, p, p.queue, 0, p.nruns, 128);
+  } else {
+    // phase 1: whole teams
+    run_loop<Acc, NW, TS>(t, smem, dynamic_smem_bytes(), &sh, p, p.queue, 0, p.n_whole, 128);
+    if (p.n_whole >= p.nruns) return;
+    // phase 2: every thread of the CTA left phase 1 together (queue 0 was
+    // empty), so its named barriers are complete
+    __syncthreads();
+    const int np = p.parts;
+    unsigned char* base = smem;
+    uint32_t region = dynamic_smem_bytes();
+    CtlShared* psh = &sh;
+    int gmax = 128;
+    if (np > 1 && t.C == 1 && (int)blockDim.x % (32 * np) == 0 && p.G <= 32 &&
+        (uint32_t)np * p.part_bytes <= region && p.part_bytes > kCtlBytes) {
+      team_init(t, p.G, np);
+      base = smem + (size_t)((int)threadIdx.x / t.nthr) * p.part_bytes;
+      psh = (CtlShared*)base;
+      base += kCtlBytes;
+      region = p.part_bytes - kCtlBytes;
+      gmax = 32;
+    }  // else (not a shape the host launches) the whole team takes these runs too
+    run_loop<Acc, NW, TS>(t, base, region, psh, p, p.queue + 1, p.n_whole, p.nruns, gmax);
   }
 }
 

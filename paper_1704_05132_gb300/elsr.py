@@ -313,6 +313,12 @@ class Batch:
         self.Ts = np.array([i.D.shape[1] for i in insts], np.int32)
         cat = lambda f: _i32(np.concatenate([np.ravel(getattr(i, f)) for i in insts]))
         arrs = [cat("D"), cat("R"), cat("kM"), cat("kR"), cat("hM"), cat("hR")]
+        if not (lanes or threads or cluster or runs_per_cta):
+            from . import autotune  # a tuned shape for this signature, when cached
+            hit = autotune.lookup_batch(insts)
+            if hit:
+                lanes, threads = hit.get("lanes", 0), hit.get("threads", 0)
+                cluster, runs_per_cta = hit.get("cluster", 0), hit.get("runs_per_cta", 0)
         b = P()
         sh = _stream_handle(stream)
         if any(getattr(i, "pM", None) is not None or getattr(i, "pR", None) is not None

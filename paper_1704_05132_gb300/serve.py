@@ -198,6 +198,9 @@ class Server:
         finally:
             srv.close()
 
+    # a request that has not retired this long after its admission is an error
+    RETIRE_LIMIT_S = 120.0
+
     def _serve(self, srv, pending, realtime, stats):
         waiting = collections.deque()
         inflight = {}  # ticket -> (request, admitted, bytes)
@@ -237,6 +240,11 @@ class Server:
                         launches))
                 progressed = True
             if not progressed:
+                if inflight:
+                    oldest = min(a for _, a, _ in inflight.values())
+                    if time.perf_counter() - t0 - oldest > self.RETIRE_LIMIT_S:
+                        raise RuntimeError(f"{len(inflight)} requests have not retired "
+                                           f"{self.RETIRE_LIMIT_S:.0f} s after admission")
                 nxt = pending[0].arrival - clock() if pending and not waiting else 0.0
                 time.sleep(min(max(nxt, 0.0), 1e-4) if nxt > 0 else 2e-5)
         stats.batches = srv.info()[1]

@@ -11,11 +11,13 @@ from paper_1704_05132_gb300 import autotune, gen
 
 
 class FakeBatch:
-    rates = {}      # (lanes, threads) -> moves per ms; "ctor" / None: fails
+    rates = {}      # (lanes, threads[, runs per CTA]) -> moves per ms; "ctor" / None: fails
     made = []
 
-    def __init__(self, insts, lanes=0, threads=0, cluster=0):
-        self.key = (lanes, threads)
+    def __init__(self, insts, lanes=0, threads=0, cluster=0, runs_per_cta=0):
+        self.key = (lanes, threads, runs_per_cta)
+        if self.key not in FakeBatch.rates and runs_per_cta == 1:
+            self.key = (lanes, threads)
         if FakeBatch.rates.get(self.key) == "ctor":
             raise RuntimeError("refused at create")
         self.closed = False
@@ -73,12 +75,17 @@ def test_batch_fastest_wins_and_failures_are_skipped(fakes):
     FakeBatch.rates = {(0, 512): 5.0, (0, 1024): "ctor", (8, 512): None, (16, 1024): 9.0,
                        (32, 512): 7.0}
     shape = autotune.tune_batch(fakes, probe_iters=4)
-    assert shape == dict(lanes=16, threads=1024, cluster=1)
+    assert shape == dict(lanes=16, threads=1024, cluster=1, runs_per_cta=1)
+    FakeBatch.rates[(16, 1024, 2)] = 9.5                # two runs per CTA, faster still
+    autotune._cache.clear()
+    assert autotune.tune_batch(fakes, probe_iters=4)["runs_per_cta"] == 2
     assert FakeBatch.made and all(b.closed for b in FakeBatch.made)
 
 
 def test_batch_nothing_ran_raises_and_caches_nothing(fakes):
     FakeBatch.rates = {(l, t): None for l in (0, 8, 16, 32) for t in (512, 1024)}
+    FakeBatch.rates.update({(l, t, p): None for l in (0, 8, 16) for t in (512, 1024)
+                            for p in (2, 4)})
     with pytest.raises(RuntimeError, match="no candidate") as ei:
         autotune.tune_batch(fakes)
     assert isinstance(ei.value.__cause__, RuntimeError)     # the last failure
@@ -90,7 +97,7 @@ def test_batch_choice_cached_in_file(fakes, tmp_path, monkeypatch):
     cache = str(tmp_path / "tune.json")
     FakeBatch.rates = {(8, 1024): 3.0, (0, 512): 1.0}
     first = autotune.tune_batch(fakes, cache_file=cache)
-    assert first == dict(lanes=8, threads=1024, cluster=1)
+    assert first == dict(lanes=8, threads=1024, cluster=1, runs_per_cta=1)
     monkeypatch.setattr(autotune, "_cache", {})     # a new process
     FakeBatch.rates, FakeBatch.made = {}, []        # any probe would now fail
     assert autotune.tune_batch(fakes, cache_file=cache) == first
@@ -107,3 +114,19 @@ def test_single_fastest_wins_and_nothing_ran_raises(fakes):
     with pytest.raises(RuntimeError, match="no candidate"):
         autotune.tune_single(gen.make_instance(4, 2, K=300, T=52))
     assert all(s.closed for s in FakeSolver.made)
+
+
+def test_batch_lookup_takes_the_cached_shape_without_probing(fakes, tmp_path, monkeypatch):
+    """lookup_batch (what a Batch created with every knob at 0 consults)
+    returns the cached choice, from memory or from the file named by
+    ELSR_AUTOTUNE_CACHE, and None when nothing is cached."""
+    assert autotune.lookup_batch(fakes) is None
+    cache = str(tmp_path / "tune.json")
+    monkeypatch.setenv("ELSR_AUTOTUNE_CACHE", cache)
+    FakeBatch.rates = {(16, 512, 2): 4.0}
+    chosen = autotune.tune_batch(fakes)
+    monkeypatch.setattr(autotune, "_cache", {})     # a new process, same file
+    FakeBatch.made = []
+    assert autotune.lookup_batch(fakes) == chosen == dict(lanes=16, threads=512, cluster=1,
+                                                          runs_per_cta=2)
+    assert FakeBatch.made == []

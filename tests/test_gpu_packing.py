@@ -48,9 +48,11 @@ def test_packed_batch_equals_unpacked_and_oracle(E, mode):
         b.run(seeds, iters=40, kmax=3, mode=mode)
         res = [_key(r) for r in b.results()]
         shape = b.launch_shape()
-        if parts > 1:
+        if parts > 1 and threads >= 512:
             assert shape["runs_per_cta"] == parts, shape
             assert 0 < shape["whole_cta_runs"] < len(insts), shape
+        elif parts > 1:  # blocks below 512 threads are not packed
+            assert shape["runs_per_cta"] == 1, shape
         if ref is None:
             ref = res
             sols = [b.solution(i) for i in (0, len(insts) - 1)]

@@ -1,6 +1,8 @@
 """Serving with continuous batching (needs a GB300): every request's result
 is the same as solving it alone (and the oracle's), admission waits for room
 in the server's pools, and requests arriving while others run join them."""
+import time
+
 import numpy as np
 import pytest
 
@@ -61,7 +63,9 @@ def test_server_admits_by_footprint_and_keeps_solutions(E):
                              keep_solutions=True)
     tickets, waiting, busy_seen = {}, list(range(5)), 0
     done = {}
+    deadline = time.monotonic() + 60.0
     while len(done) < 5:
+        assert time.monotonic() < deadline, "requests did not retire"
         while waiting:
             i = waiting[0]
             tk = srv.submit(insts[i], seed=100 + i, iters=15)
@@ -70,18 +74,20 @@ def test_server_admits_by_footprint_and_keeps_solutions(E):
                 break
             tickets[tk] = waiting.pop(0)
         for tk, st in srv.poll():
-            done[tickets[tk]] = (tk, st)
+            i = tickets[tk]
+            g = insts[i]
+            # a kept solution stays readable until released, which frees room
+            done[i] = (st, srv.solution(tk, g.K, g.T))
+            srv.release(tk)
     assert busy_seen > 0
     oracle.build()
-    for i, (tk, st) in sorted(done.items()):
+    for i, (st, (gm, gr)) in sorted(done.items()):
         g = insts[i]
         o = oracle.vns(oracle.Instance.from_arrays(g), 100 + i, 15, 3, 0)
         assert (st["best_cost"], st["traj_hash"]) == (o.best_cost, o.traj_hash)
         assert st["segments"] > 0
-        gm, gr = srv.solution(tk, g.K, g.T)
         np.testing.assert_array_equal(gm, o.gM)
         np.testing.assert_array_equal(gr, o.gR)
-        srv.release(tk)
     assert srv.info()[0] == 0
     srv.close()
 
@@ -126,7 +132,13 @@ def test_autotuner_picks_a_valid_shape_with_identical_results(E, tmp_path):
     ref = elsr.Batch(insts)
     ref.run(seeds, 15, 3, 0)
     tuned = elsr.Batch(insts, lanes=shape["lanes"], threads=shape["threads"],
-                       cluster=shape["cluster"])
+                       cluster=shape["cluster"], runs_per_cta=shape["runs_per_cta"])
+    looked_up = elsr.Batch(insts)       # every knob 0: the cached choice
+    looked_up.run(seeds, 15, 3, 0)
+    assert looked_up.launch_shape()["threads"] == shape["threads"]
+    assert [r["traj_hash"] for r in looked_up.results()] == \
+        [r["traj_hash"] for r in ref.results()]
+    looked_up.close()
     tuned.run(seeds, 15, 3, 0)
     a, b = ref.results(), tuned.results()
     assert [(r["best_cost"], r["traj_hash"]) for r in a] == \
