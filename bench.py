@@ -39,6 +39,10 @@ import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# The serving workload launches many small kernels side by side on separate
+# streams; more hardware work queues than the default 8 keep them from
+# queueing behind one another.  Read when CUDA starts, so set it first.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 WORKLOAD = {
     "workload": "plain GVNS, one instance K=50 products x T=52 periods, seed 1, "
@@ -55,6 +59,13 @@ WORKLOAD_PAPER = {
 METRIC = "candidate moves evaluated/s"
 UNIT = "moves/s"
 INT_OPS_PER_STEP = 16         # algorithmic integer operations per decode step
+# DRAM bytes (read + written) per launch, from ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum) on the current kernels.  The speculative kernel of
+# the plain run is not profiled: its figure is a one-team launch of the same
+# run (100 iterations: 264,448 B read, 0 written) scaled by the iterations, an
+# upper bound since the instance is staged once per run.
+TRAFFIC_PLAIN_PER_100_ITERS = 264_448
+TRAFFIC_BATCH_LAUNCH = 18_520_000 + 38_190_000  # batch workload launch (500 iterations)
 LANES_PER_SM = 128            # 32-bit integer lanes per SM (4 SMSPs x 32), for context
 L2_FLUSH_BYTES = 256 << 20
 
@@ -303,7 +314,8 @@ def bench_batch(torch, dev, stream, flush, peak, steps, warmup, args, cpu=True):
     tuned = None
     if not (args.lanes or args.threads or args.cluster):
         from paper_1704_05132_gb300 import autotune  # the Batch below takes its choice
-        tuned = autotune.tune_batch(insts, probe_iters=10)
+        # probes long enough that the initial descent does not dominate them
+        tuned = autotune.tune_batch(insts, probe_iters=100)
     b = elsr.Batch(insts, stream=stream, lanes=args.lanes, threads=args.threads,
                    cluster=args.cluster)
     seeds = np.arange(n, dtype=np.uint64)
@@ -331,7 +343,9 @@ def bench_batch(torch, dev, stream, flush, peak, steps, warmup, args, cpu=True):
            "gpu_launches": steps,
            "staging": {"bytes": stage_bytes,
                        "note": "instance bytes read from HBM by the launch (D, R, costs)"},
-           "roofline": roofline_alu(segs, t / steps, peak)}
+           "roofline": roofline_alu(segs, t / steps, peak,
+                                    traffic=TRAFFIC_BATCH_LAUNCH if (n, iters) == (1024, 500)
+                                    else None)}
     b.close()
     if cpu and not args.no_cpu_baseline:
         m = min(n, 64)
@@ -570,7 +584,12 @@ def run_gpu(args):
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": args.steps,
         "launch_shape": solver.launch_shape(),
-        "roofline": roofline_alu(segs_per_step, kernel_s, peak),
+        "roofline": roofline_alu(
+            segs_per_step, kernel_s, peak,
+            traffic=(TRAFFIC_PLAIN_PER_100_ITERS * iters // 100
+                     if args.instance == "medium" and not args.workers and mode == 0 else None),
+            note="traffic: one-team launch of the same run under ncu, scaled by the "
+                 "iterations (upper bound)"),
         "int_peak": dict(peak, unit_count_tops=sms * LANES_PER_SM *
                          (peak["clocks"].get("sm_mhz") or 0) * 1e6 / 1e12,
                          unit_count_note=f"{sms} SMs x {LANES_PER_SM} lanes x median SM "
@@ -590,6 +609,10 @@ def run_gpu(args):
                                            min(args.steps, 3), wwarm, sub),
             "serve": bench_serve(torch, dev, peak, sub),
         }
+        # the same stream at a load the server sustains, for its latency there
+        sub_low = argparse.Namespace(**vars(sub))
+        sub_low.rate = args.rate / 2
+        line["workloads"]["serve_half_rate"] = bench_serve(torch, dev, peak, sub_low, cpu=False)
         b, ms_ = line["workloads"]["batch"], line["workloads"]["multistart"]
         line["workloads"]["note"] = (
             "instances/s at the workloads' own budgets: plain one run at a time "

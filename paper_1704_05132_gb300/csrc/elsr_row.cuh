@@ -388,11 +388,12 @@ ELSR_HD Acc build_row(const int2* tab, int T, const RowCosts& rc,
 // current row that falls short (a deficit in the relaxed decode) is fixed
 // only when delta still covers its room there, so the moved row is feasible
 // only when delta covers the rooms of all such setups from s1 on.
-template <typename Acc, int NW>
+template <typename Acc, int NW, bool Count = true>
 ELSR_HD Acc eval_move(const int2* tab, int T, const RowCosts& rc,
                       const RowState<Acc>& cur, const int32_t* A,
                       const Acc* C, const int2* L, const int32_t* P,
-                      const Acc* Q, int j, int local, int& steps, bool count = true) {
+                      const Acc* Q, int j, int local, int& steps) {
+  constexpr bool count = Count;
   RowBits nb = cur.b;
   int t1, other;
   if (j == 1) {
@@ -433,7 +434,7 @@ ELSR_HD Acc eval_move(const int2* tab, int T, const RowCosts& rc,
     while (s < T) {
       const int n = nxt<NW>(u0, u1, s, T);
       const int2 tn = tab[n];
-      ++steps;
+      if constexpr (count) ++steps;
       if (!seg_step<Acc>(s, bitat<NW>(nb.m0, nb.m1, s), bitat<NW>(nb.r0, nb.r1, s),
                          ts, tn, T, rc, avail, S))
         return Inf<Acc>::value;
@@ -476,20 +477,20 @@ ELSR_HD Acc eval_move(const int2* tab, int T, const RowCosts& rc,
   const bool v1 = t1 > a0 && bitat<NW>(u0, u1, t1);
   const bool v2 = j == 3 && t2 > a0 && bitat<NW>(u0, u1, t2);
   if (v0) {
-    ++steps;
+    if constexpr (count) ++steps;
     const int2 te = v1 ? tt1 : (v2 ? tt2 : ts1);
     if (!seg_step<Acc>(a0, bitat<NW>(nb.m0, nb.m1, a0), bitat<NW>(nb.r0, nb.r1, a0), ta0,
                        te, T, rc, avail, S))
       return Inf<Acc>::value;
   }
   if (v1) {
-    ++steps;
+    if constexpr (count) ++steps;
     if (!seg_step<Acc>(t1, bitat<NW>(nb.m0, nb.m1, t1), bitat<NW>(nb.r0, nb.r1, t1), tt1,
                        v2 ? tt2 : ts1, T, rc, avail, S))
       return Inf<Acc>::value;
   }
   if (v2) {
-    ++steps;
+    if constexpr (count) ++steps;
     if (!seg_step<Acc>(t2, bitat<NW>(nb.m0, nb.m1, t2), bitat<NW>(nb.r0, nb.r1, t2), tt2,
                        ts1, T, rc, avail, S))
       return Inf<Acc>::value;
@@ -503,9 +504,10 @@ ELSR_HD Acc eval_move(const int2* tab, int T, const RowCosts& rc,
   // the step count takes the setups from s1 through the last one the stock
   // difference reaches; from s1 on the current row has the moved row's
   // setups, and its bits stay live in the caller anyway.  Callers that time
-  // the search pass count = false and skip these population counts.
+  // the search instantiate Count = false: no counting code at all.
   const uint64_t w0 = cur.b.m0 | cur.b.r0, w1 = cur.b.m1 | cur.b.r1;
-  const int u_s1 = count ? rank_below<NW>(w0, w1, s1) : 0;
+  int u_s1 = 0;
+  if constexpr (count) u_s1 = rank_below<NW>(w0, w1, s1);
   if (delta > 0) {
     // More stock: each later gR setup absorbs up to its room (need minus the
     // stock it had), lowering xM by as much, until delta is used up.  With
@@ -518,7 +520,7 @@ ELSR_HD Acc eval_move(const int2* tab, int T, const RowCosts& rc,
     const Acc Q0 = Q[r0], Qn = Q[cur.nR];
     const int32_t target = P0 + delta;
     if (Pn < target) {
-      if (count) steps += rank_below<NW>(w0, w1, T) - u_s1;
+      if constexpr (count) steps += rank_below<NW>(w0, w1, T) - u_s1;
       return S - (Qn - Q0);
     }
     // smallest z in [r0, nR) with P[z+1] >= target: the answer stays in
@@ -532,7 +534,7 @@ ELSR_HD Acc eval_move(const int2* tab, int T, const RowCosts& rc,
     const int32_t Pz = P[lo], Pz1 = P[lo + 1];
     const Acc Qz = Q[lo];
     const int sz = L[lo].y & 0xFFFF;
-    if (count) steps += rank_below<NW>(w0, w1, sz + 1) - u_s1;
+    if constexpr (count) steps += rank_below<NW>(w0, w1, sz + 1) - u_s1;
     if (cur.ld > lo || (cur.ld == lo && Pz1 != target)) return Inf<Acc>::value;
     return S - (Qz - Q0) - xr_weight<Acc>(rc, T, sz) * (Acc)(target - Pz);
   }
@@ -546,7 +548,7 @@ ELSR_HD Acc eval_move(const int2* tab, int T, const RowCosts& rc,
     const int sr = e.y & 0xFFFF;
     const int32_t sg = e.x, sn = sg + delta;
     if (!(e.y >> 16) && sn < 0) {
-      if (count) steps += rank_below<NW>(w0, w1, sr + 1) - u_s1;
+      if constexpr (count) steps += rank_below<NW>(w0, w1, sr + 1) - u_s1;
       return Inf<Acc>::value;
     }
     const int32_t dx = (sn < 0 ? sn : 0) - (sg < 0 ? sg : 0);
@@ -557,7 +559,7 @@ ELSR_HD Acc eval_move(const int2* tab, int T, const RowCosts& rc,
       break;
     }
   }
-  if (count) steps += rank_below<NW>(w0, w1, last + 1) - u_s1;
+  if constexpr (count) steps += rank_below<NW>(w0, w1, last + 1) - u_s1;
   return cur.ld >= r0 ? Inf<Acc>::value : S;
 }
 

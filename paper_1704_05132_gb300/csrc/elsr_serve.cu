@@ -478,7 +478,7 @@ int elsr_server_poll(elsr_server_t* s, int32_t max, int64_t* tickets, elsr_stats
       release_slot(s, slot);
     }
   }
-  for (int c = 0; c < kClasses; ++c) {
+  for (int c = kClasses - 1; c >= 0; --c) {  // the largest requests first
     const int rc = maybe_launch(s, c);
     if (rc != ELSR_OK) return rc;
   }

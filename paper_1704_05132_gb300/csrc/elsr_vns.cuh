@@ -18,6 +18,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "elsr_internal.h"
 
 namespace elsr {
@@ -271,12 +273,11 @@ __device__ __forceinline__ void restore_row(const Rows<Acc>& m, int q,
 }
 
 // Best move (packed (row cost, local index) key) of local row q in N_j over
-// this lane's share of the candidates.
-template <typename Acc, int NW>
+// this lane's share of the candidates; Count: add their decode steps.
+template <typename Acc, int NW, bool Count>
 __device__ __forceinline__ uint64_t row_best(const Rows<Acc>& m, int q,
                                              const RowState<Acc>& cur, int j, int M,
-                                             int lane, int G, uint32_t& steps,
-                                             bool count) {
+                                             int lane, int G, uint32_t& steps) {
   const int T = m.T;
   const int2* tk = m.tab_row(q);
   const int32_t* Aq = m.A + q * T;
@@ -294,16 +295,16 @@ __device__ __forceinline__ uint64_t row_best(const Rows<Acc>& m, int q,
     const SwapMasks sw = swap_masks<NW>(cur.b, T);
     for (int i = lane; i < sw.n; i += G) {
       const int l = swap_of_rank<NW>(sw, T, i);
-      const Acc S = eval_move<Acc, NW>(tk, T, rc, cur, Aq, Cq, Lq, Pq, Qq, 3, l, st, count);
+      const Acc S = eval_move<Acc, NW, Count>(tk, T, rc, cur, Aq, Cq, Lq, Pq, Qq, 3, l, st);
       best = umin64(best, pack_key(row_cost<Acc>(S, c0), (uint32_t)l));
     }
   } else {
     for (int l = lane; l < M; l += G) {
-      const Acc S = eval_move<Acc, NW>(tk, T, rc, cur, Aq, Cq, Lq, Pq, Qq, j, l, st, count);
+      const Acc S = eval_move<Acc, NW, Count>(tk, T, rc, cur, Aq, Cq, Lq, Pq, Qq, j, l, st);
       best = umin64(best, pack_key(row_cost<Acc>(S, c0), (uint32_t)l));
     }
   }
-  steps += (uint32_t)st;
+  if constexpr (Count) steps += (uint32_t)st;
   return best;
 }
 
@@ -932,7 +933,9 @@ __device__ int vnd_p(Team<Acc>& t, const int* stop = nullptr, int my_index = 0) 
         uint64_t best = ~0ull;
         if (valid) {
           const RowState<Acc> cur = t.m.state(q);
-          best = row_best<Acc, NW>(t.m, q, cur, j, M, t.lane, t.G, t.steps, t.count);
+          // counting is decided per row, so the per-move loop carries none of it
+          best = t.count ? row_best<Acc, NW, true>(t.m, q, cur, j, M, t.lane, t.G, t.steps)
+                         : row_best<Acc, NW, false>(t.m, q, cur, j, M, t.lane, t.G, t.steps);
         }
         best = group_min(t, best);
         const bool imp = valid && key_cost(best) < t.m.cost(q);
@@ -1025,16 +1028,20 @@ __device__ int vnd_g(Team<Acc>& t, const int* stop = nullptr, int my_index = 0) 
           int st = 0;
           const SwapMasks sw = swap_masks<NW>(cur.b, T);
           const int Mj = j == 3 ? sw.n : M;  // N3: non-null swaps only
-          for (int i = t.lane; i < Mj; i += t.G) {
-            const int l = j == 3 ? swap_of_rank<NW>(sw, T, i) : i;
-            const Acc S = eval_move<Acc, NW>(tk, T, rc, cur, t.m.A + q * T, t.m.C + q * T,
-                                             t.m.L + q * T, t.m.P + q * (T + 1),
-                                             t.m.Q + q * (T + 1), j, l, st, t.count);
-            const int64_t nc = row_cost<Acc>(S, c0);
-            const int64_t nt =
-                (others == INT64_MAX || nc == INT64_MAX) ? INT64_MAX : others + nc;
-            best = umin64(best, pack_key(nt, (uint32_t)(kg * M + l)));
-          }
+          // counting is decided per row, so the per-move loop carries none of it
+          auto moves = [&](auto counted) {
+            for (int i = t.lane; i < Mj; i += t.G) {
+              const int l = j == 3 ? swap_of_rank<NW>(sw, T, i) : i;
+              const Acc S = eval_move<Acc, NW, decltype(counted)::value>(
+                  tk, T, rc, cur, t.m.A + q * T, t.m.C + q * T, t.m.L + q * T,
+                  t.m.P + q * (T + 1), t.m.Q + q * (T + 1), j, l, st);
+              const int64_t nc = row_cost<Acc>(S, c0);
+              const int64_t nt =
+                  (others == INT64_MAX || nc == INT64_MAX) ? INT64_MAX : others + nc;
+              best = umin64(best, pack_key(nt, (uint32_t)(kg * M + l)));
+            }
+          };
+          if (t.count) moves(std::true_type{}); else moves(std::false_type{});
           t.steps += (uint32_t)st;
         }
         best = subwarp_min(best, GW);
@@ -1404,7 +1411,9 @@ __global__ void __launch_bounds__(MAXT, 1) vns_kernel(const VnsParams p) {
 // the host launches again while published requests remain unclaimed.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int srv_claim(const SrvQueue& q) {
-  for (int tries = 0; tries < 64; ++tries) {  // bounded: another team won each race
+  // bounded: each failed exchange means another team claimed a position, and
+  // far fewer teams than this are ever in flight
+  for (int tries = 0; tries < (1 << 16); ++tries) {
     const int h = *(volatile const int*)q.head;
     const int tl = *(volatile const int*)q.tail;
     if (h >= tl) return -1;
