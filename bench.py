@@ -304,6 +304,26 @@ def _timed_steps(torch, stream, step, steps, warmup, flush, dev):
     return ms, clk.summary()
 
 
+def bench_staging(torch, stream, flush, dev, b, insts, reps=20):
+    """The staging pass alone on the batch's instances: every row's prefix
+    tables built in device memory by the stage kernel (the row loader the
+    GVNS launch stages shared memory with), CUDA-event timed, L2 flushed
+    before each launch.  HBM bytes: D and R read, hM and hR read, tables
+    ((T + 1) int2 per row) and C0 (one int64 per row) written."""
+    rows = sum(g.K for g in insts)
+    cells = sum(g.K * g.T for g in insts)
+    nbytes = 8 * cells + 8 * rows + 8 * (cells + rows) + 8 * rows
+    ms, _ = _timed_steps(torch, stream, b.stage_tables, reps, 3, flush, dev)
+    ms.sort()
+    med = ms[len(ms) // 2] / 1e3
+    hbm = _peaks().get("hbm_gbs")
+    gbs = nbytes / med / 1e9
+    return {"kernel": "stage_kernel", "bytes": nbytes, "rows": rows, "cells": cells,
+            "ms_median": med * 1e3, "ms_min": ms[0], "launches": reps, "gbs": gbs,
+            "hbm_peak_gbs": hbm, "frac": gbs / hbm if hbm else None,
+            "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+
+
 def bench_batch(torch, dev, stream, flush, peak, steps, warmup, args, cpu=True):
     """1024 independent instances K ~ U{5..100}, T ~ U{12..52} (seed 0, ids
     0..1023), 500 iterations each, in one persistent launch per step."""
@@ -331,6 +351,7 @@ def bench_batch(torch, dev, stream, flush, peak, steps, warmup, args, cpu=True):
     moves = sum(r["moves_evaluated"] for r in st)
     t = sum(ms) / 1e3
     stage_bytes = sum(4 * (2 * g.K * g.T + 4 * g.K) for g in insts)
+    staging = bench_staging(torch, stream, flush, dev, b, insts)
     rec = {"metric": METRIC, "value": moves * steps / t, "unit": UNIT,
            "instances_per_s": n * steps / t, "ms_per_step": 1e3 * t / steps,
            "steps": steps, "warmup": warmup, "higher_is_better": True,
@@ -341,8 +362,9 @@ def bench_batch(torch, dev, stream, flush, peak, steps, warmup, args, cpu=True):
            "moves_per_step": moves, "segments_per_step": segs,
            "launch_shape": b.launch_shape(), "autotuned": tuned, "clocks": clocks,
            "gpu_launches": steps,
-           "staging": {"bytes": stage_bytes,
-                       "note": "instance bytes read from HBM by the launch (D, R, costs)"},
+           "staging": dict(staging, launch_bytes=stage_bytes,
+                           launch_note="instance bytes the GVNS launch reads from HBM "
+                                       "(D, R, costs), staged with the same row loader"),
            "roofline": roofline_alu(segs, t / steps, peak,
                                     traffic=TRAFFIC_BATCH_LAUNCH if (n, iters) == (1024, 500)
                                     else None)}

@@ -470,6 +470,18 @@ int elsr_batch_set_runs_per_cta(elsr_batch_t *b, int32_t runs_per_cta);
 int elsr_batch_packing(const elsr_batch_t *b, int32_t *runs_per_cta,
                        int32_t *whole_cta_runs);
 
+/* (Re)build, on the batch's stream, the per-row prefix tables of every
+ * instance in device memory: for row k of instance i, the cumulative demand
+ * and returns of periods 0..t and the constant part of the row cost, the
+ * quantities whose differences give the holding costs in the objective of
+ * Section 2 for any setup pattern of the row.  Runs whose
+ * rows do not fit shared memory read these tables; the batch builds them on
+ * the first such run, and this call builds them again (to prebuild them, or
+ * to time the pass: it reads D, R, hM, hR and pM once and writes
+ * (cells + rows) * 8 + rows * 8 bytes).  Asynchronous; ELSR_E_ARG for a NULL
+ * batch, ELSR_E_CUDA when the allocation or launch fails. */
+int elsr_batch_stage_tables(elsr_batch_t *b);
+
 /* Queue GVNS runs of every instance i with seeds[i] (host [n]), from the
  * initial solution.  Asynchronous, like elsr_vns_run. */
 int elsr_batch_run(elsr_batch_t *b, const uint64_t *seeds, int32_t iters,

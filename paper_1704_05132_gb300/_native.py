@@ -110,6 +110,7 @@ SIGNATURES = {
     "elsr_batch_launch_shape": (ctypes.c_int, [P, P]),
     "elsr_batch_set_runs_per_cta": (ctypes.c_int, [P, i32]),
     "elsr_batch_set_count_steps": (ctypes.c_int, [P, i32]),
+    "elsr_batch_stage_tables": (ctypes.c_int, [P]),
     "elsr_set_count_steps": (ctypes.c_int, [P, i32]),
     "elsr_batch_packing": (ctypes.c_int, [P, P, P]),
     "elsr_batch_run": (ctypes.c_int, [P, P, i32, i32, i32]),

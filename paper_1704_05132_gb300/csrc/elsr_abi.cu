@@ -473,6 +473,23 @@ int ensure_spec(elsr_batch* b, int teams) {
   return ELSR_OK;
 }
 
+// Prefix tables of every row of every instance in device memory (the tables
+// of launches whose rows do not fit shared memory), on b->stream.
+static int stage_tables(elsr_batch* b) {
+  if (!b->d_tab) {
+    ELSR_TRY_CUDA(b, dev_alloc(&b->d_tab, (size_t)(b->cells + b->rows), b->stream));
+    ELSR_TRY_CUDA(b, dev_alloc(&b->d_C0, (size_t)b->rows, b->stream));
+  }
+  StageParams sp;
+  sp.ip = b->pools();
+  sp.ninst = b->n;
+  sp.gtab = b->d_tab;
+  sp.gC0 = b->d_C0;
+  ELSR_TRY_CUDA(b, launch_stage(sp, (int)std::min<int64_t>(b->rows, 1 << 30), b->stream));
+  b->tab_ready = true;
+  return ELSR_OK;
+}
+
 // Queue the runs of b->h_runs (already ordered) on b->stream.  fj_workers > 0
 // runs the single run of b->h_runs as that many fork-join workers.
 int launch_runs(elsr_batch* b, const RowBits* start_bits, bool with_traj,
@@ -488,19 +505,7 @@ int launch_runs(elsr_batch* b, const RowBits* start_bits, bool with_traj,
   if ((rc = ensure(b, &b->d_bits, &b->bits_cap, (size_t)bits_total)) != ELSR_OK) return rc;
   if (with_traj && (rc = ensure(b, &b->d_traj, &b->traj_cap, (size_t)std::max<int64_t>(traj_entries, 1))) != ELSR_OK)
     return rc;
-  if (!ls.ts && !b->tab_ready) {
-    dev_free(b->d_tab, b->stream);
-    dev_free(b->d_C0, b->stream);
-    ELSR_TRY_CUDA(b, dev_alloc(&b->d_tab, (size_t)(b->cells + b->rows), b->stream));
-    ELSR_TRY_CUDA(b, dev_alloc(&b->d_C0, (size_t)b->rows, b->stream));
-    StageParams sp;
-    sp.ip = b->pools();
-    sp.ninst = b->n;
-    sp.gtab = b->d_tab;
-    sp.gC0 = b->d_C0;
-    ELSR_TRY_CUDA(b, launch_stage(sp, (int)std::min<int64_t>(b->rows, 1 << 30), b->stream));
-    b->tab_ready = true;
-  }
+  if (!ls.ts && !b->tab_ready && (rc = stage_tables(b)) != ELSR_OK) return rc;
   ELSR_TRY_CUDA(b, cudaMemcpyAsync(b->d_runs, b->h_runs.data(), nr * sizeof(RunDesc),
                                    cudaMemcpyHostToDevice, b->stream));
   ELSR_TRY_CUDA(b, cudaMemsetAsync(b->d_queue, 0, 2 * sizeof(int32_t), b->stream));
@@ -575,8 +580,8 @@ int launch_runs(elsr_batch* b, const RowBits* start_bits, bool with_traj,
   if (teams > 1) {
     if ((rc = ensure_spec(b, teams)) != ELSR_OK) return rc;
     ELSR_TRY_CUDA(b, cudaMemsetAsync(b->d_spec_bar, 0, 2 * sizeof(int32_t), b->stream));
-    // decision words start undecided; slot round tags start at -1
-    ELSR_TRY_CUDA(b, cudaMemsetAsync(b->d_spec_dec, 0x7f, 2 * sizeof(int32_t), b->stream));
+    // decision words start with no round's tag; slot round tags start at -1
+    ELSR_TRY_CUDA(b, cudaMemsetAsync(b->d_spec_dec, 0, 2 * sizeof(int32_t), b->stream));
     ELSR_TRY_CUDA(b, cudaMemsetAsync(b->d_spec_slots, 0xff, 2 * teams * sizeof(SpecSlot), b->stream));
     p.spec_teams = teams;
     p.spec_slots = b->d_spec_slots;
@@ -1456,6 +1461,11 @@ int elsr_batch_launch_shape(elsr_batch_t* b, int32_t* shape) {
   if (!b || !shape) return ELSR_E_ARG;
   for (int i = 0; i < 8; ++i) shape[i] = b->last_shape[i];
   return ELSR_OK;
+}
+
+int elsr_batch_stage_tables(elsr_batch_t* b) {
+  if (!b) return ELSR_E_ARG;
+  return stage_tables(b);
 }
 
 int elsr_batch_run(elsr_batch_t* b, const uint64_t* seeds, int32_t iters, int32_t kmax,

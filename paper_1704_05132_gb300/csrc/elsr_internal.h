@@ -119,8 +119,8 @@ struct VnsParams {
   int32_t cluster;       // CTAs per team the launch was configured with
   SpecSlot* spec_slots;  // [2][spec_teams]
   RowBits* spec_rows;    // [2][spec_teams][3]
-  int32_t* spec_bar;     // [2]: arrivals, generation; zero at launch
-  int32_t* spec_dec;     // [2]: per round parity, first accepting team once known
+  int32_t* spec_bar;     // [2]: speculation: tickets taken; fork-join: arrivals, generation; zero at launch
+  int32_t* spec_dec;     // [2]: per round parity, (round tag << 8) | first accepting position; zero at launch
   // fork-join launches (Algorithm 2 with one shake + VND per worker): the
   // fj_workers teams share spec_slots, spec_rows and spec_bar (0: off)
   int32_t fj_workers;

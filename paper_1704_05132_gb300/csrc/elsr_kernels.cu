@@ -32,28 +32,30 @@ using vns::subwarp_min;
 using vns::umin64;
 
 // ---------------------------------------------------------------------------
-// stage_kernel: one warp per row of every instance.
+// stage_kernel: one warp per row of every instance (rows numbered across the
+// instances in order).  A warp finds its row's instance by binary search over
+// the instances' first rows.
 // ---------------------------------------------------------------------------
 __global__ void stage_kernel(const StageParams p) {
   const int lane = threadIdx.x & 31;
-  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nw = (gridDim.x * blockDim.x) >> 5;
-  int inst = 0;
-  int64_t row_base = 0;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const InstDesc* insts = p.ip.insts;
+  if (p.ninst <= 0) return;
   for (int64_t row = gw;; row += nw) {
-    while (inst < p.ninst && row >= row_base + p.ip.insts[inst].K) {
-      row_base += p.ip.insts[inst].K;
-      ++inst;
+    int lo = 0, hi = p.ninst - 1;  // the last instance whose rows start at or before row
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (insts[mid].row_off <= row) lo = mid; else hi = mid - 1;
     }
-    if (inst >= p.ninst) return;
-    const InstDesc id = p.ip.insts[inst];
-    const int k = (int)(row - row_base);
+    const InstDesc id = insts[lo];
+    if (row >= id.row_off + id.K) return;  // past the last row
+    const int k = (int)(row - id.row_off);
     const int T = id.T;
     stage_row_warp(p.ip.D + id.cell_off + (int64_t)k * T,
                    p.ip.R + id.cell_off + (int64_t)k * T, T, lane,
                    p.gtab + id.tab_off + (int64_t)k * (T + 1),
-                   p.ip.hM[id.row_off + k], p.ip.hR[id.row_off + k],
-                   p.ip.pM ? p.ip.pM[id.row_off + k] : 0, p.gC0 + id.row_off + k);
+                   p.ip.hM[row], p.ip.hR[row], p.ip.pM ? p.ip.pM[row] : 0, p.gC0 + row);
   }
 }
 

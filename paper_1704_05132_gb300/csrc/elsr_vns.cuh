@@ -646,7 +646,7 @@ struct CtlShared {
   int ninf[2];
   int Finf;
   int abort;
-  int pad;
+  int spec_pos;                 // speculative teams: this round's position (CTA 0's word counts)
   unsigned long long acc[2];
   unsigned long long gkey[2];
   long long F;
@@ -654,6 +654,8 @@ struct CtlShared {
   unsigned long long gmin[64];  // per row group and warp: partial minima (groups > 32 lanes)
   int stopw[2];                 // wall-clock budget spent (CTA 0's word counts)
   int gstop[2];                 // mode-G speculative teams: CTA 0's verdict on the decision word
+  int spec_dec;                 // speculative teams: this round's decision (CTA 0's word counts)
+  int spec_pad;
   // a run's bookkeeping that only thread 0 of CTA 0 keeps (gvns_run): in
   // shared memory rather than in every thread's registers
   unsigned long long hash;      // trajectory hash
@@ -902,6 +904,17 @@ __device__ void team_sums(Team<Acc>& t, int64_t& F, int& ninf, long long deadlin
   t.tp ^= 1;
 }
 
+// Speculative rounds (spec_kernel) decide in a word per round parity that
+// holds (tag << 8) | d: the round's tag (round + 1, modulo 2^23) and d, the
+// first accepting position (the round's active count when none accepts).
+// A word holding another tag is undecided for this round.
+constexpr int kSpecTagMask = (1 << 23) - 1;
+
+__device__ __forceinline__ bool spec_moot(const int* word, int tag, int my_index) {
+  const int v = *(volatile const int*)word;
+  return (v >> 8) == tag && (v & 0xff) < my_index;
+}
+
 // Saturating objective of the team (sum of row costs over the cluster);
 // deadline / stop as in team_sums.
 template <typename Acc>
@@ -915,11 +928,12 @@ __device__ int64_t team_total(Team<Acc>& t, long long deadline = 0, int* stop = 
 // VND of Algorithm 1 (pipe form), mode P: every product takes its best
 // strictly improving move of N_j; the j = 1..3 sweep repeats until no product
 // of the team improves.  Returns the sweeps run, or -1 at the cap.
-// `stop` (speculative teams): a decision word in global memory and this
-// team's index; the VND gives up (returns -2) at a sweep boundary once the
-// word names an earlier team, whose iteration makes this one moot.
+// `stop` (speculative teams): the round's decision word in global memory,
+// the round's tag and this team's position; the VND gives up (returns -2) at
+// a sweep boundary once the word names an earlier position, whose iteration
+// makes this one moot.
 template <typename Acc, int NW>
-__device__ int vnd_p(Team<Acc>& t, const int* stop = nullptr, int my_index = 0) {
+__device__ int vnd_p(Team<Acc>& t, const int* stop = nullptr, int tag = 0, int my_index = 0) {
   const int T = t.T;
   int cycles = 0;
   for (;;) {
@@ -954,14 +968,14 @@ __device__ int vnd_p(Team<Acc>& t, const int* stop = nullptr, int my_index = 0) 
       }
     }
     ++cycles;
-    if (stop && t.C == 1 && t.tid == 0) t.sh->flag[t.fp] = *(volatile const int*)stop < my_index;
+    if (stop && t.C == 1 && t.tid == 0) t.sh->flag[t.fp] = spec_moot(stop, tag, my_index);
     int any = cta_sync_or(t, improved);
     int quit = 0;
     if (t.C > 1) {
       cg::cluster_group cl = cg::this_cluster();
       if (t.tid == 0) {
         int f = any;
-        if (stop && t.crank == 0 && *(volatile const int*)stop < my_index) f |= 2;
+        if (stop && t.crank == 0 && spec_moot(stop, tag, my_index)) f |= 2;
         t.sh->flag[t.fp] = f;
       }
       cl.sync();
@@ -990,7 +1004,7 @@ __device__ int vnd_p(Team<Acc>& t, const int* stop = nullptr, int my_index = 0) 
 // decision word during N3 and passes its verdict with the next sweep's N1
 // exchange, after which the whole team gives up (returns -2) at once.
 template <typename Acc, int NW>
-__device__ int vnd_g(Team<Acc>& t, const int* stop = nullptr, int my_index = 0) {
+__device__ int vnd_g(Team<Acc>& t, const int* stop = nullptr, int tag = 0, int my_index = 0) {
   CtlShared* sh = t.sh;
   const int T = t.T, C = t.C;
   int64_t F;    // sum of the feasible rows' costs (team-wide)
@@ -1000,7 +1014,7 @@ __device__ int vnd_g(Team<Acc>& t, const int* stop = nullptr, int my_index = 0) 
   team_sync(t);
   const int GW = t.G < 32 ? t.G : 32;  // lanes of the group inside one warp
   int cycles = 0, e = 0;
-  int seen = 0x7fffffff;  // thread 0 of CTA 0: the decision word as read during N3
+  int seen = 0;  // thread 0 of CTA 0: the decision word's verdict as read during N3
   for (;;) {
     bool improved = false;
     int quit = 0;
@@ -1008,8 +1022,8 @@ __device__ int vnd_g(Team<Acc>& t, const int* stop = nullptr, int my_index = 0) 
       const int M = row_moves(T, j);
       if (M <= 0) continue;
       const bool lead = stop && t.crank == 0 && t.tid == 0;
-      if (lead && j == 3) seen = *(volatile const int*)stop;
-      if (lead && j == 1) sh->gstop[e] = seen < my_index;
+      if (lead && j == 3) seen = spec_moot(stop, tag, my_index);
+      if (lead && j == 1) sh->gstop[e] = seen;
       const int64_t total = Finf ? INT64_MAX : F;
       // every warp runs the same number of row iterations (the sub-warp
       // minimum below is a full-warp shuffle)
@@ -1092,8 +1106,9 @@ __device__ int vnd_g(Team<Acc>& t, const int* stop = nullptr, int my_index = 0) 
 
 template <typename Acc, int NW>
 __device__ __forceinline__ int vnd(Team<Acc>& t, int mode, const int* stop = nullptr,
-                                   int my_index = 0) {
-  return mode == 0 ? vnd_p<Acc, NW>(t, stop, my_index) : vnd_g<Acc, NW>(t, stop, my_index);
+                                   int tag = 0, int my_index = 0) {
+  return mode == 0 ? vnd_p<Acc, NW>(t, stop, tag, my_index)
+                   : vnd_g<Acc, NW>(t, stop, tag, my_index);
 }
 
 // Shake(x, k) of Algorithm 2: k moves of N_k from splitmix64 draws keyed by
@@ -1469,14 +1484,23 @@ __global__ void __launch_bounds__(MAXT, 1) srv_kernel(const VnsParams p, const S
 // ---------------------------------------------------------------------------
 // spec_kernel: one GVNS run (mode P or G) executed by W teams that speculate on
 // consecutive iterations.  In a round every team starts from the same
-// incumbent x; team i runs iteration it0 + i (its k assumes iterations it0 ..
-// it0 + i - 1 were rejected), publishes f(x'') and its changed rows, and
-// waits at a grid barrier.  The round then commits iterations in order up to
-// the first acceptance a, exactly as the sequential loop would: every team
-// undoes its own shake, adopts the changed rows of team a, and the next round
-// starts at it0 + a + 1 (or it0 + W when nothing was accepted).  Trajectory,
+// incumbent x; the team at position i runs iteration it0 + i (its k assumes
+// iterations it0 .. it0 + i - 1 were rejected) and publishes f(x'') and its
+// changed rows.  The round commits iterations in order up to the first
+// acceptance a, exactly as the sequential loop would: every team undoes its
+// own shake, adopts the changed rows of position a, and the next round starts
+// at it0 + a + 1 (or it0 + W when nothing was accepted).  Trajectory,
 // solution and counters are those of the sequential run; work of discarded
 // speculative iterations is not counted.
+//
+// No grid barrier separates the rounds.  A team takes its position in the
+// next round by ticket as soon as it knows the decision, so the teams that
+// waited for it take the first positions and the teams whose iterations
+// became moot, which notice at their next sweep boundary, take the last.
+// Slots, published rows and decision words alternate between two round
+// parities; a team takes a ticket of round r + 1 only once every team holds
+// one of round r, so nobody still reads round r - 1's data when it is
+// overwritten.
 // ---------------------------------------------------------------------------
 constexpr long kSpinLimit = 1l << 24;  // grid-barrier polls (x ~200 ns) before giving up
 
@@ -1521,6 +1545,68 @@ __device__ __forceinline__ RowBits ldcg_bits(const RowBits* p) {
   return b;
 }
 
+// The team's position in round `round` (by ticket, in order of arrival),
+// taken once every team holds a ticket of the previous round; bit 16 set when
+// the round is already decided for an earlier position (the iteration is
+// moot).  -1 when the wait exceeded its limit.
+template <typename Acc>
+__device__ int spec_ticket(Team<Acc>& t, unsigned* tickets, int W, int round, const int* dec,
+                           int tag) {
+  if (t.crank == 0 && t.tid == 0) {
+    const unsigned base = (unsigned)W * (unsigned)round;
+    int v = 0;
+    long n = 0;
+    while ((int)(*(volatile unsigned*)tickets - base) < 0) {
+      if (++n > kSpinLimit) {
+        v = -1;
+        break;
+      }
+      __nanosleep(100);
+    }
+    if (v == 0) {
+      __threadfence();
+      const int pos = (int)(atomicAdd(tickets, 1u) - base);
+      // every team holds one ticket per round, so pos < W; anything else is
+      // reported like a wait that ran out
+      v = pos >= 0 && pos < W ? pos | (spec_moot(dec, tag, pos) ? 0x10000 : 0) : -1;
+    }
+    t.sh->spec_pos = v;
+  }
+  team_sync(t);
+  if (t.C == 1) return t.sh->spec_pos;
+  cg::cluster_group cl = cg::this_cluster();
+  return *cl.map_shared_rank(&t.sh->spec_pos, 0);
+}
+
+// The round's first accepting position (its active count when none accepts),
+// once a finished prefix of positions holds it; -1 when the wait exceeded its
+// limit.
+template <typename Acc>
+__device__ int spec_decision(Team<Acc>& t, const int* dec, int tag) {
+  if (t.crank == 0 && t.tid == 0) {
+    int v;
+    long n = 0;
+    for (;;) {
+      v = *(volatile const int*)dec;
+      if ((v >> 8) == tag) {
+        v &= 0xff;
+        break;
+      }
+      if (++n > kSpinLimit) {
+        v = -1;
+        break;
+      }
+      __nanosleep(100);
+    }
+    __threadfence();
+    t.sh->spec_dec = v;
+  }
+  team_sync(t);
+  if (t.C == 1) return t.sh->spec_dec;
+  cg::cluster_group cl = cg::this_cluster();
+  return *cl.map_shared_rank(&t.sh->spec_dec, 0);
+}
+
 template <typename Acc, int NW, bool TS, int MAXT>
 __global__ void __launch_bounds__(MAXT, 1) spec_kernel(const VnsParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -1553,33 +1639,38 @@ __global__ void __launch_bounds__(MAXT, 1) spec_kernel(const VnsParams p) {
   int it0 = rd.it0, k0 = rd.k0, round = 0;
   const int it_end = rd.it0 + rd.iters;
   const bool leader = team == 0 && t.crank == 0 && t.tid == 0;
+  unsigned* const tickets = reinterpret_cast<unsigned*>(p.spec_bar);
   while (it0 < it_end && status == 0) {
     const int par = round & 1;
+    const int tag = (round + 1) & kSpecTagMask;
     const int nact = (it_end - it0) < W ? (it_end - it0) : W;
-    const bool active = team < nact;
-    const int ks = (k0 - 1 + team) % rd.kmax + 1;
-    SpecSlot* slot = p.spec_slots + par * W + team;
-    SpecSlot* slots_w = p.spec_slots + par * W;
     int* dec = p.spec_dec + par;
-    // the other parity's decision word is next written after this round's
-    // barrier; reset it now
-    if (leader) p.spec_dec[par ^ 1] = 0x7fffffff;
+    const int tk = spec_ticket(t, tickets, W, round, dec, tag);
+    if (tk < 0) {
+      status = kStatusTimeout;
+      break;
+    }
+    const int pos = tk & 0xffff;
+    const bool shaken = pos < nact && !(tk & 0x10000);
+    const int ks = (k0 - 1 + pos) % rd.kmax + 1;
+    SpecSlot* slot = p.spec_slots + par * W + pos;
+    SpecSlot* slots_w = p.spec_slots + par * W;
     ShakePlan pl;
-    if (active) {
+    if (shaken) {
       if (t.crank == 0 && t.tid == 0) {
         slot->applied = 0ull;
         slot->steps = 0ull;
       }
-      pl = plan_shake(rd.seed, it0 + team, ks, K, T);
+      pl = plan_shake(rd.seed, it0 + pos, ks, K, T);
       apply_shake<Acc, NW>(t, pl, ks, par);
-      cyc = vnd<Acc, NW>(t, rd.mode, dec, team);
-      if (cyc != -2) {  // -2: an earlier team's iteration was accepted
+      cyc = vnd<Acc, NW>(t, rd.mode, dec, tag, pos);
+      if (cyc != -2) {  // -2: an earlier position's iteration was accepted
         const int64_t f2 = team_total(t);
         flush_counters(t, &slot->steps, &slot->applied);
 #pragma unroll
         for (int j = 0; j < kMaxShake; ++j)
           if (t.owns(pl.rows[j]) && pl.first[j] && t.lane == 0)
-            p.spec_rows[(par * W + team) * kMaxShake + j] = t.m.bits[pl.rows[j] / t.C];
+            p.spec_rows[(par * W + pos) * kMaxShake + j] = t.m.bits[pl.rows[j] / t.C];
         __threadfence();
         team_sync(t);
         if (t.crank == 0 && t.warp == 0) {
@@ -1590,8 +1681,9 @@ __global__ void __launch_bounds__(MAXT, 1) spec_kernel(const VnsParams p) {
             atomicExch(&slot->done, 2 * round + (f2 < fx ? 1 : 0));
           }
           __syncwarp();
-          // The round is decided once a finished prefix of the teams holds
-          // the first acceptance (or every team finished without one).
+          // The round is decided once a finished prefix of the positions
+          // holds the first acceptance (or every position finished without
+          // one); whoever completes that prefix writes the decision.
           int d = -1;
           for (int base = 0; base < nact && d < 0; base += 32) {
             const int i = base + t.wlane;
@@ -1603,36 +1695,29 @@ __global__ void __launch_bounds__(MAXT, 1) spec_kernel(const VnsParams p) {
             if (acc & pre) {
               d = base + __ffs(acc & pre) - 1;
             } else if (nfin >= 0 && base + nfin < nact) {
-              break;  // an unfinished team precedes any acceptance
+              break;  // an unfinished position precedes any acceptance
             } else if (base + 32 >= nact) {
-              d = nact;  // every team finished, none accepted
+              d = nact;  // every position finished, none accepted
             }
           }
-          if (t.wlane == 0 && d >= 0) atomicMin(dec, d);
+          if (t.wlane == 0 && d >= 0) {
+            __threadfence();
+            atomicExch(dec, (tag << 8) | d);
+          }
         }
       } else {
         t.steps = 0;
         t.applied = 0;
       }
     }
-    if (!grid_barrier(t, p.spec_bar, W)) {
+    const int d = spec_decision(t, dec, tag);
+    if (d < 0) {
       status = kStatusTimeout;
       break;
     }
-    // commit in iteration order up to the first acceptance: a finished team's
-    // done word is 2 * round + accepted; teams that gave up hold an older
-    // round and all sit after the first acceptance
+    // commit in iteration order up to the first acceptance
     const SpecSlot* slots = p.spec_slots + par * W;
-    int a = -1;
-    for (int base = 0; base < nact; base += 32) {
-      const int i = base + t.wlane;
-      const int v = i < nact ? __ldcg(&slots[i].done) : -1;
-      const unsigned accb = __ballot_sync(kFull, v == 2 * round + 1);
-      if (accb) {
-        a = base + __ffs(accb) - 1;
-        break;
-      }
-    }
+    const int a = d < nact ? d : -1;
     const int ncommit = a >= 0 ? a + 1 : nact;
     int capped = 0;
     for (int base = 0; base < ncommit; base += 32) {
@@ -1685,8 +1770,8 @@ __global__ void __launch_bounds__(MAXT, 1) spec_kernel(const VnsParams p) {
       break;
     }
     // every team moves to the committed solution
-    if (active && team != a) undo_shake<Acc>(t, pl, par);
-    if (a >= 0 && team != a) {
+    if (shaken && pos != a) undo_shake<Acc>(t, pl, par);
+    if (a >= 0 && pos != a) {
       const int ka = (k0 - 1 + a) % rd.kmax + 1;
       const ShakePlan pw = plan_shake(rd.seed, it0 + a, ka, K, T);
 #pragma unroll

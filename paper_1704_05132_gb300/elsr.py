@@ -357,6 +357,11 @@ class Batch:
         """Decode-step counter of the next runs (off while timing)."""
         self._chk(self._lib.elsr_batch_set_count_steps(self._b, 1 if on else 0))
 
+    def stage_tables(self):
+        """(Re)build every row's prefix tables in device memory, on the
+        batch's stream (asynchronous)."""
+        self._chk(self._lib.elsr_batch_stage_tables(self._b))
+
     def set_runs_per_cta(self, runs_per_cta: int = 0):
         """Instances per CTA (0: the library's choice)."""
         self._chk(self._lib.elsr_batch_set_runs_per_cta(self._b, runs_per_cta))

@@ -116,8 +116,8 @@ def test_production_costs_validated_on_the_host(lib):
 
 
 def test_new_entry_points_reject_a_null_handle(lib):
-    """Fork-join, time budget, checkpoint and resume return ELSR_E_ARG for a
-    NULL handle (and touch nothing)."""
+    """Fork-join, time budget, checkpoint, resume and the staging pass return
+    ELSR_E_ARG for a NULL handle (and touch nothing)."""
     ck = nat.Checkpoint()
     gm = np.zeros(4, np.uint8)
     P = ctypes.c_void_p
@@ -126,6 +126,7 @@ def test_new_entry_points_reject_a_null_handle(lib):
     assert lib.elsr_checkpoint(None, ctypes.byref(ck), None, None) == nat.ELSR_E_ARG
     assert lib.elsr_vns_resume(None, ctypes.byref(ck), gm.ctypes.data_as(P),
                                gm.ctypes.data_as(P), 5) == nat.ELSR_E_ARG
+    assert lib.elsr_batch_stage_tables(None) == nat.ELSR_E_ARG
 
 
 def test_empty_batch_refused_before_any_call():

@@ -289,6 +289,36 @@ def test_batch_with_global_tables(E):
     b.close()
 
 
+def test_staging_pass_rebuilds_the_same_tables(E):
+    """The stage kernel finds each row's instance by binary search over the
+    instances' first rows: 61 instances of 1..40 products (single-product
+    instances at both ends and in the middle) and one that forces tables into
+    global memory, staged explicitly and again after a run, give the oracle's
+    results on every instance."""
+    rng = np.random.default_rng(11)
+    insts = [gen.make_instance(11, 0, K=1, T=9)]
+    insts += [gen.make_instance(11, i, K=int(rng.integers(1, 41)), T=int(rng.integers(2, 60)))
+              for i in range(1, 30)]
+    insts += [gen.make_instance(11, 30, K=1, T=64), gen.make_instance(11, 31, K=200, T=104)]
+    insts += [gen.make_instance(11, i, K=int(rng.integers(1, 41)), T=int(rng.integers(2, 60)))
+              for i in range(32, 61)]
+    insts += [gen.make_instance(11, 61, K=1, T=3)]
+    seeds = np.arange(len(insts), dtype=np.uint64) + 40
+    b = E.Batch(insts)
+    b.stage_tables()
+    b.run(seeds, iters=3, kmax=3, mode=0)
+    first = [(r["best_cost"], r["traj_hash"]) for r in b.results()]
+    assert b.launch_shape()["tables_in_smem"] == 0
+    b.stage_tables()
+    b.stage_tables()
+    b.run(seeds, iters=3, kmax=3, mode=0)
+    assert [(r["best_cost"], r["traj_hash"]) for r in b.results()] == first
+    b.close()
+    for i, g in enumerate(insts):
+        o = oracle.vns(_inst(g), seed=int(seeds[i]), iters=3, kmax=3, mode=0)
+        assert first[i] == (o.best_cost, o.traj_hash), i
+
+
 SHAPES = [(4, 64, 1), (8, 256, 1), (16, 512, 1), (32, 512, 1), (16, 384, 1),
           (32, 64, 2), (16, 128, 3), (32, 224, 8), (8, 64, 16), (32, 32, 16),
           (64, 128, 1), (64, 448, 8), (128, 256, 4), (128, 512, 2), (64, 64, 16),
