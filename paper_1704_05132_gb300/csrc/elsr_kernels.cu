@@ -32,24 +32,35 @@ using vns::subwarp_min;
 using vns::umin64;
 
 // ---------------------------------------------------------------------------
-// stage_kernel: one warp per row of every instance (rows numbered across the
-// instances in order).  A warp finds its row's instance by binary search over
-// the instances' first rows.
+// stage_kernel: every warp stages a contiguous chunk of rows (rows numbered
+// across the instances in order).  The warp finds the instance of its first
+// row with a 32-way search over the instances' first rows (one coalesced
+// probe per level: two levels for 1024 instances) and then walks forward.
 // ---------------------------------------------------------------------------
-__global__ void stage_kernel(const StageParams p) {
+__global__ void stage_kernel(const StageParams p, int64_t total_rows) {
   const int lane = threadIdx.x & 31;
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const InstDesc* insts = p.ip.insts;
   if (p.ninst <= 0) return;
-  for (int64_t row = gw;; row += nw) {
-    int lo = 0, hi = p.ninst - 1;  // the last instance whose rows start at or before row
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (insts[mid].row_off <= row) lo = mid; else hi = mid - 1;
-    }
-    const InstDesc id = insts[lo];
-    if (row >= id.row_off + id.K) return;  // past the last row
+  const int64_t chunk = (total_rows + nw - 1) / nw;
+  const int64_t row0 = gw * chunk;
+  const int64_t row1 = row0 + chunk < total_rows ? row0 + chunk : total_rows;
+  if (row0 >= row1) return;
+  // the last instance whose rows start at or before row0: insts[lo] always
+  // qualifies, and each level narrows [lo, lo + n) to one of 32 slices
+  int lo = 0, n = p.ninst;
+  while (n > 1) {
+    const int step = (n + 31) >> 5;
+    const int i = lo + lane * step;
+    const unsigned le = __ballot_sync(kFull, i < lo + n && insts[i].row_off <= row0);
+    const int s = 31 - __clz(le);  // lane 0 (i = lo) always qualifies
+    lo += s * step;
+    n = (s + 1) * step <= n ? step : n - s * step;
+  }
+  InstDesc id = insts[lo];
+  for (int64_t row = row0; row < row1; ++row) {
+    while (row >= id.row_off + id.K) id = insts[++lo];  // next non-empty instance
     const int k = (int)(row - id.row_off);
     const int T = id.T;
     stage_row_warp(p.ip.D + id.cell_off + (int64_t)k * T,
@@ -233,18 +244,8 @@ __global__ void __launch_bounds__(128, 1) eval_wide_kernel(const EvalParams p) {
   const VnsLayout lay = vns_layout(1, T, (int)sizeof(Acc), true);
   vns::Rows<Acc> m;
   m.tab = (const int2*)(smem + lay.tab);
-  m.rc = (RowCosts*)(smem + lay.rc);
-  m.C0 = (int64_t*)(smem + lay.C0);
-  m.bits = (RowBits*)(smem + lay.bits);
-  m.S = (Acc*)(smem + lay.S);
-  m.mark = (RowMark*)(smem + lay.mark);
-  m.nR = (int32_t*)(smem + lay.nR);
-  m.A = (int32_t*)(smem + lay.A);
-  m.C = (Acc*)(smem + lay.C);
-  m.L = (int2*)(smem + lay.L);
-  m.P = (int32_t*)(smem + lay.P);
-  m.Q = (Acc*)(smem + lay.Q);
-  m.save = nullptr;
+  m.place(smem, lay.rc, lay.C0, lay.bits, lay.S, lay.mark, lay.nR, lay.A, lay.C, lay.L, lay.P,
+          lay.Q, 0);  // no save slots
   m.slot = 0;
   m.T = T;
   m.C_ = 1;
@@ -254,10 +255,10 @@ __global__ void __launch_bounds__(128, 1) eval_wide_kernel(const EvalParams p) {
   if (warp == 0) {
     stage_row_warp(p.ip.D + id.cell_off + (int64_t)k * T, p.ip.R + id.cell_off + (int64_t)k * T,
                    T, wlane, (int2*)(smem + lay.tab), p.ip.hM[ro], p.ip.hR[ro],
-                   p.ip.pM ? p.ip.pM[ro] : 0, &m.C0[0]);
+                   p.ip.pM ? p.ip.pM[ro] : 0, &m.C0()[0]);
     if (wlane == 0) {
-      m.rc[0] = vns::row_costs(p.ip, ro);
-      m.bits[0] = p.bits[k];
+      m.rc()[0] = vns::row_costs(p.ip, ro);
+      m.bits()[0] = p.bits[k];
     }
   }
   if (tid == 0) {
@@ -280,8 +281,8 @@ __global__ void __launch_bounds__(128, 1) eval_wide_kernel(const EvalParams p) {
   const int64_t F = sh_F;
   const int Finf = sh_Finf;
   const RowState<Acc> cur = m.state(0);
-  const RowCosts rc = m.rc[0];
-  const int64_t c0 = m.C0[0];
+  const RowCosts rc = m.rc()[0];
+  const int64_t c0 = m.C0()[0];
   const int64_t rck = m.cost(0);
   if (tid == 0 && p.rowcost_out) p.rowcost_out[k] = rck;
   const int infk = rck == INT64_MAX;
@@ -295,7 +296,7 @@ __global__ void __launch_bounds__(128, 1) eval_wide_kernel(const EvalParams p) {
     const uint32_t goff = j == 1 ? 0u : (j == 2 ? (uint32_t)(K * T) : 2u * K * T);
     for (int l = tid; l < M; l += nthr) {
       int st = 0;
-      const Acc S = eval_move<Acc, NW>(m.tab, T, rc, cur, m.A, m.C, m.L, m.P, m.Q, j, l, st);
+      const Acc S = eval_move<Acc, NW>(m.tab, T, rc, cur, m.A(), m.C(), m.L(), m.P(), m.Q(), j, l, st);
       const int64_t nc = row_cost<Acc>(S, c0);
       bestP = umin64(bestP, pack_key(nc, loff + (uint32_t)l));
       if (p.mode == 1) {
@@ -455,7 +456,7 @@ cudaError_t launch_stage(const StageParams& p, int total_rows, cudaStream_t s) {
   const int threads = 256;
   int blocks = (total_rows * 32 + threads - 1) / threads;
   if (blocks > 4096) blocks = 4096;
-  stage_kernel<<<blocks, threads, 0, s>>>(p);
+  stage_kernel<<<blocks, threads, 0, s>>>(p, total_rows);
   return cudaGetLastError();
 }
 

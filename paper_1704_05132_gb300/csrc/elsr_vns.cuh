@@ -158,25 +158,42 @@ __device__ __forceinline__ InstDesc ldcg_inst(const InstDesc* d) {
   return o;
 }
 
-// Shared-memory view of the rows a CTA owns in the current run.
+// The kernel's dynamic shared memory (every extern __shared__ array of a
+// kernel starts at the same address).
+extern __shared__ __align__(16) unsigned char dyn_smem[];
+
+// Shared-memory view of the rows a CTA owns in the current run.  The arrays
+// are held as 32-bit offsets into dynamic shared memory (one register each).
 template <typename Acc>
 struct Rows {
   const int2* tab;   // TS: local rows [Kc][T+1]; else global table of row 0
-  RowCosts* rc;
-  int64_t* C0;
-  RowBits* bits;
-  Acc* S;          // relaxed segment sums
-  RowMark* mark;   // first shortfall setup, L index of the last one
-  int32_t* nR;
-  int32_t* A;  // [Kc][T]
-  Acc* C;      // [Kc][T]
-  int2* L;     // [Kc][T]
-  int32_t* P;  // [Kc][T+1]
-  Acc* Q;      // [Kc][T+1]
-  unsigned char* save;
+  uint32_t o_rc, o_C0, o_bits, o_S, o_mark, o_nR, o_A, o_C, o_L, o_P, o_Q, o_save;
   uint32_t slot;
   int T, C_, crank;
   bool ts;
+
+  __device__ __forceinline__ RowCosts* rc() const { return (RowCosts*)(dyn_smem + o_rc); }
+  __device__ __forceinline__ int64_t* C0() const { return (int64_t*)(dyn_smem + o_C0); }
+  __device__ __forceinline__ RowBits* bits() const { return (RowBits*)(dyn_smem + o_bits); }
+  __device__ __forceinline__ Acc* S() const { return (Acc*)(dyn_smem + o_S); }
+  __device__ __forceinline__ RowMark* mark() const { return (RowMark*)(dyn_smem + o_mark); }
+  __device__ __forceinline__ int32_t* nR() const { return (int32_t*)(dyn_smem + o_nR); }
+  __device__ __forceinline__ int32_t* A() const { return (int32_t*)(dyn_smem + o_A); }
+  __device__ __forceinline__ Acc* C() const { return (Acc*)(dyn_smem + o_C); }
+  __device__ __forceinline__ int2* L() const { return (int2*)(dyn_smem + o_L); }
+  __device__ __forceinline__ int32_t* P() const { return (int32_t*)(dyn_smem + o_P); }
+  __device__ __forceinline__ Acc* Q() const { return (Acc*)(dyn_smem + o_Q); }
+  __device__ __forceinline__ unsigned char* save() const { return dyn_smem + o_save; }
+  // place the arrays at byte offsets of the region starting at base
+  __device__ __forceinline__ void place(unsigned char* base, uint32_t rc_, uint32_t C0_,
+                                        uint32_t bits_, uint32_t S_, uint32_t mark_,
+                                        uint32_t nR_, uint32_t A_, uint32_t C_a, uint32_t L_,
+                                        uint32_t P_, uint32_t Q_, uint32_t save_) {
+    const uint32_t b = (uint32_t)(base - dyn_smem);
+    o_rc = b + rc_; o_C0 = b + C0_; o_bits = b + bits_; o_S = b + S_; o_mark = b + mark_;
+    o_nR = b + nR_; o_A = b + A_; o_C = b + C_a; o_L = b + L_; o_P = b + P_; o_Q = b + Q_;
+    o_save = b + save_;
+  }
 
   __device__ __forceinline__ const int2* tab_row(int q) const {
     const int64_t r = ts ? q : (int64_t)q * C_ + crank;
@@ -184,19 +201,19 @@ struct Rows {
   }
   __device__ __forceinline__ RowState<Acc> state(int q) const {
     RowState<Acc> st;
-    st.b = bits[q];
-    st.S = S[q];
-    const RowMark mk = mark[q];
+    st.b = bits()[q];
+    st.S = S()[q];
+    const RowMark mk = mark()[q];
     st.bad = mk.bad;
     st.ld = mk.ld;
-    st.nR = nR[q];
+    st.nR = nR()[q];
     return st;
   }
   __device__ __forceinline__ int64_t cost(int q) const {
-    return state_cost<Acc>(S[q], mark[q].bad, T, C0[q]);
+    return state_cost<Acc>(S()[q], mark()[q].bad, T, C0()[q]);
   }
   __device__ __forceinline__ unsigned char* slot_ptr(int par, int j) const {
-    return save + (uint32_t)(par * kMaxShake + j) * slot;
+    return save() + (uint32_t)(par * kMaxShake + j) * slot;
   }
 };
 
@@ -227,20 +244,20 @@ __device__ __forceinline__ void save_row(const Rows<Acc>& m, int q, unsigned cha
   int2* sL = (int2*)(sl + slot_L_off<Acc>(T));
   int32_t* sP = (int32_t*)(sl + slot_P_off<Acc>(T));
   Acc* sQ = (Acc*)(sl + slot_Q_off<Acc>(T));
-  const int nr = m.nR[q];
+  const int nr = m.nR()[q];
   for (int s = lane; s < T; s += G) {
-    sA[s] = m.A[q * T + s];
-    sC[s] = m.C[q * T + s];
-    if (s < nr) sL[s] = m.L[q * T + s];
+    sA[s] = m.A()[q * T + s];
+    sC[s] = m.C()[q * T + s];
+    if (s < nr) sL[s] = m.L()[q * T + s];
   }
   for (int s = lane; s <= nr; s += G) {
-    sP[s] = m.P[q * (T + 1) + s];
-    sQ[s] = m.Q[q * (T + 1) + s];
+    sP[s] = m.P()[q * (T + 1) + s];
+    sQ[s] = m.Q()[q * (T + 1) + s];
   }
   if (lane == 0) {
-    *(RowBits*)sl = m.bits[q];
-    *(int64_t*)(sl + 32) = (int64_t)m.S[q];
-    *(RowMark*)(sl + 40) = m.mark[q];
+    *(RowBits*)sl = m.bits()[q];
+    *(int64_t*)(sl + 32) = (int64_t)m.S()[q];
+    *(RowMark*)(sl + 40) = m.mark()[q];
     *(int32_t*)(sl + 44) = nr;
   }
 }
@@ -256,19 +273,19 @@ __device__ __forceinline__ void restore_row(const Rows<Acc>& m, int q,
   const Acc* sQ = (const Acc*)(sl + slot_Q_off<Acc>(T));
   const int nr = *(const int32_t*)(sl + 44);
   for (int s = lane; s < T; s += G) {
-    m.A[q * T + s] = sA[s];
-    m.C[q * T + s] = sC[s];
-    if (s < nr) m.L[q * T + s] = sL[s];
+    m.A()[q * T + s] = sA[s];
+    m.C()[q * T + s] = sC[s];
+    if (s < nr) m.L()[q * T + s] = sL[s];
   }
   for (int s = lane; s <= nr; s += G) {
-    m.P[q * (T + 1) + s] = sP[s];
-    m.Q[q * (T + 1) + s] = sQ[s];
+    m.P()[q * (T + 1) + s] = sP[s];
+    m.Q()[q * (T + 1) + s] = sQ[s];
   }
   if (lane == 0) {
-    m.bits[q] = *(const RowBits*)sl;
-    m.S[q] = (Acc)(*(const int64_t*)(sl + 32));
-    m.mark[q] = *(const RowMark*)(sl + 40);
-    m.nR[q] = nr;
+    m.bits()[q] = *(const RowBits*)sl;
+    m.S()[q] = (Acc)(*(const int64_t*)(sl + 32));
+    m.mark()[q] = *(const RowMark*)(sl + 40);
+    m.nR()[q] = nr;
   }
 }
 
@@ -280,13 +297,13 @@ __device__ __forceinline__ uint64_t row_best(const Rows<Acc>& m, int q,
                                              int lane, int G, uint32_t& steps) {
   const int T = m.T;
   const int2* tk = m.tab_row(q);
-  const int32_t* Aq = m.A + q * T;
-  const Acc* Cq = m.C + q * T;
-  const int2* Lq = m.L + q * T;
-  const int32_t* Pq = m.P + q * (T + 1);
-  const Acc* Qq = m.Q + q * (T + 1);
-  const RowCosts rc = m.rc[q];
-  const int64_t c0 = m.C0[q];
+  const int32_t* Aq = m.A() + q * T;
+  const Acc* Cq = m.C() + q * T;
+  const int2* Lq = m.L() + q * T;
+  const int32_t* Pq = m.P() + q * (T + 1);
+  const Acc* Qq = m.Q() + q * (T + 1);
+  const RowCosts rc = m.rc()[q];
+  const int64_t c0 = m.C0()[q];
   uint64_t best = ~0ull;
   int st = 0;
   if (j == 3) {
@@ -327,14 +344,14 @@ __device__ __forceinline__ void rebuild_row(const Rows<Acc>& m, int q, int lane,
                                             unsigned smask) {
   const int T = m.T;
   const int2* tab = m.tab_row(q);
-  const RowBits b = m.bits[q];
-  const RowCosts rc = m.rc[q];
+  const RowBits b = m.bits()[q];
+  const RowCosts rc = m.rc()[q];
   const uint64_t u0 = b.m0 | b.r0, u1 = b.m1 | b.r1;
-  int32_t* A = m.A + q * T;
-  Acc* C = m.C + q * T;
-  int2* L = m.L + q * T;
-  int32_t* Pr = m.P + q * (T + 1);
-  Acc* Qr = m.Q + q * (T + 1);
+  int32_t* A = m.A() + q * T;
+  Acc* C = m.C() + q * T;
+  int2* L = m.L() + q * T;
+  int32_t* Pr = m.P() + q * (T + 1);
+  Acc* Qr = m.Q() + q * (T + 1);
   const int P = (T + G - 1) / G;
   const int a = lane * P, e = a + P < T ? a + P : T;
   // phase 1: composition of this lane's period functions
@@ -448,10 +465,10 @@ __device__ __forceinline__ void rebuild_row(const Rows<Acc>& m, int q, int lane,
     RowMark mk;
     mk.bad = (int16_t)bad;
     mk.ld = (int16_t)last_def;
-    m.mark[q] = mk;
-    m.S[q] = total;
+    m.mark()[q] = mk;
+    m.S()[q] = total;
     const int nr = popc64(b.r0) + (NW == 1 ? 0 : popc64(b.r1));
-    m.nR[q] = nr;
+    m.nR()[q] = nr;
     Pr[nr] = totP;
     Qr[nr] = totQ;
   }
@@ -466,14 +483,14 @@ __device__ __forceinline__ void rebuild_row_regs(const Rows<Acc>& m, int q, int 
                                                  unsigned smask) {
   const int T = m.T;
   const int2* tab = m.tab_row(q);
-  const RowBits b = m.bits[q];
-  const RowCosts rc = m.rc[q];
+  const RowBits b = m.bits()[q];
+  const RowCosts rc = m.rc()[q];
   const uint64_t u0 = b.m0 | b.r0, u1 = b.m1 | b.r1;
-  int32_t* A = m.A + q * T;
-  Acc* C = m.C + q * T;
-  int2* L = m.L + q * T;
-  int32_t* Pr = m.P + q * (T + 1);
-  Acc* Qr = m.Q + q * (T + 1);
+  int32_t* A = m.A() + q * T;
+  Acc* C = m.C() + q * T;
+  int2* L = m.L() + q * T;
+  int32_t* Pr = m.P() + q * (T + 1);
+  Acc* Qr = m.Q() + q * (T + 1);
   const int P = (T + G - 1) / G;
   const int a = lane * P, e = a + P < T ? a + P : T;
   // the first setup and the demand before it (lane 0 uses them last)
@@ -611,10 +628,10 @@ __device__ __forceinline__ void rebuild_row_regs(const Rows<Acc>& m, int q, int 
     RowMark mk;
     mk.bad = (int16_t)(dfirst != 0 ? -1 : first_bad);  // -1: demand before the first setup
     mk.ld = (int16_t)last_def;
-    m.mark[q] = mk;
-    m.S[q] = total;
+    m.mark()[q] = mk;
+    m.S()[q] = total;
     const int nr = popc64(b.r0) + (NW == 1 ? 0 : popc64(b.r1));
-    m.nR[q] = nr;
+    m.nR()[q] = nr;
     Pr[nr] = totP;
     Qr[nr] = totQ;
   }
@@ -661,6 +678,7 @@ struct CtlShared {
   unsigned long long hash;      // trajectory hash
   long long cycles, accepted;   // VND sweeps, accepted iterations
   long long deadline;           // wall-clock budget's end (ns; 0 = none)
+  RunDesc rd;                   // the run's descriptor (gvns_run reads it here)
 };
 // kSmemLimit leaves 1 KB of the CTA's shared memory to static words.
 static_assert(sizeof(CtlShared) <= 768, "static control words outgrow their reserve");
@@ -789,18 +807,8 @@ __device__ bool team_begin(Team<Acc>& t, unsigned char* smem, uint32_t region, C
   if (C != p.cluster || Lay.total > region) return false;
   Rows<Acc>& m = t.m;
   m.tab = TS ? (const int2*)(smem + Lay.tab) : (p.ip.gtab + id.tab_off);
-  m.rc = (RowCosts*)(smem + Lay.rc);
-  m.C0 = (int64_t*)(smem + Lay.C0);
-  m.bits = (RowBits*)(smem + Lay.bits);
-  m.S = (Acc*)(smem + Lay.S);
-  m.mark = (RowMark*)(smem + Lay.mark);
-  m.nR = (int32_t*)(smem + Lay.nR);
-  m.A = (int32_t*)(smem + Lay.A);
-  m.C = (Acc*)(smem + Lay.C);
-  m.L = (int2*)(smem + Lay.L);
-  m.P = (int32_t*)(smem + Lay.P);
-  m.Q = (Acc*)(smem + Lay.Q);
-  m.save = smem + Lay.save;
+  m.place(smem, Lay.rc, Lay.C0, Lay.bits, Lay.S, Lay.mark, Lay.nR, Lay.A, Lay.C, Lay.L, Lay.P,
+          Lay.Q, Lay.save);
   m.slot = Lay.slot;
   m.T = T;
   m.C_ = C;
@@ -814,13 +822,13 @@ __device__ bool team_begin(Team<Acc>& t, unsigned char* smem, uint32_t region, C
                             p.ip.R + id.cell_off + (int64_t)k * T, T, t.wlane,
                             (int2*)(smem + Lay.tab) + (int64_t)q * (T + 1),
                             ld_in<Fresh>(p.ip.hM + ro), ld_in<Fresh>(p.ip.hR + ro),
-                            p.ip.pM ? ld_in<Fresh>(p.ip.pM + ro) : 0, &m.C0[q]);
+                            p.ip.pM ? ld_in<Fresh>(p.ip.pM + ro) : 0, &m.C0()[q]);
     } else if (t.wlane == 0) {
-      m.C0[q] = p.ip.gC0[ro];
+      m.C0()[q] = p.ip.gC0[ro];
     }
     if (t.wlane == 0) {
-      m.rc[q] = row_costs<Fresh>(p.ip, ro);
-      m.bits[q] = rd.start_off >= 0 ? p.start_bits[rd.start_off + k] : all_open(T);
+      m.rc()[q] = row_costs<Fresh>(p.ip, ro);
+      m.bits()[q] = rd.start_off >= 0 ? p.start_bits[rd.start_off + k] : all_open(T);
     }
   }
   if (t.tid == 0) {
@@ -955,9 +963,9 @@ __device__ int vnd_p(Team<Acc>& t, const int* stop = nullptr, int tag = 0, int m
         const bool imp = valid && key_cost(best) < t.m.cost(q);
         if (imp) {
           if (t.lane == 0) {
-            RowBits nb = t.m.bits[q];
+            RowBits nb = t.m.bits()[q];
             apply_row_move(nb, T, j, key_index(best));
-            t.m.bits[q] = nb;
+            t.m.bits()[q] = nb;
             ++t.applied;
           }
           group_sync(t);
@@ -1037,8 +1045,8 @@ __device__ int vnd_g(Team<Acc>& t, const int* stop = nullptr, int tag = 0, int m
           const int infk = rck == INT64_MAX;
           const int64_t others = (Finf - infk > 0) ? INT64_MAX : F - (infk ? 0 : rck);
           const int2* tk = t.m.tab_row(q);
-          const RowCosts rc = t.m.rc[q];
-          const int64_t c0 = t.m.C0[q];
+          const RowCosts rc = t.m.rc()[q];
+          const int64_t c0 = t.m.C0()[q];
           int st = 0;
           const SwapMasks sw = swap_masks<NW>(cur.b, T);
           const int Mj = j == 3 ? sw.n : M;  // N3: non-null swaps only
@@ -1047,8 +1055,8 @@ __device__ int vnd_g(Team<Acc>& t, const int* stop = nullptr, int tag = 0, int m
             for (int i = t.lane; i < Mj; i += t.G) {
               const int l = j == 3 ? swap_of_rank<NW>(sw, T, i) : i;
               const Acc S = eval_move<Acc, NW, decltype(counted)::value>(
-                  tk, T, rc, cur, t.m.A + q * T, t.m.C + q * T, t.m.L + q * T,
-                  t.m.P + q * (T + 1), t.m.Q + q * (T + 1), j, l, st);
+                  tk, T, rc, cur, t.m.A() + q * T, t.m.C() + q * T, t.m.L() + q * T,
+                  t.m.P() + q * (T + 1), t.m.Q() + q * (T + 1), j, l, st);
               const int64_t nc = row_cost<Acc>(S, c0);
               const int64_t nt =
                   (others == INT64_MAX || nc == INT64_MAX) ? INT64_MAX : others + nc;
@@ -1080,9 +1088,9 @@ __device__ int vnd_g(Team<Acc>& t, const int* stop = nullptr, int tag = 0, int m
         const int qw = kw / C;
         if ((kw % C) == t.crank && (qw % t.nsub) == t.sub) {
           if (t.lane == 0) {
-            RowBits nb = t.m.bits[qw];
+            RowBits nb = t.m.bits()[qw];
             apply_row_move(nb, T, j, lw);
-            t.m.bits[qw] = nb;
+            t.m.bits()[qw] = nb;
             ++t.applied;
           }
           group_sync(t);
@@ -1153,9 +1161,9 @@ __device__ void apply_shake(Team<Acc>& t, const ShakePlan& pl, int ks, int par) 
       if (pl.first[j]) save_row<Acc>(t.m, k / t.C, t.m.slot_ptr(par, j), t.lane, t.G);
       group_sync(t);
       if (t.lane == 0) {
-        RowBits b = t.m.bits[k / t.C];
+        RowBits b = t.m.bits()[k / t.C];
         apply_row_move(b, t.T, ks, pl.locs[j]);
-        t.m.bits[k / t.C] = b;
+        t.m.bits()[k / t.C] = b;
       }
       group_sync(t);
     }
@@ -1264,8 +1272,13 @@ static_assert(sizeof(CtlShared) <= kCtlBytes, "partition control words outgrow t
 // its statistics to p.out[rd.out].  Ends with a team barrier.
 template <typename Acc, int NW>
 __device__ __forceinline__ void gvns_run(Team<Acc>& t, CtlShared* sh, const VnsParams& p,
-                                         const RunDesc& rd) {
+                                         const RunDesc& rd_in) {
   cg::cluster_group cl = cg::this_cluster();
+  // The descriptor is read from shared memory where it is needed rather than
+  // held in registers across every VND call.
+  if (t.tid == 0) sh->rd = rd_in;
+  cta_sync(t);
+  const RunDesc& rd = sh->rd;
   const int K = t.K, T = t.T;
   // Thread 0 of CTA 0 keeps the trajectory hash, the counters and the
   // wall-clock budget in shared memory: no other thread needs them, and
@@ -1324,7 +1337,7 @@ __device__ __forceinline__ void gvns_run(Team<Acc>& t, CtlShared* sh, const VnsP
   }
   cta_sync(t);  // restores of the last iteration are complete
   for (int q = t.tid; q < t.Kc; q += t.nthr)
-    p.out_bits[rd.bits_off + q * t.C + t.crank] = t.m.bits[q];
+    p.out_bits[rd.bits_off + q * t.C + t.crank] = t.m.bits()[q];
   flush_counters(t, &sh->steps, &sh->applied);
   team_sync(t);
   if (lead) {
@@ -1670,7 +1683,7 @@ __global__ void __launch_bounds__(MAXT, 1) spec_kernel(const VnsParams p) {
 #pragma unroll
         for (int j = 0; j < kMaxShake; ++j)
           if (t.owns(pl.rows[j]) && pl.first[j] && t.lane == 0)
-            p.spec_rows[(par * W + pos) * kMaxShake + j] = t.m.bits[pl.rows[j] / t.C];
+            p.spec_rows[(par * W + pos) * kMaxShake + j] = t.m.bits()[pl.rows[j] / t.C];
         __threadfence();
         team_sync(t);
         if (t.crank == 0 && t.warp == 0) {
@@ -1681,6 +1694,10 @@ __global__ void __launch_bounds__(MAXT, 1) spec_kernel(const VnsParams p) {
             atomicExch(&slot->done, 2 * round + (f2 < fx ? 1 : 0));
           }
           __syncwarp();
+          // Done word, fence, then the scan: of two teams that finish at the
+          // same time, at least one sees the other's done word, so the team
+          // that completes the prefix always finds it complete.
+          __threadfence();
           // The round is decided once a finished prefix of the positions
           // holds the first acceptance (or every position finished without
           // one); whoever completes that prefix writes the decision.
@@ -1779,7 +1796,7 @@ __global__ void __launch_bounds__(MAXT, 1) spec_kernel(const VnsParams p) {
         const int k = pw.rows[j];
         if (t.owns(k) && pw.first[j]) {
           if (t.lane == 0)
-            t.m.bits[k / t.C] = ldcg_bits(p.spec_rows + (par * W + a) * kMaxShake + j);
+            t.m.bits()[k / t.C] = ldcg_bits(p.spec_rows + (par * W + a) * kMaxShake + j);
           group_sync(t);
           group_rebuild<Acc, NW>(t, k / t.C);
         }
@@ -1800,7 +1817,7 @@ __global__ void __launch_bounds__(MAXT, 1) spec_kernel(const VnsParams p) {
   cta_sync(t);  // undo / adoption of the last round are complete
   if (team == 0) {
     for (int q = t.tid; q < t.Kc; q += t.nthr)
-      p.out_bits[rd.bits_off + q * t.C + t.crank] = t.m.bits[q];
+      p.out_bits[rd.bits_off + q * t.C + t.crank] = t.m.bits()[q];
   }
   team_sync(t);
   if (leader) {
@@ -1888,7 +1905,7 @@ __global__ void __launch_bounds__(MAXT, 1) fj_kernel(const VnsParams p) {
 #pragma unroll
     for (int j = 0; j < kMaxShake; ++j)
       if (t.owns(pl.rows[j]) && pl.first[j] && t.lane == 0)
-        p.spec_rows[(par * W + team) * kMaxShake + j] = t.m.bits[pl.rows[j] / t.C];
+        p.spec_rows[(par * W + team) * kMaxShake + j] = t.m.bits()[pl.rows[j] / t.C];
     if (t.crank == 0 && t.tid == 0) {
       slot->f2 = f2;
       slot->cycles = cyc;
@@ -1958,7 +1975,7 @@ __global__ void __launch_bounds__(MAXT, 1) fj_kernel(const VnsParams p) {
         const int k = pw.rows[j];
         if (t.owns(k) && pw.first[j]) {
           if (t.lane == 0)
-            t.m.bits[k / t.C] = ldcg_bits(p.spec_rows + (par * W + a) * kMaxShake + j);
+            t.m.bits()[k / t.C] = ldcg_bits(p.spec_rows + (par * W + a) * kMaxShake + j);
           group_sync(t);
           group_rebuild<Acc, NW>(t, k / t.C);
         }
@@ -1977,7 +1994,7 @@ __global__ void __launch_bounds__(MAXT, 1) fj_kernel(const VnsParams p) {
   cta_sync(t);  // undo / adoption of the last iteration are complete
   if (team == 0) {
     for (int q = t.tid; q < t.Kc; q += t.nthr)
-      p.out_bits[rd.bits_off + q * t.C + t.crank] = t.m.bits[q];
+      p.out_bits[rd.bits_off + q * t.C + t.crank] = t.m.bits()[q];
   }
   team_sync(t);
   if (leader) {

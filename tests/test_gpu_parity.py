@@ -319,6 +319,26 @@ def test_staging_pass_rebuilds_the_same_tables(E):
         assert first[i] == (o.best_cost, o.traj_hash), i
 
 
+def test_staging_pass_over_many_instances(E):
+    """1100 small instances and one whose tables go to global memory (three
+    levels of the stage kernel's 32-way search): a sample of runs, the first
+    and last instances among them, equals the oracle."""
+    rng = np.random.default_rng(12)
+    insts = [gen.make_instance(12, i, K=int(rng.integers(1, 9)), T=int(rng.integers(2, 20)))
+             for i in range(1100)]
+    insts.insert(700, gen.make_instance(12, 5000, K=200, T=104))
+    seeds = np.arange(len(insts), dtype=np.uint64)
+    b = E.Batch(insts)
+    b.stage_tables()
+    b.run(seeds, iters=2, kmax=3, mode=0)
+    res = b.results()
+    assert b.launch_shape()["tables_in_smem"] == 0
+    b.close()
+    for i in [0, 1, 31, 32, 33, 699, 700, 701, 1023, 1024, 1025] + list(range(1090, 1101)):
+        o = oracle.vns(_inst(insts[i]), seed=int(seeds[i]), iters=2, kmax=3, mode=0)
+        assert (res[i]["best_cost"], res[i]["traj_hash"]) == (o.best_cost, o.traj_hash), i
+
+
 SHAPES = [(4, 64, 1), (8, 256, 1), (16, 512, 1), (32, 512, 1), (16, 384, 1),
           (32, 64, 2), (16, 128, 3), (32, 224, 8), (8, 64, 16), (32, 32, 16),
           (64, 128, 1), (64, 448, 8), (128, 256, 4), (128, 512, 2), (64, 64, 16),
