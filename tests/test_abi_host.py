@@ -250,3 +250,17 @@ def test_batch_passes_instances_back_to_back(monkeypatch):
                 want = np.concatenate([getattr(i, f) if getattr(i, f) is not None
                                        else np.zeros(i.K, np.int32) for i in batch])
             np.testing.assert_array_equal(a, want, err_msg=f)
+
+
+def test_server_config_is_validated_before_any_device_call(lib):
+    """Invalid server configurations are refused with ELSR_E_ARG on the host
+    (no device is touched), and the binding's structure has the header's
+    size."""
+    assert ctypes.sizeof(nat.ServerConfig) == 40
+    h = ctypes.c_void_p()
+    for field, value in (("slots", -1), ("threads", 100), ("threads", 2048), ("max_runs", -1),
+                         ("acc64", 2), ("count_steps", -1), ("keep_solutions", 2)):
+        cfg = nat.ServerConfig()
+        setattr(cfg, field, value)
+        assert lib.elsr_server_create(ctypes.byref(h), ctypes.byref(cfg)) == nat.ELSR_E_ARG, field
+        assert not h.value
