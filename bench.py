@@ -62,10 +62,10 @@ INT_OPS_PER_STEP = 16         # algorithmic integer operations per decode step
 # DRAM bytes (read + written) per launch, from ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum) on the current kernels.  The speculative kernel of
 # the plain run is not profiled: its figure is a one-team launch of the same
-# run (100 iterations: 264,448 B read, 0 written) scaled by the iterations, an
+# run (100 iterations: 280,580 B read, 0 written) scaled by the iterations, an
 # upper bound since the instance is staged once per run.
-TRAFFIC_PLAIN_PER_100_ITERS = 264_448
-TRAFFIC_BATCH_LAUNCH = 18_520_000 + 38_190_000  # batch workload launch (500 iterations)
+TRAFFIC_PLAIN_PER_100_ITERS = 280_580
+TRAFFIC_BATCH_LAUNCH = 16_460_000 + 12_140_000  # batch workload's timed launch (500 iterations)
 LANES_PER_SM = 128            # 32-bit integer lanes per SM (4 SMSPs x 32), for context
 L2_FLUSH_BYTES = 256 << 20
 
@@ -600,6 +600,7 @@ def run_gpu(args):
                        launch="one persistent launch per GVNS run"),
         "instances_per_s": world * args.steps / t_max,
         "moves_per_step": moves_per_step,
+        "segments_per_step": segs_per_step,
         "eval_launch": eval_launch,
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
