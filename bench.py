@@ -696,7 +696,7 @@ def main():
     ap.add_argument("--rate", type=float, default=2000.0, help="serving arrivals per second")
     ap.add_argument("--requests", type=int, default=2000, help="serving requests")
     ap.add_argument("--slots", type=int, default=2048, help="serving requests in flight at most")
-    ap.add_argument("--max-runs", type=int, default=4,
+    ap.add_argument("--max-runs", type=int, default=1,
                     help="serving requests a team solves before it leaves its SMs")
     ap.add_argument("--n", type=int, default=0, help="instances / starts of a batched workload")
     ap.add_argument("--iters", type=int, default=None,

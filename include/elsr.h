@@ -521,7 +521,7 @@ typedef struct {
     int32_t threads;        /* threads per CTA, a multiple of 32 <= 1024; 0: 1024 */
     int64_t cells;          /* demand/return values the pools hold; 0: 8 Mi */
     int64_t rows;           /* product rows the pools hold; 0: 512 Ki */
-    int32_t max_runs;       /* requests a team solves before it exits; 0: 4 */
+    int32_t max_runs;       /* requests a team solves before it exits; 0: 1 */
     int32_t acc64;          /* 1: 64-bit row accumulators (admits any instance);
                                0: 32-bit (refuses instances that need 64) */
     int32_t count_steps;    /* 1: count decode steps (stats.segments); 0: not */

@@ -103,7 +103,7 @@ struct elsr_server {
   int32_t cap = 0;
   int64_t cells_cap = 0, rows_cap = 0;
   bool acc64 = false;
-  int threads = 1024, max_runs = 4, count_steps = 1, keep = 0;
+  int threads = 1024, max_runs = 1, count_steps = 1, keep = 0;
   std::string err;
 
   cudaStream_t cstream = nullptr;
@@ -273,7 +273,7 @@ int elsr_server_create(elsr_server_t** out, const elsr_server_config_t* cfg) {
   s->cells_cap = c.cells ? c.cells : kDefaultCells;
   s->rows_cap = c.rows ? c.rows : kDefaultRows;
   s->threads = c.threads ? c.threads : 1024;
-  s->max_runs = c.max_runs ? c.max_runs : 4;
+  s->max_runs = c.max_runs ? c.max_runs : 1;
   s->acc64 = c.acc64 == 1;
   s->count_steps = c.count_steps;
   s->keep = c.keep_solutions;

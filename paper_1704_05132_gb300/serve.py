@@ -165,7 +165,7 @@ class Server:
     footprint fits and waits otherwise."""
 
     def __init__(self, slots: int = 2048, cells: int = 8 << 20, rows: int = 512 << 10,
-                 max_runs: int = 4, kmax: int = 3, mode: int = nat.MODE_P,
+                 max_runs: int = 1, kmax: int = 3, mode: int = nat.MODE_P,
                  acc64: bool = False, native=None):
         self.slots, self.cells, self.rows = slots, cells, rows
         self.max_runs = max_runs
