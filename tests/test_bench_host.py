@@ -75,3 +75,21 @@ def test_clock_summary_parses_throttle_reasons(tmp_path):
     assert not os.path.exists(csv)                       # the sample file is removed
     empty = b.ClockSampler(0)
     assert empty.summary()["reasons"] == ["unsampled"]   # nvidia-smi could not start
+
+
+def test_cpu_baseline_pool_reports_all_cores_and_one_core():
+    """The batched workloads' CPU baseline: independent oracle runs on every
+    host core (spawned workers, so the module runs as `bench`), reported as
+    the whole pool's rate and as the one-core rate of the same runs (their
+    moves over the sum of their own run times)."""
+    code = ("import json, bench; print(json.dumps(bench.cpu_baseline_pool("
+            "[('batch', i, i, 3) for i in range(4)], 'four small runs')))")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    cb = json.loads(r.stdout.strip().splitlines()[-1])
+    assert cb["kind"] == "oracle" and cb["cores"] == (os.cpu_count() or 1)
+    assert cb["value"] > 0 and cb["instances_per_s"] > 0
+    one = cb["one_core"]
+    assert one["unit"] == cb["unit"] and one["value"] > 0 and one["instances_per_s"] > 0
+    assert "four small runs (4 runs" in cb["sample"]
