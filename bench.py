@@ -200,6 +200,15 @@ def cpu_baseline_pool(jobs, sample: str):
             "sample": sample + f" ({len(jobs)} runs, {moves} moves, {wall:.1f} s wall)"}
 
 
+def extrapolate_full(cb, runs, iter_scale, how):
+    """Add to a pool baseline `cb` the oracle's time for the full workload:
+    `runs` runs, each `iter_scale` times the sample's iterations, at the
+    sample's runs per second on the same cores."""
+    cb["full_workload_s_extrapolated"] = runs * iter_scale / cb["instances_per_s"]
+    cb["extrapolation"] = how
+    return cb
+
+
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
@@ -377,9 +386,11 @@ def bench_batch(torch, dev, stream, flush, peak, steps, warmup, args, cpu=True):
     b.close()
     if cpu and not args.no_cpu_baseline:
         m = min(n, 64)
-        rec["cpu_baseline"] = cpu_baseline_pool(
+        rec["cpu_baseline"] = cb = cpu_baseline_pool(
             [("batch", i, i, iters) for i in range(m)],
             f"the first {m} of the {n} instances, {iters} iterations each")
+        extrapolate_full(cb, n, 1.0, f"all {n} instances at the sample's instances/s on the "
+                                     "same cores (the sample is the workload's first instances)")
     return rec
 
 
@@ -421,9 +432,13 @@ def bench_multistart(torch, dev, stream, flush, peak, steps, warmup, args, cpu=T
     sv.close()
     if cpu and not args.no_cpu_baseline:
         m, it_s = 16, min(iters, 200)
-        rec["cpu_baseline"] = cpu_baseline_pool(
+        rec["cpu_baseline"] = cb = cpu_baseline_pool(
             [("multistart", 0, s, it_s) for s in range(m)],
             f"starts 0..{m - 1}, {it_s} of the {iters} iterations each")
+        extrapolate_full(cb, n, iters / it_s,
+                         f"all {n} starts at {iters} iterations: the sample's time per start "
+                         f"scaled by {iters}/{it_s} iterations (an estimate: the early "
+                         "iterations include the longer initial descent)")
     return rec
 
 

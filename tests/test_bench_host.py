@@ -93,3 +93,13 @@ def test_cpu_baseline_pool_reports_all_cores_and_one_core():
     one = cb["one_core"]
     assert one["unit"] == cb["unit"] and one["value"] > 0 and one["instances_per_s"] > 0
     assert "four small runs (4 runs" in cb["sample"]
+
+
+def test_full_workload_extrapolation():
+    """The oracle's full-workload time is the runs times the iteration scale
+    over the sample's runs per second."""
+    b = _bench_module()
+    cb = {"instances_per_s": 8.0}
+    out = b.extrapolate_full(cb, 4096, 5.0, "note")
+    assert out is cb and cb["full_workload_s_extrapolated"] == 4096 * 5.0 / 8.0
+    assert cb["extrapolation"] == "note"
