@@ -187,13 +187,14 @@ int elsr_set_cluster(elsr_t *h, int32_t cluster);
 /* Speculative execution of one GVNS run (mode P or G): up to `teams` clusters run
  * consecutive iterations from the same incumbent and commit them in order up
  * to the first acceptance, so trajectory, solution and counters equal the
- * sequential run's.  0 = automatic (up to 16 teams), 1 = off.  The teams
- * meet at a grid barrier every round, so all of them must be resident at
- * once; their number is sized on an idle device.  When other long-running
- * work occupies the device, teams that cannot start leave the others
- * waiting, and after a few seconds the run ends with ELSR_E_TIMEOUT instead
- * of hanging; set 1 (off) for runs that share a busy device.  Batches and
- * multi-start runs have no such barrier. */
+ * sequential run's.  0 = automatic (up to 16 teams), 1 = off.  Every round
+ * a team takes its position by ticket once all teams hold a ticket of the
+ * previous round, and waits for the round's decision, so all teams must be
+ * resident at once; their number is sized on an idle device.  When other
+ * long-running work occupies the device, teams that cannot start leave the
+ * others waiting, and after a few seconds the run ends with ELSR_E_TIMEOUT
+ * instead of hanging; set 1 (off) for runs that share a busy device.
+ * Batches and multi-start runs have no such waits. */
 int elsr_set_speculation(elsr_t *h, int32_t teams);
 
 /* Decode-step counter of the GVNS launches (elsr_stats_t.segments; a work
